@@ -1,0 +1,311 @@
+"""Throughput benchmark: noisy shots/s of the 42-qubit windowed Clifford+T
+workload on GB300, FP32 coefficients (headline) and FP64 beside it.
+
+A step = one launch sequence of the whole hot path (compiled program, all
+event kinds, noise, measurement, early discard, tallies) over one batch of
+shots. Inputs (the compiled program) are resident in HBM before timing;
+L2 (129 MB) is flushed between steps with a 512 MB memset outside the timed
+events. Multi-GPU: every rank runs its own shot range (weak scaling, no data
+path collective); the time is the max over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--shots S] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("w42: 42 qubits (38 data + 4 ancilla), seeded random stabilizer state, 18 blocks of "
+            "T on a random 4-qubit window + 60-gate Clifford + 4 ancilla parity checks + inverse + T^dag "
+            "(72 T positions), coefficient cap 2^8, uniform depolarizing p=1e-3, circuit seed 1, Philox seed 0")
+# Algorithmic work per counted unit (lane ops: FP + integer), see the design doc
+OPS_T_OUT, OPS_T_DIAG, OPS_MEAS, OPS_NOISE = 18, 9, 8, 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--shots", type=int, default=1 << 23, help="shots per step per GPU")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--first-cap", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def profile_traffic(kernel_src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "shot_kernel_w42.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch_full:\s*([0-9.e+]+)", txt)
+    if m and t and m.group(1) == kernel_src_hash:
+        return float(t.group(1))
+    return None
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.cuh", "program.h"):
+        h.update(open(os.path.join(ROOT, "paper_2512_23037_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------- oracle timing
+def oracle_rate(circ, noise, seed, budget_s, threads):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.run(circ, circ.n, noise, circ.cap, seed, 0, 400, threads=threads, records=False)
+    est = 400 / max(time.perf_counter() - t0, 1e-6)
+    n = int(max(400, min(est * budget_s, 5_000_000)))
+    t0 = time.perf_counter()
+    r = oracle.run(circ, circ.n, noise, circ.cap, seed, 1_000_000_000, n, threads=threads, records=False)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, r
+
+
+def ops_per_shot(circ, noise):
+    """Algorithmic lane ops per shot, from the oracle's exact counters on a
+    sample of the same workload (seed 0, first 2000 shots)."""
+    import oracle
+    r = oracle.run(circ, circ.n, noise, circ.cap, 0, 0, 2000, threads=os.cpu_count() or 1, records=False)
+    c = r["counts"]
+    tot = (OPS_T_OUT * c["t_out_entries"] + OPS_T_DIAG * c["t_diag_entries"] + OPS_MEAS * c["meas_entries"]
+           + OPS_NOISE * c["noise_entries"])
+    return tot / c["shots"], c
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2512_23037_gb300 import circuits as C
+    circ, noise = C.workload("w42")
+    threads = os.cpu_count() or 1
+    budget = 4.0
+    for _ in range(args.warmup):
+        oracle_rate(circ, noise, 0, 0.5, threads)
+    rates, tot_n, tot_t = [], 0, 0.0
+    for _ in range(args.steps):
+        rate, n, dt, _ = oracle_rate(circ, noise, 0, budget, threads)
+        rates.append(rate)
+        tot_n += n
+        tot_t += dt
+    value = tot_n / tot_t
+    line = {"metric": "shots/s", "value": value, "unit": "shots/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "shots/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{tot_n} shots of the same workload over {args.steps} steps "
+                                       f"(~{budget:.0f} s each, shots 1e9..)"},
+            "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2512_23037_gb300 as S
+    from paper_2512_23037_gb300 import circuits as C
+    S.load()
+    circ, noise = C.workload("w42")
+    stream = torch.cuda.current_stream()
+    n = args.shots
+    base_shot = rank * (1 << 40)  # disjoint shot ranges per rank
+    dev_props = torch.cuda.get_device_properties(local)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def time_path(precision, steps, warmup):
+        c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+        for w in range(warmup):
+            r = S.soft_run_shots(c, n, base_shot + (1 << 36) + w * n, 0, precision=precision, stream=stream,
+                                 group_size=args.group, first_cap=args.first_cap)
+            S.soft_tally(r)
+            r.free()
+        barrier()
+        total_ms, launches, kernel_ms, tallies = 0.0, 0, [], []
+        for k in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            r = S.soft_run_shots(c, n, base_shot + k * n, 0, precision=precision, stream=stream,
+                                 group_size=args.group, first_cap=args.first_cap)
+            ev1.record(stream)
+            tallies.append(S.soft_tally(r))
+            ms, nl = S.soft_run_timing(r)
+            kernel_ms.append(ms)
+            launches += nl
+            total_ms += ev0.elapsed_time(ev1)
+            r.free()
+        barrier()
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item()), launches, kernel_ms, tallies, c
+
+    clocks = Clocks(local) if rank == 0 else None
+    ms32, launches32, kms32, tal32, c32 = time_path("fp32", args.steps, args.warmup)
+    clock_info = clocks.stop() if clocks else None
+    ms64 = None
+    if not args.no_fp64:
+        ms64, launches64, kms64, tal64, _ = time_path("fp64", args.steps, args.warmup)
+
+    # end to end through the C ABI: host op list -> compile + upload -> run -> tally to host
+    barrier()
+    ops_host = circ.array()
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        c = S.soft_compile_circuit(ops_host, circ.n, noise, circ.cap)
+        r = S.soft_run_shots(c, n, base_shot + (1 << 38) + k * n, 0, precision="fp32", stream=stream)
+        S.soft_tally(r)
+        e2e_ms += 1000 * (time.perf_counter() - t0)
+        h2d = c.info["program_bytes"]
+        r.free()
+        c.free()
+    barrier()
+    t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+
+    if rank != 0:
+        return 0
+    shots_all = n * world * args.steps
+    value = shots_all / (ms32 / 1000)
+    ops_shot, counts = ops_per_shot(circ, noise)
+    peaks = measured_peaks()
+    sm_clock = peaks.get("sm_max_mhz", 2070.0)
+    sms = dev_props.multi_processor_count
+    peak_ops = sms * 128 * sm_clock * 1e6  # FP32/INT32 lanes x clock
+    # dominant kernel: the first-pass shot kernel; CUDA events around each run
+    avg_launch_ms = sum(kms32) / len(kms32)
+    achieved = ops_shot * n / (avg_launch_ms / 1000)
+    traffic = profile_traffic(kernel_hash())
+    line = {
+        "metric": "shots/s", "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shots_per_step_per_gpu": n, "coefficients": "complex64",
+                   "probabilities_and_tallies": "fp64", "l2": "flushed between steps (512 MB memset)",
+                   "parallelism": f"shot ranges x{world}"},
+        "fp64_plain": None if ms64 is None else {
+            "value": shots_all / (ms64 / 1000), "unit": "shots/s", "ms_per_step": ms64 / args.steps,
+            "dtype": "f64"},
+        "tally_last_step": tal32[-1],
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "ops_per_shot": ops_shot, "peak_basis": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz "
+                                                              "(sm_max_mhz of measured)"},
+        "gpu_launches": launches32,
+        "e2e": {"value": shots_all / (e2e_ms / 1000), "unit": "shots/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 56},
+        "clocks": clock_info,
+    }
+    if not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, ncpu, dt, _ = oracle_rate(circ, noise, 0, 12.0, threads)
+        line["cpu_baseline"] = {"value": rate, "unit": "shots/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{ncpu} shots of the same workload ({dt:.1f} s, shots 1e9..)"}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * soft.h -- C ABI of the GB300 generalized-stabilizer (GS) shot simulator.
+ *
+ * The library runs many independent noisy shots of one Clifford+T circuit.
+ * Every shot keeps a GS state |phi> = sum_a v_a d_a |psi_S> (arxiv
+ * 2512.23037, Sec. II-C, Definition "Generalized stabilizer representation"):
+ * a stabilizer/destabilizer tableau plus a sparse map of complex
+ * coefficients v. Clifford gates conjugate the tableau (Theorem 1 (1));
+ * T / T^dagger / Rz act as a I + b Z_q on the map through the Pauli-on-basis
+ * identity (Eq. T_gate, Eq. pauli_on_basis, Theorem 1 (3)); Z measurements
+ * filter or pair the map and replace tableau rows (Theorem 1 (2)); noise is
+ * sampled Paulis applied through the same identity (Sec. II-C, "Pure-state
+ * simulation model"; uniform depolarizing model of Sec. III). The shot-parallel
+ * device design replaces the staged per-op kernel pipeline of Sec. IV-B with
+ * one persistent kernel per launch.
+ *
+ * Conventions shared by every call:
+ *   - Return value: SOFT_OK (0) or a negative SOFT_E_* code. On error,
+ *     soft_last_error() returns a message for the calling thread.
+ *   - All host pointers are owned by the caller and only read/written during
+ *     the call (soft_run_shots may read `ops` nowhere: it uses the compiled
+ *     circuit). Device pointers passed in soft_run_opts stay owned by the
+ *     caller and must outlive the run's stream work.
+ *   - Handles are owned by the library; free them with the matching *_free.
+ *     One handle must not be used from two threads at once.
+ *   - Results depend only on (circuit, noise, seed, shot index): splitting a
+ *     shot range over calls or GPUs does not change them.
+ */
+#ifndef SOFT_ABI_H_
+#define SOFT_ABI_H_
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  SOFT_OK = 0,
+  SOFT_E_ARG = -1,             /* bad argument (null pointer, size, noise value, cap) */
+  SOFT_E_QUBIT_RANGE = -2,     /* qubit index >= n_qubits, equal qubits of a 2-qubit gate, n_qubits > 128 */
+  SOFT_E_RECORD_REF = -3,      /* record index not yet measured */
+  SOFT_E_UNSUPPORTED_OP = -4,  /* unknown op code or unsupported noise (p_idle != 0) */
+  SOFT_E_OOM = -5,             /* host or device allocation failed */
+  SOFT_E_CUDA = -6,            /* a CUDA runtime call failed */
+  SOFT_E_DEVICE_TIMEOUT = -7   /* reserved: a device-side bound was hit (never traps) */
+};
+
+/* Per-shot status byte. */
+enum { SOFT_SHOT_KEPT = 0, SOFT_SHOT_DISCARDED = 1, SOFT_SHOT_OVERFLOW = 2, SOFT_SHOT_ERROR = 3 };
+
+/* ---------------------------------------------------------------- circuit format */
+/* Op codes. Clifford gates (Sec. II-A generating set plus CZ, S^dag, Paulis),
+ * T / T^dag (Eq. T_gate / T_dagger, with the global phase kept so that
+ * T = diag(1, e^{i pi/4}) exactly), RZ(angle) = cos(angle/2) I - i sin(angle/2) Z,
+ * Z-basis M / R (measure, then X if -1) / MR, CPAULI (Pauli flags&3 = 1 X,
+ * 2 Y, 3 Z on q0 applied when the parity of rec[0], rec[1] is 1),
+ * DETECTOR (parity of rec[] xor INVERT = 1 => shot discarded, the early
+ * discard of Sec. V-C), OBSERVABLE (parity = 1 => logical error flag),
+ * NOISELESS_BEGIN/END (ops in between carry no noise). */
+enum {
+  SOFT_H = 0, SOFT_S = 1, SOFT_S_DAG = 2, SOFT_X = 3, SOFT_Y = 4, SOFT_Z = 5, SOFT_CX = 6, SOFT_CZ = 7,
+  SOFT_T = 8, SOFT_T_DAG = 9, SOFT_RZ = 10, SOFT_M = 11, SOFT_R = 12, SOFT_MR = 13, SOFT_CPAULI = 14,
+  SOFT_DETECTOR = 15, SOFT_OBSERVABLE = 16, SOFT_NOISELESS_BEGIN = 17, SOFT_NOISELESS_END = 18
+};
+/* DETECTOR / OBSERVABLE flags: INVERT xors 1 into the parity; CHAIN carries
+ * the parity into the next DETECTOR / OBSERVABLE instead of testing it. */
+enum { SOFT_FLAG_INVERT = 1, SOFT_FLAG_CHAIN = 2 };
+
+/* 32-byte op record. q1 only for CX (control q0, target q1) and CZ. rec[] are
+ * absolute record indices (0 = first M/MR of the circuit), -1 = unused. */
+typedef struct {
+  uint16_t op;
+  uint16_t flags;
+  uint32_t q0, q1;
+  uint32_t pad;
+  double angle;
+  int32_t rec[2];
+} soft_op;
+
+/* Uniform depolarizing noise (Sec. III): DEPOL1(p1) after every 1-qubit gate
+ * (T, T^dag, RZ included), DEPOL2(p2) after every CX/CZ (one of the 15
+ * non-identity two-qubit Paulis), X flip with p_meas before every M/MR and
+ * with p_reset after every R/MR. p_idle must be 0 (no idle layers). */
+typedef struct {
+  double p1, p2, p_meas, p_reset, p_idle;
+} soft_noise;
+
+typedef struct soft_circuit soft_circuit;
+typedef struct soft_run soft_run;
+
+typedef struct {
+  uint32_t n_qubits;
+  uint32_t n_records;     /* M and MR ops */
+  uint32_t record_words;  /* ceil(n_records / 64), at least 1 */
+  uint32_t n_sites;       /* noise sites after expansion */
+  uint32_t n_events;      /* per-shot device program length */
+  uint32_t coeff_cap;
+  uint64_t program_bytes; /* device bytes of the compiled program */
+} soft_circuit_info_t;
+
+/* Validate the op list, expand the noise model into numbered noise sites,
+ * evolve the shot-invariant X/Z part of the tableau once on the host and
+ * upload the per-shot device program to the current CUDA device.
+ *   ops: n_ops records (host); n_qubits in 1..128; noise: host struct;
+ *   coeff_cap: largest |v| a shot may hold (power of two not required,
+ *   1..65536); a shot whose |v| exceeds it after pruning ends as OVERFLOW
+ *   (the overflow mark of Sec. IV-B, "Memory layout").
+ *   out: receives a handle freed with soft_circuit_free.
+ * Errors: SOFT_E_ARG, SOFT_E_QUBIT_RANGE, SOFT_E_RECORD_REF,
+ * SOFT_E_UNSUPPORTED_OP, SOFT_E_OOM, SOFT_E_CUDA; *out is NULL then. */
+int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, const soft_noise *noise,
+                         uint32_t coeff_cap, soft_circuit **out);
+
+int soft_circuit_info(const soft_circuit *c, soft_circuit_info_t *out);
+
+/* Final X/Z words of the shot-invariant tableau (rows d_0..d_{n-1} then
+ * s_0..s_{n-1}, 2 words per row each; host buffers of 4*n words). With the
+ * per-shot sign words of soft_get_state this gives the full tableau. */
+int soft_circuit_tableau(const soft_circuit *c, uint64_t *rows_x, uint64_t *rows_z);
+
+void soft_circuit_free(soft_circuit *c);
+
+/* ---------------------------------------------------------------- runs */
+enum { SOFT_FP64 = 0, SOFT_FP32 = 1 };
+enum { SOFT_REC_NONE = 0, SOFT_REC_FIRST_K = 1, SOFT_REC_ALL = 2 };
+
+typedef struct {
+  int32_t precision;     /* SOFT_FP64 (coefficients complex128) or SOFT_FP32 (complex64;
+                            probabilities and tallies stay FP64) */
+  int32_t record_mode;   /* which shots' records and status bytes are kept */
+  uint64_t record_k;     /* K for SOFT_REC_FIRST_K */
+  void *stream;          /* cudaStream_t to launch on; NULL = legacy default stream */
+  uint32_t group_size;   /* lanes per shot: 0 = auto, else 8 or 32 */
+  uint32_t blocks_per_sm;/* 0 = as many as fit */
+  uint64_t chunk_shots;  /* shots per launch; 0 = auto */
+  uint32_t first_cap;    /* capacity of the first pass (0 = auto); shots that exceed
+                            it and not coeff_cap are rerun at coeff_cap */
+  uint32_t capture_k;    /* keep the final GS state of the first capture_k shots */
+  uint64_t *d_records;   /* optional caller device buffer, record_words per kept shot */
+  uint8_t *d_status;     /* optional caller device buffer, one byte per kept shot */
+} soft_run_opts;
+
+/* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
+ * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all
+ * randomness: noise gaps on counter (shot, 0, k), measurement uniforms on
+ * counter (shot, 1, ordinal).
+ *   opts may be NULL (FP64, no records, auto tuning, default stream).
+ *   out: receives a run handle (freed with soft_run_free) that owns the
+ *   device tallies and, unless caller buffers are given, the record/status
+ *   buffers.
+ * Errors: SOFT_E_ARG, SOFT_E_OOM, SOFT_E_CUDA. */
+int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, const soft_run_opts *opts,
+                   soft_run **out);
+
+typedef struct {
+  uint64_t shots, discarded, overflow, kept, logical_errors;
+  double sum_fidelity, sum_weight; /* reserved accumulators (0 here) */
+} soft_tally_t;
+
+/* Wait for the run's stream work and copy its tallies (Sec. V-A fields:
+ * total, discarded, kept shots and detected logical errors). */
+int soft_tally(soft_run *r, soft_tally_t *out);
+
+/* Wait, then copy records (shot-major, record_words per shot, bit j = 1 when
+ * record j measured -1; bits after a discard are 0) and status bytes of the
+ * kept shots (the first K, or all). n_words / n_status give the host buffer
+ * sizes; either pointer may be NULL. */
+int soft_get_records(soft_run *r, uint64_t *host_words, size_t n_words, uint8_t *host_status, size_t n_status);
+
+/* Wait, then copy the final GS state of shot `shot_offset` (< capture_k):
+ * sign words (4: destabilizer signs w0,w1 then stabilizer signs w0,w1),
+ * keys (2 words each) and values (re, im as double) of up to `cap` entries;
+ * *nnz receives the entry count. */
+int soft_get_state(soft_run *r, uint64_t shot_offset, uint64_t *signs, uint64_t *keys, double *vals, size_t cap,
+                   size_t *nnz);
+
+/* Device time of the run's kernels in milliseconds (CUDA events on the run's
+ * stream), and how many kernels were launched. Waits for the run. */
+int soft_run_timing(soft_run *r, double *ms, uint32_t *n_launches);
+
+void soft_run_free(soft_run *r);
+
+const char *soft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -250,7 +250,7 @@ def random_layers(seed: int, n: int = 6, depth: int = 20, n_t: int = 4, n_mid: i
     circuit ends with M on every qubit.
     """
     rng = np.random.default_rng(seed)
-    c = Circuit(n, name=f"random_layers(n={n},depth={depth},seed={seed})", cap=1 << 12)
+    c = Circuit(n, name=f"random_layers(n={n},depth={depth},seed={seed})", cap=256)
     tpos = set()
     while len(tpos) < n_t:
         tpos.add((int(rng.integers(depth)), int(rng.integers(n))))

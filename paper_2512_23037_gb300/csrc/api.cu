@@ -1,0 +1,351 @@
+// api.cu -- the C ABI of include/soft.h: circuit handles, runs, tallies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/soft.h"
+#include "compile.h"
+#include "kernels.cuh"
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return SOFT_E_CUDA;
+}
+
+constexpr double kTauFp64 = 1e-20;  // prune |v|^2 below this (FP64 coefficients)
+constexpr double kTauFp32 = 1e-10;  // FP32 coefficients: well above FP32 cancellation residue
+constexpr uint64_t kDefaultChunk = 1ull << 24;
+constexpr uint32_t kDefaultFirstCap = 64;
+}  // namespace
+
+struct soft_circuit {
+  soft::HostProgram hp;
+  int device = 0;
+  soft::EvRec *d_ev = nullptr;
+  soft::CaseB *d_cb = nullptr;
+  soft::Site *d_sites = nullptr;
+  uint64_t *d_thr = nullptr;
+  uint64_t bytes = 0;
+};
+
+struct soft_run {
+  soft_circuit *c = nullptr;
+  cudaStream_t stream = nullptr;
+  uint64_t n_shots = 0;
+  unsigned long long *d_tally = nullptr;  // 5 counters
+  unsigned long long *d_work = nullptr;   // next1, next2, n_rerun
+  uint32_t *d_rerun = nullptr;
+  uint8_t *d_status = nullptr;
+  uint64_t *d_records = nullptr;
+  bool own_status = false, own_records = false;
+  uint64_t out_limit = 0;
+  uint64_t *d_st_signs = nullptr, *d_st_keys = nullptr;
+  double *d_st_vals = nullptr;
+  uint32_t *d_st_nnz = nullptr;
+  uint64_t st_limit = 0;
+  uint32_t st_stride = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint32_t launches = 0;
+};
+
+extern "C" {
+
+const char *soft_last_error(void) { return g_err.c_str(); }
+
+int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, const soft_noise *noise,
+                         uint32_t coeff_cap, soft_circuit **out) {
+  if (!out) return fail(SOFT_E_ARG, "out is NULL");
+  *out = nullptr;
+  soft_circuit *c = new (std::nothrow) soft_circuit();
+  if (!c) return fail(SOFT_E_OOM, "host allocation failed");
+  std::string err;
+  int rc = soft::compile_program(ops, n_ops, n_qubits, noise, coeff_cap, c->hp, err);
+  if (rc != SOFT_OK) {
+    delete c;
+    return fail(rc, err);
+  }
+  cudaGetDevice(&c->device);
+  const auto &hp = c->hp;
+  size_t b_ev = hp.ev.size() * sizeof(soft::EvRec), b_cb = std::max<size_t>(1, hp.cb.size()) * sizeof(soft::CaseB),
+         b_st = std::max<size_t>(1, hp.sites.size()) * sizeof(soft::Site), b_thr = hp.thr.size() * sizeof(uint64_t);
+  cudaError_t e;
+  if ((e = cudaMalloc(&c->d_ev, b_ev)) != cudaSuccess || (e = cudaMalloc(&c->d_cb, b_cb)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_sites, b_st)) != cudaSuccess || (e = cudaMalloc(&c->d_thr, b_thr)) != cudaSuccess) {
+    soft_circuit_free(c);
+    return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed") : cuda_fail(e, "cudaMalloc");
+  }
+  if ((e = cudaMemcpy(c->d_ev, hp.ev.data(), b_ev, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!hp.cb.empty() && (e = cudaMemcpy(c->d_cb, hp.cb.data(), hp.cb.size() * sizeof(soft::CaseB),
+                                         cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!hp.sites.empty() && (e = cudaMemcpy(c->d_sites, hp.sites.data(), hp.sites.size() * sizeof(soft::Site),
+                                            cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (e = cudaMemcpy(c->d_thr, hp.thr.data(), b_thr, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    soft_circuit_free(c);
+    return cuda_fail(e, "cudaMemcpy (program upload)");
+  }
+  c->bytes = b_ev + b_cb + b_st + b_thr;
+  *out = c;
+  return SOFT_OK;
+}
+
+int soft_circuit_info(const soft_circuit *c, soft_circuit_info_t *out) {
+  if (!c || !out) return fail(SOFT_E_ARG, "null argument");
+  out->n_qubits = c->hp.n;
+  out->n_records = c->hp.n_records;
+  out->record_words = c->hp.rw;
+  out->n_sites = c->hp.n_sites;
+  out->n_events = (uint32_t)c->hp.ev.size();
+  out->coeff_cap = c->hp.cap;
+  out->program_bytes = c->bytes;
+  return SOFT_OK;
+}
+
+int soft_circuit_tableau(const soft_circuit *c, uint64_t *rows_x, uint64_t *rows_z) {
+  if (!c || !rows_x || !rows_z) return fail(SOFT_E_ARG, "null argument");
+  std::memcpy(rows_x, c->hp.fin_x.data(), c->hp.fin_x.size() * sizeof(uint64_t));
+  std::memcpy(rows_z, c->hp.fin_z.data(), c->hp.fin_z.size() * sizeof(uint64_t));
+  return SOFT_OK;
+}
+
+void soft_circuit_free(soft_circuit *c) {
+  if (!c) return;
+  cudaFree(c->d_ev);
+  cudaFree(c->d_cb);
+  cudaFree(c->d_sites);
+  cudaFree(c->d_thr);
+  delete c;
+}
+
+void soft_run_free(soft_run *r) {
+  if (!r) return;
+  if (r->stream) cudaStreamSynchronize(r->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(r->d_tally);
+  cudaFree(r->d_work);
+  cudaFree(r->d_rerun);
+  if (r->own_status) cudaFree(r->d_status);
+  if (r->own_records) cudaFree(r->d_records);
+  cudaFree(r->d_st_signs);
+  cudaFree(r->d_st_keys);
+  cudaFree(r->d_st_vals);
+  cudaFree(r->d_st_nnz);
+  if (r->ev0) cudaEventDestroy(r->ev0);
+  if (r->ev1) cudaEventDestroy(r->ev1);
+  delete r;
+}
+
+int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, const soft_run_opts *opts,
+                   soft_run **out) {
+  if (!c || !out) return fail(SOFT_E_ARG, "null argument");
+  *out = nullptr;
+  soft_run_opts o{};
+  if (opts) o = *opts;
+  if (o.precision != SOFT_FP64 && o.precision != SOFT_FP32) return fail(SOFT_E_ARG, "bad precision");
+  if (o.record_mode < SOFT_REC_NONE || o.record_mode > SOFT_REC_ALL) return fail(SOFT_E_ARG, "bad record mode");
+  if (o.group_size != 0 && o.group_size != 8 && o.group_size != 32) return fail(SOFT_E_ARG, "group_size must be 0, 8 or 32");
+  const auto &hp = c->hp;
+  const int fp32 = o.precision == SOFT_FP32;
+  const uint32_t cap = hp.cap;
+  uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap) : std::min(kDefaultFirstCap, cap);
+  const bool two_pass = cap1 < cap;
+  const uint32_t g1 = o.group_size ? o.group_size : (cap1 <= 64 ? 8u : 32u);
+  const uint32_t g2 = 32;
+  const size_t smem_limit = 227 * 1024;
+  if (soft::group_smem_bytes(fp32, hp.W, cap, hp.rw) > smem_limit)
+    return fail(SOFT_E_ARG, "coeff_cap too large for the on-chip coefficient map");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+
+  soft_run *r = new (std::nothrow) soft_run();
+  if (!r) return fail(SOFT_E_OOM, "host allocation failed");
+  r->c = c;
+  r->stream = (cudaStream_t)o.stream;
+  r->n_shots = n_shots;
+  const uint64_t chunk = o.chunk_shots ? o.chunk_shots : std::min<uint64_t>(kDefaultChunk, std::max<uint64_t>(n_shots, 1));
+  if (chunk > 0xFFFFFFFFull) {
+    soft_run_free(r);
+    return fail(SOFT_E_ARG, "chunk_shots must be < 2^32");
+  }
+  r->out_limit = o.record_mode == SOFT_REC_ALL ? n_shots : (o.record_mode == SOFT_REC_FIRST_K ? std::min(o.record_k, n_shots) : 0);
+  r->st_limit = std::min<uint64_t>(o.capture_k, n_shots);
+  r->st_stride = cap;
+#define SOFT_ALLOC(ptr, bytes)                                                                  \
+  do {                                                                                          \
+    if ((e = cudaMalloc(&(ptr), (bytes))) != cudaSuccess) {                                     \
+      soft_run_free(r);                                                                         \
+      return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed")      \
+                                            : cuda_fail(e, "cudaMalloc");                       \
+    }                                                                                           \
+  } while (0)
+  SOFT_ALLOC(r->d_tally, 5 * sizeof(unsigned long long));
+  SOFT_ALLOC(r->d_work, 3 * sizeof(unsigned long long));
+  if (two_pass) SOFT_ALLOC(r->d_rerun, chunk * sizeof(uint32_t));
+  if (r->out_limit) {
+    if (o.d_status) r->d_status = o.d_status;
+    else {
+      SOFT_ALLOC(r->d_status, r->out_limit);
+      r->own_status = true;
+    }
+    if (o.d_records) r->d_records = o.d_records;
+    else {
+      SOFT_ALLOC(r->d_records, r->out_limit * hp.rw * sizeof(uint64_t));
+      r->own_records = true;
+    }
+  }
+  if (r->st_limit) {
+    SOFT_ALLOC(r->d_st_signs, r->st_limit * 4 * sizeof(uint64_t));
+    SOFT_ALLOC(r->d_st_keys, r->st_limit * r->st_stride * 2 * sizeof(uint64_t));
+    SOFT_ALLOC(r->d_st_vals, r->st_limit * r->st_stride * 2 * sizeof(double));
+    SOFT_ALLOC(r->d_st_nnz, r->st_limit * sizeof(uint32_t));
+  }
+#undef SOFT_ALLOC
+  if ((e = cudaEventCreate(&r->ev0)) != cudaSuccess || (e = cudaEventCreate(&r->ev1)) != cudaSuccess) {
+    soft_run_free(r);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  cudaStream_t st = r->stream;
+  if ((e = cudaMemsetAsync(r->d_tally, 0, 5 * sizeof(unsigned long long), st)) != cudaSuccess) {
+    soft_run_free(r);
+    return cuda_fail(e, "cudaMemsetAsync");
+  }
+  cudaEventRecord(r->ev0, st);
+  for (uint64_t s0 = 0; s0 < n_shots; s0 += chunk) {
+    const uint64_t cnt = std::min(chunk, n_shots - s0);
+    if ((e = cudaMemsetAsync(r->d_work, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) {
+      soft_run_free(r);
+      return cuda_fail(e, "cudaMemsetAsync");
+    }
+    soft::ShotParams p{};
+    p.ev = c->d_ev;
+    p.cb = c->d_cb;
+    p.sites = c->d_sites;
+    p.thr = c->d_thr;
+    p.n_events = (uint32_t)hp.ev.size();
+    p.n_sites = hp.n_sites;
+    p.rw = hp.rw;
+    p.tau = fp32 ? kTauFp32 : kTauFp64;
+    p.seed = seed;
+    p.first_shot = first_shot + s0;
+    p.n_items = cnt;
+    p.next_item = r->d_work;
+    p.tally = r->d_tally;
+    p.rerun = r->d_rerun;
+    p.n_rerun = r->d_work + 2;
+    if (r->out_limit > s0) {
+      p.out_limit = r->out_limit - s0;
+      p.status = r->d_status + s0;
+      p.records = r->d_records + s0 * hp.rw;
+    }
+    if (r->st_limit > s0) {
+      p.st_limit = r->st_limit - s0;
+      p.st_signs = r->d_st_signs + s0 * 4;
+      p.st_keys = r->d_st_keys + s0 * r->st_stride * 2;
+      p.st_vals = r->d_st_vals + s0 * r->st_stride * 2;
+      p.st_nnz = r->d_st_nnz + s0;
+      p.st_stride = r->st_stride;
+    }
+    p.cap = cap1;
+    p.small_pass = two_pass ? 1 : 0;
+    if ((e = soft::launch_shots(p, fp32, hp.W, g1, (int)o.blocks_per_sm, st, nullptr)) != cudaSuccess) {
+      soft_run_free(r);
+      return cuda_fail(e, "shot kernel launch");
+    }
+    r->launches++;
+    if (two_pass) {
+      soft::ShotParams q = p;
+      q.cap = cap;
+      q.small_pass = 0;
+      q.list = r->d_rerun;
+      q.n_items_dev = r->d_work + 2;
+      q.next_item = r->d_work + 1;
+      if ((e = soft::launch_shots(q, fp32, hp.W, g2, (int)o.blocks_per_sm, st, nullptr)) != cudaSuccess) {
+        soft_run_free(r);
+        return cuda_fail(e, "rerun kernel launch");
+      }
+      r->launches++;
+    }
+  }
+  cudaEventRecord(r->ev1, st);
+  *out = r;
+  return SOFT_OK;
+}
+
+int soft_tally(soft_run *r, soft_tally_t *out) {
+  if (!r || !out) return fail(SOFT_E_ARG, "null argument");
+  unsigned long long t[5];
+  cudaError_t e = cudaMemcpyAsync(t, r->d_tally, sizeof t, cudaMemcpyDeviceToHost, r->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tally copy");
+  out->shots = t[0];
+  out->discarded = t[1];
+  out->overflow = t[2];
+  out->kept = t[3];
+  out->logical_errors = t[4];
+  out->sum_fidelity = 0.0;
+  out->sum_weight = 0.0;
+  return SOFT_OK;
+}
+
+int soft_get_records(soft_run *r, uint64_t *host_words, size_t n_words, uint8_t *host_status, size_t n_status) {
+  if (!r) return fail(SOFT_E_ARG, "null argument");
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  const size_t rw = r->c->hp.rw;
+  if (host_words) {
+    size_t n = std::min<size_t>(n_words, r->out_limit * rw);
+    if (n && (e = cudaMemcpy(host_words, r->d_records, n * sizeof(uint64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "records copy");
+  }
+  if (host_status) {
+    size_t n = std::min<size_t>(n_status, r->out_limit);
+    if (n && (e = cudaMemcpy(host_status, r->d_status, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "status copy");
+  }
+  return SOFT_OK;
+}
+
+int soft_get_state(soft_run *r, uint64_t off, uint64_t *signs, uint64_t *keys, double *vals, size_t cap, size_t *nnz) {
+  if (!r || !nnz) return fail(SOFT_E_ARG, "null argument");
+  if (off >= r->st_limit) return fail(SOFT_E_ARG, "shot offset was not captured");
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  uint32_t n = 0;
+  if ((e = cudaMemcpy(&n, r->d_st_nnz + off, sizeof n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "state copy");
+  *nnz = n;
+  if (signs && (e = cudaMemcpy(signs, r->d_st_signs + off * 4, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "state copy");
+  size_t m = std::min<size_t>({(size_t)n, cap, (size_t)r->st_stride});
+  if (keys && m &&
+      (e = cudaMemcpy(keys, r->d_st_keys + off * r->st_stride * 2, m * 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost)) !=
+          cudaSuccess)
+    return cuda_fail(e, "state copy");
+  if (vals && m &&
+      (e = cudaMemcpy(vals, r->d_st_vals + off * r->st_stride * 2, m * 2 * sizeof(double), cudaMemcpyDeviceToHost)) !=
+          cudaSuccess)
+    return cuda_fail(e, "state copy");
+  return SOFT_OK;
+}
+
+int soft_run_timing(soft_run *r, double *ms, uint32_t *n_launches) {
+  if (!r) return fail(SOFT_E_ARG, "null argument");
+  cudaError_t e = cudaEventSynchronize(r->ev1);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+  float f = 0.f;
+  if ((e = cudaEventElapsedTime(&f, r->ev0, r->ev1)) != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+  if (ms) *ms = (double)f;
+  if (n_launches) *n_launches = r->launches;
+  return SOFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,479 @@
+// compile.cpp -- host compiler: op list + noise model -> per-shot device program.
+//
+// One pass over the circuit evolves the X/Z words of the tableau (the part
+// that is the same in every shot), accumulates each Clifford gate's sign
+// flips into XOR masks, numbers the noise sites of the uniform depolarizing
+// model (Sec. III of arxiv 2512.23037) and emits one event per non-Clifford
+// step: T/T^dag/Rz (Eq. T_gate), Z measurement (Theorem 1 (2)), conditional
+// Paulis, parity checks.
+//
+// Clifford conjugation is derived from each gate's images of X and Z on its
+// qubits (U X U^dag, U Z U^dag); the image of any row follows by Pauli
+// multiplication, and its sign bit at zero input sign is the XOR mask entry.
+#include "compile.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace soft {
+namespace {
+
+inline int pc(uint64_t v) { return __builtin_popcountll(v); }
+
+// i^e X^x Z^z on n <= 128 qubits.
+struct Pz {
+  uint64_t x[2] = {0, 0}, z[2] = {0, 0};
+  int e = 0;
+};
+struct Row {
+  uint64_t x[2] = {0, 0}, z[2] = {0, 0};
+};
+
+Pz pmul(const Pz &a, const Pz &b) {
+  Pz o;
+  int t = 0;
+  for (int w = 0; w < 2; ++w) {
+    o.x[w] = a.x[w] ^ b.x[w];
+    o.z[w] = a.z[w] ^ b.z[w];
+    t += pc(a.z[w] & b.x[w]);
+  }
+  o.e = (a.e + b.e + 2 * t) & 3;
+  return o;
+}
+
+// The Hermitian Pauli of a row with sign bit 0.
+Pz herm(const Row &r) {
+  Pz p;
+  for (int w = 0; w < 2; ++w) {
+    p.x[w] = r.x[w];
+    p.z[w] = r.z[w];
+  }
+  p.e = (pc(r.x[0] & r.z[0]) + pc(r.x[1] & r.z[1])) & 3;
+  return p;
+}
+
+// Sign bit of a Hermitian Pauli written i^e X^x Z^z; -1 if not Hermitian.
+int sign_bit(const Pz &p) {
+  int d = (p.e - pc(p.x[0] & p.z[0]) - pc(p.x[1] & p.z[1])) & 3;
+  return (d & 1) ? -1 : (d >> 1);
+}
+
+Row row_of(const Pz &p) {
+  Row r;
+  for (int w = 0; w < 2; ++w) {
+    r.x[w] = p.x[w];
+    r.z[w] = p.z[w];
+  }
+  return r;
+}
+
+inline int bit(const uint64_t *v, uint32_t i) { return (int)((v[i >> 6] >> (i & 63)) & 1u); }
+inline void flip(uint64_t *v, uint32_t i) { v[i >> 6] ^= 1ull << (i & 63); }
+inline void put(uint64_t *v, uint32_t i, int b) {
+  if (bit(v, i) != b) flip(v, i);
+}
+
+// Local two-qubit Pauli i^e X^x Z^z (bit 0 = first qubit, bit 1 = second).
+struct L2 {
+  uint32_t x, z;
+  int e;
+};
+L2 l2mul(L2 a, L2 b) { return {a.x ^ b.x, a.z ^ b.z, (a.e + b.e + 2 * pc(a.z & b.x)) & 3}; }
+
+// Row update table: input nibble (xa, za, xb, zb) -> output nibble, sign flip.
+struct GateTab {
+  uint8_t out[16];
+  uint8_t flipb[16];
+};
+
+GateTab make_tab(L2 iXa, L2 iZa, L2 iXb, L2 iZb) {
+  GateTab t{};
+  for (uint32_t in = 0; in < 16; ++in) {
+    uint32_t xa = in & 1, za = (in >> 1) & 1, xb = (in >> 2) & 1, zb = (in >> 3) & 1;
+    L2 acc{0, 0, (int)((xa & za) + (xb & zb))};
+    if (xa) acc = l2mul(acc, iXa);
+    if (za) acc = l2mul(acc, iZa);
+    if (xb) acc = l2mul(acc, iXb);
+    if (zb) acc = l2mul(acc, iZb);
+    int d = (acc.e - pc(acc.x & acc.z)) & 3;
+    t.out[in] = (uint8_t)((acc.x & 1) | ((acc.z & 1) << 1) | (((acc.x >> 1) & 1) << 2) | (((acc.z >> 1) & 1) << 3));
+    t.flipb[in] = (uint8_t)((d >> 1) | ((d & 1) << 7));  // bit 7 marks an impossible odd phase
+  }
+  return t;
+}
+
+struct Tabs {
+  GateTab g[8];
+  Tabs() {
+    const L2 Xa{1, 0, 0}, Za{0, 1, 0}, Xb{2, 0, 0}, Zb{0, 2, 0};
+    g[SOFT_H] = make_tab(Za, Xa, Xb, Zb);
+    g[SOFT_S] = make_tab(L2{1, 1, 1}, Za, Xb, Zb);       // X -> Y
+    g[SOFT_S_DAG] = make_tab(L2{1, 1, 3}, Za, Xb, Zb);   // X -> -Y
+    g[SOFT_X] = make_tab(Xa, L2{0, 1, 2}, Xb, Zb);       // Z -> -Z
+    g[SOFT_Y] = make_tab(L2{1, 0, 2}, L2{0, 1, 2}, Xb, Zb);
+    g[SOFT_Z] = make_tab(L2{1, 0, 2}, Za, Xb, Zb);       // X -> -X
+    g[SOFT_CX] = make_tab(L2{3, 0, 0}, Za, Xb, L2{0, 3, 0});        // Xa -> XaXb, Zb -> ZaZb
+    g[SOFT_CZ] = make_tab(L2{1, 2, 0}, Za, L2{2, 1, 0}, Zb);        // Xa -> XaZb, Xb -> ZaXb
+  }
+};
+const Tabs &tabs() {
+  static Tabs t;
+  return t;
+}
+
+struct Tableau {
+  uint32_t n = 0;
+  std::vector<Row> d, s;
+  uint64_t pend_d[2] = {0, 0}, pend_s[2] = {0, 0};  // sign XOR since the last event
+
+  void init(uint32_t nq) {
+    n = nq;
+    d.assign(n, Row{});
+    s.assign(n, Row{});
+    for (uint32_t i = 0; i < n; ++i) {
+      flip(d[i].x, i);
+      flip(s[i].z, i);
+    }
+  }
+
+  int apply_row(const GateTab &t, Row &r, uint32_t a, uint32_t b, bool two) {
+    uint32_t in = (uint32_t)bit(r.x, a) | ((uint32_t)bit(r.z, a) << 1);
+    if (two) in |= ((uint32_t)bit(r.x, b) << 2) | ((uint32_t)bit(r.z, b) << 3);
+    uint32_t o = t.out[in];
+    put(r.x, a, (int)(o & 1));
+    put(r.z, a, (int)((o >> 1) & 1));
+    if (two) {
+      put(r.x, b, (int)((o >> 2) & 1));
+      put(r.z, b, (int)((o >> 3) & 1));
+    }
+    return t.flipb[in];
+  }
+
+  bool gate(int op, uint32_t a, uint32_t b) {
+    const GateTab &t = tabs().g[op];
+    bool two = (op == SOFT_CX || op == SOFT_CZ);
+    for (uint32_t i = 0; i < n; ++i) {
+      int fd = apply_row(t, d[i], a, b, two);
+      int fs = apply_row(t, s[i], a, b, two);
+      if ((fd | fs) & 0x80) return false;
+      if (fd) flip(pend_d, i);
+      if (fs) flip(pend_s, i);
+    }
+    return true;
+  }
+
+  static bool anti(const Pz &q, const Row &r) {
+    int t = 0;
+    for (int w = 0; w < 2; ++w) t += pc((q.x[w] & r.z[w]) ^ (q.z[w] & r.x[w]));
+    return t & 1;
+  }
+
+  // Q = i^e0 d_beta s_gamma at zero signs.
+  bool decompose(const Pz &q, uint64_t beta[2], uint64_t gamma[2], uint32_t *e0) const {
+    beta[0] = beta[1] = gamma[0] = gamma[1] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      if (anti(q, s[i])) flip(beta, i);
+      if (anti(q, d[i])) flip(gamma, i);
+    }
+    Pz acc;
+    for (uint32_t i = 0; i < n; ++i)
+      if (bit(beta, i)) acc = pmul(acc, herm(d[i]));
+    for (uint32_t i = 0; i < n; ++i)
+      if (bit(gamma, i)) acc = pmul(acc, herm(s[i]));
+    for (int w = 0; w < 2; ++w)
+      if (acc.x[w] != q.x[w] || acc.z[w] != q.z[w]) return false;
+    *e0 = (uint32_t)((q.e - acc.e) & 3);
+    return true;
+  }
+};
+
+Pz single(int code, uint32_t q) {
+  Pz p;
+  if (code == 1 || code == 2) flip(p.x, q);
+  if (code == 3 || code == 2) flip(p.z, q);
+  p.e = (code == 2) ? 1 : 0;
+  return p;
+}
+
+bool is1q(int op) {
+  return op == SOFT_H || op == SOFT_S || op == SOFT_S_DAG || op == SOFT_X || op == SOFT_Y || op == SOFT_Z ||
+         op == SOFT_T || op == SOFT_T_DAG || op == SOFT_RZ;
+}
+bool is2q(int op) { return op == SOFT_CX || op == SOFT_CZ; }
+bool isclifford(int op) { return op <= SOFT_CZ; }
+
+uint64_t gap_thr(double p, uint64_t g) {
+  double q = -std::expm1((double)(g + 1) * std::log1p(-p));
+  if (!(q > 0.0)) return 0;
+  if (q >= 1.0) return UINT64_MAX;
+  double t = std::ldexp(q, 64);
+  if (t >= 18446744073709551615.0) return UINT64_MAX;
+  return (uint64_t)t;
+}
+
+}  // namespace
+
+int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noise *noise, uint32_t cap,
+                    HostProgram &P, std::string &err) {
+  if (!noise || (!ops && n_ops)) {
+    err = "null argument";
+    return SOFT_E_ARG;
+  }
+  if (n == 0 || n > 128) {
+    err = "n_qubits must be in 1..128";
+    return SOFT_E_QUBIT_RANGE;
+  }
+  if (cap == 0 || cap > 65536) {
+    err = "coeff_cap must be in 1..65536";
+    return SOFT_E_ARG;
+  }
+  const double ps[4] = {noise->p1, noise->p2, noise->p_meas, noise->p_reset};
+  for (double p : ps)
+    if (!(p >= 0.0 && p < 1.0)) {
+      err = "noise probabilities must be in [0, 1)";
+      return SOFT_E_ARG;
+    }
+  if (noise->p_idle != 0.0) {
+    err = "idle noise is not supported (p_idle must be 0)";
+    return SOFT_E_UNSUPPORTED_OP;
+  }
+  P = HostProgram{};
+  P.n = n;
+  P.W = n <= 64 ? 1 : 2;
+  P.cap = cap;
+  P.pmax = std::fmax(std::fmax(noise->p1, noise->p2), std::fmax(noise->p_meas, noise->p_reset));
+  Tableau tb;
+  tb.init(n);
+  bool noiseless = false;
+  uint32_t nrec = 0, ord = 0;
+
+  auto add_site = [&](uint32_t q0, uint32_t q1, bool two, double p) -> bool {
+    Site s{};
+    s.dsd[0] = tb.pend_d[0];
+    s.dsd[1] = tb.pend_d[1];
+    s.dss[0] = tb.pend_s[0];
+    s.dss[1] = tb.pend_s[1];
+    s.two = two ? 1u : 0u;
+    for (int k = 0; k < (two ? 2 : 1); ++k) {
+      uint32_t q = k == 0 ? q0 : q1;
+      uint32_t e;
+      if (!tb.decompose(single(1, q), s.bx[k], s.gx[k], &e)) return false;
+      if (!tb.decompose(single(3, q), s.bz[k], s.gz[k], &e)) return false;
+    }
+    uint32_t c0 = 0;
+    for (int code = 1; code <= (two ? 15 : 3); ++code) {
+      Pz Q = two ? pmul(single(code >> 2, q0), single(code & 3, q1)) : single(code, q0);
+      uint64_t b[2], g[2];
+      uint32_t e;
+      if (!tb.decompose(Q, b, g, &e)) return false;
+      c0 |= (e & 3u) << (2 * code);
+    }
+    s.c0 = c0;
+    if (p >= P.pmax) {
+      s.always = 1;
+      s.thin = 0xFFFFFFFFu;
+    } else {
+      s.always = 0;
+      s.thin = (uint32_t)std::floor(std::ldexp(p / P.pmax, 32));
+    }
+    P.sites.push_back(s);
+    return true;
+  };
+
+  auto new_event = [&](uint32_t type) -> EvRec & {
+    EvRec e{};
+    e.type = type;
+    e.site_begin = (uint32_t)P.sites.size();
+    e.dsd[0] = tb.pend_d[0];
+    e.dsd[1] = tb.pend_d[1];
+    e.dss[0] = tb.pend_s[0];
+    e.dss[1] = tb.pend_s[1];
+    tb.pend_d[0] = tb.pend_d[1] = tb.pend_s[0] = tb.pend_s[1] = 0;
+    e.r0 = e.r1 = -1;
+    P.ev.push_back(e);
+    return P.ev.back();
+  };
+
+  auto pauli_event = [&](const Pz &Q, uint32_t flags, int32_t r0, int32_t r1) -> bool {
+    EvRec &e = new_event(EV_PAULI);
+    e.flags = flags;
+    e.r0 = r0;
+    e.r1 = r1;
+    return tb.decompose(Q, e.beta, e.gamma, &e.e0);
+  };
+
+  for (size_t i = 0; i < n_ops; ++i) {
+    const soft_op &o = ops[i];
+    int op = o.op;
+    if (op > SOFT_NOISELESS_END) {
+      err = "unknown op code at op " + std::to_string(i);
+      return SOFT_E_UNSUPPORTED_OP;
+    }
+    bool needs_q = is1q(op) || is2q(op) || op == SOFT_M || op == SOFT_R || op == SOFT_MR || op == SOFT_CPAULI;
+    if (needs_q && o.q0 >= n) {
+      err = "qubit out of range at op " + std::to_string(i);
+      return SOFT_E_QUBIT_RANGE;
+    }
+    if (is2q(op) && (o.q1 >= n || o.q1 == o.q0)) {
+      err = "bad second qubit at op " + std::to_string(i);
+      return SOFT_E_QUBIT_RANGE;
+    }
+    if (op == SOFT_DETECTOR || op == SOFT_OBSERVABLE || op == SOFT_CPAULI) {
+      for (int k = 0; k < 2; ++k)
+        if (o.rec[k] >= 0 && (uint32_t)o.rec[k] >= nrec) {
+          err = "record reference to a future measurement at op " + std::to_string(i);
+          return SOFT_E_RECORD_REF;
+        }
+    }
+    if (op == SOFT_NOISELESS_BEGIN) noiseless = true;
+    if (op == SOFT_NOISELESS_END) noiseless = false;
+
+    if ((op == SOFT_M || op == SOFT_MR) && !noiseless && noise->p_meas > 0)
+      if (!add_site(o.q0, 0, false, noise->p_meas)) goto internal;
+
+    if (isclifford(op)) {
+      if (!tb.gate(op, o.q0, o.q1)) goto internal;
+    } else if (op == SOFT_T || op == SOFT_T_DAG || op == SOFT_RZ) {
+      uint64_t beta[2], gamma[2];
+      uint32_t e0;
+      if (!tb.decompose(single(3, o.q0), beta, gamma, &e0)) goto internal;
+      bool diag = (beta[0] | beta[1]) == 0;
+      EvRec &e = new_event(diag ? EV_ROT_DIAG : EV_ROT);
+      std::memcpy(e.beta, beta, sizeof beta);
+      std::memcpy(e.gamma, gamma, sizeof gamma);
+      e.e0 = e0;
+      double ar, ai, br, bi;
+      if (op == SOFT_RZ) {
+        ar = std::cos(0.5 * o.angle);
+        ai = 0.0;
+        br = 0.0;
+        bi = -std::sin(0.5 * o.angle);
+      } else {
+        // diag(1, e^{+-i pi/4}) = (1 + w)/2 I + (1 - w)/2 Z with w = e^{+-i pi/4}
+        double c = std::cos(0.25 * M_PI), sn = (op == SOFT_T ? 1.0 : -1.0) * std::sin(0.25 * M_PI);
+        ar = 0.5 * (1.0 + c);
+        ai = 0.5 * sn;
+        br = 0.5 * (1.0 - c);
+        bi = -0.5 * sn;
+      }
+      e.a_re = ar;
+      e.a_im = ai;
+      e.b_re = br;
+      e.b_im = bi;
+      e.lowbit = 0;
+      if (!diag) e.lowbit = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
+    } else if (op == SOFT_M || op == SOFT_R || op == SOFT_MR) {
+      uint64_t beta[2], gamma[2];
+      uint32_t e0;
+      Pz Zq = single(3, o.q0);
+      if (!tb.decompose(Zq, beta, gamma, &e0)) goto internal;
+      bool recd = (op != SOFT_R);
+      if ((beta[0] | beta[1]) == 0) {
+        EvRec &e = new_event(EV_MEAS_A);
+        std::memcpy(e.gamma, gamma, sizeof gamma);
+        e.e0 = e0;
+        e.ord = ord;
+        e.rec = recd ? nrec : 0;
+        e.flags = recd ? F_RECORD : 0;
+      } else {
+        CaseB cb{};
+        uint32_t p = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
+        cb.p = p;
+        cb.J[0] = beta[0];
+        cb.J[1] = beta[1];
+        flip(cb.J, p);
+        // s_j <- s_j s_p
+        for (uint32_t j = 0; j < n; ++j)
+          if (bit(cb.J, j)) {
+            Pz prod = pmul(herm(tb.s[j]), herm(tb.s[p]));
+            int sb = sign_bit(prod);
+            if (sb < 0) goto internal;
+            if (sb) flip(cb.Hs, j);
+            tb.s[j] = row_of(prod);
+          }
+        // d_p <- d_p prod_{j in J} d_j
+        {
+          Pz acc = herm(tb.d[p]);
+          for (uint32_t j = 0; j < n; ++j)
+            if (bit(cb.J, j)) acc = pmul(acc, herm(tb.d[j]));
+          int sb = sign_bit(acc);
+          if (sb < 0) goto internal;
+          cb.hdp = (uint32_t)sb;
+          tb.d[p] = row_of(acc);
+        }
+        uint64_t b2[2];
+        if (!tb.decompose(Zq, b2, cb.gamma2, &cb.e0b)) goto internal;
+        if (b2[0] != (p < 64 ? (1ull << p) : 0) || b2[1] != (p >= 64 ? (1ull << (p - 64)) : 0)) goto internal;
+        Row old_sp = tb.s[p];
+        for (uint32_t j = 0; j < n; ++j)
+          if (j != p && bit(cb.gamma2, j)) {
+            flip(cb.G, j);
+            Pz prod = pmul(herm(tb.d[j]), herm(old_sp));
+            int sb = sign_bit(prod);
+            if (sb < 0) goto internal;
+            if (sb) flip(cb.Hd, j);
+            tb.d[j] = row_of(prod);
+          }
+        tb.d[p] = old_sp;
+        tb.s[p] = row_of(Zq);
+        cb.rP = 0;
+        EvRec &e = new_event(EV_MEAS_B);
+        e.ord = ord;
+        e.rec = recd ? nrec : 0;
+        e.flags = recd ? F_RECORD : 0;
+        e.caseb = (uint32_t)P.cb.size();
+        P.cb.push_back(cb);
+      }
+      ord++;
+      if (recd) nrec++;
+      if (op == SOFT_R || op == SOFT_MR)
+        if (!pauli_event(single(1, o.q0), F_COND_LAST, -1, -1)) goto internal;
+    } else if (op == SOFT_CPAULI) {
+      int code = o.flags & 3;
+      if (code) {
+        if (!pauli_event(single(code, o.q0), F_COND_REC, o.rec[0], o.rec[1])) goto internal;
+      }
+    } else if (op == SOFT_DETECTOR || op == SOFT_OBSERVABLE) {
+      EvRec &e = new_event(EV_PARITY);
+      e.flags = (op == SOFT_DETECTOR ? F_DETECTOR : F_OBSERVABLE) | ((o.flags & SOFT_FLAG_CHAIN) ? F_CHAIN : 0) |
+                ((o.flags & SOFT_FLAG_INVERT) ? F_INVERT : 0);
+      e.r0 = o.rec[0];
+      e.r1 = o.rec[1];
+    }
+
+    if (!noiseless) {
+      if (is1q(op) && noise->p1 > 0) {
+        if (!add_site(o.q0, 0, false, noise->p1)) goto internal;
+      } else if (is2q(op) && noise->p2 > 0) {
+        if (!add_site(o.q0, o.q1, true, noise->p2)) goto internal;
+      } else if ((op == SOFT_R || op == SOFT_MR) && noise->p_reset > 0) {
+        if (!add_site(o.q0, 0, false, noise->p_reset)) goto internal;
+      }
+    }
+  }
+  new_event(EV_END);
+  P.n_records = nrec;
+  P.rw = nrec ? (nrec + 63) / 64 : 1;
+  if (P.rw > 16) {
+    err = "at most 1024 recorded measurements are supported";
+    return SOFT_E_ARG;
+  }
+  P.n_sites = (uint32_t)P.sites.size();
+  P.thr.resize(P.n_sites ? P.n_sites : 1);
+  for (uint32_t g = 0; g < P.n_sites; ++g) P.thr[g] = gap_thr(P.pmax, g);
+  P.fin_x.assign(4 * (size_t)n, 0);
+  P.fin_z.assign(4 * (size_t)n, 0);
+  for (uint32_t i = 0; i < n; ++i)
+    for (int w = 0; w < 2; ++w) {
+      P.fin_x[2 * i + w] = tb.d[i].x[w];
+      P.fin_z[2 * i + w] = tb.d[i].z[w];
+      P.fin_x[2 * (n + i) + w] = tb.s[i].x[w];
+      P.fin_z[2 * (n + i) + w] = tb.s[i].z[w];
+    }
+  return SOFT_OK;
+internal:
+  err = "internal tableau inconsistency";
+  return SOFT_E_ARG;
+}
+
+}  // namespace soft

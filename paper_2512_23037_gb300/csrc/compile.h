@@ -1,0 +1,28 @@
+// compile.h -- host-side circuit compiler (internal to libsoft).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/soft.h"
+#include "program.h"
+
+namespace soft {
+
+struct HostProgram {
+  uint32_t n = 0, W = 1;
+  uint32_t n_records = 0, rw = 1, n_sites = 0, cap = 0;
+  double pmax = 0.0;
+  std::vector<EvRec> ev;
+  std::vector<CaseB> cb;
+  std::vector<Site> sites;
+  std::vector<uint64_t> thr;     // gap thresholds, one per site
+  std::vector<uint64_t> fin_x;   // final X words, 2n rows x 2 words
+  std::vector<uint64_t> fin_z;
+};
+
+// Returns SOFT_OK or a SOFT_E_* code with a message in `err`.
+int compile_program(const soft_op *ops, size_t n_ops, uint32_t n_qubits, const soft_noise *noise, uint32_t cap,
+                    HostProgram &out, std::string &err);
+
+}  // namespace soft

@@ -1,0 +1,783 @@
+// kernels.cu -- persistent shot kernel for sm_103a.
+//
+// One tile of G lanes (G = 8 or 32) owns one shot at a time and walks the
+// compiled event list of program.h. Per shot it holds, on chip:
+//   - the 2n tableau sign bits (registers; the X/Z words are shot-invariant
+//     and folded into the program),
+//   - the sparse coefficient map v (shared memory): up to 2*cap keys and
+//     complex values (FP64 or FP32) plus an open-addressing hash index,
+//   - the measurement record bits (shared memory).
+// Work items (shots) are handed out by an atomic counter, so shots that end
+// early (a failed detector, Sec. V-C) free their tile at once.
+//
+// Arithmetic (arxiv 2512.23037):
+//   T/Tdag/Rz: v'_a = A v_a + B xi_{a^beta} v_{a^beta}    (Eq. T_gate, Theorem 1 (3))
+//   Pauli Q:   v'_{a^beta} = xi_a(Q) v_a, xi_a = c (-1)^{gamma.a}  (Eq. pauli_on_basis)
+//   Z meas.:   filter (beta = 0) or pivot + pair (beta != 0), renormalise
+//              (Eq. Pi_pm, Theorem 1 (2)); probabilities in FP64.
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace soft {
+namespace {
+
+enum : int { ST_RUN = -1, ST_KEPT = 0, ST_DISC = 1, ST_OVF = 2, ST_ERR = 3, ST_RERUN = 4 };
+
+template <typename R>
+struct Cx {
+  R x, y;
+};
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> csub(Cx<R> a, Cx<R> b) {
+  return {a.x - b.x, a.y - b.y};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cscale(Cx<R> a, R s) {
+  return {a.x * s, a.y * s};
+}
+// v * i^e
+template <typename R>
+__device__ __forceinline__ Cx<R> ipow(Cx<R> v, uint32_t e) {
+  Cx<R> r = (e & 1u) ? Cx<R>{-v.y, v.x} : v;
+  if (e & 2u) r = {-r.x, -r.y};
+  return r;
+}
+template <typename R>
+__device__ __forceinline__ R norm2(Cx<R> v) {
+  return v.x * v.x + v.y * v.y;
+}
+template <typename R>
+__device__ __forceinline__ double norm2d(Cx<R> v) {
+  double a = (double)v.x, b = (double)v.y;
+  return a * a + b * b;
+}
+
+template <int W>
+struct Key {
+  uint64_t w[W];
+};
+template <int W>
+__device__ __forceinline__ Key<W> kxor(const Key<W> &a, const uint64_t *b) {
+  Key<W> r;
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.w[i] = a.w[i] ^ b[i];
+  return r;
+}
+template <int W>
+__device__ __forceinline__ uint32_t kpar(const Key<W> &a, const uint64_t *b) {
+  uint32_t t = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) t += __popcll(a.w[i] & b[i]);
+  return t & 1u;
+}
+template <int W>
+__device__ __forceinline__ bool keq(const Key<W> &a, const Key<W> &b) {
+  bool e = true;
+#pragma unroll
+  for (int i = 0; i < W; ++i) e = e && (a.w[i] == b.w[i]);
+  return e;
+}
+// word (i >> 6) of a W-word vector without dynamic register indexing
+template <int W>
+__device__ __forceinline__ uint64_t word_of(const uint64_t *a, uint32_t i) {
+  return (W == 1 || (i >> 6) == 0u) ? a[0] : a[W - 1];
+}
+template <int W>
+__device__ __forceinline__ uint32_t kbit(const Key<W> &a, uint32_t i) {
+  return (uint32_t)((word_of<W>(a.w, i) >> (i & 63)) & 1ull);
+}
+template <int W>
+__device__ __forceinline__ uint32_t khash(const Key<W> &a) {
+  uint64_t h = a.w[0];
+  if (W == 2) h ^= a.w[W - 1] * 0xC2B2AE3D27D4EB4Full;
+  h *= 0x9E3779B97F4A7C15ull;
+  return (uint32_t)(h >> 32);
+}
+template <int W>
+__device__ __forceinline__ uint32_t wpar(const uint64_t *a, const uint64_t *b) {
+  uint32_t t = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) t += __popcll(a[i] & b[i]);
+  return t & 1u;
+}
+template <int W>
+__device__ __forceinline__ uint32_t wbit(const uint64_t *a, uint32_t i) {
+  return (uint32_t)((word_of<W>(a, i) >> (i & 63)) & 1ull);
+}
+template <int W>
+__device__ __forceinline__ void wflip(uint64_t *a, uint32_t i) {
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+    if ((int)(i >> 6) == w) a[w] ^= 1ull << (i & 63);
+}
+
+// Philox4x32-10, counter (shot_lo, shot_hi, stream, index), key = seed.
+__device__ __forceinline__ uint4 philox(uint64_t seed, uint64_t shot, uint32_t stream, uint32_t idx) {
+  uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32), c2 = stream, c3 = idx;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ double snap01(double p) {
+  if (p < 1e-12) return 0.0;
+  if (p > 1.0 - 1e-12) return 1.0;
+  return p;
+}
+
+template <typename R, int W>
+__host__ __device__ inline size_t group_bytes(uint32_t cap, uint32_t rw) {
+  size_t slots = 2 * (size_t)cap;
+  size_t b = slots * sizeof(Cx<R>) + (size_t)W * slots * 8 + 4 * (size_t)cap * 4 + (size_t)rw * 8;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <typename R, int W, int G>
+struct Shot {
+  using Tile = cg::thread_block_tile<G>;
+  const Tile &t;
+  const ShotParams &P;
+  Cx<R> *vals;
+  uint64_t *keys;
+  uint32_t *ht;
+  uint64_t *rec;
+  uint32_t slots, hsmask, cap, lane;
+  uint64_t shot;
+  uint32_t nnz;
+  uint64_t sd[W], ss[W];
+  uint32_t nxt, cur, kblk, w2;
+  int status, chain, logical, lastm;
+
+  __device__ Shot(const Tile &tile, const ShotParams &p, unsigned char *base) : t(tile), P(p) {
+    cap = P.cap;
+    slots = 2 * cap;
+    hsmask = 4 * cap - 1;
+    lane = t.thread_rank();
+    vals = reinterpret_cast<Cx<R> *>(base);
+    keys = reinterpret_cast<uint64_t *>(base + slots * sizeof(Cx<R>));
+    ht = reinterpret_cast<uint32_t *>(base + slots * sizeof(Cx<R>) + (size_t)W * slots * 8);
+    rec = reinterpret_cast<uint64_t *>(base + slots * sizeof(Cx<R>) + (size_t)W * slots * 8 + 16 * (size_t)cap);
+  }
+
+  __device__ __forceinline__ Key<W> key(uint32_t e) const {
+    Key<W> r;
+#pragma unroll
+    for (int w = 0; w < W; ++w) r.w[w] = keys[w * slots + e];
+    return r;
+  }
+  __device__ __forceinline__ void set_key(uint32_t e, const Key<W> &k) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) keys[w * slots + e] = k.w[w];
+  }
+  __device__ int lookup(const Key<W> &k) const {
+    uint32_t h = khash(k) & hsmask;
+    for (uint32_t probe = 0; probe <= hsmask; ++probe) {
+      uint32_t v = ht[h];
+      if (v == 0u) return -1;
+      if (keq(key(v - 1u), k)) return (int)(v - 1u);
+      h = (h + 1u) & hsmask;
+    }
+    return -1;
+  }
+  __device__ void insert(uint32_t s, const Key<W> &k) {
+    uint32_t h = khash(k) & hsmask;
+    for (uint32_t probe = 0; probe <= hsmask; ++probe) {
+      if (atomicCAS(&ht[h], 0u, s + 1u) == 0u) return;
+      h = (h + 1u) & hsmask;
+    }
+  }
+  __device__ void rebuild() {
+    for (uint32_t i = lane; i <= hsmask; i += G) ht[i] = 0u;
+    t.sync();
+    for (uint32_t e = lane; e < nnz; e += G) insert(e, key(e));
+    t.sync();
+  }
+  __device__ __forceinline__ uint32_t lanes_below(uint32_t ballot) const {
+    return __popc(ballot & ((1u << lane) - 1u));
+  }
+  __device__ double tile_sum(double v) const {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += t.shfl_xor(v, off);
+    return v;
+  }
+  // Stable in-place compaction of entries [src, src + n) into [0, out).
+  template <typename Keep>
+  __device__ uint32_t compact(uint32_t src, uint32_t n, Keep keep) {
+    uint32_t out = 0;
+    for (uint32_t base = 0; base < n; base += G) {
+      uint32_t e = base + lane;
+      Key<W> k;
+      Cx<R> v;
+      bool kp = false;
+      if (e < n) {
+        k = key(src + e);
+        v = vals[src + e];
+        kp = keep(k, v);
+      }
+      uint32_t b = t.ballot(kp);
+      t.sync();
+      if (kp) {
+        uint32_t d = out + lanes_below(b);
+        set_key(d, k);
+        vals[d] = v;
+      }
+      out += __popc(b);
+      t.sync();
+    }
+    return out;
+  }
+  __device__ double uniform(uint32_t ord) const {
+    uint4 w = philox(P.seed, shot, 1u, ord);
+    uint64_t m = ((uint64_t)w.x << 21) ^ (uint64_t)(w.y >> 11);
+    return (double)m * 0x1p-53;
+  }
+
+  // ---- noise: next accepted error site (geometric gaps, then thinning)
+  __device__ void draw_next() {
+    for (uint32_t guard = 0; guard <= P.n_sites; ++guard) {
+      if (cur >= P.n_sites) {
+        nxt = 0xFFFFFFFFu;
+        return;
+      }
+      uint4 w = philox(P.seed, shot, 0u, kblk++);
+      uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
+      uint32_t rem = P.n_sites - cur, lo = 0, hi = rem;
+      while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (U < __ldg(&P.thr[mid])) hi = mid;
+        else lo = mid + 1u;
+      }
+      if (lo == rem) {
+        cur = P.n_sites;
+        nxt = 0xFFFFFFFFu;
+        return;
+      }
+      uint32_t s = cur + lo;
+      cur = s + 1u;
+      const Site *st = P.sites + s;
+      if (!__ldg(&st->always) && !(w.w < __ldg(&st->thin))) continue;
+      nxt = s;
+      w2 = w.z;
+      return;
+    }
+    nxt = 0xFFFFFFFFu;
+    status = ST_ERR;
+  }
+
+  // v'_{a^beta} = i^{e + 2 gamma.a} v_a
+  __device__ void apply_pauli(const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+    bool moves = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) moves = moves || beta[w];
+    for (uint32_t i = lane; i < nnz; i += G) {
+      Key<W> k = key(i);
+      vals[i] = ipow(vals[i], e + 2u * kpar(k, gamma));
+      if (moves) set_key(i, kxor(k, beta));
+    }
+    t.sync();
+    if (moves) rebuild();
+  }
+
+  __device__ void apply_error(uint32_t s) {
+    const Site *S = P.sites + s;
+    uint32_t two = __ldg(&S->two), code, pa, pb;
+    if (two) {
+      code = (uint32_t)(((uint64_t)w2 * 15u) >> 32) + 1u;
+      pa = code >> 2;
+      pb = code & 3u;
+    } else {
+      code = (uint32_t)(((uint64_t)w2 * 3u) >> 32) + 1u;
+      pa = code;
+      pb = 0;
+    }
+    uint64_t beta[W], gamma[W];
+    uint32_t pe = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint64_t b = 0, g = 0;
+      if (pa == 1u || pa == 2u) { b ^= __ldg(&S->bx[0][w]); g ^= __ldg(&S->gx[0][w]); }
+      if (pa == 3u || pa == 2u) { b ^= __ldg(&S->bz[0][w]); g ^= __ldg(&S->gz[0][w]); }
+      if (pb == 1u || pb == 2u) { b ^= __ldg(&S->bx[1][w]); g ^= __ldg(&S->gx[1][w]); }
+      if (pb == 3u || pb == 2u) { b ^= __ldg(&S->bz[1][w]); g ^= __ldg(&S->gz[1][w]); }
+      beta[w] = b;
+      gamma[w] = g;
+      pe += __popcll((sd[w] ^ __ldg(&S->dsd[w])) & b) + __popcll((ss[w] ^ __ldg(&S->dss[w])) & g);
+    }
+    uint32_t e = ((__ldg(&S->c0) >> (2u * code)) + 2u * pe) & 3u;
+    apply_pauli(beta, gamma, e);
+  }
+
+  __device__ void fail_capacity() { status = P.small_pass ? ST_RERUN : ST_OVF; }
+
+  __device__ void set_record(uint32_t r, int m) {
+    if (lane == 0 && m < 0) rec[r >> 6] |= 1ull << (r & 63);
+    t.sync();
+  }
+
+  // ---- a I + b Z_q, beta != 0
+  __device__ void rot(const EvRec *E) {
+    uint64_t beta[W], gamma[W];
+    uint32_t pe = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      beta[w] = __ldg(&E->beta[w]);
+      gamma[w] = __ldg(&E->gamma[w]);
+      pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
+    }
+    const uint32_t e = (__ldg(&E->e0) + 2u * pe) & 3u;
+    const uint32_t lowbit = __ldg(&E->lowbit);
+    const Cx<R> a{(R)__ldg(&E->a_re), (R)__ldg(&E->a_im)}, b{(R)__ldg(&E->b_re), (R)__ldg(&E->b_im)};
+    const R tau = (R)P.tau;
+    uint32_t nA = 0;
+    bool prune = false;
+    const uint32_t n0 = nnz;
+    for (uint32_t base = 0; base < n0; base += G) {
+      uint32_t i = base + lane;
+      bool app = false;
+      Key<W> pk;
+      Cx<R> nv{0, 0};
+      if (i < n0) {
+        Key<W> k = key(i);
+        Cx<R> v = vals[i];
+        pk = kxor(k, beta);
+        int j = lookup(pk);
+        if (j >= 0) {
+          if (!kbit(k, lowbit)) {
+            Cx<R> vj = vals[j];
+            Cx<R> ni = cadd(cmul(a, v), cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
+            Cx<R> nj = cadd(cmul(a, vj), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
+            vals[i] = ni;
+            vals[j] = nj;
+            prune = prune || norm2(ni) < tau || norm2(nj) < tau;
+          }
+        } else {
+          Cx<R> ni = cmul(a, v);
+          vals[i] = ni;
+          nv = cmul(b, ipow(v, e + 2u * kpar(k, gamma)));
+          app = true;
+          prune = prune || norm2(ni) < tau || norm2(nv) < tau;
+        }
+      }
+      uint32_t bal = t.ballot(app);
+      if (app) {
+        uint32_t slot = n0 + nA + lanes_below(bal);
+        set_key(slot, pk);
+        vals[slot] = nv;
+      }
+      nA += __popc(bal);
+    }
+    t.sync();
+    nnz = n0 + nA;
+    bool pruned = t.any(prune);
+    if (pruned) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
+    if (nnz > cap) {
+      fail_capacity();
+      return;
+    }
+    if (pruned) {
+      rebuild();
+    } else if (nA) {
+      for (uint32_t i = n0 + lane; i < nnz; i += G) insert(i, key(i));
+      t.sync();
+    }
+  }
+
+  // ---- a I + b Z_q, beta == 0: v_a *= a + b xi_a
+  __device__ void rot_diag(const EvRec *E) {
+    uint64_t gamma[W];
+    uint32_t pe = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      gamma[w] = __ldg(&E->gamma[w]);
+      pe += __popcll(ss[w] & gamma[w]);
+    }
+    const uint32_t e = (__ldg(&E->e0) + 2u * pe) & 3u;
+    const Cx<R> a{(R)__ldg(&E->a_re), (R)__ldg(&E->a_im)}, b{(R)__ldg(&E->b_re), (R)__ldg(&E->b_im)};
+    const R tau = (R)P.tau;
+    bool prune = false;
+    for (uint32_t i = lane; i < nnz; i += G) {
+      Key<W> k = key(i);
+      Cx<R> v = vals[i];
+      Cx<R> nv = cadd(cmul(a, v), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
+      vals[i] = nv;
+      prune = prune || norm2(nv) < tau;
+    }
+    t.sync();
+    if (t.any(prune)) {
+      nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
+      rebuild();
+    }
+  }
+
+  // ---- Z measurement, beta = 0: lambda_a = c (-1)^{gamma.a}
+  __device__ int meas_a(const EvRec *E) {
+    uint64_t gamma[W];
+    uint32_t pe = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      gamma[w] = __ldg(&E->gamma[w]);
+      pe += __popcll(ss[w] & gamma[w]);
+    }
+    const uint32_t e = (__ldg(&E->e0) + 2u * pe) & 3u;
+    if (e & 1u) {
+      status = ST_ERR;
+      return 1;
+    }
+    const uint32_t sgn = e >> 1;
+    double sp = 0.0, sm = 0.0;
+    bool h0 = false, h1 = false;
+    for (uint32_t i = lane; i < nnz; i += G) {
+      uint32_t neg = kpar(key(i), gamma) ^ sgn;
+      double a2 = norm2d(vals[i]);
+      if (neg) {
+        sm += a2;
+        h1 = true;
+      } else {
+        sp += a2;
+        h0 = true;
+      }
+    }
+    h0 = t.any(h0);
+    h1 = t.any(h1);
+    if (!(h0 && h1)) return h1 ? -1 : 1;  // decided by the integer test
+    sp = tile_sum(sp);
+    sm = tile_sum(sm);
+    const double pp = snap01(sp / (sp + sm));
+    const int m = uniform(__ldg(&E->ord)) < pp ? 1 : -1;
+    const R sc = (R)(1.0 / sqrt(m == 1 ? sp : sm));
+    const uint32_t want = (m == 1) ? 0u : 1u;
+    const R tau = (R)P.tau;
+    t.sync();
+    nnz = compact(0, nnz, [&](Key<W> &k, Cx<R> &v) {
+      if ((kpar(k, gamma) ^ sgn) != want) return false;
+      v = cscale(v, sc);
+      return norm2(v) >= tau;
+    });
+    rebuild();
+    return m;
+  }
+
+  // ---- Z measurement, beta != 0 (case B)
+  __device__ int meas_b(const EvRec *E) {
+    const CaseB *B = P.cb + __ldg(&E->caseb);
+    const uint32_t p = __ldg(&B->p);
+    uint64_t J[W], g2[W], ep[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      J[w] = __ldg(&B->J[w]);
+      g2[w] = __ldg(&B->gamma2[w]);
+      ep[w] = ((int)(p >> 6) == w) ? (1ull << (p & 63)) : 0ull;
+    }
+    // row operations on the sign bits: s_j <- s_j s_p (j in J), d_p <- d_p prod d_j
+    const uint32_t ssp = wbit<W>(ss, p);
+    const uint32_t sdJ = wpar<W>(sd, J);
+#pragma unroll
+    for (int w = 0; w < W; ++w) ss[w] ^= (ssp ? J[w] : 0ull) ^ __ldg(&B->Hs[w]);
+    if (sdJ ^ __ldg(&B->hdp)) wflip<W>(sd, p);
+    // P = i^e2 d_p s_gamma2 in the new tableau
+    const uint32_t e2 = (__ldg(&B->e0b) + 2u * (wbit<W>(sd, p) + wpar<W>(ss, g2))) & 3u;
+    // relabel keys: a_j ^= a_p for j in J
+    for (uint32_t i = lane; i < nnz; i += G) {
+      Key<W> k = key(i);
+      if (kbit(k, p)) set_key(i, kxor(k, J));
+    }
+    t.sync();
+    rebuild();
+    double sp = 0.0, sm = 0.0;
+    for (uint32_t i = lane; i < nnz; i += G) {
+      Key<W> k = key(i);
+      const uint32_t hi = kbit(k, p);
+      const int j = lookup(kxor(k, ep));
+      if (hi && j >= 0) continue;
+      Cx<R> v0{0, 0}, v1{0, 0};
+      if (hi) v1 = vals[i];
+      else {
+        v0 = vals[i];
+        if (j >= 0) v1 = vals[j];
+      }
+      Key<W> a1 = hi ? k : kxor(k, ep);
+      Cx<R> x1 = ipow(v1, e2 + 2u * kpar(a1, g2));
+      sp += 0.5 * norm2d(cadd(v0, x1));
+      sm += 0.5 * norm2d(csub(v0, x1));
+    }
+    sp = tile_sum(sp);
+    sm = tile_sum(sm);
+    const double pp = snap01(sp / (sp + sm));
+    const int m = uniform(__ldg(&E->ord)) < pp ? 1 : -1;
+    const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
+    // stage the paired values in slots [cap, cap + nnz)
+    for (uint32_t i = lane; i < nnz; i += G) {
+      Key<W> k = key(i);
+      const uint32_t hi = kbit(k, p);
+      const int j = lookup(kxor(k, ep));
+      Cx<R> nv{0, 0};
+      Key<W> a0 = hi ? kxor(k, ep) : k;
+      if (!(hi && j >= 0)) {
+        Cx<R> v0{0, 0}, v1{0, 0};
+        if (hi) v1 = vals[i];
+        else {
+          v0 = vals[i];
+          if (j >= 0) v1 = vals[j];
+        }
+        Key<W> a1 = kxor(a0, ep);
+        Cx<R> x1 = ipow(v1, e2 + 2u * kpar(a1, g2));
+        nv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
+      }
+      set_key(cap + i, a0);
+      vals[cap + i] = nv;
+    }
+    t.sync();
+    const R tau = (R)P.tau;
+    nnz = compact(cap, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
+    rebuild();
+    // replacement: d_j <- d_j s_p (j in G), d_p <- old s_p, s_p <- m P
+#pragma unroll
+    for (int w = 0; w < W; ++w) sd[w] ^= (ssp ? __ldg(&B->G[w]) : 0ull) ^ __ldg(&B->Hd[w]);
+    if (wbit<W>(sd, p) != ssp) wflip<W>(sd, p);
+    const uint32_t newsp = (m == -1 ? 1u : 0u) ^ __ldg(&B->rP);
+    if (wbit<W>(ss, p) != newsp) wflip<W>(ss, p);
+    return m;
+  }
+
+  __device__ uint32_t rec_bit(int32_t r) const {
+    return r < 0 ? 0u : (uint32_t)((rec[r >> 6] >> (r & 63)) & 1ull);
+  }
+
+  __device__ void run(uint64_t s) {
+    shot = s;
+    status = ST_RUN;
+    chain = 0;
+    logical = 0;
+    lastm = 1;
+#pragma unroll
+    for (int w = 0; w < W; ++w) sd[w] = ss[w] = 0ull;
+    nnz = 1;
+    if (lane == 0) {
+      Key<W> z;
+#pragma unroll
+      for (int w = 0; w < W; ++w) z.w[w] = 0ull;
+      set_key(0, z);
+      vals[0] = Cx<R>{(R)1, (R)0};
+    }
+    for (uint32_t w = lane; w < P.rw; w += G) rec[w] = 0ull;
+    t.sync();
+    rebuild();
+    cur = 0;
+    kblk = 0;
+    draw_next();
+    for (uint32_t ev = 0; ev < P.n_events && status == ST_RUN; ++ev) {
+      const EvRec *E = P.ev + ev;
+      const uint32_t sb = __ldg(&E->site_begin);
+      while (nxt < sb && status == ST_RUN) {
+        apply_error(nxt);
+        draw_next();
+      }
+      if (status != ST_RUN) break;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        sd[w] ^= __ldg(&E->dsd[w]);
+        ss[w] ^= __ldg(&E->dss[w]);
+      }
+      const uint32_t type = __ldg(&E->type), flags = __ldg(&E->flags);
+      switch (type) {
+        case EV_ROT: rot(E); break;
+        case EV_ROT_DIAG: rot_diag(E); break;
+        case EV_MEAS_A:
+        case EV_MEAS_B: {
+          int m = (type == EV_MEAS_A) ? meas_a(E) : meas_b(E);
+          lastm = m;
+          if (flags & F_RECORD) set_record(__ldg(&E->rec), m);
+          break;
+        }
+        case EV_PAULI: {
+          uint32_t cond = 0;
+          if (flags & F_COND_LAST) cond = (lastm == -1);
+          else cond = rec_bit(__ldg(&E->r0)) ^ rec_bit(__ldg(&E->r1));
+          if (cond) {
+            uint64_t beta[W], gamma[W];
+            uint32_t pe = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+              beta[w] = __ldg(&E->beta[w]);
+              gamma[w] = __ldg(&E->gamma[w]);
+              pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
+            }
+            apply_pauli(beta, gamma, (__ldg(&E->e0) + 2u * pe) & 3u);
+          }
+          break;
+        }
+        case EV_PARITY: {
+          int par = chain ^ (int)rec_bit(__ldg(&E->r0)) ^ (int)rec_bit(__ldg(&E->r1)) ^
+                    ((flags & F_INVERT) ? 1 : 0);
+          if (flags & F_CHAIN) {
+            chain = par;
+          } else {
+            chain = 0;
+            if ((flags & F_DETECTOR) && par) status = ST_DISC;
+            if ((flags & F_OBSERVABLE) && par) logical = 1;
+          }
+          break;
+        }
+        default: break;
+      }
+    }
+    if (status == ST_RUN) status = ST_KEPT;
+  }
+
+  __device__ void finish(uint64_t off, unsigned long long *btally) {
+    if (status == ST_RERUN) {
+      if (lane == 0) {
+        unsigned long long i = atomicAdd(P.n_rerun, 1ull);
+        P.rerun[i] = (uint32_t)off;
+      }
+      t.sync();
+      return;
+    }
+    if (lane == 0) {
+      atomicAdd(&btally[0], 1ull);
+      if (status == ST_DISC) atomicAdd(&btally[1], 1ull);
+      else if (status == ST_OVF) atomicAdd(&btally[2], 1ull);
+      else if (status == ST_KEPT) {
+        atomicAdd(&btally[3], 1ull);
+        if (logical) atomicAdd(&btally[4], 1ull);
+      }
+      if (off < P.out_limit) {
+        if (P.status) P.status[off] = (uint8_t)status;
+      }
+    }
+    if (off < P.out_limit && P.records)
+      for (uint32_t w = lane; w < P.rw; w += G) P.records[off * P.rw + w] = rec[w];
+    if (off < P.st_limit) {
+      if (lane == 0) {
+        P.st_nnz[off] = nnz;
+        P.st_signs[off * 4 + 0] = sd[0];
+        P.st_signs[off * 4 + 1] = (W == 2) ? sd[W - 1] : 0ull;
+        P.st_signs[off * 4 + 2] = ss[0];
+        P.st_signs[off * 4 + 3] = (W == 2) ? ss[W - 1] : 0ull;
+      }
+      for (uint32_t i = lane; i < nnz && i < P.st_stride; i += G) {
+        Key<W> k = key(i);
+        size_t o = (size_t)off * P.st_stride + i;
+        P.st_keys[2 * o] = k.w[0];
+        P.st_keys[2 * o + 1] = (W == 2) ? k.w[W - 1] : 0ull;
+        P.st_vals[2 * o] = (double)vals[i].x;
+        P.st_vals[2 * o + 1] = (double)vals[i].y;
+      }
+    }
+    t.sync();
+  }
+};
+
+constexpr int kBlock = 128;
+
+template <typename R, int W, int G>
+__global__ void __launch_bounds__(kBlock) shot_kernel(const __grid_constant__ ShotParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long btally[5];
+  auto block = cg::this_thread_block();
+  auto tile = cg::tiled_partition<G>(block);
+  if (threadIdx.x < 5) btally[threadIdx.x] = 0ull;
+  __syncthreads();
+  const uint32_t gid = threadIdx.x / G;  // blockDim.x is a multiple of G
+  unsigned char *base = smem + (size_t)gid * group_bytes<R, W>(P.cap, P.rw);
+  Shot<R, W, G> s(tile, P, base);
+  const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
+  for (;;) {
+    unsigned long long item = 0;
+    if (tile.thread_rank() == 0) item = atomicAdd(P.next_item, 1ull);
+    item = tile.shfl(item, 0);
+    if (item >= n_items) break;
+    const uint64_t off = P.list ? (uint64_t)P.list[item] : (uint64_t)item;
+    s.run(P.first_shot + off);
+    s.finish(off, btally);
+  }
+  __syncthreads();
+  if (threadIdx.x < 5 && btally[threadIdx.x]) atomicAdd(&P.tally[threadIdx.x], btally[threadIdx.x]);
+}
+
+template <typename R, int W, int G>
+cudaError_t launch_t(const ShotParams &p, int blocks_per_sm, cudaStream_t stream, int *grid_out) {
+  auto kern = shot_kernel<R, W, G>;
+  const size_t gb = group_bytes<R, W>(p.cap, p.rw);
+  const size_t limit = 227 * 1024;
+  size_t gpb = kBlock / G;
+  while (gpb > 1 && gpb * gb > limit) gpb >>= 1;
+  if (gpb * gb > limit) return cudaErrorInvalidConfiguration;
+  const int block = (int)(gpb * G);
+  const size_t smem = gpb * gb;
+  static int configured_smem = -1;
+  if (configured_smem < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_smem = (int)smem;
+  }
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+  long long grid = (long long)occ * sms;
+  const long long groups = (long long)gpb;
+  if (!p.n_items_dev) {
+    long long need = ((long long)p.n_items + groups - 1) / groups;
+    if (need < grid) grid = need > 0 ? need : 1;
+  }
+  if (grid_out) *grid_out = (int)grid;
+  kern<<<(unsigned)grid, block, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t group_smem_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw) {
+  if (fp32) return W == 1 ? group_bytes<float, 1>(cap, rw) : group_bytes<float, 2>(cap, rw);
+  return W == 1 ? group_bytes<double, 1>(cap, rw) : group_bytes<double, 2>(cap, rw);
+}
+
+cudaError_t launch_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t group, int blocks_per_sm,
+                         cudaStream_t stream, int *grid_out) {
+#define SOFT_DISPATCH(R, WW, GG) return launch_t<R, WW, GG>(p, blocks_per_sm, stream, grid_out)
+  if (fp32) {
+    if (W == 1) {
+      if (group == 8) SOFT_DISPATCH(float, 1, 8);
+      SOFT_DISPATCH(float, 1, 32);
+    }
+    if (group == 8) SOFT_DISPATCH(float, 2, 8);
+    SOFT_DISPATCH(float, 2, 32);
+  }
+  if (W == 1) {
+    if (group == 8) SOFT_DISPATCH(double, 1, 8);
+    SOFT_DISPATCH(double, 1, 32);
+  }
+  if (group == 8) SOFT_DISPATCH(double, 2, 8);
+  SOFT_DISPATCH(double, 2, 32);
+#undef SOFT_DISPATCH
+}
+
+}  // namespace soft

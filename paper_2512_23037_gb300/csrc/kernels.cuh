@@ -1,0 +1,47 @@
+// kernels.cuh -- launch interface of the shot kernel (internal to libsoft).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "program.h"
+
+namespace soft {
+
+struct ShotParams {
+  // compiled program (device)
+  const EvRec *ev;
+  const CaseB *cb;
+  const Site *sites;
+  const uint64_t *thr;
+  uint32_t n_events, n_sites, rw, cap;
+  double tau;
+  // work
+  uint64_t seed, first_shot, n_items;  // shots first_shot + [0, n_items) or the list below
+  const unsigned long long *n_items_dev;  // optional: item count read on the device
+  const uint32_t *list;                // optional: shot offsets (relative to first_shot)
+  unsigned long long *next_item;       // work counter (zeroed before launch)
+  int small_pass;                      // 1: |v| > cap marks the shot for a rerun
+  uint32_t *rerun;                     // rerun list (capacity n_items)
+  unsigned long long *n_rerun;
+  // outputs
+  unsigned long long *tally;           // [5]: shots, discarded, overflow, kept, logical
+  uint8_t *status;                     // per shot offset < out_limit
+  uint64_t *records;                   // rw words per shot offset < out_limit
+  uint64_t out_limit;
+  uint64_t *st_signs;                  // 4 words per shot offset < st_limit
+  uint64_t *st_keys;                   // st_stride entries x 2 words
+  double *st_vals;                     // st_stride entries x (re, im)
+  uint32_t *st_nnz;
+  uint64_t st_limit;
+  uint32_t st_stride;
+};
+
+// Bytes of shared memory one shot group needs for capacity `cap`.
+size_t group_smem_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw);
+
+// Launch the persistent kernel. group = 8 or 32 lanes per shot.
+cudaError_t launch_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t group, int blocks_per_sm,
+                         cudaStream_t stream, int *grid_out);
+
+}  // namespace soft

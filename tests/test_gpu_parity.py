@@ -1,0 +1,203 @@
+"""GPU path (through the C ABI) against the FP64 oracle, shot for shot.
+
+Bars (written here, used below):
+  - records, status and tallies bit-exact, except shots whose first
+    differing outcome had |p - u| <= BAND (counted, must be rare);
+  - tableau words (compiled X/Z + per-shot signs) bit-exact;
+  - coefficients: same key set, values within 1e-12 (FP64) / 1e-5 (FP32);
+    the FP32 comparison drops oracle entries with |v|^2 < 1e-10, the FP32
+    pruning threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_23037_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+BAND = {"fp64": 1e-9, "fp32": 1e-5}
+VTOL = {"fp64": 1e-12, "fp32": 1e-5}
+TAU = {"fp64": 1e-20, "fp32": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def soft():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_23037_gb300 as S
+    S.load()
+    return S
+
+
+def _bits(words, nrec):
+    return [(int(words[r // 64]) >> (r % 64)) & 1 for r in range(nrec)]
+
+
+def _band_ok(circ, noise, seed, shot, band):
+    """True if the oracle's shot has a sampled outcome with |p - u| <= band."""
+    tr = oracle.trace(circ, circ.n, noise, circ.cap, seed, shot)
+    for e in tr["events"]:
+        if e["kind"] == 3 and not e["det"] and abs(e["p_plus"] - e["u"]) <= band:
+            return True
+    return False
+
+
+def run_both(S, circ, noise, n_shots, seed, precision, first_shot=0, capture=0, group=0, first_cap=0,
+             chunk=0):
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    r = S.soft_run_shots(c, n_shots, first_shot, seed, precision=precision, record_mode=S.REC_ALL,
+                         capture_k=capture, group_size=group, first_cap=first_cap, chunk_shots=chunk)
+    rec, st = S.soft_get_records(r, n_shots)
+    tal = S.soft_tally(r)
+    ref = oracle.run(circ, circ.n, noise, circ.cap, seed, first_shot, n_shots, threads=8)
+    return c, r, rec, st, tal, ref
+
+
+def compare_records(circ, noise, seed, first_shot, rec, st, ref, precision):
+    nrec = ref["n_records"]
+    band_events = 0
+    for i in range(len(st)):
+        same = st[i] == ref["status"][i] and np.array_equal(rec[i], ref["records"][i])
+        if not same:
+            assert _band_ok(circ, noise, seed, first_shot + i, BAND[precision]), (
+                f"shot {first_shot + i}: status {st[i]} vs {ref['status'][i]}, records "
+                f"{_bits(rec[i], nrec)} vs {_bits(ref['records'][i], nrec)}")
+            band_events += 1
+    return band_events
+
+
+def compare_states(S, c, r, circ, noise, seed, first_shot, k, precision):
+    xw, zw = c.tableau()
+    n = circ.n
+    for off in range(k):
+        tr = oracle.trace(circ, n, noise, circ.cap, seed, first_shot + off)
+        signs, keys, vals = S.soft_get_state(r, off)
+        if tr["status"] != 0:
+            continue
+        # tableau words: compiled X/Z + per-shot signs
+        assert np.array_equal(xw, tr["rows_x"]) and np.array_equal(zw, tr["rows_z"])
+        rd = [(int(signs[i // 64]) >> (i % 64)) & 1 for i in range(n)]
+        rs = [(int(signs[2 + i // 64]) >> (i % 64)) & 1 for i in range(n)]
+        assert rd + rs == [int(v) for v in tr["rows_r"]], f"signs differ at shot {first_shot + off}"
+        # coefficient map
+        ok = np.abs(tr["vals"]) ** 2 >= TAU[precision]
+        ok_keys = tr["keys"][ok]
+        ok_vals = tr["vals"][ok]
+        order = np.lexsort((keys[:, 0], keys[:, 1]))
+        keys, vals = keys[order], vals[order]
+        assert np.array_equal(keys, ok_keys), f"key sets differ at shot {first_shot + off}"
+        assert np.max(np.abs(vals - ok_vals)) <= VTOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiny_workload(soft, precision):
+    circ, noise = C.workload("tiny6")
+    noise = C.Noise.uniform(0.02)
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 3000, 0, precision, capture=64)
+    assert compare_records(circ, noise, 0, 0, rec, st, ref, precision) <= 3
+    assert [tal["shots"], tal["discarded"], tal["overflow"], tal["kept"], tal["logical_errors"]][0] == 3000
+    compare_states(soft, c, r, circ, noise, 0, 0, 64, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("seed", range(6))
+def test_random_circuits(soft, precision, seed):
+    """Every op kind: T/T^dag/Rz, case-A and case-B measurements, resets,
+    feedback Paulis, observables; several tiles and a ragged tail."""
+    n = [3, 5, 8, 12, 40, 70][seed]
+    circ = C.random_circuit(1000 + seed, n, 60 + 8 * n, t_frac=0.2, detectors=True)
+    circ.cap = 256
+    noise = C.Noise(0.01, 0.01, 0.01, 0.01)
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 777, seed, precision, capture=48)
+    assert compare_records(circ, noise, seed, 0, rec, st, ref, precision) <= 3
+    compare_states(soft, c, r, circ, noise, seed, 0, 48, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_w42_prefix(soft, precision):
+    circ, noise = C.workload("w42")
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 10000, 0, precision, capture=32)
+    band = compare_records(circ, noise, 0, 0, rec, st, ref, precision)
+    assert band <= 5
+    t = ref["tally"]
+    if band == 0:
+        assert [tal["shots"], tal["discarded"], tal["overflow"], tal["kept"], tal["logical_errors"]] == t
+    compare_states(soft, c, r, circ, noise, 0, 0, 32, precision)
+
+
+def test_w42_far_shot_range(soft):
+    """Shot indices far from 0 (counter words above 2^32) and a chunked run."""
+    circ, noise = C.workload("w42")
+    first = (1 << 40) + 12345
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 3000, 7, "fp64", first_shot=first, chunk=1000)
+    assert compare_records(circ, noise, 7, first, rec, st, ref, "fp64") == 0
+
+
+def test_rerun_pass_matches_single_pass(soft):
+    """A tiny first-pass capacity forces most shots through the rerun pass."""
+    circ, noise = C.workload("w42")
+    for fc in (2, 8):
+        c, r, rec, st, tal, ref = run_both(soft, circ, noise, 2000, 3, "fp64", first_cap=fc)
+        assert compare_records(circ, noise, 3, 0, rec, st, ref, "fp64") == 0
+
+
+@pytest.mark.parametrize("group", [8, 32])
+def test_group_sizes(soft, group):
+    circ, noise = C.workload("w42")
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 2000, 5, "fp32", group=group)
+    assert compare_records(circ, noise, 5, 0, rec, st, ref, "fp32") <= 2
+
+
+def test_overflow_status(soft):
+    c = C.Circuit(6, cap=8)
+    for q in range(6):
+        c.gate(C.H, q)
+        c.gate(C.T, q)
+    c.measure(0)
+    _, _, rec, st, tal, ref = run_both(soft, c, C.Noise(), 50, 0, "fp64")
+    assert list(st) == list(ref["status"]) == [2] * 50
+    assert tal["overflow"] == 50
+
+
+def test_noiseless_w42_all_kept(soft):
+    circ, _ = C.workload("w42")
+    S = soft
+    c = S.soft_compile_circuit(circ.array(), circ.n, C.Noise(), circ.cap)
+    r = S.soft_run_shots(c, 20000, 0, 0, precision="fp32")
+    t = S.soft_tally(r)
+    assert (t["shots"], t["discarded"], t["overflow"], t["kept"], t["logical_errors"]) == (20000, 0, 0, 20000, 0)
+
+
+def test_zero_and_one_shot(soft):
+    circ, noise = C.workload("tiny6")
+    S = soft
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    r = S.soft_run_shots(c, 0, 0, 0)
+    assert S.soft_tally(r)["shots"] == 0
+    c2, r2, rec, st, tal, ref = run_both(S, circ, noise, 1, 0, "fp64")
+    assert tal["shots"] == 1 and compare_records(circ, noise, 0, 0, rec, st, ref, "fp64") == 0
+
+
+def test_bench_config_sampled(soft):
+    """The bench's launch configuration (w42, FP32, 2^22 shots, default
+    tuning): tallies are consistent and sampled shots match the oracle."""
+    S = soft
+    circ, noise = C.workload("w42")
+    n = 1 << 22
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    r = S.soft_run_shots(c, n, 0, 0, precision="fp32", record_mode=S.REC_ALL)
+    rec, st = S.soft_get_records(r, n)
+    t = S.soft_tally(r)
+    assert t["shots"] == n and t["discarded"] + t["overflow"] + t["kept"] == n
+    assert np.sum(st == 1) == t["discarded"] and np.sum(st == 0) == t["kept"]
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(n, size=300, replace=False))
+    band = 0
+    for s in sample:
+        ref = oracle.run(circ, circ.n, noise, circ.cap, 0, int(s), 1)
+        if not (ref["status"][0] == st[s] and np.array_equal(ref["records"][0], rec[s])):
+            assert _band_ok(circ, noise, 0, int(s), BAND["fp32"])
+            band += 1
+    assert band <= 2
