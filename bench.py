@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--group", type=int, default=0)
     ap.add_argument("--first-cap", type=int, default=0)
+    ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer between steps (0 = none)")
     return ap.parse_args()
 
 
@@ -202,7 +203,7 @@ def main():
     n = args.shots
     base_shot = rank * (1 << 40)  # disjoint shot ranges per rank
     dev_props = torch.cuda.get_device_properties(local)
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def barrier():
         if world > 1:
@@ -219,7 +220,8 @@ def main():
         barrier()
         total_ms, launches, kernel_ms, tallies = 0.0, 0, [], []
         for k in range(steps):
-            flush.zero_()
+            if args.flush_mb:
+                flush.zero_()
             torch.cuda.synchronize()
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
