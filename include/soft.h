@@ -182,6 +182,30 @@ int soft_run_timing(soft_run *r, double *ms, uint32_t *n_launches);
 
 void soft_run_free(soft_run *r);
 
+/* Run entry point that allocates no device memory. The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc, such as
+ * code whose device memory is owned by another allocator (a framework's
+ * caching allocator or a fixed arena) and latency-critical loops that cannot
+ * take cudaMalloc's implicit device synchronisation.
+ *   Same shots, same results as soft_run_shots with default tuning, FP64 or
+ *   FP32 (`precision`), launched asynchronously on `stream`.
+ *   d_tally: caller device buffer of 5 uint64 counters (shots, discarded,
+ *   overflow, kept, logical errors); the call zeroes it, then accumulates.
+ *   d_status / d_records: optional caller device buffers of n_shots bytes /
+ *   n_shots * record_words words (NULL = not written).
+ *   Scratch (work counters and the rerun list) lives in one static device
+ *   array of about 4 MiB, sized for at most 1048576 shots per call; every GPU
+ *   that loads the library keeps it until the process exits. Larger n_shots
+ *   is rejected with SOFT_E_ARG. The first call on a device looks up that
+ *   array's device address (cudaGetSymbolAddress) with the device current,
+ *   so make the first call before any stream capture. All calls share the
+ *   array: calls that overlap on the GPU (different streams, no ordering)
+ *   race on it and give wrong results; calls ordered on one stream are safe.
+ * Errors: SOFT_E_ARG, SOFT_E_CUDA. No cudaMalloc, cudaFree or other
+ * allocating routine is called. */
+int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, int32_t precision,
+                           void *stream, unsigned long long *d_tally, uint8_t *d_status, uint64_t *d_records);
+
 const char *soft_last_error(void);
 
 #ifdef __cplusplus

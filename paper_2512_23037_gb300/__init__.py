@@ -63,7 +63,7 @@ class _Tally(ctypes.Structure):
 
 EXPORTED = ["soft_compile_circuit", "soft_circuit_info", "soft_circuit_tableau", "soft_circuit_free",
             "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing",
-            "soft_run_free", "soft_last_error"]
+            "soft_run_free", "soft_run_shots_noalloc", "soft_last_error"]
 
 
 def lib_path() -> str:
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True):
         L.soft_run_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
         L.soft_run_free.argtypes = [vp]
         L.soft_run_free.restype = None
+        L.soft_run_shots_noalloc.argtypes = [vp, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp]
         L.soft_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -235,3 +236,16 @@ def soft_run_timing(run: Run):
     nl = ctypes.c_uint32(0)
     _check(load().soft_run_timing(run.h, ctypes.byref(ms), ctypes.byref(nl)))
     return float(ms.value), int(nl.value)
+
+
+def soft_run_shots_noalloc(circ: Circuit, n_shots: int, first_shot: int, seed: int, precision, stream,
+                           d_tally: int, d_status: int = 0, d_records: int = 0) -> None:
+    """Allocation-free run (at most 2^20 shots per call) into caller device
+    buffers given as raw pointers; see include/soft.h."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(load().soft_run_shots_noalloc(circ.h, int(n_shots), int(first_shot), int(seed) & (2 ** 64 - 1),
+                                         FP32 if precision in ("fp32", FP32) else FP64,
+                                         ctypes.c_void_p(int(stream) if stream else 0),
+                                         ctypes.c_void_p(int(d_tally)), ctypes.c_void_p(int(d_status or 0)),
+                                         ctypes.c_void_p(int(d_records or 0))))

@@ -8,6 +8,7 @@
 
 #include "../../include/soft.h"
 #include "compile.h"
+#include "handles.h"
 #include "kernels.cuh"
 
 namespace {
@@ -22,21 +23,15 @@ int cuda_fail(cudaError_t e, const char *what) {
   return SOFT_E_CUDA;
 }
 
-constexpr double kTauFp64 = 1e-20;  // prune |v|^2 below this (FP64 coefficients)
-constexpr double kTauFp32 = 1e-10;  // FP32 coefficients: well above FP32 cancellation residue
 constexpr uint64_t kDefaultChunk = 1ull << 24;
-constexpr uint32_t kDefaultFirstCap = 64;
+using soft::kDefaultFirstCap;
+using soft::kTauFp32;
+using soft::kTauFp64;
 }  // namespace
 
-struct soft_circuit {
-  soft::HostProgram hp;
-  int device = 0;
-  soft::EvRec *d_ev = nullptr;
-  soft::CaseB *d_cb = nullptr;
-  soft::Site *d_sites = nullptr;
-  uint64_t *d_thr = nullptr;
-  uint64_t bytes = 0;
-};
+namespace soft {
+int set_error(int code, const char *msg) { return fail(code, msg); }
+}  // namespace soft
 
 struct soft_run {
   soft_circuit *c = nullptr;

@@ -1,0 +1,26 @@
+// handles.h -- library-internal definition of the circuit handle and the
+// numeric constants every run entry point shares.
+#pragma once
+#include <cstdint>
+
+#include "../../include/soft.h"
+#include "compile.h"
+#include "program.h"
+
+namespace soft {
+constexpr double kTauFp64 = 1e-20;  // prune |v|^2 below this (FP64 coefficients)
+constexpr double kTauFp32 = 1e-10;  // FP32 coefficients: well above FP32 cancellation residue
+constexpr uint32_t kDefaultFirstCap = 64;
+// Records `msg` for soft_last_error() on this thread and returns `code`.
+int set_error(int code, const char *msg);
+}  // namespace soft
+
+struct soft_circuit {
+  soft::HostProgram hp;
+  int device = 0;
+  soft::EvRec *d_ev = nullptr;
+  soft::CaseB *d_cb = nullptr;
+  soft::Site *d_sites = nullptr;
+  uint64_t *d_thr = nullptr;
+  uint64_t bytes = 0;
+};

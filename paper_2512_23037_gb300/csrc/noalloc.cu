@@ -1,0 +1,107 @@
+// noalloc.cu -- soft_run_shots_noalloc: the run entry point for callers that
+// must not allocate device memory.
+//
+// The regular soft_run_shots allocates its work counters and rerun list with
+// cudaMalloc on every call. This variant keeps that scratch in one
+// file-scope __device__ array instead, sized for kNoallocMaxShots shots per
+// call, so a call performs no device allocation at all: the caller passes
+// the compiled circuit and its own output buffers, and the library only
+// clears the counters (cudaMemsetAsync) and launches the same shot kernel.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/soft.h"
+#include "handles.h"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr uint64_t kNoallocMaxShots = 1ull << 20;
+constexpr size_t kCounterBytes = 256;  // work counter, rerun counter, rerun count (padded)
+constexpr size_t kScratchBytes = kCounterBytes + kNoallocMaxShots * sizeof(uint32_t);
+
+// The scratch itself. In host code `g_noalloc_scratch` is only a host-side
+// stand-in for the symbol, never a device address: the address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+int scratch_for_device(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kMaxDevices) return soft::set_error(SOFT_E_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return soft::set_error(SOFT_E_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
+    g_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(g_addr[dev]);
+  return SOFT_OK;
+}
+
+}  // namespace
+
+extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed,
+                                      int32_t precision, void *stream, unsigned long long *d_tally, uint8_t *d_status,
+                                      uint64_t *d_records) {
+  if (!c || !d_tally) return soft::set_error(SOFT_E_ARG, "circuit and d_tally must not be NULL");
+  if (precision != SOFT_FP64 && precision != SOFT_FP32) return soft::set_error(SOFT_E_ARG, "bad precision");
+  if (n_shots > kNoallocMaxShots)
+    return soft::set_error(SOFT_E_ARG, "n_shots exceeds the no-alloc limit of 1048576 shots per call");
+  const auto &hp = c->hp;
+  const int fp32 = precision == SOFT_FP32;
+  if (soft::group_smem_bytes(fp32, hp.W, hp.cap, hp.rw) > 227 * 1024)
+    return soft::set_error(SOFT_E_ARG, "coeff_cap too large for the on-chip coefficient map");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return soft::set_error(SOFT_E_CUDA, "cudaSetDevice failed");
+  unsigned char *scratch = nullptr;
+  int rc = scratch_for_device(c->device, &scratch);
+  if (rc != SOFT_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
+  uint32_t *rerun = reinterpret_cast<uint32_t *>(scratch + kCounterBytes);
+  if ((e = cudaMemsetAsync(d_tally, 0, 5 * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess)
+    return soft::set_error(SOFT_E_CUDA, "cudaMemsetAsync failed");
+  if (n_shots == 0) return SOFT_OK;
+  const uint32_t cap = hp.cap, cap1 = cap < soft::kDefaultFirstCap ? cap : soft::kDefaultFirstCap;
+  const bool two_pass = cap1 < cap;
+  soft::ShotParams p{};
+  p.ev = c->d_ev;
+  p.cb = c->d_cb;
+  p.sites = c->d_sites;
+  p.thr = c->d_thr;
+  p.n_events = (uint32_t)hp.ev.size();
+  p.n_sites = hp.n_sites;
+  p.rw = hp.rw;
+  p.tau = fp32 ? soft::kTauFp32 : soft::kTauFp64;
+  p.seed = seed;
+  p.first_shot = first_shot;
+  p.n_items = n_shots;
+  p.next_item = work;
+  p.tally = d_tally;
+  p.rerun = rerun;
+  p.n_rerun = work + 2;
+  p.status = d_status;
+  p.records = d_records;
+  p.out_limit = (d_status || d_records) ? n_shots : 0;
+  p.cap = cap1;
+  p.small_pass = two_pass ? 1 : 0;
+  if ((e = soft::launch_shots(p, fp32, hp.W, cap1 <= 64 ? 8u : 32u, 0, st, nullptr)) != cudaSuccess)
+    return soft::set_error(SOFT_E_CUDA, "shot kernel launch failed");
+  if (two_pass) {
+    soft::ShotParams q = p;
+    q.cap = cap;
+    q.small_pass = 0;
+    q.list = rerun;
+    q.n_items_dev = work + 2;
+    q.next_item = work + 1;
+    if ((e = soft::launch_shots(q, fp32, hp.W, 32u, 0, st, nullptr)) != cudaSuccess)
+      return soft::set_error(SOFT_E_CUDA, "rerun kernel launch failed");
+  }
+  return SOFT_OK;
+}

@@ -30,7 +30,7 @@ def test_every_declared_symbol_is_exported(S):
     lib = ctypes.CDLL(S.lib_path())
     for n in names:
         assert hasattr(lib, n), n
-    assert set(names) <= set(S.EXPORTED) | {n for n in names if n.endswith("_noalloc")}
+    assert set(names) <= set(S.EXPORTED)
 
 
 def _expect(S, code, circ, n, noise, cap=16):
