@@ -201,7 +201,8 @@ def main():
     circ, noise = C.workload("w42")
     stream = torch.cuda.current_stream()
     n = args.shots
-    base_shot = rank * (1 << 40)  # disjoint shot ranges per rank
+    from paper_2512_23037_gb300.sharding import shot_range
+    base_shot, _ = shot_range(rank, world, n)  # disjoint shot ranges per rank
     dev_props = torch.cuda.get_device_properties(local)
     flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
@@ -255,7 +256,8 @@ def main():
     for k in range(args.steps):
         t0 = time.perf_counter()
         c = S.soft_compile_circuit(ops_host, circ.n, noise, circ.cap)
-        r = S.soft_run_shots(c, n, base_shot + (1 << 38) + k * n, 0, precision="fp32", stream=stream)
+        r = S.soft_run_shots(c, n, base_shot + (1 << 38) + k * n, 0, precision="fp32", stream=stream,
+                             group_size=args.group, first_cap=args.first_cap)
         S.soft_tally(r)
         e2e_ms += 1000 * (time.perf_counter() - t0)
         h2d = c.info["program_bytes"]

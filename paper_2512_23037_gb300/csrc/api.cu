@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/soft.h"
 #include "compile.h"
@@ -71,15 +72,32 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
   }
   cudaGetDevice(&c->device);
   const auto &hp = c->hp;
-  size_t b_ev = hp.ev.size() * sizeof(soft::EvRec), b_cb = std::max<size_t>(1, hp.cb.size()) * sizeof(soft::CaseB),
+  // narrow the events to the one-word layout when n <= 64
+  std::vector<soft::Ev<1>> ev1;
+  const void *ev_src = hp.ev.data();
+  size_t b_ev = hp.ev.size() * sizeof(soft::Ev<2>);
+  if (hp.W == 1) {
+    ev1.resize(hp.ev.size());
+    for (size_t i = 0; i < hp.ev.size(); ++i) {
+      const auto &s = hp.ev[i];
+      ev1[i] = soft::Ev<1>{s.w0, s.site_begin, s.a, s.b, {s.dsd[0]}, {s.dss[0]}, {s.beta[0]}, {s.gamma[0]}};
+    }
+    ev_src = ev1.data();
+    b_ev = ev1.size() * sizeof(soft::Ev<1>);
+  }
+  size_t b_cf = std::max<size_t>(1, hp.coefs.size()) * sizeof(soft::Coef),
+         b_cb = std::max<size_t>(1, hp.cb.size()) * sizeof(soft::CaseB),
          b_st = std::max<size_t>(1, hp.sites.size()) * sizeof(soft::Site), b_thr = hp.thr.size() * sizeof(uint64_t);
   cudaError_t e;
-  if ((e = cudaMalloc(&c->d_ev, b_ev)) != cudaSuccess || (e = cudaMalloc(&c->d_cb, b_cb)) != cudaSuccess ||
-      (e = cudaMalloc(&c->d_sites, b_st)) != cudaSuccess || (e = cudaMalloc(&c->d_thr, b_thr)) != cudaSuccess) {
+  if ((e = cudaMalloc(&c->d_ev, b_ev)) != cudaSuccess || (e = cudaMalloc(&c->d_coef, b_cf)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_cb, b_cb)) != cudaSuccess || (e = cudaMalloc(&c->d_sites, b_st)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_thr, b_thr)) != cudaSuccess) {
     soft_circuit_free(c);
     return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed") : cuda_fail(e, "cudaMalloc");
   }
-  if ((e = cudaMemcpy(c->d_ev, hp.ev.data(), b_ev, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  if ((e = cudaMemcpy(c->d_ev, ev_src, b_ev, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!hp.coefs.empty() && (e = cudaMemcpy(c->d_coef, hp.coefs.data(), hp.coefs.size() * sizeof(soft::Coef),
+                                            cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (!hp.cb.empty() && (e = cudaMemcpy(c->d_cb, hp.cb.data(), hp.cb.size() * sizeof(soft::CaseB),
                                          cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (!hp.sites.empty() && (e = cudaMemcpy(c->d_sites, hp.sites.data(), hp.sites.size() * sizeof(soft::Site),
@@ -88,7 +106,7 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
     soft_circuit_free(c);
     return cuda_fail(e, "cudaMemcpy (program upload)");
   }
-  c->bytes = b_ev + b_cb + b_st + b_thr;
+  c->bytes = b_ev + b_cf + b_cb + b_st + b_thr;
   *out = c;
   return SOFT_OK;
 }
@@ -115,6 +133,7 @@ int soft_circuit_tableau(const soft_circuit *c, uint64_t *rows_x, uint64_t *rows
 void soft_circuit_free(soft_circuit *c) {
   if (!c) return;
   cudaFree(c->d_ev);
+  cudaFree(c->d_coef);
   cudaFree(c->d_cb);
   cudaFree(c->d_sites);
   cudaFree(c->d_thr);
@@ -153,7 +172,7 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
   const uint32_t cap = hp.cap;
   uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap) : std::min(kDefaultFirstCap, cap);
   const bool two_pass = cap1 < cap;
-  const uint32_t g1 = o.group_size ? o.group_size : (cap1 <= 64 ? 8u : 32u);
+  const uint32_t g1 = o.group_size ? o.group_size : 32u;
   const uint32_t g2 = 32;
   const size_t smem_limit = 227 * 1024;
   if (soft::group_smem_bytes(fp32, hp.W, cap, hp.rw) > smem_limit)
@@ -222,6 +241,7 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
     }
     soft::ShotParams p{};
     p.ev = c->d_ev;
+    p.coef = c->d_coef;
     p.cb = c->d_cb;
     p.sites = c->d_sites;
     p.thr = c->d_thr;

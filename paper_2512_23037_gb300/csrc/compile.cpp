@@ -280,26 +280,40 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
     return true;
   };
 
-  auto new_event = [&](uint32_t type) -> EvRec & {
-    EvRec e{};
-    e.type = type;
+  auto new_event = [&](uint32_t type, uint32_t flags, uint32_t e0, uint32_t lowbit) -> Ev<2> & {
+    Ev<2> e{};
+    e.w0 = ev_pack(type, flags, e0, lowbit);
     e.site_begin = (uint32_t)P.sites.size();
     e.dsd[0] = tb.pend_d[0];
     e.dsd[1] = tb.pend_d[1];
     e.dss[0] = tb.pend_s[0];
     e.dss[1] = tb.pend_s[1];
     tb.pend_d[0] = tb.pend_d[1] = tb.pend_s[0] = tb.pend_s[1] = 0;
-    e.r0 = e.r1 = -1;
+    e.a = e.b = kNoRec;
     P.ev.push_back(e);
     return P.ev.back();
   };
 
   auto pauli_event = [&](const Pz &Q, uint32_t flags, int32_t r0, int32_t r1) -> bool {
-    EvRec &e = new_event(EV_PAULI);
-    e.flags = flags;
-    e.r0 = r0;
-    e.r1 = r1;
-    return tb.decompose(Q, e.beta, e.gamma, &e.e0);
+    uint64_t beta[2], gamma[2];
+    uint32_t e0;
+    if (!tb.decompose(Q, beta, gamma, &e0)) return false;
+    Ev<2> &e = new_event(EV_PAULI, flags, e0, 0);
+    e.a = (uint32_t)r0;
+    e.b = (uint32_t)r1;
+    std::memcpy(e.beta, beta, sizeof beta);
+    std::memcpy(e.gamma, gamma, sizeof gamma);
+    return true;
+  };
+
+  auto coef_index = [&](double ar, double ai, double br, double bi) -> uint32_t {
+    for (size_t k = 0; k < P.coefs.size(); ++k) {
+      const Coef &c = P.coefs[k];
+      if (c.a_re == ar && c.a_im == ai && c.b_re == br && c.b_im == bi) return (uint32_t)k;
+    }
+    Coef c{ar, ai, br, bi, (float)ar, (float)ai, (float)br, (float)bi};
+    P.coefs.push_back(c);
+    return (uint32_t)(P.coefs.size() - 1);
   };
 
   for (size_t i = 0; i < n_ops; ++i) {
@@ -338,10 +352,6 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
       uint32_t e0;
       if (!tb.decompose(single(3, o.q0), beta, gamma, &e0)) goto internal;
       bool diag = (beta[0] | beta[1]) == 0;
-      EvRec &e = new_event(diag ? EV_ROT_DIAG : EV_ROT);
-      std::memcpy(e.beta, beta, sizeof beta);
-      std::memcpy(e.gamma, gamma, sizeof gamma);
-      e.e0 = e0;
       double ar, ai, br, bi;
       if (op == SOFT_RZ) {
         ar = std::cos(0.5 * o.angle);
@@ -356,12 +366,13 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
         br = 0.5 * (1.0 - c);
         bi = -0.5 * sn;
       }
-      e.a_re = ar;
-      e.a_im = ai;
-      e.b_re = br;
-      e.b_im = bi;
-      e.lowbit = 0;
-      if (!diag) e.lowbit = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
+      uint32_t lowbit = 0;
+      if (!diag) lowbit = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
+      uint32_t ci = coef_index(ar, ai, br, bi);
+      Ev<2> &e = new_event(diag ? EV_ROT_DIAG : EV_ROT, 0, e0, lowbit);
+      e.a = ci;
+      std::memcpy(e.beta, beta, sizeof beta);
+      std::memcpy(e.gamma, gamma, sizeof gamma);
     } else if (op == SOFT_M || op == SOFT_R || op == SOFT_MR) {
       uint64_t beta[2], gamma[2];
       uint32_t e0;
@@ -369,12 +380,10 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
       if (!tb.decompose(Zq, beta, gamma, &e0)) goto internal;
       bool recd = (op != SOFT_R);
       if ((beta[0] | beta[1]) == 0) {
-        EvRec &e = new_event(EV_MEAS_A);
+        Ev<2> &e = new_event(EV_MEAS_A, recd ? F_RECORD : 0, e0, 0);
         std::memcpy(e.gamma, gamma, sizeof gamma);
-        e.e0 = e0;
-        e.ord = ord;
-        e.rec = recd ? nrec : 0;
-        e.flags = recd ? F_RECORD : 0;
+        e.a = ord;
+        e.b = recd ? nrec : 0;
       } else {
         CaseB cb{};
         uint32_t p = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
@@ -417,11 +426,10 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
         tb.d[p] = old_sp;
         tb.s[p] = row_of(Zq);
         cb.rP = 0;
-        EvRec &e = new_event(EV_MEAS_B);
-        e.ord = ord;
-        e.rec = recd ? nrec : 0;
-        e.flags = recd ? F_RECORD : 0;
-        e.caseb = (uint32_t)P.cb.size();
+        Ev<2> &e = new_event(EV_MEAS_B, recd ? F_RECORD : 0, 0, 0);
+        e.a = ord;
+        e.b = recd ? nrec : 0;
+        e.beta[0] = P.cb.size();
         P.cb.push_back(cb);
       }
       ord++;
@@ -434,11 +442,11 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
         if (!pauli_event(single(code, o.q0), F_COND_REC, o.rec[0], o.rec[1])) goto internal;
       }
     } else if (op == SOFT_DETECTOR || op == SOFT_OBSERVABLE) {
-      EvRec &e = new_event(EV_PARITY);
-      e.flags = (op == SOFT_DETECTOR ? F_DETECTOR : F_OBSERVABLE) | ((o.flags & SOFT_FLAG_CHAIN) ? F_CHAIN : 0) |
-                ((o.flags & SOFT_FLAG_INVERT) ? F_INVERT : 0);
-      e.r0 = o.rec[0];
-      e.r1 = o.rec[1];
+      uint32_t fl = (op == SOFT_DETECTOR ? F_DETECTOR : F_OBSERVABLE) | ((o.flags & SOFT_FLAG_CHAIN) ? F_CHAIN : 0) |
+                    ((o.flags & SOFT_FLAG_INVERT) ? F_INVERT : 0);
+      Ev<2> &e = new_event(EV_PARITY, fl, 0, 0);
+      e.a = (uint32_t)o.rec[0];
+      e.b = (uint32_t)o.rec[1];
     }
 
     if (!noiseless) {
@@ -451,7 +459,7 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
       }
     }
   }
-  new_event(EV_END);
+  new_event(EV_END, 0, 0, 0);
   P.n_records = nrec;
   P.rw = nrec ? (nrec + 63) / 64 : 1;
   if (P.rw > 16) {

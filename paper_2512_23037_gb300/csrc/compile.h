@@ -13,7 +13,8 @@ struct HostProgram {
   uint32_t n = 0, W = 1;
   uint32_t n_records = 0, rw = 1, n_sites = 0, cap = 0;
   double pmax = 0.0;
-  std::vector<EvRec> ev;
+  std::vector<Ev<2>> ev;          // events in the two-word layout (narrowed at upload when W = 1)
+  std::vector<Coef> coefs;
   std::vector<CaseB> cb;
   std::vector<Site> sites;
   std::vector<uint64_t> thr;     // gap thresholds, one per site

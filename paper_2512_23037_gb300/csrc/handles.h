@@ -18,7 +18,8 @@ int set_error(int code, const char *msg);
 struct soft_circuit {
   soft::HostProgram hp;
   int device = 0;
-  soft::EvRec *d_ev = nullptr;
+  void *d_ev = nullptr;  // Ev<W> array, W = hp.W
+  soft::Coef *d_coef = nullptr;
   soft::CaseB *d_cb = nullptr;
   soft::Site *d_sites = nullptr;
   uint64_t *d_thr = nullptr;

@@ -149,10 +149,18 @@ __device__ __forceinline__ double snap01(double p) {
   return p;
 }
 
+__host__ __device__ inline uint32_t pow2_at_least(uint32_t v) {
+  uint32_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+// Hash slots for a group of capacity `cap`: a power of two >= 4 cap (load <= 1/4).
+__host__ __device__ inline uint32_t hash_slots(uint32_t cap) { return pow2_at_least(4u * cap < 16u ? 16u : 4u * cap); }
+
 template <typename R, int W>
 __host__ __device__ inline size_t group_bytes(uint32_t cap, uint32_t rw) {
   size_t slots = 2 * (size_t)cap;
-  size_t b = slots * sizeof(Cx<R>) + (size_t)W * slots * 8 + 4 * (size_t)cap * 4 + (size_t)rw * 8;
+  size_t b = slots * sizeof(Cx<R>) + (size_t)W * slots * 8 + 4 * (size_t)hash_slots(cap) + (size_t)rw * 8;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -165,7 +173,7 @@ struct Shot {
   uint64_t *keys;
   uint32_t *ht;
   uint64_t *rec;
-  uint32_t slots, hsmask, cap, lane;
+  uint32_t slots, hsmask, hsmax, cap, lane;
   uint64_t shot;
   uint32_t nnz;
   uint64_t sd[W], ss[W];
@@ -175,12 +183,19 @@ struct Shot {
   __device__ Shot(const Tile &tile, const ShotParams &p, unsigned char *base) : t(tile), P(p) {
     cap = P.cap;
     slots = 2 * cap;
-    hsmask = 4 * cap - 1;
+    hsmax = P.hs_max;
+    hsmask = 15u;
     lane = t.thread_rank();
     vals = reinterpret_cast<Cx<R> *>(base);
     keys = reinterpret_cast<uint64_t *>(base + slots * sizeof(Cx<R>));
     ht = reinterpret_cast<uint32_t *>(base + slots * sizeof(Cx<R>) + (size_t)W * slots * 8);
-    rec = reinterpret_cast<uint64_t *>(base + slots * sizeof(Cx<R>) + (size_t)W * slots * 8 + 16 * (size_t)cap);
+    rec = reinterpret_cast<uint64_t *>(base + slots * sizeof(Cx<R>) + (size_t)W * slots * 8 + 4 * (size_t)hsmax);
+  }
+  // hash size for n live entries: power of two >= 4 n, at least 16, at most hsmax
+  __device__ __forceinline__ uint32_t hs_for(uint32_t n) const {
+    uint32_t want = 4u * n < 16u ? 16u : 4u * n;
+    uint32_t p = 1u << (32 - __clz(want - 1u));
+    return p < hsmax ? p : hsmax;
   }
 
   __device__ __forceinline__ Key<W> key(uint32_t e) const {
@@ -211,7 +226,9 @@ struct Shot {
     }
   }
   __device__ void rebuild() {
-    for (uint32_t i = lane; i <= hsmask; i += G) ht[i] = 0u;
+    hsmask = hs_for(nnz) - 1u;
+    uint4 *h4 = reinterpret_cast<uint4 *>(ht);
+    for (uint32_t i = lane; i <= (hsmask >> 2); i += G) h4[i] = make_uint4(0u, 0u, 0u, 0u);
     t.sync();
     for (uint32_t e = lane; e < nnz; e += G) insert(e, key(e));
     t.sync();
@@ -339,18 +356,28 @@ struct Shot {
   }
 
   // ---- a I + b Z_q, beta != 0
-  __device__ void rot(const EvRec *E) {
-    uint64_t beta[W], gamma[W];
+  __device__ __forceinline__ void coef(uint32_t ci, Cx<R> &a, Cx<R> &b) const {
+    const Coef *C = P.coef + ci;
+    if (sizeof(R) == 4) {
+      float4 f = __ldg(reinterpret_cast<const float4 *>(&C->fa_re));
+      a = Cx<R>{(R)f.x, (R)f.y};
+      b = Cx<R>{(R)f.z, (R)f.w};
+    } else {
+      double2 d0 = __ldg(reinterpret_cast<const double2 *>(&C->a_re));
+      double2 d1 = __ldg(reinterpret_cast<const double2 *>(&C->b_re));
+      a = Cx<R>{(R)d0.x, (R)d0.y};
+      b = Cx<R>{(R)d1.x, (R)d1.y};
+    }
+  }
+
+  __device__ void rot(uint32_t w0, uint32_t ci, const uint64_t *beta, const uint64_t *gamma) {
     uint32_t pe = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      beta[w] = __ldg(&E->beta[w]);
-      gamma[w] = __ldg(&E->gamma[w]);
-      pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
-    }
-    const uint32_t e = (__ldg(&E->e0) + 2u * pe) & 3u;
-    const uint32_t lowbit = __ldg(&E->lowbit);
-    const Cx<R> a{(R)__ldg(&E->a_re), (R)__ldg(&E->a_im)}, b{(R)__ldg(&E->b_re), (R)__ldg(&E->b_im)};
+    for (int w = 0; w < W; ++w) pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
+    const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
+    const uint32_t lowbit = ev_lowbit(w0);
+    Cx<R> a, b;
+    coef(ci, a, b);
     const R tau = (R)P.tau;
     uint32_t nA = 0;
     bool prune = false;
@@ -398,7 +425,7 @@ struct Shot {
       fail_capacity();
       return;
     }
-    if (pruned) {
+    if (pruned || hs_for(nnz) - 1u > hsmask) {
       rebuild();
     } else if (nA) {
       for (uint32_t i = n0 + lane; i < nnz; i += G) insert(i, key(i));
@@ -407,16 +434,13 @@ struct Shot {
   }
 
   // ---- a I + b Z_q, beta == 0: v_a *= a + b xi_a
-  __device__ void rot_diag(const EvRec *E) {
-    uint64_t gamma[W];
+  __device__ void rot_diag(uint32_t w0, uint32_t ci, const uint64_t *gamma) {
     uint32_t pe = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      gamma[w] = __ldg(&E->gamma[w]);
-      pe += __popcll(ss[w] & gamma[w]);
-    }
-    const uint32_t e = (__ldg(&E->e0) + 2u * pe) & 3u;
-    const Cx<R> a{(R)__ldg(&E->a_re), (R)__ldg(&E->a_im)}, b{(R)__ldg(&E->b_re), (R)__ldg(&E->b_im)};
+    for (int w = 0; w < W; ++w) pe += __popcll(ss[w] & gamma[w]);
+    const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
+    Cx<R> a, b;
+    coef(ci, a, b);
     const R tau = (R)P.tau;
     bool prune = false;
     for (uint32_t i = lane; i < nnz; i += G) {
@@ -434,40 +458,35 @@ struct Shot {
   }
 
   // ---- Z measurement, beta = 0: lambda_a = c (-1)^{gamma.a}
-  __device__ int meas_a(const EvRec *E) {
-    uint64_t gamma[W];
+  __device__ int meas_a(uint32_t w0, uint32_t ord, const uint64_t *gamma) {
     uint32_t pe = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      gamma[w] = __ldg(&E->gamma[w]);
-      pe += __popcll(ss[w] & gamma[w]);
-    }
-    const uint32_t e = (__ldg(&E->e0) + 2u * pe) & 3u;
+    for (int w = 0; w < W; ++w) pe += __popcll(ss[w] & gamma[w]);
+    const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
     if (e & 1u) {
       status = ST_ERR;
       return 1;
     }
     const uint32_t sgn = e >> 1;
-    double sp = 0.0, sm = 0.0;
+    // integer test first: the outcome is decided when every lambda_a agrees
     bool h0 = false, h1 = false;
     for (uint32_t i = lane; i < nnz; i += G) {
-      uint32_t neg = kpar(key(i), gamma) ^ sgn;
-      double a2 = norm2d(vals[i]);
-      if (neg) {
-        sm += a2;
-        h1 = true;
-      } else {
-        sp += a2;
-        h0 = true;
-      }
+      if (kpar(key(i), gamma) ^ sgn) h1 = true;
+      else h0 = true;
     }
     h0 = t.any(h0);
     h1 = t.any(h1);
-    if (!(h0 && h1)) return h1 ? -1 : 1;  // decided by the integer test
+    if (!(h0 && h1)) return h1 ? -1 : 1;
+    double sp = 0.0, sm = 0.0;
+    for (uint32_t i = lane; i < nnz; i += G) {
+      double a2 = norm2d(vals[i]);
+      if (kpar(key(i), gamma) ^ sgn) sm += a2;
+      else sp += a2;
+    }
     sp = tile_sum(sp);
     sm = tile_sum(sm);
     const double pp = snap01(sp / (sp + sm));
-    const int m = uniform(__ldg(&E->ord)) < pp ? 1 : -1;
+    const int m = uniform(ord) < pp ? 1 : -1;
     const R sc = (R)(1.0 / sqrt(m == 1 ? sp : sm));
     const uint32_t want = (m == 1) ? 0u : 1u;
     const R tau = (R)P.tau;
@@ -482,8 +501,8 @@ struct Shot {
   }
 
   // ---- Z measurement, beta != 0 (case B)
-  __device__ int meas_b(const EvRec *E) {
-    const CaseB *B = P.cb + __ldg(&E->caseb);
+  __device__ int meas_b(uint32_t ord, uint32_t cbi) {
+    const CaseB *B = P.cb + cbi;
     const uint32_t p = __ldg(&B->p);
     uint64_t J[W], g2[W], ep[W];
 #pragma unroll
@@ -527,7 +546,7 @@ struct Shot {
     sp = tile_sum(sp);
     sm = tile_sum(sm);
     const double pp = snap01(sp / (sp + sm));
-    const int m = uniform(__ldg(&E->ord)) < pp ? 1 : -1;
+    const int m = uniform(ord) < pp ? 1 : -1;
     const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
     // stage the paired values in slots [cap, cap + nnz)
     for (uint32_t i = lane; i < nnz; i += G) {
@@ -589,49 +608,55 @@ struct Shot {
     cur = 0;
     kblk = 0;
     draw_next();
+    const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(P.ev);
     for (uint32_t ev = 0; ev < P.n_events && status == ST_RUN; ++ev) {
-      const EvRec *E = P.ev + ev;
-      const uint32_t sb = __ldg(&E->site_begin);
-      while (nxt < sb && status == ST_RUN) {
+      const Ev<W> *E = evs + ev;
+      const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
+      // dsd, dss, beta, gamma: 4 W words after the header
+      uint64_t body[4 * W];
+      const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(&E->dsd[0]);
+#pragma unroll
+      for (int k = 0; k < 2 * W; ++k) {
+        ulonglong2 v = __ldg(bp + k);
+        body[2 * k] = v.x;
+        body[2 * k + 1] = v.y;
+      }
+      const uint64_t *dsd = body, *dss = body + W, *beta = body + 2 * W, *gamma = body + 3 * W;
+      while (nxt < hdr.y && status == ST_RUN) {
         apply_error(nxt);
         draw_next();
       }
       if (status != ST_RUN) break;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
-        sd[w] ^= __ldg(&E->dsd[w]);
-        ss[w] ^= __ldg(&E->dss[w]);
+        sd[w] ^= dsd[w];
+        ss[w] ^= dss[w];
       }
-      const uint32_t type = __ldg(&E->type), flags = __ldg(&E->flags);
+      const uint32_t w0 = hdr.x, type = ev_type(w0), flags = ev_flags(w0);
       switch (type) {
-        case EV_ROT: rot(E); break;
-        case EV_ROT_DIAG: rot_diag(E); break;
+        case EV_ROT: rot(w0, hdr.z, beta, gamma); break;
+        case EV_ROT_DIAG: rot_diag(w0, hdr.z, gamma); break;
         case EV_MEAS_A:
         case EV_MEAS_B: {
-          int m = (type == EV_MEAS_A) ? meas_a(E) : meas_b(E);
+          int m = (type == EV_MEAS_A) ? meas_a(w0, hdr.z, gamma) : meas_b(hdr.z, (uint32_t)beta[0]);
           lastm = m;
-          if (flags & F_RECORD) set_record(__ldg(&E->rec), m);
+          if (flags & F_RECORD) set_record(hdr.w, m);
           break;
         }
         case EV_PAULI: {
           uint32_t cond = 0;
           if (flags & F_COND_LAST) cond = (lastm == -1);
-          else cond = rec_bit(__ldg(&E->r0)) ^ rec_bit(__ldg(&E->r1));
+          else cond = rec_bit((int32_t)hdr.z) ^ rec_bit((int32_t)hdr.w);
           if (cond) {
-            uint64_t beta[W], gamma[W];
             uint32_t pe = 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-              beta[w] = __ldg(&E->beta[w]);
-              gamma[w] = __ldg(&E->gamma[w]);
-              pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
-            }
-            apply_pauli(beta, gamma, (__ldg(&E->e0) + 2u * pe) & 3u);
+            for (int w = 0; w < W; ++w) pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
+            apply_pauli(beta, gamma, (ev_e0(w0) + 2u * pe) & 3u);
           }
           break;
         }
         case EV_PARITY: {
-          int par = chain ^ (int)rec_bit(__ldg(&E->r0)) ^ (int)rec_bit(__ldg(&E->r1)) ^
+          int par = chain ^ (int)rec_bit((int32_t)hdr.z) ^ (int)rec_bit((int32_t)hdr.w) ^
                     ((flags & F_INVERT) ? 1 : 0);
           if (flags & F_CHAIN) {
             chain = par;
@@ -720,7 +745,9 @@ __global__ void __launch_bounds__(kBlock) shot_kernel(const __grid_constant__ Sh
 }
 
 template <typename R, int W, int G>
-cudaError_t launch_t(const ShotParams &p, int blocks_per_sm, cudaStream_t stream, int *grid_out) {
+cudaError_t launch_t(const ShotParams &p0, int blocks_per_sm, cudaStream_t stream, int *grid_out) {
+  ShotParams p = p0;
+  p.hs_max = hash_slots(p.cap);
   auto kern = shot_kernel<R, W, G>;
   const size_t gb = group_bytes<R, W>(p.cap, p.rw);
   const size_t limit = 227 * 1024;

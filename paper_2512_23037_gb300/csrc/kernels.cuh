@@ -10,11 +10,13 @@ namespace soft {
 
 struct ShotParams {
   // compiled program (device)
-  const EvRec *ev;
+  const void *ev;  // Ev<W>
+  const Coef *coef;
   const CaseB *cb;
   const Site *sites;
   const uint64_t *thr;
   uint32_t n_events, n_sites, rw, cap;
+  uint32_t hs_max;  // hash slots per group: power of two >= 4 * cap
   double tau;
   // work
   uint64_t seed, first_shot, n_items;  // shots first_shot + [0, n_items) or the list below

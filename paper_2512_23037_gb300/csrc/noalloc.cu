@@ -72,6 +72,7 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
   const bool two_pass = cap1 < cap;
   soft::ShotParams p{};
   p.ev = c->d_ev;
+  p.coef = c->d_coef;
   p.cb = c->d_cb;
   p.sites = c->d_sites;
   p.thr = c->d_thr;
@@ -91,7 +92,7 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
   p.out_limit = (d_status || d_records) ? n_shots : 0;
   p.cap = cap1;
   p.small_pass = two_pass ? 1 : 0;
-  if ((e = soft::launch_shots(p, fp32, hp.W, cap1 <= 64 ? 8u : 32u, 0, st, nullptr)) != cudaSuccess)
+  if ((e = soft::launch_shots(p, fp32, hp.W, 32u, 0, st, nullptr)) != cudaSuccess)
     return soft::set_error(SOFT_E_CUDA, "shot kernel launch failed");
   if (two_pass) {
     soft::ShotParams q = p;

@@ -14,6 +14,12 @@
 #pragma once
 #include <cstdint>
 
+#ifdef __CUDACC__
+#define SOFT_HD __host__ __device__
+#else
+#define SOFT_HD
+#endif
+
 namespace soft {
 
 enum EvType : uint32_t {
@@ -33,21 +39,39 @@ enum : uint32_t {
   F_CHAIN = 16,      // PARITY: carry into the next parity op
   F_INVERT = 32,     // PARITY
   F_COND_LAST = 64,  // PAULI: apply if the last measurement gave -1
-  F_COND_REC = 128   // PAULI: apply if parity of records r0, r1 is 1
+  F_COND_REC = 128   // PAULI: apply if parity of records a, b is 1
 };
 
-struct alignas(16) EvRec {
-  uint32_t type, flags, site_begin, e0;  // site_begin: sites numbered before this event
-  uint32_t ord, rec;                      // MEAS: RNG ordinal, record index
-  int32_t r0, r1;                         // record references
-  uint64_t dsd[2], dss[2];                // sign XOR masks applied before the event
-  uint64_t beta[2], gamma[2];
-  double a_re, a_im, b_re, b_im;          // ROT: a, b
-  uint32_t lowbit, caseb, pad0, pad1;     // ROT: lowest set bit of beta; MEAS_B: CaseB index
+// Header word 0: type (bits 0-3) | flags (4-11) | e0 (12-13) | lowbit (16-23).
+SOFT_HD inline uint32_t ev_type(uint32_t w0) { return w0 & 15u; }
+SOFT_HD inline uint32_t ev_flags(uint32_t w0) { return (w0 >> 4) & 255u; }
+SOFT_HD inline uint32_t ev_e0(uint32_t w0) { return (w0 >> 12) & 3u; }
+SOFT_HD inline uint32_t ev_lowbit(uint32_t w0) { return (w0 >> 16) & 255u; }
+inline uint32_t ev_pack(uint32_t type, uint32_t flags, uint32_t e0, uint32_t lowbit) {
+  return (type & 15u) | ((flags & 255u) << 4) | ((e0 & 3u) << 12) | ((lowbit & 255u) << 16);
+}
+
+// One event; W = 64-bit words per n-bit vector (1 for n <= 64, else 2).
+//   ROT/ROT_DIAG: a = coefficient index, beta/gamma of Z_q
+//   MEAS_A:       a = RNG ordinal, b = record index, gamma of Z_q
+//   MEAS_B:       a = RNG ordinal, b = record index, beta[0] = CaseB index
+//   PAULI:        a, b = record refs (F_COND_REC), beta/gamma of the Pauli
+//   PARITY:       a, b = record refs (0xFFFFFFFF = none)
+template <int W>
+struct alignas(16) Ev {
+  uint32_t w0, site_begin, a, b;
+  uint64_t dsd[W], dss[W];    // sign XOR masks applied before the event
+  uint64_t beta[W], gamma[W];
+};
+
+// a I + b Z_q coefficients, FP64 and the FP32 copies the FP32 kernel uses.
+struct alignas(16) Coef {
+  double a_re, a_im, b_re, b_im;
+  float fa_re, fa_im, fb_re, fb_im;
 };
 
 // Constants of a case-B measurement of P (pivot p, J = other rows whose
-// stabilizer anticommutes with P). See EV_MEAS_B in kernels.cu.
+// stabilizer anticommutes with P). See meas_b in kernels.cu.
 struct alignas(16) CaseB {
   uint64_t J[2];       // rows j with s_j <- s_j s_p
   uint64_t Hs[2];      // sign bit of s_j s_p at zero signs
@@ -64,5 +88,7 @@ struct alignas(16) Site {
   uint64_t bx[2][2], gx[2][2], bz[2][2], gz[2][2];
   uint32_t two, thin, always, c0;
 };
+
+constexpr uint32_t kNoRec = 0xFFFFFFFFu;
 
 }  // namespace soft
