@@ -12,6 +12,9 @@ LIB = os.path.join(OUT, "libsoft.so")
 SOURCES = ["compile.cpp", "kernels.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+for _v in ("SOFT_MIN_BLOCKS_F32", "SOFT_MIN_BLOCKS_F64"):  # register-budget experiments
+    if os.environ.get(_v):
+        FLAGS += [f"-D{_v}={int(os.environ[_v])}"]
 
 
 def _nvcc():

@@ -179,6 +179,11 @@ struct Shot {
   uint64_t sd[W], ss[W];
   uint32_t nxt, cur, kblk, w2;
   int status, chain, logical, lastm;
+  // register mode (G = 32 only): while |v| <= 32, lane i < nnz holds entry i
+  static constexpr bool kRegCapable = (G == 32);
+  bool reg;
+  Key<W> rk;
+  Cx<R> rv;
 
   __device__ Shot(const Tile &tile, const ShotParams &p, unsigned char *base) : t(tile), P(p) {
     cap = P.cap;
@@ -307,6 +312,10 @@ struct Shot {
 
   // v'_{a^beta} = i^{e + 2 gamma.a} v_a
   __device__ void apply_pauli(const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+    if (kRegCapable && reg) {
+      reg_pauli(beta, gamma, e);
+      return;
+    }
     bool moves = false;
 #pragma unroll
     for (int w = 0; w < W; ++w) moves = moves || beta[w];
@@ -350,6 +359,176 @@ struct Shot {
 
   __device__ void fail_capacity() { status = P.small_pass ? ST_RERUN : ST_OVF; }
 
+  // ---------------------------------------------------------------- register mode
+  __device__ __forceinline__ uint32_t vmask() const { return nnz >= 32u ? 0xFFFFFFFFu : ((1u << nnz) - 1u); }
+  __device__ __forceinline__ uint32_t match_key(const Key<W> &k) const {
+    uint32_t m = __match_any_sync(0xFFFFFFFFu, (unsigned long long)k.w[0]);
+    if (W == 2) m &= __match_any_sync(0xFFFFFFFFu, (unsigned long long)k.w[W - 1]);
+    return m;
+  }
+  __device__ __forceinline__ Cx<R> shfl_c(Cx<R> v, uint32_t src) const {
+    return Cx<R>{t.shfl(v.x, src), t.shfl(v.y, src)};
+  }
+  // registers -> slots [0, nnz) (used before the shared-memory path takes over)
+  __device__ void reg_spill() {
+    if (lane < nnz) {
+      set_key(lane, rk);
+      vals[lane] = rv;
+    }
+    t.sync();
+    reg = false;
+  }
+  // slots [0, nnz) -> registers (nnz <= 32)
+  __device__ void reg_load() {
+    if (lane < nnz) {
+      rk = key(lane);
+      rv = vals[lane];
+    }
+    t.sync();
+    reg = true;
+  }
+  // keep the entries whose lane has `keep` set, in lane order (staged through shared memory)
+  __device__ void reg_compact(bool keep) {
+    const uint32_t b = t.ballot(keep);
+    if (b == vmask()) return;
+    if (keep) {
+      const uint32_t d = lanes_below(b);
+      set_key(d, rk);
+      vals[d] = rv;
+    }
+    t.sync();
+    nnz = __popc(b);
+    if (lane < nnz) {
+      rk = key(lane);
+      rv = vals[lane];
+    }
+    t.sync();
+  }
+
+  __device__ void reg_pauli(const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+    if (lane < nnz) {
+      rv = ipow(rv, e + 2u * kpar(rk, gamma));
+      rk = kxor(rk, beta);
+    }
+  }
+
+  __device__ void reg_rot(uint32_t e, uint32_t lowbit, Cx<R> a, Cx<R> b, const uint64_t *beta,
+                          const uint64_t *gamma) {
+    const R tau = (R)P.tau;
+    const bool valid = lane < nnz;
+    const Key<W> pk = kxor(rk, beta);
+    const Key<W> canon = kbit(rk, lowbit) ? pk : rk;  // the pair's member with bit lowbit clear
+    const uint32_t partner = match_key(canon) & vmask() & ~(1u << lane);
+    const uint32_t pl = partner ? (uint32_t)(__ffs(partner) - 1) : lane;
+    const Cx<R> vj = shfl_c(rv, pl);
+    const bool has = valid && partner != 0u;
+    const bool app = valid && !has;
+    Cx<R> nv{0, 0}, av{0, 0};
+    if (valid) {
+      nv = cmul(a, rv);
+      if (has) nv = cadd(nv, cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
+      else av = cmul(b, ipow(rv, e + 2u * kpar(rk, gamma)));
+    }
+    const uint32_t ab = t.ballot(app);
+    const uint32_t nA = __popc(ab);
+    const bool small = (valid && norm2(nv) < tau) || (app && norm2(av) < tau);
+    const bool prune = t.any(small);
+    if (nnz + nA <= 32u) {
+      if (nA) {
+        if (app) {
+          const uint32_t d = lanes_below(ab);
+          set_key(d, pk);
+          vals[d] = av;
+        }
+        t.sync();
+        if (valid) rv = nv;
+        else if (lane < nnz + nA) {
+          rk = key(lane - nnz);
+          rv = vals[lane - nnz];
+        }
+        t.sync();
+        nnz += nA;
+      } else if (valid) {
+        rv = nv;
+      }
+      if (prune) reg_compact(lane < nnz && norm2(rv) >= tau);
+      if (nnz > cap) fail_capacity();
+      return;
+    }
+    // more than 32 entries: continue in shared memory with the hash index
+    if (valid) {
+      set_key(lane, rk);
+      vals[lane] = nv;
+    }
+    if (app) {
+      const uint32_t d = nnz + lanes_below(ab);
+      set_key(d, pk);
+      vals[d] = av;
+    }
+    t.sync();
+    reg = false;
+    nnz += nA;
+    if (prune) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
+    if (nnz > cap) {
+      fail_capacity();
+      return;
+    }
+    rebuild();
+  }
+
+  __device__ void reg_rot_diag(uint32_t e, Cx<R> a, Cx<R> b, const uint64_t *gamma) {
+    const R tau = (R)P.tau;
+    const bool valid = lane < nnz;
+    if (valid) rv = cadd(cmul(a, rv), cmul(b, ipow(rv, e + 2u * kpar(rk, gamma))));
+    if (t.any(valid && norm2(rv) < tau)) reg_compact(valid && norm2(rv) >= tau);
+  }
+
+  __device__ int reg_meas_a(uint32_t sgn, uint32_t ord, const uint64_t *gamma) {
+    const bool valid = lane < nnz;
+    const bool neg = valid && (kpar(rk, gamma) ^ sgn);
+    const bool h1 = t.any(neg), h0 = t.any(valid && !neg);
+    if (!(h0 && h1)) return h1 ? -1 : 1;
+    const double a2 = valid ? norm2d(rv) : 0.0;
+    const double sp = tile_sum(neg ? 0.0 : a2), sm = tile_sum(neg ? a2 : 0.0);
+    const double pp = snap01(sp / (sp + sm));
+    const int m = uniform(ord) < pp ? 1 : -1;
+    const R sc = (R)(1.0 / sqrt(m == 1 ? sp : sm));
+    bool keep = valid && (neg == (m == -1));
+    if (keep) rv = cscale(rv, sc);
+    reg_compact(keep && norm2(rv) >= (R)P.tau);
+    return m;
+  }
+
+  __device__ int reg_meas_b(uint32_t p, const uint64_t *J, const uint64_t *g2, const uint64_t *ep, uint32_t e2,
+                            uint32_t ord) {
+    const bool valid = lane < nnz;
+    if (valid && kbit(rk, p)) rk = kxor(rk, J);  // relabel a_j ^= a_p
+    const uint32_t hi = kbit(rk, p);
+    const Key<W> a0 = hi ? kxor(rk, ep) : rk;
+    const uint32_t partner = match_key(a0) & vmask() & ~(1u << lane);
+    const uint32_t pl = partner ? (uint32_t)(__ffs(partner) - 1) : lane;
+    const Cx<R> vj = shfl_c(rv, pl);
+    const bool owner = valid && (!hi || partner == 0u);
+    Cx<R> v0{0, 0}, v1{0, 0};
+    if (hi) v1 = rv;
+    else {
+      v0 = rv;
+      if (partner) v1 = vj;
+    }
+    const Cx<R> x1 = ipow(v1, e2 + 2u * kpar(kxor(a0, ep), g2));
+    const double sp = tile_sum(owner ? 0.5 * norm2d(cadd(v0, x1)) : 0.0);
+    const double sm = tile_sum(owner ? 0.5 * norm2d(csub(v0, x1)) : 0.0);
+    const double pp = snap01(sp / (sp + sm));
+    const int m = uniform(ord) < pp ? 1 : -1;
+    const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
+    if (owner) {
+      rv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
+      rk = a0;
+    }
+    reg_compact(owner && norm2(rv) >= (R)P.tau);
+    return m;
+  }
+
   __device__ void set_record(uint32_t r, int m) {
     if (lane == 0 && m < 0) rec[r >> 6] |= 1ull << (r & 63);
     t.sync();
@@ -378,6 +557,10 @@ struct Shot {
     const uint32_t lowbit = ev_lowbit(w0);
     Cx<R> a, b;
     coef(ci, a, b);
+    if (kRegCapable && reg) {
+      reg_rot(e, lowbit, a, b, beta, gamma);
+      return;
+    }
     const R tau = (R)P.tau;
     uint32_t nA = 0;
     bool prune = false;
@@ -441,6 +624,10 @@ struct Shot {
     const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
     Cx<R> a, b;
     coef(ci, a, b);
+    if (kRegCapable && reg) {
+      reg_rot_diag(e, a, b, gamma);
+      return;
+    }
     const R tau = (R)P.tau;
     bool prune = false;
     for (uint32_t i = lane; i < nnz; i += G) {
@@ -468,6 +655,7 @@ struct Shot {
       return 1;
     }
     const uint32_t sgn = e >> 1;
+    if (kRegCapable && reg) return reg_meas_a(sgn, ord, gamma);
     // integer test first: the outcome is decided when every lambda_a agrees
     bool h0 = false, h1 = false;
     for (uint32_t i = lane; i < nnz; i += G) {
@@ -519,6 +707,23 @@ struct Shot {
     if (sdJ ^ __ldg(&B->hdp)) wflip<W>(sd, p);
     // P = i^e2 d_p s_gamma2 in the new tableau
     const uint32_t e2 = (__ldg(&B->e0b) + 2u * (wbit<W>(sd, p) + wpar<W>(ss, g2))) & 3u;
+    int m;
+    if (kRegCapable && reg) {
+      m = reg_meas_b(p, J, g2, ep, e2, ord);
+    } else {
+      m = smem_meas_b(p, J, g2, ep, e2, ord);
+    }
+    // replacement: d_j <- d_j s_p (j in G), d_p <- old s_p, s_p <- m P
+#pragma unroll
+    for (int w = 0; w < W; ++w) sd[w] ^= (ssp ? __ldg(&B->G[w]) : 0ull) ^ __ldg(&B->Hd[w]);
+    if (wbit<W>(sd, p) != ssp) wflip<W>(sd, p);
+    const uint32_t newsp = (m == -1 ? 1u : 0u) ^ __ldg(&B->rP);
+    if (wbit<W>(ss, p) != newsp) wflip<W>(ss, p);
+    return m;
+  }
+
+  __device__ int smem_meas_b(uint32_t p, const uint64_t *J, const uint64_t *g2, const uint64_t *ep, uint32_t e2,
+                             uint32_t ord) {
     // relabel keys: a_j ^= a_p for j in J
     for (uint32_t i = lane; i < nnz; i += G) {
       Key<W> k = key(i);
@@ -573,12 +778,6 @@ struct Shot {
     const R tau = (R)P.tau;
     nnz = compact(cap, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
     rebuild();
-    // replacement: d_j <- d_j s_p (j in G), d_p <- old s_p, s_p <- m P
-#pragma unroll
-    for (int w = 0; w < W; ++w) sd[w] ^= (ssp ? __ldg(&B->G[w]) : 0ull) ^ __ldg(&B->Hd[w]);
-    if (wbit<W>(sd, p) != ssp) wflip<W>(sd, p);
-    const uint32_t newsp = (m == -1 ? 1u : 0u) ^ __ldg(&B->rP);
-    if (wbit<W>(ss, p) != newsp) wflip<W>(ss, p);
     return m;
   }
 
@@ -595,16 +794,24 @@ struct Shot {
 #pragma unroll
     for (int w = 0; w < W; ++w) sd[w] = ss[w] = 0ull;
     nnz = 1;
-    if (lane == 0) {
-      Key<W> z;
+    Key<W> z;
 #pragma unroll
-      for (int w = 0; w < W; ++w) z.w[w] = 0ull;
-      set_key(0, z);
-      vals[0] = Cx<R>{(R)1, (R)0};
-    }
+    for (int w = 0; w < W; ++w) z.w[w] = 0ull;
     for (uint32_t w = lane; w < P.rw; w += G) rec[w] = 0ull;
-    t.sync();
-    rebuild();
+    if (kRegCapable) {
+      reg = true;
+      rk = z;
+      rv = Cx<R>{(R)(lane == 0 ? 1 : 0), (R)0};
+      t.sync();
+    } else {
+      reg = false;
+      if (lane == 0) {
+        set_key(0, z);
+        vals[0] = Cx<R>{(R)1, (R)0};
+      }
+      t.sync();
+      rebuild();
+    }
     cur = 0;
     kblk = 0;
     draw_next();
@@ -622,6 +829,7 @@ struct Shot {
         body[2 * k + 1] = v.y;
       }
       const uint64_t *dsd = body, *dss = body + W, *beta = body + 2 * W, *gamma = body + 3 * W;
+      if (kRegCapable && !reg && nnz <= 32u) reg_load();
       while (nxt < hdr.y && status == ST_RUN) {
         apply_error(nxt);
         draw_next();
@@ -697,6 +905,7 @@ struct Shot {
     if (off < P.out_limit && P.records)
       for (uint32_t w = lane; w < P.rw; w += G) P.records[off * P.rw + w] = rec[w];
     if (off < P.st_limit) {
+      if (kRegCapable && reg) reg_spill();
       if (lane == 0) {
         P.st_nnz[off] = nnz;
         P.st_signs[off * 4 + 0] = sd[0];
@@ -718,9 +927,17 @@ struct Shot {
 };
 
 constexpr int kBlock = 128;
+// Register budget: resident 128-thread blocks per SM the compiler must allow
+// (FP32: 6 -> 80 registers, FP64: 5 -> 96 registers), tuned on GB300.
+#ifndef SOFT_MIN_BLOCKS_F32
+#define SOFT_MIN_BLOCKS_F32 6
+#endif
+#ifndef SOFT_MIN_BLOCKS_F64
+#define SOFT_MIN_BLOCKS_F64 5
+#endif
 
 template <typename R, int W, int G>
-__global__ void __launch_bounds__(kBlock) shot_kernel(const __grid_constant__ ShotParams P) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 : SOFT_MIN_BLOCKS_F64) shot_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long btally[5];
   auto block = cg::this_thread_block();
