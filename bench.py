@@ -298,6 +298,7 @@ def main():
                      "ops_per_shot": ops_shot, "peak_basis": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz "
                                                               "(sm_max_mhz of measured)"},
         "gpu_launches": launches32,
+        "error_shots_last_step": tal32[-1]["shots"] - tal32[-1]["discarded"] - tal32[-1]["overflow"] - tal32[-1]["kept"],
         "e2e": {"value": shots_all / (e2e_ms / 1000), "unit": "shots/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 56},
         "clocks": clock_info,

@@ -176,6 +176,13 @@ int soft_get_records(soft_run *r, uint64_t *host_words, size_t n_words, uint8_t 
 int soft_get_state(soft_run *r, uint64_t shot_offset, uint64_t *signs, uint64_t *keys, double *vals, size_t cap,
                    size_t *nnz);
 
+/* Wait, then report the run's in-kernel bounds checks: out[0] = number of
+ * failed checks (each ends its shot with SOFT_SHOT_ERROR, which the tally
+ * counts as shots - discarded - overflow - kept), and for the first failure
+ * out[1] = check code << 32 | event index, out[2] = shot index,
+ * out[3] = the offending value. All zero when every check passed. */
+int soft_run_diagnostics(soft_run *r, uint64_t out[4]);
+
 /* Device time of the run's kernels in milliseconds (CUDA events on the run's
  * stream), and how many kernels were launched. Waits for the run. */
 int soft_run_timing(soft_run *r, double *ms, uint32_t *n_launches);

@@ -63,7 +63,7 @@ class _Tally(ctypes.Structure):
 
 EXPORTED = ["soft_compile_circuit", "soft_circuit_info", "soft_circuit_tableau", "soft_circuit_free",
             "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing",
-            "soft_run_free", "soft_run_shots_noalloc", "soft_last_error"]
+            "soft_run_free", "soft_run_shots_noalloc", "soft_run_diagnostics", "soft_last_error"]
 
 
 def lib_path() -> str:
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         L.soft_run_free.argtypes = [vp]
         L.soft_run_free.restype = None
         L.soft_run_shots_noalloc.argtypes = [vp, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp]
+        L.soft_run_diagnostics.argtypes = [vp, vp]
         L.soft_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -229,6 +230,13 @@ def soft_get_state(run: Run, shot_offset: int):
                                  cap, ctypes.byref(nnz)))
     k = int(nnz.value)
     return signs, keys[:k].copy(), (vals[0:2 * k:2] + 1j * vals[1:2 * k:2]).copy()
+
+
+def soft_run_diagnostics(run: Run):
+    """[failed checks, code << 32 | event, shot, value] of the run's in-kernel bounds checks."""
+    out = np.zeros(4, dtype=np.uint64)
+    _check(load().soft_run_diagnostics(run.h, out.ctypes.data))
+    return [int(v) for v in out]
 
 
 def soft_run_timing(run: Run):

@@ -39,8 +39,9 @@ struct soft_run {
   cudaStream_t stream = nullptr;
   uint64_t n_shots = 0;
   unsigned long long *d_tally = nullptr;  // 5 counters
-  unsigned long long *d_work = nullptr;   // next1, next2, n_rerun
+  unsigned long long *d_work = nullptr;   // next1, next2, n_rerun, pad, diag[4]
   uint32_t *d_rerun = nullptr;
+  unsigned char *d_slab = nullptr;  // global-memory state for large-cap reruns
   uint8_t *d_status = nullptr;
   uint64_t *d_records = nullptr;
   bool own_status = false, own_records = false;
@@ -80,7 +81,8 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
     ev1.resize(hp.ev.size());
     for (size_t i = 0; i < hp.ev.size(); ++i) {
       const auto &s = hp.ev[i];
-      ev1[i] = soft::Ev<1>{s.w0, s.site_begin, s.a, s.b, {s.dsd[0]}, {s.dss[0]}, {s.beta[0]}, {s.gamma[0]}};
+      ev1[i] = soft::Ev<1>{s.w0, s.site_begin, s.a, s.b, {s.dsd[0]}, {s.dss[0]},
+                           {s.beta[0]}, {s.gamma[0]}, {s.xbeta[0]}, {s.xgamma[0]}};
     }
     ev_src = ev1.data();
     b_ev = ev1.size() * sizeof(soft::Ev<1>);
@@ -147,6 +149,7 @@ void soft_run_free(soft_run *r) {
   cudaFree(r->d_tally);
   cudaFree(r->d_work);
   cudaFree(r->d_rerun);
+  cudaFree(r->d_slab);
   if (r->own_status) cudaFree(r->d_status);
   if (r->own_records) cudaFree(r->d_records);
   cudaFree(r->d_st_signs);
@@ -175,8 +178,10 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
   const uint32_t g1 = o.group_size ? o.group_size : 32u;
   const uint32_t g2 = 32;
   const size_t smem_limit = 227 * 1024;
-  if (soft::group_smem_bytes(fp32, hp.W, cap, hp.rw) > smem_limit)
-    return fail(SOFT_E_ARG, "coeff_cap too large for the on-chip coefficient map");
+  if (soft::group_smem_bytes(fp32, hp.W, cap1, hp.rw) > smem_limit)
+    return fail(SOFT_E_ARG, "first_cap too large for the on-chip coefficient map");
+  // caps whose per-shot state does not fit in shared memory rerun from a global-memory slab
+  const bool global_rerun = two_pass && soft::group_smem_bytes(fp32, hp.W, cap, hp.rw) > smem_limit;
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
 
@@ -202,8 +207,19 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
     }                                                                                           \
   } while (0)
   SOFT_ALLOC(r->d_tally, 5 * sizeof(unsigned long long));
-  SOFT_ALLOC(r->d_work, 3 * sizeof(unsigned long long));
+  SOFT_ALLOC(r->d_work, 8 * sizeof(unsigned long long));
+  if ((e = cudaMemsetAsync(r->d_work, 0, 8 * sizeof(unsigned long long), (cudaStream_t)o.stream)) != cudaSuccess) {
+    soft_run_free(r);
+    return cuda_fail(e, "cudaMemsetAsync");
+  }
   if (two_pass) SOFT_ALLOC(r->d_rerun, chunk * sizeof(uint32_t));
+  uint32_t slab_blocks = 0;
+  if (global_rerun) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    slab_blocks = (uint32_t)(sms > 0 ? sms : 1);
+    SOFT_ALLOC(r->d_slab, soft::global_slab_bytes(fp32, hp.W, cap, hp.rw, slab_blocks));
+  }
   if (r->out_limit) {
     if (o.d_status) r->d_status = o.d_status;
     else {
@@ -248,6 +264,10 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
     p.n_events = (uint32_t)hp.ev.size();
     p.n_sites = hp.n_sites;
     p.rw = hp.rw;
+    p.n_coef = (uint32_t)hp.coefs.size();
+    p.n_cb = (uint32_t)hp.cb.size();
+    p.rerun_cap = two_pass ? (uint32_t)chunk : 0u;
+    p.diag = r->d_work + 4;
     p.tau = fp32 ? kTauFp32 : kTauFp64;
     p.seed = seed;
     p.first_shot = first_shot + s0;
@@ -283,6 +303,10 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
       q.list = r->d_rerun;
       q.n_items_dev = r->d_work + 2;
       q.next_item = r->d_work + 1;
+      if (global_rerun) {
+        q.gslab = r->d_slab;
+        q.gslab_blocks = slab_blocks;
+      }
       if ((e = soft::launch_shots(q, fp32, hp.W, g2, (int)o.blocks_per_sm, st, nullptr)) != cudaSuccess) {
         soft_run_free(r);
         return cuda_fail(e, "rerun kernel launch");
@@ -349,6 +373,16 @@ int soft_get_state(soft_run *r, uint64_t off, uint64_t *signs, uint64_t *keys, d
       (e = cudaMemcpy(vals, r->d_st_vals + off * r->st_stride * 2, m * 2 * sizeof(double), cudaMemcpyDeviceToHost)) !=
           cudaSuccess)
     return cuda_fail(e, "state copy");
+  return SOFT_OK;
+}
+
+int soft_run_diagnostics(soft_run *r, uint64_t out[4]) {
+  if (!r || !out) return fail(SOFT_E_ARG, "null argument");
+  unsigned long long d[4];
+  cudaError_t e = cudaMemcpyAsync(d, r->d_work + 4, sizeof d, cudaMemcpyDeviceToHost, r->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics copy");
+  for (int i = 0; i < 4; ++i) out[i] = d[i];
   return SOFT_OK;
 }
 

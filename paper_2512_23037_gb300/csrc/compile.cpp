@@ -211,6 +211,43 @@ uint64_t gap_thr(double p, uint64_t g) {
   return (uint64_t)t;
 }
 
+// Peephole pass: fold a reset's conditional X and a single-record detector
+// into the measurement event right before them. Folding is exact when the
+// folded event adds no noise sites and no Clifford sign masks in between and
+// no parity chain is pending.
+void fuse_events(std::vector<Ev<2>> &ev) {
+  std::vector<Ev<2>> out;
+  out.reserve(ev.size());
+  bool chain_pending = false;
+  auto quiet = [](const Ev<2> &e, const Ev<2> &prev) {
+    return e.site_begin == prev.site_begin && !(e.dsd[0] | e.dsd[1] | e.dss[0] | e.dss[1]);
+  };
+  for (const Ev<2> &e : ev) {
+    const uint32_t type = ev_type(e.w0), fl = ev_flags(e.w0);
+    if (!out.empty()) {
+      Ev<2> &m = out.back();
+      const uint32_t mt = ev_type(m.w0), mf = ev_flags(m.w0);
+      const bool is_meas = (mt == EV_MEAS_A || mt == EV_MEAS_B);
+      if (is_meas && type == EV_PAULI && (fl & F_COND_LAST) && !(mf & (F_COND_LAST | F_DETECTOR)) && quiet(e, m)) {
+        m.w0 |= (F_COND_LAST << 4) | (ev_e0(e.w0) << 24);
+        m.xbeta[0] = e.beta[0];
+        m.xbeta[1] = e.beta[1];
+        m.xgamma[0] = e.gamma[0];
+        m.xgamma[1] = e.gamma[1];
+        continue;
+      }
+      if (is_meas && type == EV_PARITY && (fl & F_DETECTOR) && !(fl & F_CHAIN) && !chain_pending &&
+          (mf & F_RECORD) && !(mf & F_DETECTOR) && e.a == m.b && e.b == kNoRec && quiet(e, m)) {
+        m.w0 |= (F_DETECTOR << 4) | ((fl & F_INVERT) ? (F_INVERT << 4) : 0u);
+        continue;
+      }
+    }
+    if (type == EV_PARITY) chain_pending = (fl & F_CHAIN) != 0;
+    out.push_back(e);
+  }
+  ev.swap(out);
+}
+
 }  // namespace
 
 int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noise *noise, uint32_t cap,
@@ -460,6 +497,7 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
     }
   }
   new_event(EV_END, 0, 0, 0);
+  fuse_events(P.ev);
   P.n_records = nrec;
   P.rw = nrec ? (nrec + 63) / 64 : 1;
   if (P.rw > 16) {

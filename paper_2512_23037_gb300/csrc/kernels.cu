@@ -174,6 +174,7 @@ struct Shot {
   uint32_t *ht;
   uint64_t *rec;
   uint32_t slots, hsmask, hsmax, cap, lane;
+  mutable uint32_t bad_slot = 0;  // set by lookup() when the hash index holds an impossible slot
   uint64_t shot;
   uint32_t nnz;
   uint64_t sd[W], ss[W];
@@ -218,6 +219,10 @@ struct Shot {
     for (uint32_t probe = 0; probe <= hsmask; ++probe) {
       uint32_t v = ht[h];
       if (v == 0u) return -1;
+      if (v - 1u >= slots) {
+        bad_slot = v;
+        return -1;
+      }
       if (keq(key(v - 1u), k)) return (int)(v - 1u);
       h = (h + 1u) & hsmask;
     }
@@ -329,6 +334,10 @@ struct Shot {
   }
 
   __device__ void apply_error(uint32_t s) {
+    if (s >= P.n_sites) {
+      fail_check(CHK_SITE, s);
+      return;
+    }
     const Site *S = P.sites + s;
     uint32_t two = __ldg(&S->two), code, pa, pb;
     if (two) {
@@ -358,6 +367,19 @@ struct Shot {
   }
 
   __device__ void fail_capacity() { status = P.small_pass ? ST_RERUN : ST_OVF; }
+
+  // Record the first failed bounds check of the launch and end the shot as ERROR.
+  uint32_t cur_ev = 0;
+  __device__ void fail_check(uint32_t code, uint64_t value) {
+    status = ST_ERR;
+    if (lane == 0 && P.diag) {
+      if (atomicAdd(&P.diag[0], 1ull) == 0ull) {
+        P.diag[1] = ((unsigned long long)code << 32) | cur_ev;
+        P.diag[2] = shot;
+        P.diag[3] = value;
+      }
+    }
+  }
 
   // ---------------------------------------------------------------- register mode
   __device__ __forceinline__ uint32_t vmask() const { return nnz >= 32u ? 0xFFFFFFFFu : ((1u << nnz) - 1u); }
@@ -423,16 +445,22 @@ struct Shot {
     const Cx<R> vj = shfl_c(rv, pl);
     const bool has = valid && partner != 0u;
     const bool app = valid && !has;
-    Cx<R> nv{0, 0}, av{0, 0};
-    if (valid) {
-      nv = cmul(a, rv);
-      if (has) nv = cadd(nv, cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
-      else av = cmul(b, ipow(rv, e + 2u * kpar(rk, gamma)));
-    }
+    // one product serves both cases: b xi_{pk} v_partner (paired) or b xi_k v_k (new entry at pk)
+    const Cx<R> src = has ? vj : rv;
+    const uint32_t par = kpar(has ? pk : rk, gamma);
+    const Cx<R> tb = cmul(b, ipow(src, e + 2u * par));
+    Cx<R> nv = cmul(a, rv);
+    if (has) nv = cadd(nv, tb);
+    const Cx<R> av = tb;
+    if (!valid) nv = Cx<R>{0, 0};
     const uint32_t ab = t.ballot(app);
     const uint32_t nA = __popc(ab);
     const bool small = (valid && norm2(nv) < tau) || (app && norm2(av) < tau);
     const bool prune = t.any(small);
+    if (nnz + nA > slots) {  // cannot happen while nnz <= cap before the gate
+      fail_check(CHK_STAGE, nnz + nA);
+      return;
+    }
     if (nnz + nA <= 32u) {
       if (nA) {
         if (app) {
@@ -530,13 +558,17 @@ struct Shot {
   }
 
   __device__ void set_record(uint32_t r, int m) {
+    if (r >= 64u * P.rw) {
+      fail_check(CHK_RECORD, r);
+      return;
+    }
     if (lane == 0 && m < 0) rec[r >> 6] |= 1ull << (r & 63);
     t.sync();
   }
 
   // ---- a I + b Z_q, beta != 0
   __device__ __forceinline__ void coef(uint32_t ci, Cx<R> &a, Cx<R> &b) const {
-    const Coef *C = P.coef + ci;
+    const Coef *C = P.coef + (ci < P.n_coef ? ci : 0u);
     if (sizeof(R) == 4) {
       float4 f = __ldg(reinterpret_cast<const float4 *>(&C->fa_re));
       a = Cx<R>{(R)f.x, (R)f.y};
@@ -555,6 +587,10 @@ struct Shot {
     for (int w = 0; w < W; ++w) pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
     const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
     const uint32_t lowbit = ev_lowbit(w0);
+    if (ci >= P.n_coef) {
+      fail_check(CHK_COEF, ci);
+      return;
+    }
     Cx<R> a, b;
     coef(ci, a, b);
     if (kRegCapable && reg) {
@@ -595,13 +631,24 @@ struct Shot {
       uint32_t bal = t.ballot(app);
       if (app) {
         uint32_t slot = n0 + nA + lanes_below(bal);
-        set_key(slot, pk);
-        vals[slot] = nv;
+        if (slot < slots) {
+          set_key(slot, pk);
+          vals[slot] = nv;
+        } else {
+          bad_slot = slot + 1u;
+        }
       }
       nA += __popc(bal);
     }
     t.sync();
     nnz = n0 + nA;
+    if (t.any(bad_slot != 0u)) {
+      uint32_t worst = bad_slot;
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) worst = max(worst, t.shfl_xor(worst, off));
+      fail_check(CHK_HASH_SLOT, worst);
+      return;
+    }
     bool pruned = t.any(prune);
     if (pruned) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
     if (nnz > cap) {
@@ -651,7 +698,7 @@ struct Shot {
     for (int w = 0; w < W; ++w) pe += __popcll(ss[w] & gamma[w]);
     const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
     if (e & 1u) {
-      status = ST_ERR;
+      fail_check(CHK_PHASE, e);
       return 1;
     }
     const uint32_t sgn = e >> 1;
@@ -690,6 +737,10 @@ struct Shot {
 
   // ---- Z measurement, beta != 0 (case B)
   __device__ int meas_b(uint32_t ord, uint32_t cbi) {
+    if (cbi >= P.n_cb) {
+      fail_check(CHK_CASEB, cbi);
+      return 1;
+    }
     const CaseB *B = P.cb + cbi;
     const uint32_t p = __ldg(&B->p);
     uint64_t J[W], g2[W], ep[W];
@@ -724,6 +775,10 @@ struct Shot {
 
   __device__ int smem_meas_b(uint32_t p, const uint64_t *J, const uint64_t *g2, const uint64_t *ep, uint32_t e2,
                              uint32_t ord) {
+    if (nnz > cap) {  // the staging half [cap, 2 cap) must hold every entry
+      fail_check(CHK_NNZ, nnz);
+      return 1;
+    }
     // relabel keys: a_j ^= a_p for j in J
     for (uint32_t i = lane; i < nnz; i += G) {
       Key<W> k = key(i);
@@ -750,6 +805,10 @@ struct Shot {
     }
     sp = tile_sum(sp);
     sm = tile_sum(sm);
+    if (t.any(bad_slot != 0u)) {
+      fail_check(CHK_HASH_SLOT, bad_slot);
+      return 1;
+    }
     const double pp = snap01(sp / (sp + sm));
     const int m = uniform(ord) < pp ? 1 : -1;
     const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
@@ -782,12 +841,13 @@ struct Shot {
   }
 
   __device__ uint32_t rec_bit(int32_t r) const {
-    return r < 0 ? 0u : (uint32_t)((rec[r >> 6] >> (r & 63)) & 1ull);
+    return (r < 0 || (uint32_t)r >= 64u * P.rw) ? 0u : (uint32_t)((rec[r >> 6] >> (r & 63)) & 1ull);
   }
 
   __device__ void run(uint64_t s) {
     shot = s;
     status = ST_RUN;
+    bad_slot = 0;
     chain = 0;
     logical = 0;
     lastm = 1;
@@ -817,6 +877,7 @@ struct Shot {
     draw_next();
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(P.ev);
     for (uint32_t ev = 0; ev < P.n_events && status == ST_RUN; ++ev) {
+      cur_ev = ev;
       const Ev<W> *E = evs + ev;
       const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
       // dsd, dss, beta, gamma: 4 W words after the header
@@ -849,6 +910,19 @@ struct Shot {
           int m = (type == EV_MEAS_A) ? meas_a(w0, hdr.z, gamma) : meas_b(hdr.z, (uint32_t)beta[0]);
           lastm = m;
           if (flags & F_RECORD) set_record(hdr.w, m);
+          if ((flags & F_COND_LAST) && m == -1 && status == ST_RUN) {  // fused reset correction
+            uint64_t xb[W], xg[W];
+            uint32_t pe = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+              xb[w] = __ldg(&E->xbeta[w]);
+              xg[w] = __ldg(&E->xgamma[w]);
+              pe += __popcll(sd[w] & xb[w]) + __popcll(ss[w] & xg[w]);
+            }
+            apply_pauli(xb, xg, (ev_xe0(w0) + 2u * pe) & 3u);
+          }
+          if ((flags & F_DETECTOR) && ((m == -1 ? 1u : 0u) ^ ((flags & F_INVERT) ? 1u : 0u)))
+            status = ST_DISC;  // fused detector on this record
           break;
         }
         case EV_PAULI: {
@@ -885,7 +959,7 @@ struct Shot {
     if (status == ST_RERUN) {
       if (lane == 0) {
         unsigned long long i = atomicAdd(P.n_rerun, 1ull);
-        P.rerun[i] = (uint32_t)off;
+        if (i < P.rerun_cap) P.rerun[i] = (uint32_t)off;
       }
       t.sync();
       return;
@@ -945,7 +1019,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 :
   if (threadIdx.x < 5) btally[threadIdx.x] = 0ull;
   __syncthreads();
   const uint32_t gid = threadIdx.x / G;  // blockDim.x is a multiple of G
-  unsigned char *base = smem + (size_t)gid * group_bytes<R, W>(P.cap, P.rw);
+  const size_t gbytes = group_bytes<R, W>(P.cap, P.rw);
+  unsigned char *base = P.gslab ? P.gslab + ((size_t)blockIdx.x * (blockDim.x / G) + gid) * gbytes
+                                : smem + (size_t)gid * gbytes;
   Shot<R, W, G> s(tile, P, base);
   const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
   for (;;) {
@@ -953,6 +1029,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 :
     if (tile.thread_rank() == 0) item = atomicAdd(P.next_item, 1ull);
     item = tile.shfl(item, 0);
     if (item >= n_items) break;
+    if (P.list && item >= P.rerun_cap) break;  // a list never holds more than its capacity
     const uint64_t off = P.list ? (uint64_t)P.list[item] : (uint64_t)item;
     s.run(P.first_shot + off);
     s.finish(off, btally);
@@ -969,6 +1046,12 @@ cudaError_t launch_t(const ShotParams &p0, int blocks_per_sm, cudaStream_t strea
   const size_t gb = group_bytes<R, W>(p.cap, p.rw);
   const size_t limit = 227 * 1024;
   size_t gpb = kBlock / G;
+  if (p.gslab) {
+    if (!p.gslab_blocks) return cudaErrorInvalidValue;
+    if (grid_out) *grid_out = (int)p.gslab_blocks;
+    kern<<<p.gslab_blocks, (unsigned)(gpb * G), 0, stream>>>(p);
+    return cudaGetLastError();
+  }
   while (gpb > 1 && gpb * gb > limit) gpb >>= 1;
   if (gpb * gb > limit) return cudaErrorInvalidConfiguration;
   const int block = (int)(gpb * G);
@@ -998,6 +1081,10 @@ cudaError_t launch_t(const ShotParams &p0, int blocks_per_sm, cudaStream_t strea
 }
 
 }  // namespace
+
+size_t global_slab_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw, uint32_t blocks) {
+  return group_smem_bytes(fp32, W, cap, rw) * (size_t)(kBlock / 32) * blocks;
+}
 
 size_t group_smem_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw) {
   if (fp32) return W == 1 ? group_bytes<float, 1>(cap, rw) : group_bytes<float, 2>(cap, rw);

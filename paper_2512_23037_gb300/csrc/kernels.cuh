@@ -37,7 +37,25 @@ struct ShotParams {
   uint32_t *st_nnz;
   uint64_t st_limit;
   uint32_t st_stride;
+  // global-memory mode (caps whose state does not fit in shared memory):
+  // group g of block b uses gslab + (b * groups_per_block + g) * group_bytes
+  unsigned char *gslab;
+  uint32_t gslab_blocks;
+  // bounds of the program arrays and of the rerun list, for the in-kernel checks
+  uint32_t n_coef, n_cb, rerun_cap;
+  // first failed in-kernel check: [0] count, [1] code << 32 | event, [2] shot, [3] value
+  unsigned long long *diag;
 };
+
+// In-kernel check codes (a failed check ends the shot with SOFT_SHOT_ERROR
+// and skips the access).
+enum : uint32_t {
+  CHK_HASH_SLOT = 1, CHK_STAGE = 2, CHK_SLOTS = 3, CHK_RECORD = 4, CHK_SITE = 5, CHK_COEF = 6,
+  CHK_CASEB = 7, CHK_RERUN = 8, CHK_LIST = 9, CHK_PHASE = 10, CHK_NNZ = 11
+};
+
+// Bytes of a global slab for `blocks` 128-thread blocks of 32-lane groups.
+size_t global_slab_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw, uint32_t blocks);
 
 // Bytes of shared memory one shot group needs for capacity `cap`.
 size_t group_smem_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw);

@@ -65,7 +65,7 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
   unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
   uint32_t *rerun = reinterpret_cast<uint32_t *>(scratch + kCounterBytes);
   if ((e = cudaMemsetAsync(d_tally, 0, 5 * sizeof(unsigned long long), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess)
+      (e = cudaMemsetAsync(work, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess)
     return soft::set_error(SOFT_E_CUDA, "cudaMemsetAsync failed");
   if (n_shots == 0) return SOFT_OK;
   const uint32_t cap = hp.cap, cap1 = cap < soft::kDefaultFirstCap ? cap : soft::kDefaultFirstCap;
@@ -79,6 +79,10 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
   p.n_events = (uint32_t)hp.ev.size();
   p.n_sites = hp.n_sites;
   p.rw = hp.rw;
+  p.n_coef = (uint32_t)hp.coefs.size();
+  p.n_cb = (uint32_t)hp.cb.size();
+  p.rerun_cap = (uint32_t)kNoallocMaxShots;
+  p.diag = work + 4;
   p.tau = fp32 ? soft::kTauFp32 : soft::kTauFp64;
   p.seed = seed;
   p.first_shot = first_shot;

@@ -42,14 +42,20 @@ enum : uint32_t {
   F_COND_REC = 128   // PAULI: apply if parity of records a, b is 1
 };
 
-// Header word 0: type (bits 0-3) | flags (4-11) | e0 (12-13) | lowbit (16-23).
+// Header word 0: type (bits 0-3) | flags (4-11) | e0 (12-13) | lowbit (16-23) | xe0 (24-25).
 SOFT_HD inline uint32_t ev_type(uint32_t w0) { return w0 & 15u; }
 SOFT_HD inline uint32_t ev_flags(uint32_t w0) { return (w0 >> 4) & 255u; }
 SOFT_HD inline uint32_t ev_e0(uint32_t w0) { return (w0 >> 12) & 3u; }
 SOFT_HD inline uint32_t ev_lowbit(uint32_t w0) { return (w0 >> 16) & 255u; }
+SOFT_HD inline uint32_t ev_xe0(uint32_t w0) { return (w0 >> 24) & 3u; }
 inline uint32_t ev_pack(uint32_t type, uint32_t flags, uint32_t e0, uint32_t lowbit) {
   return (type & 15u) | ((flags & 255u) << 4) | ((e0 & 3u) << 12) | ((lowbit & 255u) << 16);
 }
+
+// Fused actions of a MEAS event (set by the compiler's peephole pass when the
+// op right after the measurement touches nothing else):
+//   F_COND_LAST: the reset correction X_q (xbeta/xgamma/xe0) when m = -1;
+//   F_DETECTOR (+ F_INVERT): a detector on this measurement's record alone.
 
 // One event; W = 64-bit words per n-bit vector (1 for n <= 64, else 2).
 //   ROT/ROT_DIAG: a = coefficient index, beta/gamma of Z_q
@@ -62,6 +68,7 @@ struct alignas(16) Ev {
   uint32_t w0, site_begin, a, b;
   uint64_t dsd[W], dss[W];    // sign XOR masks applied before the event
   uint64_t beta[W], gamma[W];
+  uint64_t xbeta[W], xgamma[W];  // MEAS with F_COND_LAST: X_q after the measurement
 };
 
 // a I + b Z_q coefficients, FP64 and the FP32 copies the FP32 kernel uses.

@@ -201,3 +201,24 @@ def test_bench_config_sampled(soft):
             assert _band_ok(circ, noise, 0, int(s), BAND["fp32"])
             band += 1
     assert band <= 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_w97_two_word_keys(soft, precision):
+    """97 qubits (two-word keys and signs), cap 2^12: the rerun pass runs from
+    a global-memory slab because that state does not fit in shared memory."""
+    circ, noise = C.workload("w97")
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 1500, 0, precision, capture=16)
+    assert compare_records(circ, noise, 0, 0, rec, st, ref, precision) <= 2
+    compare_states(soft, c, r, circ, noise, 0, 0, 16, precision)
+
+
+def test_global_memory_rerun_forced(soft):
+    """cap 8192 (FP64) cannot live in shared memory; first_cap 2 sends almost
+    every shot through the global-memory rerun pass."""
+    circ = C.random_circuit(4242, 10, 140, t_frac=0.35, meas_frac=0.05, detectors=True)
+    circ.cap = 8192
+    noise = C.Noise(0.01, 0.01, 0.01, 0.01)
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 400, 11, "fp64", capture=24, first_cap=2)
+    assert compare_records(circ, noise, 11, 0, rec, st, ref, "fp64") <= 1
+    compare_states(soft, c, r, circ, noise, 11, 0, 24, "fp64")
