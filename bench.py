@@ -28,6 +28,15 @@ sys.path.insert(0, ROOT)
 WORKLOAD = ("w42: 42 qubits (38 data + 4 ancilla), seeded random stabilizer state, 18 blocks of "
             "T on a random 4-qubit window + 60-gate Clifford + 4 ancilla parity checks + inverse + T^dag "
             "(72 T positions), coefficient cap 2^8, uniform depolarizing p=1e-3, circuit seed 1, Philox seed 0")
+WORKLOADS = {
+    "w42": WORKLOAD,
+    "w97": ("w97: 97 qubits (89 data + 8 ancilla), 24 blocks of T on a random 6-qubit window + 160-gate Clifford "
+            "+ 8 ancilla parity checks + inverse + T^dag (144 T positions), coefficient cap 2^12, uniform "
+            "depolarizing p=5e-4, circuit seed 4, Philox seed 0"),
+    "batch64": ("batch64: one launch over 64 windowed circuits, qubits uniform 17..49, window 2..6 (caps 2^4..2^12), "
+                "6..24 blocks, p log-uniform in [1e-4, 3e-3], shots per circuit geometric with mean 1e6 "
+                "(77.1 M shots per step), generator seed 2"),
+}
 # Algorithmic work per counted unit (lane ops: FP + integer), see the design doc
 OPS_T_OUT, OPS_T_DIAG, OPS_MEAS, OPS_NOISE = 18, 9, 8, 3
 
@@ -44,6 +53,10 @@ def parse():
     ap.add_argument("--group", type=int, default=0)
     ap.add_argument("--first-cap", type=int, default=0)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer between steps (0 = none)")
+    ap.add_argument("--workload", default="w42", choices=["w42", "w97", "batch64"])
+    ap.add_argument("--graph", action="store_true", help="replay chunks from a captured CUDA graph")
+    ap.add_argument("--chunk", type=int, default=0, help="shots per chunk (0 = library default)")
+    ap.add_argument("--autotune", action="store_true", help="time launch-shape candidates first")
     return ap.parse_args()
 
 
@@ -155,6 +168,22 @@ def ops_per_shot(circ, noise):
     return tot / c["shots"], c
 
 
+def ops_per_shot_items(items):
+    """Shot-weighted algorithmic ops per shot over a workload's circuits."""
+    if len(items) == 1:
+        return ops_per_shot(items[0][0], items[0][1])
+    import oracle
+    tot_ops, tot_w = 0.0, 0
+    for c, nz, shots in items:
+        r = oracle.run(c, c.n, nz, c.cap, 0, 0, 200, threads=os.cpu_count() or 1, records=False)
+        k = r["counts"]
+        ops = (OPS_T_OUT * k["t_out_entries"] + OPS_T_DIAG * k["t_diag_entries"] + OPS_MEAS * k["meas_entries"]
+               + OPS_NOISE * k["noise_entries"]) / k["shots"]
+        tot_ops += ops * shots
+        tot_w += shots
+    return tot_ops / tot_w, None
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -198,24 +227,38 @@ def main():
     import paper_2512_23037_gb300 as S
     from paper_2512_23037_gb300 import circuits as C
     S.load()
-    circ, noise = C.workload("w42")
-    stream = torch.cuda.current_stream()
-    n = args.shots
+    if args.workload == "batch64":
+        items = C.batch_of_windowed(2, 64)
+    else:
+        circ0, noise0 = C.workload(args.workload)
+        items = [(circ0, noise0, args.shots)]
+    stream = torch.cuda.current_stream() if not args.graph else torch.cuda.Stream()
+    n = sum(s for _, _, s in items)  # shots per step per GPU
     from paper_2512_23037_gb300.sharding import shot_range
     base_shot, _ = shot_range(rank, world, n)  # disjoint shot ranges per rank
     dev_props = torch.cuda.get_device_properties(local)
     flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    tune = {"group_size": args.group, "first_cap": args.first_cap, "chunk_shots": args.chunk}
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def compile_all():
+        return [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz, _ in items]
+
+    def launch(handles, first, precision):
+        if len(handles) == 1:
+            return S.soft_run_shots(handles[0], items[0][2], first, 0, precision=precision, stream=stream,
+                                    graph=args.graph, **tune)
+        return S.soft_run_batch(handles, [s for _, _, s in items], [first] * len(handles), 0, precision=precision,
+                                stream=stream, graph=args.graph, **tune)
+
     def time_path(precision, steps, warmup):
-        c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+        hs = compile_all()
         for w in range(warmup):
-            r = S.soft_run_shots(c, n, base_shot + (1 << 36) + w * n, 0, precision=precision, stream=stream,
-                                 group_size=args.group, first_cap=args.first_cap)
+            r = launch(hs, base_shot + (1 << 36) + w * n, precision)
             S.soft_tally(r)
             r.free()
         barrier()
@@ -227,8 +270,7 @@ def main():
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            r = S.soft_run_shots(c, n, base_shot + k * n, 0, precision=precision, stream=stream,
-                                 group_size=args.group, first_cap=args.first_cap)
+            r = launch(hs, base_shot + k * n, precision)
             ev1.record(stream)
             tallies.append(S.soft_tally(r))
             ms, nl = S.soft_run_timing(r)
@@ -240,7 +282,14 @@ def main():
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         if world > 1:
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item()), launches, kernel_ms, tallies, c
+        return float(t.item()), launches, kernel_ms, tallies, hs
+
+    tuned = None
+    if args.autotune:
+        from paper_2512_23037_gb300.autotune import autotune
+        res = autotune(compile_all(), precision="fp32", stream=stream)
+        tune.update(res["best"])
+        tuned = {"best": res["best"], "table_ms": [[round(ms, 3), kw] for ms, kw in res["table"]]}
 
     clocks = Clocks(local) if rank == 0 else None
     ms32, launches32, kms32, tal32, c32 = time_path("fp32", args.steps, args.warmup)
@@ -249,20 +298,20 @@ def main():
     if not args.no_fp64:
         ms64, launches64, kms64, tal64, _ = time_path("fp64", args.steps, args.warmup)
 
-    # end to end through the C ABI: host op list -> compile + upload -> run -> tally to host
+    # end to end through the C ABI: host op lists -> compile + upload -> run -> tally to host
     barrier()
-    ops_host = circ.array()
-    e2e_ms = 0.0
+    ops_host = [c.array() for c, _, _ in items]
+    e2e_ms, h2d = 0.0, 0
     for k in range(args.steps):
         t0 = time.perf_counter()
-        c = S.soft_compile_circuit(ops_host, circ.n, noise, circ.cap)
-        r = S.soft_run_shots(c, n, base_shot + (1 << 38) + k * n, 0, precision="fp32", stream=stream,
-                             group_size=args.group, first_cap=args.first_cap)
+        hs = [S.soft_compile_circuit(a, c.n, nz, c.cap) for a, (c, nz, _) in zip(ops_host, items)]
+        r = launch(hs, base_shot + (1 << 38) + k * n, "fp32")
         S.soft_tally(r)
         e2e_ms += 1000 * (time.perf_counter() - t0)
-        h2d = c.info["program_bytes"]
+        h2d = sum(h.info["program_bytes"] for h in hs)
         r.free()
-        c.free()
+        for h in hs:
+            h.free()
     barrier()
     t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
     if world > 1:
@@ -273,7 +322,7 @@ def main():
         return 0
     shots_all = n * world * args.steps
     value = shots_all / (ms32 / 1000)
-    ops_shot, counts = ops_per_shot(circ, noise)
+    ops_shot, counts = ops_per_shot_items(items)
     peaks = measured_peaks()
     sm_clock = peaks.get("sm_max_mhz", 2070.0)
     sms = dev_props.multi_processor_count
@@ -286,9 +335,10 @@ def main():
         "metric": "shots/s", "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "shots_per_step_per_gpu": n, "coefficients": "complex64",
+        "config": {"workload": WORKLOADS[args.workload], "shots_per_step_per_gpu": n, "coefficients": "complex64",
                    "probabilities_and_tallies": "fp64", "l2": "flushed between steps (512 MB memset)",
-                   "parallelism": f"shot ranges x{world}"},
+                   "parallelism": f"shot ranges x{world}", "graph_replay": bool(args.graph),
+                   "launch_shape": {k: v for k, v in tune.items() if v} or "library default"},
         "fp64_plain": None if ms64 is None else {
             "value": shots_all / (ms64 / 1000), "unit": "shots/s", "ms_per_step": ms64 / args.steps,
             "dtype": "f64"},
@@ -303,11 +353,13 @@ def main():
                 "d2h_bytes_per_step": 56},
         "clocks": clock_info,
     }
+    if tuned:
+        line["autotune"] = tuned
     if not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        rate, ncpu, dt, _ = oracle_rate(circ, noise, 0, 12.0, threads)
+        rate, ncpu, dt, _ = oracle_rate(items[0][0], items[0][1], 0, 12.0, threads)
         line["cpu_baseline"] = {"value": rate, "unit": "shots/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{ncpu} shots of the same workload ({dt:.1f} s, shots 1e9..)"}
+                                "sample": f"{ncpu} shots of {'the same workload' if len(items) == 1 else 'circuit 0 of the batch'} ({dt:.1f} s, shots 1e9..)"}
     print(json.dumps(line))
     return 0
 

@@ -140,7 +140,12 @@ typedef struct {
   uint32_t capture_k;    /* keep the final GS state of the first capture_k shots */
   uint64_t *d_records;   /* optional caller device buffer, record_words per kept shot */
   uint8_t *d_status;     /* optional caller device buffer, one byte per kept shot */
+  uint32_t groups_per_block; /* shots resident per 128-thread block: 0 = 4, else 1..4 */
+  uint32_t flags;        /* SOFT_RUN_GRAPH: capture one chunk (counter reset, both passes,
+                            device-side advance of the chunk base) in a CUDA graph and
+                            replay it for every full chunk; needs a non-NULL stream */
 } soft_run_opts;
+enum { SOFT_RUN_GRAPH = 1 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
  * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all
@@ -159,9 +164,24 @@ typedef struct {
   double sum_fidelity, sum_weight; /* reserved accumulators (0 here) */
 } soft_tally_t;
 
+/* One persistent launch sequence over up to 64 compiled circuits (shots and
+ * circuits whose coefficient caps differ share the kernel; a shot's overflow
+ * threshold is its own circuit's cap). Circuit i runs shots
+ * [first_shots[i], first_shots[i] + n_shots[i]). All circuits must be on one
+ * device and all have n <= 64 qubits or all n > 64. Records and state capture
+ * are not available for batches (record_mode must be NONE, capture_k 0).
+ * Results per shot are identical to soft_run_shots of that circuit alone.
+ * Errors: SOFT_E_ARG, SOFT_E_OOM, SOFT_E_CUDA. */
+int soft_run_batch(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t *first_shots, uint32_t n_circ,
+                   uint64_t seed, const soft_run_opts *opts, soft_run **out);
+
 /* Wait for the run's stream work and copy its tallies (Sec. V-A fields:
- * total, discarded, kept shots and detected logical errors). */
+ * total, discarded, kept shots and detected logical errors), summed over
+ * the circuits of a batch. */
 int soft_tally(soft_run *r, soft_tally_t *out);
+
+/* Tally of circuit `index` of a batch run (index 0 for soft_run_shots). */
+int soft_tally_batch(soft_run *r, uint32_t index, soft_tally_t *out);
 
 /* Wait, then copy records (shot-major, record_words per shot, bit j = 1 when
  * record j measured -1; bits after a discard are 0) and status bytes of the

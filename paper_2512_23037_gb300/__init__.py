@@ -29,6 +29,7 @@ SOFT_OK = 0
 FP64, FP32 = 0, 1
 REC_NONE, REC_FIRST_K, REC_ALL = 0, 1, 2
 SHOT_KEPT, SHOT_DISCARDED, SHOT_OVERFLOW, SHOT_ERROR = 0, 1, 2, 3
+RUN_GRAPH = 1
 
 
 class SoftError(RuntimeError):
@@ -52,7 +53,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("record_mode", ctypes.c_int32), ("record_k", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("group_size", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("chunk_shots", ctypes.c_uint64), ("first_cap", ctypes.c_uint32), ("capture_k", ctypes.c_uint32),
-                ("d_records", ctypes.c_void_p), ("d_status", ctypes.c_void_p)]
+                ("d_records", ctypes.c_void_p), ("d_status", ctypes.c_void_p),
+                ("groups_per_block", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class _Tally(ctypes.Structure):
@@ -63,7 +65,8 @@ class _Tally(ctypes.Structure):
 
 EXPORTED = ["soft_compile_circuit", "soft_circuit_info", "soft_circuit_tableau", "soft_circuit_free",
             "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing",
-            "soft_run_free", "soft_run_shots_noalloc", "soft_run_diagnostics", "soft_last_error"]
+            "soft_run_free", "soft_run_shots_noalloc", "soft_run_diagnostics", "soft_run_batch",
+            "soft_tally_batch", "soft_last_error"]
 
 
 def lib_path() -> str:
@@ -95,6 +98,8 @@ def load(build_if_missing: bool = True):
         L.soft_run_free.restype = None
         L.soft_run_shots_noalloc.argtypes = [vp, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp]
         L.soft_run_diagnostics.argtypes = [vp, vp]
+        L.soft_run_batch.argtypes = [vp, vp, vp, u32, u64, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
+        L.soft_tally_batch.argtypes = [vp, u32, ctypes.POINTER(_Tally)]
         L.soft_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -170,13 +175,9 @@ def soft_compile_circuit(ops, n_qubits: int, noise, coeff_cap: int) -> Circuit:
     return Circuit(out.value, n_qubits)
 
 
-def soft_run_shots(circ: Circuit, n_shots: int, first_shot: int = 0, seed: int = 0, precision="fp64",
-                   record_mode=REC_NONE, record_k: int = 0, stream=None, group_size: int = 0,
-                   blocks_per_sm: int = 0, chunk_shots: int = 0, first_cap: int = 0, capture_k: int = 0,
-                   d_records=None, d_status=None) -> Run:
-    """Launch shots asynchronously on `stream` (a torch.cuda.Stream, a raw
-    cudaStream_t int, or None for torch's current stream when torch is
-    imported, else the legacy default stream)."""
+def _opts(precision="fp64", record_mode=REC_NONE, record_k=0, stream=None, group_size=0, blocks_per_sm=0,
+          chunk_shots=0, first_cap=0, capture_k=0, d_records=None, d_status=None, groups_per_block=0,
+          graph=False) -> _Opts:
     o = _Opts()
     o.precision = FP32 if precision in ("fp32", FP32) else FP64
     o.record_mode = int(record_mode)
@@ -198,10 +199,45 @@ def soft_run_shots(circ: Circuit, n_shots: int, first_shot: int = 0, seed: int =
     o.capture_k = int(capture_k)
     o.d_records = ctypes.c_void_p(int(d_records) if d_records else 0)
     o.d_status = ctypes.c_void_p(int(d_status) if d_status else 0)
+    o.groups_per_block = int(groups_per_block)
+    o.flags = RUN_GRAPH if graph else 0
+    return o
+
+
+def soft_run_shots(circ: Circuit, n_shots: int, first_shot: int = 0, seed: int = 0, precision="fp64",
+                   record_mode=REC_NONE, record_k: int = 0, stream=None, group_size: int = 0,
+                   blocks_per_sm: int = 0, chunk_shots: int = 0, first_cap: int = 0, capture_k: int = 0,
+                   d_records=None, d_status=None, groups_per_block: int = 0, graph: bool = False) -> Run:
+    """Launch shots asynchronously on `stream` (a torch.cuda.Stream, a raw
+    cudaStream_t int, or None for torch's current stream when torch is
+    imported, else the legacy default stream)."""
+    o = _opts(precision, record_mode, record_k, stream, group_size, blocks_per_sm, chunk_shots, first_cap,
+              capture_k, d_records, d_status, groups_per_block, graph)
     out = ctypes.c_void_p()
     _check(load().soft_run_shots(circ.h, int(n_shots), int(first_shot), int(seed) & (2 ** 64 - 1), ctypes.byref(o),
                                  ctypes.byref(out)))
     return Run(out.value, circ, n_shots)
+
+
+def soft_run_batch(circs, n_shots, first_shots, seed: int = 0, **kw) -> Run:
+    """One launch sequence over several compiled circuits; tallies per circuit
+    with soft_tally_batch."""
+    n = len(circs)
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in circs])
+    ns = (ctypes.c_uint64 * n)(*[int(v) for v in n_shots])
+    fs = (ctypes.c_uint64 * n)(*[int(v) for v in first_shots])
+    o = _opts(**kw)
+    out = ctypes.c_void_p()
+    _check(load().soft_run_batch(hs, ns, fs, n, int(seed) & (2 ** 64 - 1), ctypes.byref(o), ctypes.byref(out)))
+    r = Run(out.value, circs[0], sum(int(v) for v in n_shots))
+    r.circuits = list(circs)
+    return r
+
+
+def soft_tally_batch(run: Run, index: int) -> dict:
+    t = _Tally()
+    _check(load().soft_tally_batch(run.h, int(index), ctypes.byref(t)))
+    return {f: (float(getattr(t, f)) if f.startswith("sum") else int(getattr(t, f))) for f, _ in _Tally._fields_}
 
 
 def soft_tally(run: Run) -> dict:

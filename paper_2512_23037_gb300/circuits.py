@@ -427,6 +427,27 @@ def workload(name: str) -> tuple:
     raise KeyError(name)
 
 
+def batch_of_windowed(seed: int = 2, n_circuits: int = 64, mean_shots: float = 1e6):
+    """Many windowed circuits for one batched launch (multi-circuit workload).
+
+    Per circuit: qubits uniform in 17..49 (4 ancillas, the rest data), window
+    w uniform in 2..6 (cap 4^w: 2^4..2^12), blocks uniform in 6..24, noise p
+    log-uniform in [1e-4, 3e-3], shot count geometric with the given mean.
+    Returns a list of (circuit, noise, n_shots)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_circuits):
+        n = int(rng.integers(17, 50))
+        w = int(rng.integers(2, 7))
+        blocks = int(rng.integers(6, 25))
+        p = float(np.exp(rng.uniform(np.log(1e-4), np.log(3e-3))))
+        shots = int(rng.geometric(1.0 / mean_shots)) if mean_shots > 1 else 1
+        circ, noise = windowed(1000 + k, n_data=n - 4, n_anc=4, blocks=blocks, w=w, n_cliff=max(20, 2 * (n - 4)),
+                               checks=4, p=p)
+        out.append((circ, noise, shots))
+    return out
+
+
 def random_circuit(seed: int, n: int, n_ops: int, t_frac=0.15, meas_frac=0.1, rz=True,
                    resets=True, feedback=True, detectors=False) -> Circuit:
     """Random op mix over every op kind, for differential tests on small n."""

@@ -35,14 +35,15 @@ int set_error(int code, const char *msg) { return fail(code, msg); }
 }  // namespace soft
 
 struct soft_run {
-  soft_circuit *c = nullptr;
   cudaStream_t stream = nullptr;
-  uint64_t n_shots = 0;
-  unsigned long long *d_tally = nullptr;  // 5 counters
-  unsigned long long *d_work = nullptr;   // next1, next2, n_rerun, pad, diag[4]
+  uint32_t n_circ = 0;
+  std::vector<soft_circuit *> circs;       // borrowed: must outlive the run's stream work
+  std::vector<uint64_t> n_shots;
+  unsigned long long *d_tally = nullptr;   // 5 counters per circuit
+  unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4]
   uint32_t *d_rerun = nullptr;
-  unsigned char *d_slab = nullptr;  // global-memory state for large-cap reruns
-  uint8_t *d_status = nullptr;
+  unsigned char *d_slab = nullptr;         // global-memory state for large-cap reruns
+  uint8_t *d_status = nullptr;             // circuit 0 only
   uint64_t *d_records = nullptr;
   bool own_status = false, own_records = false;
   uint64_t out_limit = 0;
@@ -51,6 +52,8 @@ struct soft_run {
   uint32_t *d_st_nnz = nullptr;
   uint64_t st_limit = 0;
   uint32_t st_stride = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   uint32_t launches = 0;
 };
@@ -156,48 +159,89 @@ void soft_run_free(soft_run *r) {
   cudaFree(r->d_st_keys);
   cudaFree(r->d_st_vals);
   cudaFree(r->d_st_nnz);
+  if (r->graph_exec) cudaGraphExecDestroy(r->graph_exec);
+  if (r->graph) cudaGraphDestroy(r->graph);
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
   delete r;
 }
 
-int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, const soft_run_opts *opts,
-                   soft_run **out) {
-  if (!c || !out) return fail(SOFT_E_ARG, "null argument");
+}  // extern "C"
+
+namespace {
+
+soft::CircDev circ_desc(const soft_circuit *c) {
+  soft::CircDev d{};
+  d.ev = c->d_ev;
+  d.coef = c->d_coef;
+  d.cb = c->d_cb;
+  d.sites = c->d_sites;
+  d.thr = c->d_thr;
+  d.n_events = (uint32_t)c->hp.ev.size();
+  d.n_sites = c->hp.n_sites;
+  d.rw = c->hp.rw;
+  d.cap = c->hp.cap;
+  d.n_coef = (uint32_t)c->hp.coefs.size();
+  d.n_cb = (uint32_t)c->hp.cb.size();
+  return d;
+}
+
+// Shared launcher of soft_run_shots and soft_run_batch.
+int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t *first_shots, uint32_t n_circ,
+             uint64_t seed, const soft_run_opts *opts, soft_run **out) {
+  if (!circs || !n_shots || !first_shots || !out || n_circ == 0) return fail(SOFT_E_ARG, "null argument or empty batch");
   *out = nullptr;
+  if (n_circ > (uint32_t)soft::kMaxCirc) return fail(SOFT_E_ARG, "at most 64 circuits per batch");
   soft_run_opts o{};
   if (opts) o = *opts;
   if (o.precision != SOFT_FP64 && o.precision != SOFT_FP32) return fail(SOFT_E_ARG, "bad precision");
   if (o.record_mode < SOFT_REC_NONE || o.record_mode > SOFT_REC_ALL) return fail(SOFT_E_ARG, "bad record mode");
   if (o.group_size != 0 && o.group_size != 8 && o.group_size != 32) return fail(SOFT_E_ARG, "group_size must be 0, 8 or 32");
-  const auto &hp = c->hp;
+  if (o.groups_per_block > 4) return fail(SOFT_E_ARG, "groups_per_block must be 0..4");
+  if (n_circ > 1 && (o.record_mode != SOFT_REC_NONE || o.capture_k))
+    return fail(SOFT_E_ARG, "records and state capture are per single-circuit run");
+  const bool use_graph = (o.flags & SOFT_RUN_GRAPH) != 0;
+  if (use_graph && !o.stream) return fail(SOFT_E_ARG, "graph replay needs a non-default stream");
   const int fp32 = o.precision == SOFT_FP32;
-  const uint32_t cap = hp.cap;
-  uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap) : std::min(kDefaultFirstCap, cap);
-  const bool two_pass = cap1 < cap;
+  uint32_t W = 0, cap_max = 0, rw_max = 1;
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < n_circ; ++i) {
+    if (!circs[i]) return fail(SOFT_E_ARG, "null circuit");
+    if (W && circs[i]->hp.W != W) return fail(SOFT_E_ARG, "all circuits of a batch need n <= 64 or all n > 64");
+    if (circs[i]->device != circs[0]->device) return fail(SOFT_E_ARG, "all circuits of a batch must be on one device");
+    W = circs[i]->hp.W;
+    cap_max = std::max(cap_max, circs[i]->hp.cap);
+    rw_max = std::max(rw_max, circs[i]->hp.rw);
+    total += n_shots[i];
+  }
+  const uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap_max) : std::min(kDefaultFirstCap, cap_max);
+  const bool two_pass = cap1 < cap_max;
   const uint32_t g1 = o.group_size ? o.group_size : 32u;
   const uint32_t g2 = 32;
-  const size_t smem_limit = 227 * 1024;
-  if (soft::group_smem_bytes(fp32, hp.W, cap1, hp.rw) > smem_limit)
+  const size_t smem_limit = 227 * 1024 - 5 * sizeof(unsigned long long) * soft::kMaxCirc;
+  if (soft::group_smem_bytes(fp32, W, cap1, rw_max) > smem_limit)
     return fail(SOFT_E_ARG, "first_cap too large for the on-chip coefficient map");
-  // caps whose per-shot state does not fit in shared memory rerun from a global-memory slab
-  const bool global_rerun = two_pass && soft::group_smem_bytes(fp32, hp.W, cap, hp.rw) > smem_limit;
-  cudaError_t e = cudaSetDevice(c->device);
+  const bool global_rerun = two_pass && soft::group_smem_bytes(fp32, W, cap_max, rw_max) > smem_limit;
+  const int dev = circs[0]->device;
+  cudaError_t e = cudaSetDevice(dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
 
   soft_run *r = new (std::nothrow) soft_run();
   if (!r) return fail(SOFT_E_OOM, "host allocation failed");
-  r->c = c;
   r->stream = (cudaStream_t)o.stream;
-  r->n_shots = n_shots;
-  const uint64_t chunk = o.chunk_shots ? o.chunk_shots : std::min<uint64_t>(kDefaultChunk, std::max<uint64_t>(n_shots, 1));
+  r->n_circ = n_circ;
+  r->circs.assign(circs, circs + n_circ);
+  r->n_shots.assign(n_shots, n_shots + n_circ);
+  const uint64_t chunk = o.chunk_shots ? o.chunk_shots : std::min<uint64_t>(kDefaultChunk, std::max<uint64_t>(total, 1));
   if (chunk > 0xFFFFFFFFull) {
     soft_run_free(r);
     return fail(SOFT_E_ARG, "chunk_shots must be < 2^32");
   }
-  r->out_limit = o.record_mode == SOFT_REC_ALL ? n_shots : (o.record_mode == SOFT_REC_FIRST_K ? std::min(o.record_k, n_shots) : 0);
-  r->st_limit = std::min<uint64_t>(o.capture_k, n_shots);
-  r->st_stride = cap;
+  const uint64_t n0 = n_shots[0];
+  r->out_limit = o.record_mode == SOFT_REC_ALL ? n0 : (o.record_mode == SOFT_REC_FIRST_K ? std::min(o.record_k, n0) : 0);
+  r->st_limit = std::min<uint64_t>(o.capture_k, n0);
+  r->st_stride = circs[0]->hp.cap;
+  cudaStream_t st = r->stream;
 #define SOFT_ALLOC(ptr, bytes)                                                                  \
   do {                                                                                          \
     if ((e = cudaMalloc(&(ptr), (bytes))) != cudaSuccess) {                                     \
@@ -206,19 +250,15 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
                                             : cuda_fail(e, "cudaMalloc");                       \
     }                                                                                           \
   } while (0)
-  SOFT_ALLOC(r->d_tally, 5 * sizeof(unsigned long long));
+  SOFT_ALLOC(r->d_tally, 5 * n_circ * sizeof(unsigned long long));
   SOFT_ALLOC(r->d_work, 8 * sizeof(unsigned long long));
-  if ((e = cudaMemsetAsync(r->d_work, 0, 8 * sizeof(unsigned long long), (cudaStream_t)o.stream)) != cudaSuccess) {
-    soft_run_free(r);
-    return cuda_fail(e, "cudaMemsetAsync");
-  }
   if (two_pass) SOFT_ALLOC(r->d_rerun, chunk * sizeof(uint32_t));
   uint32_t slab_blocks = 0;
   if (global_rerun) {
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     slab_blocks = (uint32_t)(sms > 0 ? sms : 1);
-    SOFT_ALLOC(r->d_slab, soft::global_slab_bytes(fp32, hp.W, cap, hp.rw, slab_blocks));
+    SOFT_ALLOC(r->d_slab, soft::global_slab_bytes(fp32, W, cap_max, rw_max, slab_blocks));
   }
   if (r->out_limit) {
     if (o.d_status) r->d_status = o.d_status;
@@ -228,7 +268,7 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
     }
     if (o.d_records) r->d_records = o.d_records;
     else {
-      SOFT_ALLOC(r->d_records, r->out_limit * hp.rw * sizeof(uint64_t));
+      SOFT_ALLOC(r->d_records, r->out_limit * circs[0]->hp.rw * sizeof(uint64_t));
       r->own_records = true;
     }
   }
@@ -243,75 +283,123 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
     soft_run_free(r);
     return cuda_fail(e, "cudaEventCreate");
   }
-  cudaStream_t st = r->stream;
-  if ((e = cudaMemsetAsync(r->d_tally, 0, 5 * sizeof(unsigned long long), st)) != cudaSuccess) {
+  if ((e = cudaMemsetAsync(r->d_tally, 0, 5 * n_circ * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(r->d_work, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess) {
     soft_run_free(r);
     return cuda_fail(e, "cudaMemsetAsync");
   }
+  // launch parameters: one descriptor per circuit, items laid out circuit after circuit
+  soft::ShotParams p{};
+  p.n_circ = n_circ;
+  uint64_t begin = 0;
+  for (uint32_t i = 0; i < n_circ; ++i) {
+    p.circ[i] = circ_desc(circs[i]);
+    p.circ[i].item_begin = begin;
+    p.circ[i].n_shots = n_shots[i];
+    p.circ[i].first_shot = first_shots[i];
+    p.circ[i].tally = r->d_tally + 5 * i;
+    begin += n_shots[i];
+  }
+  p.circ[0].status = r->d_status;
+  p.circ[0].records = r->d_records;
+  p.circ[0].out_limit = r->out_limit;
+  p.rw_max = rw_max;
+  p.tau = fp32 ? kTauFp32 : kTauFp64;
+  p.seed = seed;
+  p.next_item = r->d_work;
+  p.rerun = r->d_rerun;
+  p.rerun_cap = two_pass ? (uint32_t)chunk : 0u;
+  p.n_rerun = r->d_work + 2;
+  p.diag = r->d_work + 4;
+  p.groups_per_block = o.groups_per_block;
+  if (r->st_limit) {
+    p.st_limit = r->st_limit;
+    p.st_signs = r->d_st_signs;
+    p.st_keys = r->d_st_keys;
+    p.st_vals = r->d_st_vals;
+    p.st_nnz = r->d_st_nnz;
+    p.st_stride = r->st_stride;
+  }
+  p.cap = cap1;
+  p.hs_max = soft::hash_slots_for(cap1);
+  p.small_pass = two_pass ? 1 : 0;
+  soft::ShotParams q = p;
+  q.cap = cap_max;
+  q.hs_max = soft::hash_slots_for(cap_max);
+  q.small_pass = 0;
+  q.list = r->d_rerun;
+  q.n_items_dev = r->d_work + 2;
+  q.next_item = r->d_work + 1;
+  if (global_rerun) {
+    q.gslab = r->d_slab;
+    q.gslab_blocks = slab_blocks;
+  }
+  soft::LaunchCfg c1{}, c2{};
+  p.n_items = std::min(chunk, total);
+  if ((e = soft::prepare_shots(p, fp32, W, g1, (int)o.blocks_per_sm, &c1)) != cudaSuccess ||
+      (two_pass && (e = soft::prepare_shots(q, fp32, W, g2, (int)o.blocks_per_sm, &c2)) != cudaSuccess)) {
+    soft_run_free(r);
+    return cuda_fail(e, "shot kernel configuration");
+  }
   cudaEventRecord(r->ev0, st);
-  for (uint64_t s0 = 0; s0 < n_shots; s0 += chunk) {
-    const uint64_t cnt = std::min(chunk, n_shots - s0);
-    if ((e = cudaMemsetAsync(r->d_work, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) {
-      soft_run_free(r);
-      return cuda_fail(e, "cudaMemsetAsync");
-    }
-    soft::ShotParams p{};
-    p.ev = c->d_ev;
-    p.coef = c->d_coef;
-    p.cb = c->d_cb;
-    p.sites = c->d_sites;
-    p.thr = c->d_thr;
-    p.n_events = (uint32_t)hp.ev.size();
-    p.n_sites = hp.n_sites;
-    p.rw = hp.rw;
-    p.n_coef = (uint32_t)hp.coefs.size();
-    p.n_cb = (uint32_t)hp.cb.size();
-    p.rerun_cap = two_pass ? (uint32_t)chunk : 0u;
-    p.diag = r->d_work + 4;
-    p.tau = fp32 ? kTauFp32 : kTauFp64;
-    p.seed = seed;
-    p.first_shot = first_shot + s0;
-    p.n_items = cnt;
-    p.next_item = r->d_work;
-    p.tally = r->d_tally;
-    p.rerun = r->d_rerun;
-    p.n_rerun = r->d_work + 2;
-    if (r->out_limit > s0) {
-      p.out_limit = r->out_limit - s0;
-      p.status = r->d_status + s0;
-      p.records = r->d_records + s0 * hp.rw;
-    }
-    if (r->st_limit > s0) {
-      p.st_limit = r->st_limit - s0;
-      p.st_signs = r->d_st_signs + s0 * 4;
-      p.st_keys = r->d_st_keys + s0 * r->st_stride * 2;
-      p.st_vals = r->d_st_vals + s0 * r->st_stride * 2;
-      p.st_nnz = r->d_st_nnz + s0;
-      p.st_stride = r->st_stride;
-    }
-    p.cap = cap1;
-    p.small_pass = two_pass ? 1 : 0;
-    if ((e = soft::launch_shots(p, fp32, hp.W, g1, (int)o.blocks_per_sm, st, nullptr)) != cudaSuccess) {
-      soft_run_free(r);
-      return cuda_fail(e, "shot kernel launch");
-    }
+  // one chunk of items [base, base + cnt): clear counters, first pass, rerun pass
+  auto enqueue_chunk = [&](uint64_t base, uint64_t cnt, bool dev_base) -> cudaError_t {
+    cudaError_t err;
+    if ((err = cudaMemsetAsync(r->d_work, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
+    soft::ShotParams a = p, b = q;
+    a.n_items = b.n_items = cnt;
+    a.item_base = b.item_base = base;
+    if (dev_base) a.item_base_dev = b.item_base_dev = r->d_work + 3;
+    if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
     r->launches++;
     if (two_pass) {
-      soft::ShotParams q = p;
-      q.cap = cap;
-      q.small_pass = 0;
-      q.list = r->d_rerun;
-      q.n_items_dev = r->d_work + 2;
-      q.next_item = r->d_work + 1;
-      if (global_rerun) {
-        q.gslab = r->d_slab;
-        q.gslab_blocks = slab_blocks;
-      }
-      if ((e = soft::launch_shots(q, fp32, hp.W, g2, (int)o.blocks_per_sm, st, nullptr)) != cudaSuccess) {
-        soft_run_free(r);
-        return cuda_fail(e, "rerun kernel launch");
-      }
+      if ((err = soft::launch_prepared(c2, b, st)) != cudaSuccess) return err;
       r->launches++;
+    }
+    return cudaSuccess;
+  };
+  uint64_t s0 = 0;
+  const uint64_t n_full = total / chunk;
+  if (use_graph && n_full >= 2) {
+    // capture one full chunk plus the device-side advance of the item base, replay it
+    unsigned long long zero = 0;
+    if ((e = cudaMemcpyAsync(r->d_work + 3, &zero, sizeof zero, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      soft_run_free(r);
+      return cuda_fail(e, "graph set-up");
+    }
+    const uint32_t launches_before = r->launches;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      soft_run_free(r);
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    cudaError_t ce = enqueue_chunk(0, chunk, true);
+    if (ce == cudaSuccess) ce = soft::launch_advance(r->d_work + 3, chunk, st);
+    e = cudaStreamEndCapture(st, &r->graph);
+    if (ce != cudaSuccess || e != cudaSuccess) {
+      soft_run_free(r);
+      return cuda_fail(ce != cudaSuccess ? ce : e, "graph capture");
+    }
+    if ((e = cudaGraphInstantiate(&r->graph_exec, r->graph, 0)) != cudaSuccess) {
+      soft_run_free(r);
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    const uint32_t per_chunk = r->launches - launches_before + 1;  // + the advance kernel
+    r->launches = launches_before;
+    for (uint64_t k = 0; k < n_full; ++k) {
+      if ((e = cudaGraphLaunch(r->graph_exec, st)) != cudaSuccess) {
+        soft_run_free(r);
+        return cuda_fail(e, "cudaGraphLaunch");
+      }
+      r->launches += per_chunk;
+    }
+    s0 = n_full * chunk;
+  }
+  for (; s0 < total; s0 += chunk) {
+    const uint64_t cnt = std::min(chunk, total - s0);
+    if ((e = enqueue_chunk(s0, cnt, false)) != cudaSuccess) {
+      soft_run_free(r);
+      return cuda_fail(e, "shot kernel launch");
     }
   }
   cudaEventRecord(r->ev1, st);
@@ -319,10 +407,25 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
   return SOFT_OK;
 }
 
-int soft_tally(soft_run *r, soft_tally_t *out) {
-  if (!r || !out) return fail(SOFT_E_ARG, "null argument");
+}  // namespace
+
+extern "C" {
+
+int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, const soft_run_opts *opts,
+                   soft_run **out) {
+  if (!c || !out) return fail(SOFT_E_ARG, "null argument");
+  return run_many(&c, &n_shots, &first_shot, 1, seed, opts, out);
+}
+
+int soft_run_batch(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t *first_shots, uint32_t n_circ,
+                   uint64_t seed, const soft_run_opts *opts, soft_run **out) {
+  return run_many(circs, n_shots, first_shots, n_circ, seed, opts, out);
+}
+
+int soft_tally_batch(soft_run *r, uint32_t index, soft_tally_t *out) {
+  if (!r || !out || index >= r->n_circ) return fail(SOFT_E_ARG, "bad argument");
   unsigned long long t[5];
-  cudaError_t e = cudaMemcpyAsync(t, r->d_tally, sizeof t, cudaMemcpyDeviceToHost, r->stream);
+  cudaError_t e = cudaMemcpyAsync(t, r->d_tally + 5 * index, sizeof t, cudaMemcpyDeviceToHost, r->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
   if (e != cudaSuccess) return cuda_fail(e, "tally copy");
   out->shots = t[0];
@@ -335,11 +438,30 @@ int soft_tally(soft_run *r, soft_tally_t *out) {
   return SOFT_OK;
 }
 
+int soft_tally(soft_run *r, soft_tally_t *out) {
+  if (!r || !out) return fail(SOFT_E_ARG, "null argument");
+  std::vector<unsigned long long> t(5 * (size_t)r->n_circ);
+  cudaError_t e = cudaMemcpyAsync(t.data(), r->d_tally, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  r->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tally copy");
+  uint64_t s[5] = {0, 0, 0, 0, 0};
+  for (size_t i = 0; i < t.size(); ++i) s[i % 5] += t[i];
+  out->shots = s[0];
+  out->discarded = s[1];
+  out->overflow = s[2];
+  out->kept = s[3];
+  out->logical_errors = s[4];
+  out->sum_fidelity = 0.0;
+  out->sum_weight = 0.0;
+  return SOFT_OK;
+}
+
 int soft_get_records(soft_run *r, uint64_t *host_words, size_t n_words, uint8_t *host_status, size_t n_status) {
   if (!r) return fail(SOFT_E_ARG, "null argument");
   cudaError_t e = cudaStreamSynchronize(r->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  const size_t rw = r->c->hp.rw;
+  const size_t rw = r->circs[0]->hp.rw;
   if (host_words) {
     size_t n = std::min<size_t>(n_words, r->out_limit * rw);
     if (n && (e = cudaMemcpy(host_words, r->d_records, n * sizeof(uint64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)

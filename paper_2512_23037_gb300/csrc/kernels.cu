@@ -174,6 +174,8 @@ struct Shot {
   uint32_t *ht;
   uint64_t *rec;
   uint32_t slots, hsmask, hsmax, cap, lane;
+  const CircDev *C = nullptr;  // the circuit of the current shot
+  uint32_t ecap = 0;           // min(circuit cap, on-chip cap): |v| above it ends or reruns the shot
   mutable uint32_t bad_slot = 0;  // set by lookup() when the hash index holds an impossible slot
   uint64_t shot;
   uint32_t nnz;
@@ -196,6 +198,7 @@ struct Shot {
     keys = reinterpret_cast<uint64_t *>(base + slots * sizeof(Cx<R>));
     ht = reinterpret_cast<uint32_t *>(base + slots * sizeof(Cx<R>) + (size_t)W * slots * 8);
     rec = reinterpret_cast<uint64_t *>(base + slots * sizeof(Cx<R>) + (size_t)W * slots * 8 + 4 * (size_t)hsmax);
+    (void)P.rw_max;
   }
   // hash size for n live entries: power of two >= 4 n, at least 16, at most hsmax
   __device__ __forceinline__ uint32_t hs_for(uint32_t n) const {
@@ -285,27 +288,29 @@ struct Shot {
 
   // ---- noise: next accepted error site (geometric gaps, then thinning)
   __device__ void draw_next() {
-    for (uint32_t guard = 0; guard <= P.n_sites; ++guard) {
-      if (cur >= P.n_sites) {
+    const uint32_t n_sites = C->n_sites;
+    const uint64_t *thr = C->thr;
+    for (uint32_t guard = 0; guard <= n_sites; ++guard) {
+      if (cur >= n_sites) {
         nxt = 0xFFFFFFFFu;
         return;
       }
       uint4 w = philox(P.seed, shot, 0u, kblk++);
       uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
-      uint32_t rem = P.n_sites - cur, lo = 0, hi = rem;
+      uint32_t rem = n_sites - cur, lo = 0, hi = rem;
       while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
-        if (U < __ldg(&P.thr[mid])) hi = mid;
+        if (U < __ldg(&thr[mid])) hi = mid;
         else lo = mid + 1u;
       }
       if (lo == rem) {
-        cur = P.n_sites;
+        cur = n_sites;
         nxt = 0xFFFFFFFFu;
         return;
       }
       uint32_t s = cur + lo;
       cur = s + 1u;
-      const Site *st = P.sites + s;
+      const Site *st = C->sites + s;
       if (!__ldg(&st->always) && !(w.w < __ldg(&st->thin))) continue;
       nxt = s;
       w2 = w.z;
@@ -334,11 +339,11 @@ struct Shot {
   }
 
   __device__ void apply_error(uint32_t s) {
-    if (s >= P.n_sites) {
+    if (s >= C->n_sites) {
       fail_check(CHK_SITE, s);
       return;
     }
-    const Site *S = P.sites + s;
+    const Site *S = C->sites + s;
     uint32_t two = __ldg(&S->two), code, pa, pb;
     if (two) {
       code = (uint32_t)(((uint64_t)w2 * 15u) >> 32) + 1u;
@@ -366,7 +371,7 @@ struct Shot {
     apply_pauli(beta, gamma, e);
   }
 
-  __device__ void fail_capacity() { status = P.small_pass ? ST_RERUN : ST_OVF; }
+  __device__ void fail_capacity() { status = (P.small_pass && C->cap > cap) ? ST_RERUN : ST_OVF; }
 
   // Record the first failed bounds check of the launch and end the shot as ERROR.
   uint32_t cur_ev = 0;
@@ -480,7 +485,7 @@ struct Shot {
         rv = nv;
       }
       if (prune) reg_compact(lane < nnz && norm2(rv) >= tau);
-      if (nnz > cap) fail_capacity();
+      if (nnz > ecap) fail_capacity();
       return;
     }
     // more than 32 entries: continue in shared memory with the hash index
@@ -497,7 +502,7 @@ struct Shot {
     reg = false;
     nnz += nA;
     if (prune) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
-    if (nnz > cap) {
+    if (nnz > ecap) {
       fail_capacity();
       return;
     }
@@ -558,7 +563,7 @@ struct Shot {
   }
 
   __device__ void set_record(uint32_t r, int m) {
-    if (r >= 64u * P.rw) {
+    if (r >= 64u * C->rw) {
       fail_check(CHK_RECORD, r);
       return;
     }
@@ -568,14 +573,14 @@ struct Shot {
 
   // ---- a I + b Z_q, beta != 0
   __device__ __forceinline__ void coef(uint32_t ci, Cx<R> &a, Cx<R> &b) const {
-    const Coef *C = P.coef + (ci < P.n_coef ? ci : 0u);
+    const Coef *cf = C->coef + (ci < C->n_coef ? ci : 0u);
     if (sizeof(R) == 4) {
-      float4 f = __ldg(reinterpret_cast<const float4 *>(&C->fa_re));
+      float4 f = __ldg(reinterpret_cast<const float4 *>(&cf->fa_re));
       a = Cx<R>{(R)f.x, (R)f.y};
       b = Cx<R>{(R)f.z, (R)f.w};
     } else {
-      double2 d0 = __ldg(reinterpret_cast<const double2 *>(&C->a_re));
-      double2 d1 = __ldg(reinterpret_cast<const double2 *>(&C->b_re));
+      double2 d0 = __ldg(reinterpret_cast<const double2 *>(&cf->a_re));
+      double2 d1 = __ldg(reinterpret_cast<const double2 *>(&cf->b_re));
       a = Cx<R>{(R)d0.x, (R)d0.y};
       b = Cx<R>{(R)d1.x, (R)d1.y};
     }
@@ -587,7 +592,7 @@ struct Shot {
     for (int w = 0; w < W; ++w) pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
     const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
     const uint32_t lowbit = ev_lowbit(w0);
-    if (ci >= P.n_coef) {
+    if (ci >= C->n_coef) {
       fail_check(CHK_COEF, ci);
       return;
     }
@@ -651,7 +656,7 @@ struct Shot {
     }
     bool pruned = t.any(prune);
     if (pruned) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
-    if (nnz > cap) {
+    if (nnz > ecap) {
       fail_capacity();
       return;
     }
@@ -737,11 +742,11 @@ struct Shot {
 
   // ---- Z measurement, beta != 0 (case B)
   __device__ int meas_b(uint32_t ord, uint32_t cbi) {
-    if (cbi >= P.n_cb) {
+    if (cbi >= C->n_cb) {
       fail_check(CHK_CASEB, cbi);
       return 1;
     }
-    const CaseB *B = P.cb + cbi;
+    const CaseB *B = C->cb + cbi;
     const uint32_t p = __ldg(&B->p);
     uint64_t J[W], g2[W], ep[W];
 #pragma unroll
@@ -841,7 +846,7 @@ struct Shot {
   }
 
   __device__ uint32_t rec_bit(int32_t r) const {
-    return (r < 0 || (uint32_t)r >= 64u * P.rw) ? 0u : (uint32_t)((rec[r >> 6] >> (r & 63)) & 1ull);
+    return (r < 0 || (uint32_t)r >= 64u * C->rw) ? 0u : (uint32_t)((rec[r >> 6] >> (r & 63)) & 1ull);
   }
 
   __device__ void run(uint64_t s) {
@@ -857,7 +862,8 @@ struct Shot {
     Key<W> z;
 #pragma unroll
     for (int w = 0; w < W; ++w) z.w[w] = 0ull;
-    for (uint32_t w = lane; w < P.rw; w += G) rec[w] = 0ull;
+    ecap = C->cap < cap ? C->cap : cap;
+    for (uint32_t w = lane; w < C->rw; w += G) rec[w] = 0ull;
     if (kRegCapable) {
       reg = true;
       rk = z;
@@ -875,8 +881,9 @@ struct Shot {
     cur = 0;
     kblk = 0;
     draw_next();
-    const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(P.ev);
-    for (uint32_t ev = 0; ev < P.n_events && status == ST_RUN; ++ev) {
+    const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
+    const uint32_t n_events = C->n_events;
+    for (uint32_t ev = 0; ev < n_events && status == ST_RUN; ++ev) {
       cur_ev = ev;
       const Ev<W> *E = evs + ev;
       const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
@@ -955,30 +962,28 @@ struct Shot {
     if (status == ST_RUN) status = ST_KEPT;
   }
 
-  __device__ void finish(uint64_t off, unsigned long long *btally) {
+  __device__ void finish(uint64_t local, uint64_t off, uint32_t ci, unsigned long long (*btally)[5]) {
     if (status == ST_RERUN) {
       if (lane == 0) {
         unsigned long long i = atomicAdd(P.n_rerun, 1ull);
-        if (i < P.rerun_cap) P.rerun[i] = (uint32_t)off;
+        if (i < P.rerun_cap) P.rerun[i] = (uint32_t)local;
       }
       t.sync();
       return;
     }
     if (lane == 0) {
-      atomicAdd(&btally[0], 1ull);
-      if (status == ST_DISC) atomicAdd(&btally[1], 1ull);
-      else if (status == ST_OVF) atomicAdd(&btally[2], 1ull);
+      atomicAdd(&btally[ci][0], 1ull);
+      if (status == ST_DISC) atomicAdd(&btally[ci][1], 1ull);
+      else if (status == ST_OVF) atomicAdd(&btally[ci][2], 1ull);
       else if (status == ST_KEPT) {
-        atomicAdd(&btally[3], 1ull);
-        if (logical) atomicAdd(&btally[4], 1ull);
+        atomicAdd(&btally[ci][3], 1ull);
+        if (logical) atomicAdd(&btally[ci][4], 1ull);
       }
-      if (off < P.out_limit) {
-        if (P.status) P.status[off] = (uint8_t)status;
-      }
+      if (off < C->out_limit && C->status) C->status[off] = (uint8_t)status;
     }
-    if (off < P.out_limit && P.records)
-      for (uint32_t w = lane; w < P.rw; w += G) P.records[off * P.rw + w] = rec[w];
-    if (off < P.st_limit) {
+    if (off < C->out_limit && C->records)
+      for (uint32_t w = lane; w < C->rw; w += G) C->records[off * C->rw + w] = rec[w];
+    if (ci == 0 && off < P.st_limit) {
       if (kRegCapable && reg) reg_spill();
       if (lane == 0) {
         P.st_nnz[off] = nnz;
@@ -1011,46 +1016,63 @@ constexpr int kBlock = 128;
 #endif
 
 template <typename R, int W, int G>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 : SOFT_MIN_BLOCKS_F64) shot_kernel(const __grid_constant__ ShotParams P) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 : SOFT_MIN_BLOCKS_F64) shot_kernel(
+    const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long btally[5];
+  __shared__ unsigned long long btally[kMaxCirc][5];
   auto block = cg::this_thread_block();
   auto tile = cg::tiled_partition<G>(block);
-  if (threadIdx.x < 5) btally[threadIdx.x] = 0ull;
+  const uint32_t n_circ = P.n_circ < (uint32_t)kMaxCirc ? P.n_circ : (uint32_t)kMaxCirc;
+  for (uint32_t i = threadIdx.x; i < 5 * n_circ; i += blockDim.x) btally[i / 5][i % 5] = 0ull;
   __syncthreads();
   const uint32_t gid = threadIdx.x / G;  // blockDim.x is a multiple of G
-  const size_t gbytes = group_bytes<R, W>(P.cap, P.rw);
+  const size_t gbytes = group_bytes<R, W>(P.cap, P.rw_max);
   unsigned char *base = P.gslab ? P.gslab + ((size_t)blockIdx.x * (blockDim.x / G) + gid) * gbytes
                                 : smem + (size_t)gid * gbytes;
   Shot<R, W, G> s(tile, P, base);
   const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
+  const unsigned long long item_base = P.item_base_dev ? *P.item_base_dev : P.item_base;
   for (;;) {
     unsigned long long item = 0;
     if (tile.thread_rank() == 0) item = atomicAdd(P.next_item, 1ull);
     item = tile.shfl(item, 0);
     if (item >= n_items) break;
     if (P.list && item >= P.rerun_cap) break;  // a list never holds more than its capacity
-    const uint64_t off = P.list ? (uint64_t)P.list[item] : (uint64_t)item;
-    s.run(P.first_shot + off);
-    s.finish(off, btally);
+    const uint64_t local = P.list ? (uint64_t)P.list[item] : (uint64_t)item;
+    const uint64_t g = item_base + local;
+    // circuit of item g: the last one whose item range starts at or before g
+    uint32_t lo = 0, hi = n_circ;
+    while (hi - lo > 1u) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (P.circ[mid].item_begin <= g) lo = mid;
+      else hi = mid;
+    }
+    s.C = &P.circ[lo];
+    const uint64_t off = g - s.C->item_begin;
+    s.run(s.C->first_shot + off);
+    s.finish(local, off, lo, btally);
   }
   __syncthreads();
-  if (threadIdx.x < 5 && btally[threadIdx.x]) atomicAdd(&P.tally[threadIdx.x], btally[threadIdx.x]);
+  for (uint32_t i = threadIdx.x; i < 5 * n_circ; i += blockDim.x)
+    if (btally[i / 5][i % 5]) atomicAdd(&P.circ[i / 5].tally[i % 5], btally[i / 5][i % 5]);
 }
 
+__global__ void advance_kernel(unsigned long long *item_base, unsigned long long step) { *item_base += step; }
+
 template <typename R, int W, int G>
-cudaError_t launch_t(const ShotParams &p0, int blocks_per_sm, cudaStream_t stream, int *grid_out) {
-  ShotParams p = p0;
-  p.hs_max = hash_slots(p.cap);
+cudaError_t prepare_t(const ShotParams &p, int blocks_per_sm, LaunchCfg *cfg) {
   auto kern = shot_kernel<R, W, G>;
-  const size_t gb = group_bytes<R, W>(p.cap, p.rw);
-  const size_t limit = 227 * 1024;
+  const size_t gb = group_bytes<R, W>(p.cap, p.rw_max);
+  const size_t limit = 227 * 1024 - sizeof(unsigned long long) * 5 * kMaxCirc;
   size_t gpb = kBlock / G;
+  if (p.groups_per_block && p.groups_per_block < gpb) gpb = p.groups_per_block;
+  cfg->kern = reinterpret_cast<const void *>(kern);
   if (p.gslab) {
     if (!p.gslab_blocks) return cudaErrorInvalidValue;
-    if (grid_out) *grid_out = (int)p.gslab_blocks;
-    kern<<<p.gslab_blocks, (unsigned)(gpb * G), 0, stream>>>(p);
-    return cudaGetLastError();
+    cfg->grid = p.gslab_blocks;
+    cfg->block = (unsigned)(gpb * G);
+    cfg->smem = 0;
+    return cudaSuccess;
   }
   while (gpb > 1 && gpb * gb > limit) gpb >>= 1;
   if (gpb * gb > limit) return cudaErrorInvalidConfiguration;
@@ -1075,12 +1097,18 @@ cudaError_t launch_t(const ShotParams &p0, int blocks_per_sm, cudaStream_t strea
     long long need = ((long long)p.n_items + groups - 1) / groups;
     if (need < grid) grid = need > 0 ? need : 1;
   }
-  if (grid_out) *grid_out = (int)grid;
-  kern<<<(unsigned)grid, block, smem, stream>>>(p);
-  return cudaGetLastError();
+  cfg->grid = (unsigned)grid;
+  cfg->block = (unsigned)block;
+  cfg->smem = smem;
+  return cudaSuccess;
 }
 
 }  // namespace
+
+cudaError_t launch_advance(unsigned long long *item_base, unsigned long long step, cudaStream_t stream) {
+  advance_kernel<<<1, 1, 0, stream>>>(item_base, step);
+  return cudaGetLastError();
+}
 
 size_t global_slab_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw, uint32_t blocks) {
   return group_smem_bytes(fp32, W, cap, rw) * (size_t)(kBlock / 32) * blocks;
@@ -1091,9 +1119,9 @@ size_t group_smem_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw) {
   return W == 1 ? group_bytes<double, 1>(cap, rw) : group_bytes<double, 2>(cap, rw);
 }
 
-cudaError_t launch_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t group, int blocks_per_sm,
-                         cudaStream_t stream, int *grid_out) {
-#define SOFT_DISPATCH(R, WW, GG) return launch_t<R, WW, GG>(p, blocks_per_sm, stream, grid_out)
+cudaError_t prepare_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t group, int blocks_per_sm,
+                          LaunchCfg *cfg) {
+#define SOFT_DISPATCH(R, WW, GG) return prepare_t<R, WW, GG>(p, blocks_per_sm, cfg)
   if (fp32) {
     if (W == 1) {
       if (group == 8) SOFT_DISPATCH(float, 1, 8);
@@ -1110,5 +1138,23 @@ cudaError_t launch_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t gro
   SOFT_DISPATCH(double, 2, 32);
 #undef SOFT_DISPATCH
 }
+
+cudaError_t launch_prepared(const LaunchCfg &cfg, const ShotParams &p, cudaStream_t stream) {
+  void *args[] = {const_cast<ShotParams *>(&p)};
+  return cudaLaunchKernel(cfg.kern, dim3(cfg.grid), dim3(cfg.block), args, cfg.smem, stream);
+}
+
+cudaError_t launch_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t group, int blocks_per_sm,
+                         cudaStream_t stream, int *grid_out) {
+  LaunchCfg cfg{};
+  ShotParams q = p;
+  q.hs_max = hash_slots(q.cap);
+  cudaError_t e = prepare_shots(q, fp32, W, group, blocks_per_sm, &cfg);
+  if (e != cudaSuccess) return e;
+  if (grid_out) *grid_out = (int)cfg.grid;
+  return launch_prepared(cfg, q, stream);
+}
+
+uint32_t hash_slots_for(uint32_t cap) { return hash_slots(cap); }
 
 }  // namespace soft

@@ -8,32 +8,47 @@
 
 namespace soft {
 
-struct ShotParams {
-  // compiled program (device)
+constexpr int kMaxCirc = 64;  // circuits per launch (descriptors travel in the kernel parameters)
+
+// One compiled circuit as seen by a launch. Work items [item_begin,
+// item_begin + n_shots) of the launch's global item range are this circuit's
+// shots first_shot + (item - item_begin).
+struct CircDev {
   const void *ev;  // Ev<W>
   const Coef *coef;
   const CaseB *cb;
   const Site *sites;
   const uint64_t *thr;
-  uint32_t n_events, n_sites, rw, cap;
+  uint32_t n_events, n_sites, rw, cap;  // cap: this circuit's coefficient cap
+  uint32_t n_coef, n_cb, pad0, pad1;
+  uint64_t item_begin, n_shots, first_shot;
+  unsigned long long *tally;  // [5]: shots, discarded, overflow, kept, logical
+  uint8_t *status;            // per shot offset < out_limit
+  uint64_t *records;          // rw words per shot offset < out_limit
+  uint64_t out_limit;
+};
+
+struct ShotParams {
+  uint32_t n_circ;
+  uint32_t cap;     // capacity of the on-chip map of this launch (first pass: small)
+  uint32_t rw_max;  // record words reserved per group
   uint32_t hs_max;  // hash slots per group: power of two >= 4 * cap
   double tau;
-  // work
-  uint64_t seed, first_shot, n_items;  // shots first_shot + [0, n_items) or the list below
-  const unsigned long long *n_items_dev;  // optional: item count read on the device
-  const uint32_t *list;                // optional: shot offsets (relative to first_shot)
-  unsigned long long *next_item;       // work counter (zeroed before launch)
-  int small_pass;                      // 1: |v| > cap marks the shot for a rerun
-  uint32_t *rerun;                     // rerun list (capacity n_items)
+  uint64_t seed;
+  // work: global items item_base + [0, n_items) or item_base + list[0 .. n_items)
+  uint64_t item_base, n_items;
+  const unsigned long long *item_base_dev;  // optional: read on the device (graph replay)
+  const unsigned long long *n_items_dev;    // optional: item count read on the device
+  const uint32_t *list;
+  unsigned long long *next_item;  // work counter (zeroed before launch)
+  int small_pass;                 // 1: a shot whose |v| exceeds cap but not its circuit's cap is rerun
+  uint32_t rerun_cap;
+  uint32_t *rerun;                // rerun list of local items (capacity rerun_cap)
   unsigned long long *n_rerun;
-  // outputs
-  unsigned long long *tally;           // [5]: shots, discarded, overflow, kept, logical
-  uint8_t *status;                     // per shot offset < out_limit
-  uint64_t *records;                   // rw words per shot offset < out_limit
-  uint64_t out_limit;
-  uint64_t *st_signs;                  // 4 words per shot offset < st_limit
-  uint64_t *st_keys;                   // st_stride entries x 2 words
-  double *st_vals;                     // st_stride entries x (re, im)
+  // final GS state of circuit 0's first st_limit shots
+  uint64_t *st_signs;  // 4 words per shot
+  uint64_t *st_keys;   // st_stride entries x 2 words
+  double *st_vals;     // st_stride entries x (re, im)
   uint32_t *st_nnz;
   uint64_t st_limit;
   uint32_t st_stride;
@@ -41,10 +56,10 @@ struct ShotParams {
   // group g of block b uses gslab + (b * groups_per_block + g) * group_bytes
   unsigned char *gslab;
   uint32_t gslab_blocks;
-  // bounds of the program arrays and of the rerun list, for the in-kernel checks
-  uint32_t n_coef, n_cb, rerun_cap;
+  uint32_t groups_per_block;  // 0 = 4 (block of 128 threads for 32-lane groups)
   // first failed in-kernel check: [0] count, [1] code << 32 | event, [2] shot, [3] value
   unsigned long long *diag;
+  CircDev circ[kMaxCirc];
 };
 
 // In-kernel check codes (a failed check ends the shot with SOFT_SHOT_ERROR
@@ -54,14 +69,33 @@ enum : uint32_t {
   CHK_CASEB = 7, CHK_RERUN = 8, CHK_LIST = 9, CHK_PHASE = 10, CHK_NNZ = 11
 };
 
-// Bytes of a global slab for `blocks` 128-thread blocks of 32-lane groups.
-size_t global_slab_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw, uint32_t blocks);
-
 // Bytes of shared memory one shot group needs for capacity `cap`.
 size_t group_smem_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw);
+
+// Bytes of a global slab for `blocks` blocks of 4 32-lane groups.
+size_t global_slab_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw, uint32_t blocks);
+
+// A resolved launch of the shot kernel (kernel, grid, block, dynamic smem).
+struct LaunchCfg {
+  const void *kern;
+  unsigned grid, block;
+  size_t smem;
+};
+
+// Resolve the launch (sets the kernel's shared-memory attribute, queries
+// occupancy). `p.hs_max` must already be hash_slots_for(p.cap). Not a stream
+// operation, so it may run before a stream capture.
+cudaError_t prepare_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t group, int blocks_per_sm,
+                          LaunchCfg *cfg);
+// Launch a prepared configuration on `stream` (capturable).
+cudaError_t launch_prepared(const LaunchCfg &cfg, const ShotParams &p, cudaStream_t stream);
+uint32_t hash_slots_for(uint32_t cap);
 
 // Launch the persistent kernel. group = 8 or 32 lanes per shot.
 cudaError_t launch_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t group, int blocks_per_sm,
                          cudaStream_t stream, int *grid_out);
+
+// Device-side item_base += step (advances graph-replayed chunks).
+cudaError_t launch_advance(unsigned long long *item_base, unsigned long long step, cudaStream_t stream);
 
 }  // namespace soft

@@ -71,29 +71,35 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
   const uint32_t cap = hp.cap, cap1 = cap < soft::kDefaultFirstCap ? cap : soft::kDefaultFirstCap;
   const bool two_pass = cap1 < cap;
   soft::ShotParams p{};
-  p.ev = c->d_ev;
-  p.coef = c->d_coef;
-  p.cb = c->d_cb;
-  p.sites = c->d_sites;
-  p.thr = c->d_thr;
-  p.n_events = (uint32_t)hp.ev.size();
-  p.n_sites = hp.n_sites;
-  p.rw = hp.rw;
-  p.n_coef = (uint32_t)hp.coefs.size();
-  p.n_cb = (uint32_t)hp.cb.size();
-  p.rerun_cap = (uint32_t)kNoallocMaxShots;
-  p.diag = work + 4;
+  p.n_circ = 1;
+  soft::CircDev &d = p.circ[0];
+  d.ev = c->d_ev;
+  d.coef = c->d_coef;
+  d.cb = c->d_cb;
+  d.sites = c->d_sites;
+  d.thr = c->d_thr;
+  d.n_events = (uint32_t)hp.ev.size();
+  d.n_sites = hp.n_sites;
+  d.rw = hp.rw;
+  d.cap = hp.cap;
+  d.n_coef = (uint32_t)hp.coefs.size();
+  d.n_cb = (uint32_t)hp.cb.size();
+  d.item_begin = 0;
+  d.n_shots = n_shots;
+  d.first_shot = first_shot;
+  d.tally = d_tally;
+  d.status = d_status;
+  d.records = d_records;
+  d.out_limit = (d_status || d_records) ? n_shots : 0;
+  p.rw_max = hp.rw;
   p.tau = fp32 ? soft::kTauFp32 : soft::kTauFp64;
   p.seed = seed;
-  p.first_shot = first_shot;
   p.n_items = n_shots;
   p.next_item = work;
-  p.tally = d_tally;
   p.rerun = rerun;
+  p.rerun_cap = (uint32_t)kNoallocMaxShots;
   p.n_rerun = work + 2;
-  p.status = d_status;
-  p.records = d_records;
-  p.out_limit = (d_status || d_records) ? n_shots : 0;
+  p.diag = work + 4;
   p.cap = cap1;
   p.small_pass = two_pass ? 1 : 0;
   if ((e = soft::launch_shots(p, fp32, hp.W, 32u, 0, st, nullptr)) != cudaSuccess)

@@ -222,3 +222,69 @@ def test_global_memory_rerun_forced(soft):
     c, r, rec, st, tal, ref = run_both(soft, circ, noise, 400, 11, "fp64", capture=24, first_cap=2)
     assert compare_records(circ, noise, 11, 0, rec, st, ref, "fp64") <= 1
     compare_states(soft, c, r, circ, noise, 11, 0, 24, "fp64")
+
+
+def _small_batch():
+    """Windowed circuits with different qubit counts, windows (caps), block
+    counts and noise levels."""
+    specs = [(17, 2, 3, 2e-3), (21, 3, 4, 1e-3), (26, 4, 3, 3e-3), (19, 5, 2, 5e-4), (30, 2, 5, 2e-3),
+             (23, 6, 2, 1e-3)]
+    out = []
+    for k, (n, w, blocks, p) in enumerate(specs):
+        circ, noise = C.windowed(300 + k, n_data=n - 4, n_anc=4, blocks=blocks, w=w, n_cliff=30, checks=4, p=p)
+        out.append((circ, noise, 300 + 97 * k))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_matches_single_runs_and_oracle(soft, precision):
+    """One launch over six circuits: per-circuit tallies equal the circuits'
+    own runs, and (FP64) the oracle's."""
+    S = soft
+    batch = _small_batch()
+    circs = [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz, _ in batch]
+    shots = [n for _, _, n in batch]
+    firsts = [1000 * k for k in range(len(batch))]
+    r = S.soft_run_batch(circs, shots, firsts, 21, precision=precision)
+    for i, ((circ, noise, n), h) in enumerate(zip(batch, circs)):
+        tb = S.soft_tally_batch(r, i)
+        r1 = S.soft_run_shots(h, n, firsts[i], 21, precision=precision)
+        t1 = S.soft_tally(r1)
+        key = ("shots", "discarded", "overflow", "kept", "logical_errors")
+        assert [tb[k] for k in key] == [t1[k] for k in key], i
+        if precision == "fp64":
+            ref = oracle.run(circ, circ.n, noise, circ.cap, 21, firsts[i], n, threads=8, records=False)
+            assert [tb[k] for k in key] == ref["tally"], i
+    tot = S.soft_tally(r)
+    assert tot["shots"] == sum(shots)
+
+
+def test_batch_with_global_memory_reruns(soft):
+    """A batch where one circuit's cap (2^12) forces global-memory reruns."""
+    S = soft
+    batch = _small_batch()
+    circs = [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz, _ in batch]
+    shots = [n for _, _, n in batch]
+    r = S.soft_run_batch(circs, shots, [0] * len(batch), 3, precision="fp64", first_cap=4)
+    for i, (circ, noise, n) in enumerate(batch):
+        ref = oracle.run(circ, circ.n, noise, circ.cap, 3, 0, n, threads=8, records=False)
+        t = S.soft_tally_batch(r, i)
+        assert [t["shots"], t["discarded"], t["overflow"], t["kept"], t["logical_errors"]] == ref["tally"], i
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replayed_chunks(soft, precision):
+    """Chunks replayed from one captured CUDA graph give the same records."""
+    import torch
+    S = soft
+    circ, noise = C.workload("w42")
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    stream = torch.cuda.Stream()
+    n, chunk = 5000, 1000
+    r = S.soft_run_shots(c, n, 77, 4, precision=precision, record_mode=S.REC_ALL, chunk_shots=chunk,
+                         stream=stream, graph=True)
+    rec, st = S.soft_get_records(r, n)
+    ms, launches = S.soft_run_timing(r)
+    assert launches >= 5 * 2
+    ref = oracle.run(circ, circ.n, noise, circ.cap, 4, 77, n, threads=8)
+    assert compare_records(circ, noise, 4, 77, rec, st, ref, precision) <= 1
