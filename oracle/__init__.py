@@ -84,6 +84,12 @@ def lib():
             L.or_count_sites.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p,
                                          ctypes.POINTER(ctypes.c_uint32)]
             L.or_count_sites.restype = ctypes.c_uint32
+            L.or_errors.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p,
+                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]
+            L.or_project.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p,
+                                     ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                     ctypes.c_uint32, ctypes.c_int64, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             _lib = L
         return _lib
 
@@ -179,3 +185,55 @@ def trace(ops, n_qubits, noise, cap, seed, shot, stop_after=None, max_events=1 <
     return {"events": ev[:min(int(nev.value), max_events)], "rows_x": rx, "rows_z": rz, "rows_r": rr,
             "keys": keys[:k].copy(), "vals": (vals[0:2 * k:2] + 1j * vals[1:2 * k:2]).copy(),
             "status": int(st.value), "logical": int(lg.value), "records": rec}
+
+
+PROJ_OK, PROJ_OVERFLOW, PROJ_ERROR, PROJ_ZERO = 0, 2, 3, 4
+
+
+def project(ops, n_qubits, noise, cap, seed, pattern, theta=None, shift_op=-1, shift=0.0):
+    """Projection run of the fixed error pattern of shot `pattern`: detector
+    measurements forced to their passing outcome, observable measurements to
+    0, unnormalised. Returns (status, n_acc, n_fid); the post-selected output
+    fidelity is F = n_fid / n_acc."""
+    a = _ops_array(ops)
+    nz = _noise_arr(noise)
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+    na, nf = ctypes.c_double(0), ctypes.c_double(0)
+    st = lib().or_project(a.ctypes.data, len(a), n_qubits, nz.ctypes.data, cap, seed, pattern,
+                          th.ctypes.data if th is not None else None, 0 if th is None else len(th), int(shift_op),
+                          float(shift), ctypes.byref(na), ctypes.byref(nf))
+    return int(st), float(na.value), float(nf.value)
+
+
+def fidelity_grad(ops, n_qubits, noise, cap, seed, pattern, theta):
+    """F and dF/dtheta of one pattern by the parameter-shift rule: the squared
+    norms are trigonometric polynomials of degree 1 in each Rz angle, so
+    d/dx = [N(x + pi/2) - N(x - pi/2)] / 2 per gate occurrence, summed with the
+    occurrence's sign (+theta_k or -theta_k)."""
+    a = _ops_array(ops)
+    st, na, nf = project(a, n_qubits, noise, cap, seed, pattern, theta)
+    if st != PROJ_OK:
+        return st, na, nf, None
+    F = nf / na
+    grad = np.zeros(len(theta))
+    for i in np.nonzero((a["op"] == 10) & (a["pad"] > 0))[0]:
+        k = int(a["pad"][i]) - 1
+        sgn = -1.0 if (a["flags"][i] & 1) else 1.0
+        _, ap, fp = project(a, n_qubits, noise, cap, seed, pattern, theta, int(i), np.pi / 2)
+        _, am, fm = project(a, n_qubits, noise, cap, seed, pattern, theta, int(i), -np.pi / 2)
+        dna, dnf = (ap - am) / 2, (fp - fm) / 2
+        grad[k] += sgn * (dnf - F * dna) / na
+    return st, na, nf, grad
+
+
+def errors(ops, n_qubits, noise, seed, pattern, max_out=4096):
+    """(sites, codes) of every error of shot `pattern`'s noise stream."""
+    a = _ops_array(ops)
+    nz = _noise_arr(noise)
+    sites = np.zeros(max_out, dtype=np.uint32)
+    codes = np.zeros(max_out, dtype=np.uint32)
+    k = lib().or_errors(a.ctypes.data, len(a), n_qubits, nz.ctypes.data, seed, pattern, sites.ctypes.data,
+                        codes.ctypes.data, max_out)
+    if k < 0:
+        raise RuntimeError("bad circuit")
+    return sites[:k].copy(), codes[:k].copy()

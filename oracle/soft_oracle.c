@@ -513,7 +513,13 @@ static pauli error_pauli(const circ *c, uint32_t site, uint32_t word2, const or_
 /* ------------------------------------------------------------------------ */
 
 /* a I + b Z_q (Theorem 1 (3)). Returns status. */
+static int apply_rot_tau(gs_state *st, const circ *c, int q, double complex a, double complex b, double tau,
+                         or_counts *cnt);
 static int apply_rot(gs_state *st, const circ *c, int q, double complex a, double complex b, or_counts *cnt) {
+  return apply_rot_tau(st, c, q, a, b, c->tau, cnt);
+}
+static int apply_rot_tau(gs_state *st, const circ *c, int q, double complex a, double complex b, double tau,
+                         or_counts *cnt) {
   pauli Z = pauli_single(3, q);
   uint64_t beta[MW], gamma[MW];
   int ce;
@@ -530,7 +536,7 @@ static int apply_rot(gs_state *st, const circ *c, int q, double complex a, doubl
     st->e[n0 + i] = t;
   }
   st->ne = 2 * n0;
-  normalize_map(st, c->tau);
+  normalize_map(st, tau);
   if (cnt) {
     if ((beta[0] | beta[1]) == 0) cnt->t_diag_entries += n0;
     else cnt->t_out_entries += st->ne;
@@ -1043,4 +1049,294 @@ uint32_t or_count_sites(const or_op *ops, size_t n_ops, uint32_t n_qubits, const
   if (n_records) *n_records = rc ? 0 : c.n_records;
   circ_free(&c);
   return ns;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection mode: one fixed error pattern, outcomes forced, unnormalised.   */
+/* ------------------------------------------------------------------------ */
+static double sq_norm(const gs_state *st) { return map_norm(st); }
+
+/* Project onto the eigenvalue m of the Hermitian Pauli P without
+ * renormalising: Pi_m = (I + m P)/2 (Eq. Pi_pm). Case B leaves the pairs'
+ * combination (v_a0 + m xi_a1 v_a1)/sqrt(2) in the replaced tableau's basis,
+ * which is Pi_m |phi> expressed there. Returns status. */
+static int project(gs_state *st, const pauli *P, int m, double tau_rel) {
+  uint64_t beta[MW], gamma[MW];
+  int ce;
+  if (decompose(st, P, beta, gamma, &ce)) return OR_ST_ERROR;
+  if ((beta[0] | beta[1]) == 0) {
+    if (ce & 1) return OR_ST_ERROR;
+    int sgn = (ce == 2);
+    size_t o = 0;
+    for (size_t i = 0; i < st->ne; ++i) {
+      uint64_t t[MW];
+      for (int w = 0; w < MW; ++w) t[w] = gamma[w] & st->e[i].k[w];
+      int lam_neg = (popc2(t) & 1) ^ sgn;
+      if ((lam_neg ? -1 : +1) == m) st->e[o++] = st->e[i];
+    }
+    st->ne = o;
+    normalize_map(st, tau_rel * sq_norm(st));
+    return OR_ST_OK;
+  }
+  int n = st->n, p = -1;
+  for (int i = 0; i < n; ++i)
+    if (getbit(beta, i)) {
+      p = i;
+      break;
+    }
+  uint64_t J[MW] = {beta[0], beta[1]};
+  flipbit(J, p);
+  pauli sp_ = row_to_pauli(&st->s[p]);
+  for (int j = 0; j < n; ++j)
+    if (getbit(J, j)) {
+      pauli sj = row_to_pauli(&st->s[j]);
+      pauli prod = pauli_mul(&sj, &sp_);
+      if (pauli_to_row(&prod, &st->s[j])) return OR_ST_ERROR;
+    }
+  pauli dp = row_to_pauli(&st->d[p]);
+  for (int j = 0; j < n; ++j)
+    if (getbit(J, j)) {
+      pauli dj = row_to_pauli(&st->d[j]);
+      dp = pauli_mul(&dp, &dj);
+    }
+  if (pauli_to_row(&dp, &st->d[p])) return OR_ST_ERROR;
+  for (size_t i = 0; i < st->ne; ++i)
+    if (getbit(st->e[i].k, p))
+      for (int w = 0; w < MW; ++w) st->e[i].k[w] ^= J[w];
+  qsort(st->e, st->ne, sizeof(entry), cmp_entry);
+  uint64_t beta2[MW], gamma2[MW];
+  int ce2;
+  if (decompose(st, P, beta2, gamma2, &ce2)) return OR_ST_ERROR;
+  /* combine each a0 with a1 = a0 ^ e_p: new value (v0 + m xi_a1 v1)/sqrt(2) at a0 */
+  size_t n0 = st->ne;
+  entry *out = (entry *)malloc((n0 + 1) * sizeof(entry));
+  if (!out) return OR_ST_ERROR;
+  size_t no = 0;
+  for (size_t i = 0; i < n0; ++i) {
+    entry a0 = st->e[i];
+    int hi = getbit(a0.k, p);
+    if (hi) flipbit(a0.k, p);
+    uint64_t a1k[MW] = {a0.k[0], a0.k[1]};
+    flipbit(a1k, p);
+    double complex add = hi ? (double)m * xi_of(ce2, gamma2, a1k) * st->e[i].v : st->e[i].v;
+    size_t f = no;
+    for (size_t t = 0; t < no; ++t)
+      if (cmp_entry(&out[t], &a0) == 0) {
+        f = t;
+        break;
+      }
+    if (f == no) {
+      out[no] = a0;
+      out[no].v = 0.0;
+      no++;
+    }
+    out[f].v += add / sqrt(2.0);
+  }
+  memcpy(st->e, out, no * sizeof(entry));
+  st->ne = no;
+  free(out);
+  row old_sp = st->s[p];
+  pauli osp = row_to_pauli(&old_sp);
+  for (int j = 0; j < n; ++j)
+    if (j != p && getbit(gamma2, j)) {
+      pauli dj = row_to_pauli(&st->d[j]);
+      pauli prod = pauli_mul(&dj, &osp);
+      if (pauli_to_row(&prod, &st->d[j])) return OR_ST_ERROR;
+    }
+  st->d[p] = old_sp;
+  row newsp;
+  if (pauli_to_row(P, &newsp)) return OR_ST_ERROR;
+  if (m == -1) newsp.r ^= 1;
+  st->s[p] = newsp;
+  normalize_map(st, tau_rel * sq_norm(st));
+  return OR_ST_OK;
+}
+
+/* Outcome of a measurement of P that must be deterministic: +1 / -1, or 0 if
+ * the state is not an eigenstate (case B, or eigenvalues that disagree). */
+static int deterministic_outcome(const gs_state *st, const pauli *P) {
+  uint64_t beta[MW], gamma[MW];
+  int ce;
+  if (decompose(st, P, beta, gamma, &ce)) return 0;
+  if ((beta[0] | beta[1]) != 0 || (ce & 1)) return 0;
+  int sgn = (ce == 2), first = -1;
+  for (size_t i = 0; i < st->ne; ++i) {
+    uint64_t t[MW];
+    for (int w = 0; w < MW; ++w) t[w] = gamma[w] & st->e[i].k[w];
+    int lam_neg = (popc2(t) & 1) ^ sgn;
+    if (first < 0) first = lam_neg;
+    else if (first != lam_neg) return 0;
+  }
+  return first ? -1 : +1;
+}
+
+int or_project(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t cap, uint64_t seed,
+               uint64_t pattern, const double *theta, uint32_t n_theta, int64_t shift_op, double shift, double *n_acc,
+               double *n_fid) {
+  circ c;
+  int rc = circ_build(&c, ops, n_ops, n_qubits, noise, cap);
+  if (rc) {
+    circ_free(&c);
+    return OR_ST_ERROR;
+  }
+  /* record roles: 1 post-selected (single-record detector), 2 fidelity (observable), 3 unsupported */
+  uint8_t *role = (uint8_t *)calloc(c.n_records + 1, 1);
+  uint8_t *target = (uint8_t *)calloc(c.n_records + 1, 1);
+  gs_state *st = (gs_state *)calloc(1, sizeof(gs_state));
+  if (!role || !target || !st) {
+    free(role); free(target); free(st); circ_free(&c);
+    return OR_ST_ERROR;
+  }
+  int chain = 0;
+  for (size_t i = 0; i < n_ops; ++i) {
+    const or_op *o = &ops[i];
+    if (o->op == OR_DETECTOR) {
+      int single = o->rec[0] >= 0 && o->rec[1] < 0 && !(o->flags & OR_FLAG_CHAIN) && !chain;
+      for (int r = 0; r < 2; ++r)
+        if (o->rec[r] >= 0) {
+          if (single) {
+            role[o->rec[r]] = 1;
+            target[o->rec[r]] = (o->flags & OR_FLAG_INVERT) ? 1 : 0;
+          } else {
+            role[o->rec[r]] = 3;
+          }
+        }
+      chain = (o->flags & OR_FLAG_CHAIN) != 0;
+    } else if (o->op == OR_OBSERVABLE) {
+      for (int r = 0; r < 2; ++r)
+        if (o->rec[r] >= 0 && role[o->rec[r]] == 0) role[o->rec[r]] = 2;
+      chain = (o->flags & OR_FLAG_CHAIN) != 0;
+    }
+  }
+  const double tau_rel = 1e-20;
+  init_state(st, c.n);
+  noise_stream ns = {0, 0, UINT32_MAX, 0};
+  next_error(&c, seed, pattern, &ns);
+  uint64_t rb[64];
+  memset(rb, 0, sizeof rb);
+  uint32_t nrec = 0;
+  int status = OR_ST_OK, seen_fid = 0;
+  *n_acc = *n_fid = 0.0;
+  for (size_t i = 0; i < n_ops && status == OR_ST_OK; ++i) {
+    const or_op *o = &ops[i];
+    int op = o->op;
+    status = apply_error_if_due(st, &c, seed, pattern, &ns, c.pre_site[i], i, NULL, NULL);
+    if (status) break;
+    switch (op) {
+      case OR_H: case OR_S: case OR_SDAG: case OR_X: case OR_Y: case OR_Z: case OR_CX: case OR_CZ:
+        apply_clifford(st, op, (int)o->q0, (int)o->q1);
+        break;
+      case OR_T: case OR_TDAG: case OR_RZ: {
+        double complex a, b;
+        double ang = 0.0;
+        if (op == OR_RZ) {
+          ang = o->angle;
+          if (theta && o->pad > 0 && o->pad <= n_theta) ang = ((o->flags & 1) ? -1.0 : 1.0) * theta[o->pad - 1];
+        } else {
+          ang = (op == OR_T) ? kPi / 4.0 : -kPi / 4.0;
+        }
+        if (op == OR_RZ) {
+          if ((int64_t)i == shift_op) ang += shift;
+          a = cos(ang / 2.0);
+          b = -I * sin(ang / 2.0);
+        } else {
+          double complex w = cexp(I * ((op == OR_T) ? kPi : -kPi) / 4.0);
+          a = (1.0 + w) / 2.0;
+          b = (1.0 - w) / 2.0;
+        }
+        int r = apply_rot_tau(st, &c, (int)o->q0, a, b, tau_rel * sq_norm(st), NULL);
+        if (r) status = r;
+        break;
+      }
+      case OR_M: case OR_R: case OR_MR: {
+        pauli Z = pauli_single(3, (int)o->q0);
+        int m;
+        if (op == OR_R) {
+          m = deterministic_outcome(st, &Z);
+          if (m == 0) {
+            status = OR_ST_ERROR;
+            break;
+          }
+        } else {
+          int rl = role[nrec];
+          if (rl == 1) m = target[nrec] ? -1 : +1;
+          else if (rl == 2) {
+            if (!seen_fid) {
+              *n_acc = sq_norm(st);
+              seen_fid = 1;
+            }
+            m = +1;
+          } else {
+            status = OR_ST_ERROR;
+            break;
+          }
+          int r = project(st, &Z, m, tau_rel);
+          if (r) {
+            status = r;
+            break;
+          }
+          if (m == -1) flipbit(rb, (int)nrec);
+          nrec++;
+        }
+        if ((op == OR_R || op == OR_MR) && m == -1) {
+          pauli X = pauli_single(1, (int)o->q0);
+          if (apply_pauli(st, &X, NULL)) status = OR_ST_ERROR;
+        }
+        break;
+      }
+      case OR_CPAULI: {
+        int par = 0;
+        for (int r = 0; r < 2; ++r)
+          if (o->rec[r] >= 0) par ^= getbit(rb, o->rec[r]);
+        if (par && (o->flags & 3)) {
+          pauli q = pauli_single(o->flags & 3, (int)o->q0);
+          if (apply_pauli(st, &q, NULL)) status = OR_ST_ERROR;
+        }
+        break;
+      }
+      default:
+        break;
+    }
+    if (status) break;
+    if (st->ne > c.cap) {
+      status = OR_ST_OVERFLOW;
+      break;
+    }
+    status = apply_error_if_due(st, &c, seed, pattern, &ns, c.post_site[i], i, NULL, NULL);
+  }
+  if (status == OR_ST_OK) {
+    *n_fid = sq_norm(st);
+    if (!seen_fid) *n_acc = *n_fid;
+    if (!(*n_acc > 0.0)) status = 4; /* zero acceptance */
+  }
+  free(role); free(target); free(st->e); free(st); circ_free(&c);
+  return status;
+}
+
+/* The error pattern of shot `pattern`: every accepted error site and its
+ * Pauli code, in site order, from the same noise stream as or_run. */
+int or_errors(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint64_t seed,
+              uint64_t pattern, uint32_t *sites, uint32_t *codes, uint32_t max_out) {
+  circ c;
+  int rc = circ_build(&c, ops, n_ops, n_qubits, noise, 1);
+  if (rc) {
+    circ_free(&c);
+    return -1;
+  }
+  noise_stream ns = {0, 0, UINT32_MAX, 0};
+  next_error(&c, seed, pattern, &ns);
+  uint32_t k = 0;
+  while (ns.site != UINT32_MAX) {
+    uint32_t code;
+    if (c.site_two[ns.site]) code = (uint32_t)(((uint64_t)ns.word2 * 15u) >> 32) + 1u;
+    else code = (uint32_t)(((uint64_t)ns.word2 * 3u) >> 32) + 1u;
+    if (k < max_out) {
+      sites[k] = ns.site;
+      codes[k] = code;
+    }
+    k++;
+    next_error(&c, seed, pattern, &ns);
+  }
+  circ_free(&c);
+  return (int)k;
 }

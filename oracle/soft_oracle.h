@@ -77,6 +77,16 @@ int or_trace(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *
              uint64_t *rows_x, uint64_t *rows_z, uint8_t *rows_r, uint64_t *keys, double *vals, size_t keys_cap,
              size_t *n_keys, uint64_t *records, uint32_t rw, int *status_out, int *logical_out);
 
+/* Projection run of the error pattern of shot `pattern` (see soft_oracle.c).
+ * Returns 0 ok, 2 overflow, 3 unsupported/error, 4 zero acceptance. */
+int or_project(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t cap, uint64_t seed,
+               uint64_t pattern, const double *theta, uint32_t n_theta, int64_t shift_op, double shift, double *n_acc,
+               double *n_fid);
+
+/* Error sites and Pauli codes of shot `pattern`; returns the count. */
+int or_errors(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint64_t seed,
+              uint64_t pattern, uint32_t *sites, uint32_t *codes, uint32_t max_out);
+
 uint32_t or_count_sites(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t *n_records);
 
 #ifdef __cplusplus

@@ -7,7 +7,10 @@ propagates Pauli strings through Clifford gates with lookup tables derived
 here from explicit 2x2 / 4x4 matrices (U P U^dagger), not from tableau rules.
 
 Op record (32 bytes, little endian), shared with the C ABI:
-  op u16, flags u16, q0 u32, q1 u32, pad u32, angle f64, rec i32[2]
+  op u16, flags u16, q0 u32, q1 u32, param u32, angle f64, rec i32[2]
+A parameterised RZ carries param = k + 1 and flags bit 0 = 1 for the angle
+-theta_k (0 for +theta_k); its `angle` field holds the current value used by
+plain runs, and gradient runs substitute the parameter vector.
 
 Noise model (uniform depolarizing, Sec. III of arxiv 2512.23037): DEPOL1(p1)
 after every one-qubit gate (T/T^dagger/Rz included), DEPOL2(p2) after every
@@ -66,9 +69,11 @@ class Circuit:
     def _add(self, op, q0=0, q1=0, flags=0, angle=0.0, rec=(-1, -1)):
         self.ops.append((op, flags, q0, q1, 0, angle, (int(rec[0]), int(rec[1]))))
 
-    def gate(self, op, *qs, angle=0.0):
+    def gate(self, op, *qs, angle=0.0, param=None, negate=False):
         if op in TWO_Q:
             self._add(op, qs[0], qs[1])
+        elif param is not None:
+            self.ops.append((op, 1 if negate else 0, qs[0], 0, int(param) + 1, float(angle), (-1, -1)))
         else:
             self._add(op, qs[0], angle=angle)
 
@@ -349,7 +354,7 @@ def windowed(seed: int, n_data: int = 38, n_anc: int = 4, blocks: int = 18, w: i
             if angs is None:
                 c.gate(T, q)
             else:
-                c.gate(RZ, q, angle=angs[j])
+                c.gate(RZ, q, angle=angs[j], param=pos - w + j)
         # random Clifford C from {CX, CZ, H}
         C = []
         for _ in range(n_cliff):
@@ -402,7 +407,7 @@ def windowed(seed: int, n_data: int = 38, n_anc: int = 4, blocks: int = 18, w: i
             if angs is None:
                 c.gate(T_DAG, q)
             else:
-                c.gate(RZ, q, angle=-angs[j])
+                c.gate(RZ, q, angle=-angs[j], param=pos - w + j, negate=True)
     c.noiseless(True)
     for g in reversed(V):
         c.gate(_inverse_op(g[0]), *g[1:])
@@ -413,6 +418,12 @@ def windowed(seed: int, n_data: int = 38, n_anc: int = 4, blocks: int = 18, w: i
     return c, Noise.uniform(p)
 
 
+def rz_thetas(seed: int = 1, n: int = 72, sigma: float = 0.01):
+    """theta_i = pi/4 + N(0, sigma) (the angles of the differentiation workload)."""
+    rng = np.random.default_rng(seed)
+    return np.pi / 4 + rng.normal(0.0, sigma, size=n)
+
+
 def workload(name: str) -> tuple:
     """Named seeded workloads: 'tiny6' (6 qubits, 4 T, 3 mid-circuit M),
     'w42' (42 qubits, 18 windows of 4, cap 2^8, p=1e-3), 'w97' (97 qubits,
@@ -421,6 +432,8 @@ def workload(name: str) -> tuple:
         return random_layers(0)
     if name == "w42":
         return windowed(1)
+    if name == "w42rz":  # every T / T^dag pair of w42 becomes Rz(+theta_i) / Rz(-theta_i)
+        return windowed(1, rz_angles=rz_thetas(1, 72))
     if name == "w97":
         return windowed(4, n_data=89, n_anc=8, blocks=24, w=6, n_cliff=160, checks=8, p=5e-4,
                         cliff_two_q_frac=0.75)
@@ -446,6 +459,41 @@ def batch_of_windowed(seed: int = 2, n_circuits: int = 64, mean_shots: float = 1
                                checks=4, p=p)
         out.append((circ, noise, shots))
     return out
+
+
+def random_param_circuit(seed: int, n: int, n_ops: int, n_params: int, n_checks: int = 3, p: float = 0.02):
+    """Random circuit whose post-selected fidelity depends on every parameter:
+    H on all qubits, then a mix of Clifford gates and parameterised Rz gates
+    (random parameter, random sign), non-resetting mid-circuit Z measurements
+    each with a detector (random expected parity), and finally Z measurement of
+    every qubit with one observable each (the fidelity measurements)."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(n, name=f"random_param_circuit(n={n},ops={n_ops},seed={seed})", cap=256)
+    for q in range(n):
+        c.gate(H, q)
+    checks_at = set(int(v) for v in rng.choice(np.arange(n_ops // 3, n_ops), size=n_checks, replace=False))
+    for i in range(n_ops):
+        if i in checks_at:
+            r = c.measure(int(rng.integers(n)))
+            c.detector([r], invert=bool(rng.integers(2)))
+        u = rng.random()
+        if u < 0.35:
+            k = int(rng.integers(n_params))
+            neg = bool(rng.integers(2))
+            c.gate(RZ, int(rng.integers(n)), angle=0.0, param=k, negate=neg)
+        elif u < 0.65 and n >= 2:
+            a, b = (int(v) for v in rng.choice(n, size=2, replace=False))
+            c.gate(CX if rng.random() < 0.5 else CZ, a, b)
+        else:
+            c.gate(CLIFFORD_1Q[int(rng.integers(6))], int(rng.integers(n)))
+    for q in range(n):
+        c.gate(H, q)
+    c.noiseless(True)
+    recs = [c.measure(q) for q in range(n)]
+    c.noiseless(False)
+    for r in recs:
+        c.observable([r])
+    return c, Noise.uniform(p)
 
 
 def random_circuit(seed: int, n: int, n_ops: int, t_frac=0.15, meas_frac=0.1, rz=True,

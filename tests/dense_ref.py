@@ -288,3 +288,88 @@ def record_distribution(circ: C.Circuit, noise: C.Noise):
                 raise ValueError("record_distribution handles gates and M only")
         branches = nb
     return {bits: float(np.real(np.trace(rho))) for bits, rho in branches}
+
+
+def project_pattern(circ: C.Circuit, noise: C.Noise, sites, codes, theta=None):
+    """Dense projection run of one error pattern: detector measurements are
+    projected onto their passing outcome, observable measurements onto 0,
+    nothing is renormalised. Returns (n_acc, n_fid) or None when a reset is
+    not deterministic."""
+    n = circ.n
+    layout = site_layout(circ.ops, noise)
+    errs = {layout[int(s)]: int(k) for s, k in zip(sites, codes)}
+    role, target = {}, {}
+    chain = 0
+    for o in circ.ops:
+        op, fl, rec = o[0], o[1], o[6]
+        if op == C.DETECTOR:
+            single = rec[0] >= 0 and rec[1] < 0 and not (fl & C.FLAG_CHAIN) and not chain
+            for r in rec:
+                if r >= 0:
+                    role[r] = 1 if single else 3
+                    target[r] = fl & C.FLAG_INVERT
+            chain = fl & C.FLAG_CHAIN
+        elif op == C.OBSERVABLE:
+            for r in rec:
+                if r >= 0 and r not in role:
+                    role[r] = 2
+            chain = fl & C.FLAG_CHAIN
+    psi = np.zeros(1 << n, complex)
+    psi[0] = 1
+    n_acc = None
+    rec_i = 0
+    bits = {}
+
+    def err(i, where, o):
+        nonlocal psi
+        code = errs.get((i, where))
+        if code is None:
+            return
+        if o[0] in C.TWO_Q and where == "post":
+            psi = apply_pauli_code(psi, n, code >> 2, o[2])
+            psi = apply_pauli_code(psi, n, code & 3, o[3])
+        else:
+            psi = apply_pauli_code(psi, n, code, o[2])
+
+    idx = np.arange(1 << n)
+    for i, o in enumerate(circ.ops):
+        op, fl, q0, q1, prm, ang, rec = o
+        err(i, "pre", o)
+        if op in C.ONE_Q:
+            if op == C.RZ and theta is not None and prm > 0:
+                ang = (-1.0 if fl & 1 else 1.0) * theta[prm - 1]
+            psi = apply_1q(psi, n, q0, one_q_matrix(op, ang))
+        elif op in C.TWO_Q:
+            psi = apply_2q(psi, n, op, q0, q1)
+        elif op in (C.M, C.R, C.MR):
+            one = ((idx >> q0) & 1) == 1
+            if op == C.R:
+                p1 = np.sum(np.abs(psi[one]) ** 2) / np.sum(np.abs(psi) ** 2)
+                if 1e-12 < p1 < 1 - 1e-12:
+                    return None
+                bit = 1 if p1 > 0.5 else 0
+            else:
+                rl = role.get(rec_i, 0)
+                if rl == 1:
+                    bit = target[rec_i]
+                elif rl == 2:
+                    if n_acc is None:
+                        n_acc = float(np.sum(np.abs(psi) ** 2))
+                    bit = 0
+                else:
+                    return None
+                psi = np.where(one if bit else ~one, psi, 0)
+                bits[rec_i] = bit
+                rec_i += 1
+            if op in (C.R, C.MR) and bit == 1:
+                psi = apply_1q(psi, n, q0, PAULI[1])
+        elif op == C.CPAULI:
+            par = 0
+            for r in rec:
+                if r >= 0:
+                    par ^= bits[r]
+            if par and (fl & 3):
+                psi = apply_1q(psi, n, q0, PAULI[fl & 3])
+        err(i, "post", o)
+    n_fid = float(np.sum(np.abs(psi) ** 2))
+    return (n_fid if n_acc is None else n_acc), n_fid
