@@ -233,6 +233,32 @@ void soft_run_free(soft_run *r);
 int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, int32_t precision,
                            void *stream, unsigned long long *d_tally, uint8_t *d_status, uint64_t *d_records);
 
+/* Post-selected output fidelity and its gradient for fixed error patterns
+ * (differentiation of Rz angles; the paper's T gates, Eq. T_gate, with the
+ * angle made a parameter). A pattern is the noise draw of one shot index of
+ * the circuit's noise model (same Philox stream as soft_run_shots). Every
+ * measurement whose record a single-record DETECTOR reads is projected onto
+ * its passing outcome (post-selection as projection, not sampling), every
+ * measurement an OBSERVABLE reads is projected onto 0, resets must be
+ * decided, nothing is renormalised; with phi_pre the state before the first
+ * observable-read measurement and phi_end the final state,
+ *   N_acc = |phi_pre|^2 (the acceptance probability), F = |phi_end|^2 / N_acc.
+ * dF/dtheta_k comes from one forward pass and two reverse (adjoint) sweeps
+ * in the GS basis, one warp per pattern.
+ *   theta: host array of n_params angles; a parameterised RZ (op.pad = k+1,
+ *   flags bit 0 = negated) uses +-theta_k. n_params must cover every k.
+ *   Patterns [first_pattern, first_pattern + n_patterns), key `seed`.
+ *   Caller device buffers: d_fid, d_pacc (n_patterns doubles), d_grad
+ *   (n_patterns x n_params doubles, row-major), d_status (n_patterns bytes:
+ *   0 ok, 1 zero acceptance (skipped, F = 0), 2 unsupported (a map above 32
+ *   entries, an undecided reset, a multi-record detector), 3 error).
+ * Synchronous: returns after the work on `stream` finished. Scratch (the
+ * per-warp tape) is allocated and freed inside the call.
+ * Errors: SOFT_E_ARG, SOFT_E_OOM, SOFT_E_CUDA. */
+int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t n_params, uint64_t n_patterns,
+                       uint64_t first_pattern, uint64_t seed, int32_t precision, void *stream, double *d_fid,
+                       double *d_pacc, double *d_grad, uint8_t *d_status);
+
 const char *soft_last_error(void);
 
 #ifdef __cplusplus

@@ -66,7 +66,7 @@ class _Tally(ctypes.Structure):
 EXPORTED = ["soft_compile_circuit", "soft_circuit_info", "soft_circuit_tableau", "soft_circuit_free",
             "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing",
             "soft_run_free", "soft_run_shots_noalloc", "soft_run_diagnostics", "soft_run_batch",
-            "soft_tally_batch", "soft_last_error"]
+            "soft_tally_batch", "soft_fidelity_grad", "soft_last_error"]
 
 
 def lib_path() -> str:
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
         L.soft_run_diagnostics.argtypes = [vp, vp]
         L.soft_run_batch.argtypes = [vp, vp, vp, u32, u64, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
         L.soft_tally_batch.argtypes = [vp, u32, ctypes.POINTER(_Tally)]
+        L.soft_fidelity_grad.argtypes = [vp, vp, u32, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp, vp]
         L.soft_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -293,3 +294,27 @@ def soft_run_shots_noalloc(circ: Circuit, n_shots: int, first_shot: int, seed: i
                                          ctypes.c_void_p(int(stream) if stream else 0),
                                          ctypes.c_void_p(int(d_tally)), ctypes.c_void_p(int(d_status or 0)),
                                          ctypes.c_void_p(int(d_records or 0))))
+
+
+def soft_fidelity_grad(circ: Circuit, theta, n_patterns: int, first_pattern: int = 0, seed: int = 0,
+                       precision="fp64", stream=None):
+    """Post-selected fidelity F, acceptance N_acc, dF/dtheta and status of
+    fixed error patterns (see include/soft.h). Returns torch tensors on the
+    current CUDA device: F (n,), p_acc (n,), grad (n, n_params), status (n,)."""
+    import torch
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+    n = int(n_patterns)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fid = torch.zeros(n, dtype=torch.float64, device=dev)
+    pacc = torch.zeros(n, dtype=torch.float64, device=dev)
+    grad = torch.zeros((n, len(th)), dtype=torch.float64, device=dev)
+    status = torch.zeros(n, dtype=torch.uint8, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(load().soft_fidelity_grad(circ.h, th.ctypes.data if len(th) else None, len(th), n, int(first_pattern),
+                                     int(seed) & (2 ** 64 - 1), FP32 if precision in ("fp32", FP32) else FP64,
+                                     ctypes.c_void_p(int(stream) if stream else 0), fid.data_ptr(),
+                                     pacc.data_ptr(), grad.data_ptr() if len(th) else None, status.data_ptr()))
+    return fid, pacc, grad, status

@@ -1,0 +1,32 @@
+// adjoint.cuh -- launch interface of the fidelity-gradient kernel (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "program.h"
+
+namespace soft {
+
+struct GradParams {
+  const void *ev;  // Ev<W>
+  const Coef *coef;  // coefficients for the current parameter vector
+  const CaseB *cb;
+  const Site *sites;
+  const uint64_t *thr;
+  uint32_t n_events, n_sites, rw, n_rot, n_params, blocks;
+  double tau_rel;  // prune |v|^2 below tau_rel times the squared norm
+  uint64_t seed, first_pattern, n_patterns;
+  unsigned long long *next;  // work counter (zeroed before launch)
+  double *fid, *pacc, *grad;  // per pattern: F, N_acc, dF/dtheta (n_params)
+  uint8_t *status;            // per pattern: 0 ok, 1 zero acceptance, 2 unsupported, 3 error
+  unsigned char *tape;        // one slot of tape_stride bytes per resident warp
+  size_t tape_stride;
+};
+
+size_t grad_smem_per_warp(int fp32, uint32_t W, uint32_t rw);
+size_t grad_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events);
+uint32_t grad_warps_per_block();
+cudaError_t launch_grad(const GradParams &p, int fp32, uint32_t W, cudaStream_t st);
+
+}  // namespace soft

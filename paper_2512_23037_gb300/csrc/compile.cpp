@@ -12,6 +12,7 @@
 // multiplication, and its sign bit at zero input sign is the XOR mask entry.
 #include "compile.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -343,15 +344,34 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
     return true;
   };
 
-  auto coef_index = [&](double ar, double ai, double br, double bi) -> uint32_t {
+  // fixed angles share entries by value; a parameterised angle gets one entry per (parameter, sign)
+  auto coef_index = [&](double ar, double ai, double br, double bi, int32_t param) -> uint32_t {
     for (size_t k = 0; k < P.coefs.size(); ++k) {
       const Coef &c = P.coefs[k];
-      if (c.a_re == ar && c.a_im == ai && c.b_re == br && c.b_im == bi) return (uint32_t)k;
+      if (param >= 0 ? P.coef_param[k] == param
+                     : (P.coef_param[k] < 0 && c.a_re == ar && c.a_im == ai && c.b_re == br && c.b_im == bi))
+        return (uint32_t)k;
     }
     Coef c{ar, ai, br, bi, (float)ar, (float)ai, (float)br, (float)bi};
     P.coefs.push_back(c);
+    P.coef_param.push_back(param);
     return (uint32_t)(P.coefs.size() - 1);
   };
+  // records read by OBSERVABLE ops (fidelity measurements of gradient runs)
+  std::vector<uint8_t> observed;
+  {
+    uint32_t nr = 0;
+    for (size_t i = 0; i < n_ops; ++i) {
+      int op = ops[i].op;
+      if (op == SOFT_M || op == SOFT_MR) nr++;
+      if (op == SOFT_OBSERVABLE)
+        for (int k = 0; k < 2; ++k)
+          if (ops[i].rec[k] >= 0 && (uint32_t)ops[i].rec[k] < nr) {
+            if (observed.size() <= (size_t)ops[i].rec[k]) observed.resize(ops[i].rec[k] + 1, 0);
+            observed[ops[i].rec[k]] = 1;
+          }
+    }
+  }
 
   for (size_t i = 0; i < n_ops; ++i) {
     const soft_op &o = ops[i];
@@ -405,9 +425,16 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
       }
       uint32_t lowbit = 0;
       if (!diag) lowbit = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
-      uint32_t ci = coef_index(ar, ai, br, bi);
+      int32_t param = -1;
+      if (op == SOFT_RZ && o.pad > 0) {
+        param = (int32_t)(((o.pad - 1) << 1) | (o.flags & 1));
+        P.n_params = std::max<uint32_t>(P.n_params, o.pad);
+      }
+      uint32_t ci = coef_index(ar, ai, br, bi, param);
       Ev<2> &e = new_event(diag ? EV_ROT_DIAG : EV_ROT, 0, e0, lowbit);
       e.a = ci;
+      e.b = param >= 0 ? (uint32_t)param : kNoRec;
+      P.n_rot++;
       std::memcpy(e.beta, beta, sizeof beta);
       std::memcpy(e.gamma, gamma, sizeof gamma);
     } else if (op == SOFT_M || op == SOFT_R || op == SOFT_MR) {
@@ -417,7 +444,8 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
       if (!tb.decompose(Zq, beta, gamma, &e0)) goto internal;
       bool recd = (op != SOFT_R);
       if ((beta[0] | beta[1]) == 0) {
-        Ev<2> &e = new_event(EV_MEAS_A, recd ? F_RECORD : 0, e0, 0);
+        const uint32_t fidf = (recd && nrec < observed.size() && observed[nrec]) ? F_FIDELITY : 0u;
+        Ev<2> &e = new_event(EV_MEAS_A, (recd ? F_RECORD : 0) | fidf, e0, 0);
         std::memcpy(e.gamma, gamma, sizeof gamma);
         e.a = ord;
         e.b = recd ? nrec : 0;
@@ -463,7 +491,8 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
         tb.d[p] = old_sp;
         tb.s[p] = row_of(Zq);
         cb.rP = 0;
-        Ev<2> &e = new_event(EV_MEAS_B, recd ? F_RECORD : 0, 0, 0);
+        const uint32_t fidf = (recd && nrec < observed.size() && observed[nrec]) ? F_FIDELITY : 0u;
+        Ev<2> &e = new_event(EV_MEAS_B, (recd ? F_RECORD : 0) | fidf, 0, 0);
         e.a = ord;
         e.b = recd ? nrec : 0;
         e.beta[0] = P.cb.size();

@@ -15,6 +15,9 @@ struct HostProgram {
   double pmax = 0.0;
   std::vector<Ev<2>> ev;          // events in the two-word layout (narrowed at upload when W = 1)
   std::vector<Coef> coefs;
+  std::vector<int32_t> coef_param;  // per coefficient: parameter << 1 | negated, or -1 (fixed angle)
+  uint32_t n_params = 0;            // 1 + largest parameter index of a parameterised RZ
+  uint32_t n_rot = 0;               // ROT + ROT_DIAG events
   std::vector<CaseB> cb;
   std::vector<Site> sites;
   std::vector<uint64_t> thr;     // gap thresholds, one per site

@@ -1,0 +1,136 @@
+// device_common.cuh -- device helpers shared by the shot kernel and the
+// adjoint kernel (complex arithmetic, packed keys, Philox4x32-10).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace soft {
+namespace dev {
+
+template <typename R>
+struct Cx {
+  R x, y;
+};
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> csub(Cx<R> a, Cx<R> b) {
+  return {a.x - b.x, a.y - b.y};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cscale(Cx<R> a, R s) {
+  return {a.x * s, a.y * s};
+}
+// v * i^e
+template <typename R>
+__device__ __forceinline__ Cx<R> ipow(Cx<R> v, uint32_t e) {
+  Cx<R> r = (e & 1u) ? Cx<R>{-v.y, v.x} : v;
+  if (e & 2u) r = {-r.x, -r.y};
+  return r;
+}
+template <typename R>
+__device__ __forceinline__ R norm2(Cx<R> v) {
+  return v.x * v.x + v.y * v.y;
+}
+template <typename R>
+__device__ __forceinline__ double norm2d(Cx<R> v) {
+  double a = (double)v.x, b = (double)v.y;
+  return a * a + b * b;
+}
+
+template <int W>
+struct Key {
+  uint64_t w[W];
+};
+template <int W>
+__device__ __forceinline__ Key<W> kxor(const Key<W> &a, const uint64_t *b) {
+  Key<W> r;
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.w[i] = a.w[i] ^ b[i];
+  return r;
+}
+template <int W>
+__device__ __forceinline__ uint32_t kpar(const Key<W> &a, const uint64_t *b) {
+  uint32_t t = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) t += __popcll(a.w[i] & b[i]);
+  return t & 1u;
+}
+template <int W>
+__device__ __forceinline__ bool keq(const Key<W> &a, const Key<W> &b) {
+  bool e = true;
+#pragma unroll
+  for (int i = 0; i < W; ++i) e = e && (a.w[i] == b.w[i]);
+  return e;
+}
+// word (i >> 6) of a W-word vector without dynamic register indexing
+template <int W>
+__device__ __forceinline__ uint64_t word_of(const uint64_t *a, uint32_t i) {
+  return (W == 1 || (i >> 6) == 0u) ? a[0] : a[W - 1];
+}
+template <int W>
+__device__ __forceinline__ uint32_t kbit(const Key<W> &a, uint32_t i) {
+  return (uint32_t)((word_of<W>(a.w, i) >> (i & 63)) & 1ull);
+}
+template <int W>
+__device__ __forceinline__ uint32_t khash(const Key<W> &a) {
+  uint64_t h = a.w[0];
+  if (W == 2) h ^= a.w[W - 1] * 0xC2B2AE3D27D4EB4Full;
+  h *= 0x9E3779B97F4A7C15ull;
+  return (uint32_t)(h >> 32);
+}
+template <int W>
+__device__ __forceinline__ uint32_t wpar(const uint64_t *a, const uint64_t *b) {
+  uint32_t t = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) t += __popcll(a[i] & b[i]);
+  return t & 1u;
+}
+template <int W>
+__device__ __forceinline__ uint32_t wbit(const uint64_t *a, uint32_t i) {
+  return (uint32_t)((word_of<W>(a, i) >> (i & 63)) & 1ull);
+}
+template <int W>
+__device__ __forceinline__ void wflip(uint64_t *a, uint32_t i) {
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+    if ((int)(i >> 6) == w) a[w] ^= 1ull << (i & 63);
+}
+
+// Philox4x32-10, counter (shot_lo, shot_hi, stream, index), key = seed.
+__device__ __forceinline__ uint4 philox(uint64_t seed, uint64_t shot, uint32_t stream, uint32_t idx) {
+  uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32), c2 = stream, c3 = idx;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ double snap01(double p) {
+  if (p < 1e-12) return 0.0;
+  if (p > 1.0 - 1e-12) return 1.0;
+  return p;
+}
+
+
+}  // namespace dev
+}  // namespace soft

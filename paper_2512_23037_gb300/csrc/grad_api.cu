@@ -1,0 +1,92 @@
+// grad_api.cu -- soft_fidelity_grad: post-selected fidelity and its gradient
+// for fixed error patterns (C ABI, see include/soft.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/soft.h"
+#include "adjoint.cuh"
+#include "handles.h"
+
+extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t n_params, uint64_t n_patterns,
+                                  uint64_t first_pattern, uint64_t seed, int32_t precision, void *stream,
+                                  double *d_fid, double *d_pacc, double *d_grad, uint8_t *d_status) {
+  if (!c || !d_fid || !d_pacc || !d_status || (n_params && (!theta || !d_grad)))
+    return soft::set_error(SOFT_E_ARG, "null argument");
+  if (precision != SOFT_FP64 && precision != SOFT_FP32) return soft::set_error(SOFT_E_ARG, "bad precision");
+  const auto &hp = c->hp;
+  if (n_params < hp.n_params) return soft::set_error(SOFT_E_ARG, "theta shorter than the circuit's parameter count");
+  if (n_patterns == 0) return SOFT_OK;
+  const int fp32 = precision == SOFT_FP32;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return soft::set_error(SOFT_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // coefficients a I + b Z for this parameter vector: Rz(s theta_k) = cos(s theta_k/2) I - i sin(s theta_k/2) Z
+  std::vector<soft::Coef> coefs(hp.coefs);
+  for (size_t k = 0; k < coefs.size(); ++k) {
+    const int32_t cp = hp.coef_param[k];
+    if (cp < 0) continue;
+    const double ang = ((cp & 1) ? -1.0 : 1.0) * theta[cp >> 1];
+    const double cr = std::cos(0.5 * ang), si = -std::sin(0.5 * ang);
+    coefs[k] = soft::Coef{cr, 0.0, 0.0, si, (float)cr, 0.0f, 0.0f, (float)si};
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const uint32_t wpb = soft::grad_warps_per_block();
+  uint64_t blocks = (uint64_t)(sms > 0 ? sms : 1) * 4;
+  blocks = std::min<uint64_t>(blocks, (n_patterns + wpb - 1) / wpb);
+  const size_t stride = soft::grad_tape_bytes(fp32, hp.W, hp.n_rot, (uint32_t)hp.ev.size());
+  soft::Coef *d_coef = nullptr;
+  unsigned long long *d_next = nullptr;
+  unsigned char *d_tape = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_coef);
+    cudaFree(d_next);
+    cudaFree(d_tape);
+  };
+  if ((e = cudaMalloc(&d_coef, std::max<size_t>(1, coefs.size()) * sizeof(soft::Coef))) != cudaSuccess ||
+      (e = cudaMalloc(&d_next, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&d_tape, stride * blocks * wpb)) != cudaSuccess) {
+    cleanup();
+    return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
+  }
+  if ((!coefs.empty() && (e = cudaMemcpyAsync(d_coef, coefs.data(), coefs.size() * sizeof(soft::Coef),
+                                              cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
+      (e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st)) != cudaSuccess) {
+    cleanup();
+    return soft::set_error(SOFT_E_CUDA, "upload failed");
+  }
+  soft::GradParams p{};
+  p.ev = c->d_ev;
+  p.coef = d_coef;
+  p.cb = c->d_cb;
+  p.sites = c->d_sites;
+  p.thr = c->d_thr;
+  p.n_events = (uint32_t)hp.ev.size();
+  p.n_sites = hp.n_sites;
+  p.rw = hp.rw;
+  p.n_rot = hp.n_rot;
+  p.n_params = n_params;
+  p.blocks = (uint32_t)blocks;
+  p.tau_rel = fp32 ? 1e-10 : 1e-20;
+  p.seed = seed;
+  p.first_pattern = first_pattern;
+  p.n_patterns = n_patterns;
+  p.next = d_next;
+  p.fid = d_fid;
+  p.pacc = d_pacc;
+  p.grad = d_grad;
+  p.status = d_status;
+  p.tape = d_tape;
+  p.tape_stride = stride;
+  if ((e = soft::launch_grad(p, fp32, hp.W, st)) != cudaSuccess) {
+    cleanup();
+    return soft::set_error(SOFT_E_CUDA, "gradient kernel launch failed");
+  }
+  e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return soft::set_error(SOFT_E_CUDA, "gradient kernel failed");
+  return SOFT_OK;
+}

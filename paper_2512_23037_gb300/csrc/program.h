@@ -34,6 +34,7 @@ enum EvType : uint32_t {
 
 enum : uint32_t {
   F_RECORD = 1,      // MEAS: append the outcome to the record
+  F_FIDELITY = 2,    // MEAS: an OBSERVABLE reads this record (projected onto 0 in gradient runs)
   F_DETECTOR = 4,    // PARITY
   F_OBSERVABLE = 8,  // PARITY
   F_CHAIN = 16,      // PARITY: carry into the next parity op
@@ -58,7 +59,8 @@ inline uint32_t ev_pack(uint32_t type, uint32_t flags, uint32_t e0, uint32_t low
 //   F_DETECTOR (+ F_INVERT): a detector on this measurement's record alone.
 
 // One event; W = 64-bit words per n-bit vector (1 for n <= 64, else 2).
-//   ROT/ROT_DIAG: a = coefficient index, beta/gamma of Z_q
+//   ROT/ROT_DIAG: a = coefficient index, b = parameter << 1 | negated (kNoRec: fixed angle),
+//                 beta/gamma of Z_q
 //   MEAS_A:       a = RNG ordinal, b = record index, gamma of Z_q
 //   MEAS_B:       a = RNG ordinal, b = record index, beta[0] = CaseB index
 //   PAULI:        a, b = record refs (F_COND_REC), beta/gamma of the Pauli
