@@ -74,6 +74,10 @@ def lib():
                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, u64p,
                                  ctypes.POINTER(_Counts)]
+            L.or_run_ex.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p,
+                                    ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                    u64p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Counts)]
             L.or_trace.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p,
                                    ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_size_t,
                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
@@ -131,11 +135,17 @@ def count_sites(ops, n_qubits, noise):
     return int(ns), int(nrec.value)
 
 
-def run(ops, n_qubits, noise, cap, seed, first_shot, n_shots, threads=1, records=True):
+RUN_FIDELITY = 1
+
+
+def run(ops, n_qubits, noise, cap, seed, first_shot, n_shots, threads=1, records=True, fidelity=False):
     """Run shots [first_shot, first_shot + n_shots). Returns a dict with
     status (u8 per shot), records (u64 words per shot, bit j = 1 for outcome
     -1 of record j), tally [shots, discarded, overflow, kept, logical_errors]
-    and the work counters."""
+    and the work counters. With fidelity=True every measurement an OBSERVABLE
+    reads is projected onto +1: `fid` holds each shot's F (product of those
+    conditional probabilities; 0 for shots not kept) and `fsum` = [sum of F
+    over kept shots, kept shots]."""
     a = _ops_array(ops)
     nz = _noise_arr(noise)
     _, nrec = count_sites(a, n_qubits, noise)
@@ -143,14 +153,18 @@ def run(ops, n_qubits, noise, cap, seed, first_shot, n_shots, threads=1, records
     status = np.zeros(n_shots, dtype=np.uint8)
     recs = np.zeros((n_shots, rw), dtype=np.uint64) if records else None
     tally = (ctypes.c_uint64 * 5)()
+    fsum = np.zeros(2, dtype=np.float64)
+    fid = np.zeros(n_shots, dtype=np.float64) if fidelity else None
     cnt = _Counts()
-    rc = lib().or_run(a.ctypes.data, len(a), n_qubits, nz.ctypes.data, cap, seed, first_shot, n_shots,
-                      threads, status.ctypes.data, recs.ctypes.data if recs is not None else None, rw,
-                      tally, ctypes.byref(cnt))
+    rc = lib().or_run_ex(a.ctypes.data, len(a), n_qubits, nz.ctypes.data, cap, seed, first_shot, n_shots,
+                         threads, RUN_FIDELITY if fidelity else 0, status.ctypes.data,
+                         recs.ctypes.data if recs is not None else None, rw, tally, fsum.ctypes.data,
+                         fid.ctypes.data if fid is not None else None, ctypes.byref(cnt))
     if rc != 0:
         raise RuntimeError(f"oracle run failed: {rc}")
     return {"status": status, "records": recs, "tally": [int(v) for v in tally],
-            "counts": {f: int(getattr(cnt, f)) for f, _ in _Counts._fields_}, "rw": rw, "n_records": nrec}
+            "counts": {f: int(getattr(cnt, f)) for f, _ in _Counts._fields_}, "rw": rw, "n_records": nrec,
+            "fid": fid, "fsum": fsum}
 
 
 def trace(ops, n_qubits, noise, cap, seed, shot, stop_after=None, max_events=1 << 16, max_keys=1 << 16):

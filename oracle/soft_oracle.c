@@ -363,13 +363,31 @@ typedef struct {
   double tau;
   double pmax;
   uint32_t n_sites;
-  int32_t *pre_site;  /* per op: site index of the flip before M/MR, or -1 */
+  int32_t *pre_site;  /* per op: site index of the flip before a measurement, or -1 */
   int32_t *post_site; /* per op: site index after the op, or -1 */
   double *site_p;
-  uint8_t *site_two; /* 1 for a two-qubit depolarizing site */
-  uint64_t *thr;     /* gap thresholds, n_sites entries */
+  uint8_t *site_kind; /* SITE_DEPOL1, SITE_DEPOL2 or SITE_FLIP */
+  uint8_t *site_code; /* SITE_FLIP: the Pauli code it applies */
+  uint64_t *thr;      /* gap thresholds, n_sites entries */
   uint32_t n_records;
+  uint8_t *observed;  /* per record: 1 if an OBSERVABLE reads it */
+  int fid_ok;         /* no DETECTOR at or after the first observed measurement */
 } circ;
+
+/* Noise site kinds: one-qubit depolarizing (X, Y, Z uniform), two-qubit
+ * depolarizing (15 Paulis uniform), and a flip (one fixed Pauli). */
+enum { SITE_DEPOL1 = 0, SITE_DEPOL2 = 1, SITE_FLIP = 2 };
+
+/* Pauli code that anticommutes with the single-qubit Pauli `code`: X for Z
+ * and Y, Z for X. Applied before a measurement it flips the outcome. */
+static int flip_code_for(int code) { return code == 1 ? 3 : 1; }
+
+/* MPP chains: first op of the chain that ends at op i. */
+static size_t mpp_chain_start(const or_op *ops, size_t i) {
+  size_t j = i;
+  while (j > 0 && ops[j - 1].op == OR_MPP && (ops[j - 1].flags & OR_MPP_MORE)) --j;
+  return j;
+}
 
 static int is_1q_gate(int op) {
   return op == OR_H || op == OR_S || op == OR_SDAG || op == OR_X || op == OR_Y || op == OR_Z || op == OR_T ||
@@ -381,8 +399,30 @@ static void circ_free(circ *c) {
   free(c->pre_site);
   free(c->post_site);
   free(c->site_p);
-  free(c->site_two);
+  free(c->site_kind);
+  free(c->site_code);
   free(c->thr);
+  free(c->observed);
+}
+
+/* Product of the Pauli factors of the MPP chain ops[first..last]. */
+static pauli mpp_product(const or_op *ops, size_t first, size_t last) {
+  pauli P;
+  memset(&P, 0, sizeof P);
+  for (size_t j = first; j <= last; ++j) {
+    pauli a = pauli_single(ops[j].flags & 3, (int)ops[j].q0);
+    P = pauli_mul(&P, &a);
+    if ((ops[j].flags >> 2) & 3) {
+      pauli b = pauli_single((ops[j].flags >> 2) & 3, (int)ops[j].q1);
+      P = pauli_mul(&P, &b);
+    }
+  }
+  return P;
+}
+
+/* True for an op that measures and appends a record: M, MR, or the last op of an MPP chain. */
+static int records_outcome(const or_op *o) {
+  return o->op == OR_M || o->op == OR_MR || (o->op == OR_MPP && !(o->flags & OR_MPP_MORE));
 }
 
 static int circ_build(circ *c, const or_op *ops, size_t n_ops, uint32_t n, const or_noise *noise, uint32_t cap) {
@@ -398,18 +438,32 @@ static int circ_build(circ *c, const or_op *ops, size_t n_ops, uint32_t n, const
   c->pre_site = (int32_t *)malloc((n_ops + 1) * sizeof(int32_t));
   c->post_site = (int32_t *)malloc((n_ops + 1) * sizeof(int32_t));
   c->site_p = (double *)malloc((2 * n_ops + 1) * sizeof(double));
-  c->site_two = (uint8_t *)malloc(2 * n_ops + 1);
-  if (!c->pre_site || !c->post_site || !c->site_p || !c->site_two) return OR_E_OOM;
+  c->site_kind = (uint8_t *)malloc(2 * n_ops + 1);
+  c->site_code = (uint8_t *)malloc(2 * n_ops + 1);
+  if (!c->pre_site || !c->post_site || !c->site_p || !c->site_kind || !c->site_code) return OR_E_OOM;
   int noiseless = 0;
   uint32_t ns = 0, nrec = 0;
+  uint64_t mpp_q[MW] = {0, 0}; /* qubits already in the open MPP chain */
   for (size_t i = 0; i < n_ops; ++i) {
     const or_op *o = &ops[i];
     c->pre_site[i] = -1;
     c->post_site[i] = -1;
     int op = o->op;
-    if (op > OR_NOISELESS_END) return OR_E_UNSUPPORTED_OP;
-    if (is_1q_gate(op) || is_2q_gate(op) || op == OR_M || op == OR_R || op == OR_MR || op == OR_CPAULI) {
+    if (op > OR_MPP) return OR_E_UNSUPPORTED_OP;
+    if (i > 0 && ops[i - 1].op == OR_MPP && (ops[i - 1].flags & OR_MPP_MORE) && op != OR_MPP) return OR_E_ARG;
+    if (is_1q_gate(op) || is_2q_gate(op) || op == OR_M || op == OR_R || op == OR_MR || op == OR_CPAULI ||
+        op == OR_MPP) {
       if (o->q0 >= n) return OR_E_QUBIT_RANGE;
+    }
+    if (op == OR_MPP) {
+      int pa = o->flags & 3, pb = (o->flags >> 2) & 3;
+      if (pa == 0 || (o->flags & ~(uint32_t)(15 | OR_MPP_MORE))) return OR_E_ARG;
+      if (pb && (o->q1 >= n || o->q1 == o->q0)) return OR_E_QUBIT_RANGE;
+      if (getbit(mpp_q, (int)o->q0) || (pb && getbit(mpp_q, (int)o->q1))) return OR_E_ARG; /* repeated qubit */
+      flipbit(mpp_q, (int)o->q0);
+      if (pb) flipbit(mpp_q, (int)o->q1);
+      if (!(o->flags & OR_MPP_MORE)) mpp_q[0] = mpp_q[1] = 0;
+      else if (i + 1 == n_ops) return OR_E_ARG; /* open chain at the end */
     }
     if (is_2q_gate(op) && (o->q1 >= n || o->q1 == o->q0)) return OR_E_QUBIT_RANGE;
     if (op == OR_DETECTOR || op == OR_OBSERVABLE || op == OR_CPAULI) {
@@ -419,29 +473,55 @@ static int circ_build(circ *c, const or_op *ops, size_t n_ops, uint32_t n, const
     if (op == OR_NOISELESS_BEGIN) noiseless = 1;
     if (op == OR_NOISELESS_END) noiseless = 0;
     if (!noiseless) {
-      if ((op == OR_M || op == OR_MR) && noise->p_meas > 0) {
+      /* measurement flip: X before M/MR; before an MPP chain, the Pauli on its
+       * first qubit that anticommutes with the chain's first factor */
+      int first_mpp = op == OR_MPP && mpp_chain_start(ops, i) == i;
+      if ((op == OR_M || op == OR_MR || first_mpp) && noise->p_meas > 0) {
         c->site_p[ns] = noise->p_meas;
-        c->site_two[ns] = 0;
+        c->site_kind[ns] = SITE_FLIP;
+        c->site_code[ns] = (uint8_t)(op == OR_MPP ? flip_code_for(o->flags & 3) : 1);
         c->pre_site[i] = (int32_t)ns++;
       }
       if (is_1q_gate(op) && noise->p1 > 0) {
         c->site_p[ns] = noise->p1;
-        c->site_two[ns] = 0;
+        c->site_kind[ns] = SITE_DEPOL1;
+        c->site_code[ns] = 0;
         c->post_site[i] = (int32_t)ns++;
       } else if (is_2q_gate(op) && noise->p2 > 0) {
         c->site_p[ns] = noise->p2;
-        c->site_two[ns] = 1;
+        c->site_kind[ns] = SITE_DEPOL2;
+        c->site_code[ns] = 0;
         c->post_site[i] = (int32_t)ns++;
       } else if ((op == OR_R || op == OR_MR) && noise->p_reset > 0) {
         c->site_p[ns] = noise->p_reset;
-        c->site_two[ns] = 0;
+        c->site_kind[ns] = SITE_FLIP;
+        c->site_code[ns] = 1;
         c->post_site[i] = (int32_t)ns++;
       }
     }
-    if (op == OR_M || op == OR_MR) nrec++;
+    if (records_outcome(o)) nrec++;
   }
   c->n_sites = ns;
   c->n_records = nrec;
+  /* records read by OBSERVABLE ops, and whether a DETECTOR follows the first of their measurements */
+  c->observed = (uint8_t *)calloc(nrec + 1, 1);
+  if (!c->observed) return OR_E_OOM;
+  for (size_t i = 0; i < n_ops; ++i)
+    if (ops[i].op == OR_OBSERVABLE)
+      for (int r = 0; r < 2; ++r)
+        if (ops[i].rec[r] >= 0 && (uint32_t)ops[i].rec[r] < nrec) c->observed[ops[i].rec[r]] = 1;
+  c->fid_ok = 1;
+  {
+    uint32_t rcount = 0;
+    int seen = 0;
+    for (size_t i = 0; i < n_ops; ++i) {
+      if (records_outcome(&ops[i])) {
+        if (c->observed[rcount]) seen = 1;
+        rcount++;
+      }
+      if (ops[i].op == OR_DETECTOR && seen) c->fid_ok = 0;
+    }
+  }
   c->thr = (uint64_t *)malloc((ns + 1) * sizeof(uint64_t));
   if (!c->thr) return OR_E_OOM;
   for (uint32_t g = 0; g < ns; ++g) c->thr[g] = or_gap_threshold(c->pmax, g);
@@ -493,10 +573,22 @@ static void next_error(const circ *c, uint64_t seed, uint64_t shot, noise_stream
   }
 }
 
-/* Pauli of an error: K = 3 picks X, Y, Z; K = 15 picks (P_a, P_b) with
- * 4*P_a + P_b = idx + 1 in the code 0 I, 1 X, 2 Y, 3 Z. */
+/* Pauli code of an error at `site` with choice word `word2`: a depolarizing
+ * site picks idx = floor(word2 K / 2^32) with K = 3 (X, Y, Z) or K = 15
+ * ((P_a, P_b) with 4 P_a + P_b = idx + 1, code 0 I, 1 X, 2 Y, 3 Z); a flip
+ * site applies its fixed code. */
+static int error_code(const circ *c, uint32_t site, uint32_t word2) {
+  if (c->site_kind[site] == SITE_FLIP) return c->site_code[site];
+  if (c->site_kind[site] == SITE_DEPOL2) return (int)(((uint64_t)word2 * 15u) >> 32) + 1;
+  return (int)(((uint64_t)word2 * 3u) >> 32) + 1;
+}
+
 static pauli error_pauli(const circ *c, uint32_t site, uint32_t word2, const or_op *o, int *code_out) {
-  if (c->site_two[site]) {
+  if (c->site_kind[site] == SITE_FLIP) {
+    *code_out = c->site_code[site];
+    return pauli_single(c->site_code[site], (int)o->q0);
+  }
+  if (c->site_kind[site] == SITE_DEPOL2) {
     uint32_t idx = (uint32_t)(((uint64_t)word2 * 15u) >> 32);
     int pa = (int)((idx + 1) >> 2), pb = (int)((idx + 1) & 3);
     pauli A = pauli_single(pa, (int)o->q0), B = pauli_single(pb, (int)o->q1);
@@ -559,8 +651,10 @@ static double snap(double p) {
 }
 
 /* Measure the Hermitian Pauli P (Theorem 1 (2), Eq. Pi_pm). */
+/* With `force` set the outcome is +1 whenever p_+ > 0 (a projection onto +1,
+ * renormalised), and -1 only when +1 is impossible. */
 static int measure(gs_state *st, const circ *c, const pauli *P, uint64_t seed, uint64_t shot, uint32_t ordinal,
-                   meas_info *mi, or_counts *cnt) {
+                   int force, meas_info *mi, or_counts *cnt) {
   uint64_t beta[MW], gamma[MW];
   int ce;
   if (decompose(st, P, beta, gamma, &ce)) return OR_ST_ERROR;
@@ -592,7 +686,7 @@ static int measure(gs_state *st, const circ *c, const pauli *P, uint64_t seed, u
     mi->det = 0;
     double pp = snap(sp / (sp + sm));
     mi->p_plus = pp;
-    mi->m = (mi->u < pp) ? +1 : -1;
+    mi->m = force ? (pp > 0.0 ? +1 : -1) : ((mi->u < pp) ? +1 : -1);
     double keep = (mi->m == 1) ? sp : sm;
     double scale = 1.0 / sqrt(keep);
     size_t o = 0;
@@ -693,7 +787,7 @@ static int measure(gs_state *st, const circ *c, const pauli *P, uint64_t seed, u
   if (cnt) cnt->meas_entries += n0;
   double pp = snap(s_plus / (s_plus + s_minus));
   mi->p_plus = pp;
-  mi->m = (mi->u < pp) ? +1 : -1;
+  mi->m = force ? (pp > 0.0 ? +1 : -1) : ((mi->u < pp) ? +1 : -1);
   double sm_ = (mi->m == 1) ? s_plus : s_minus;
   double scale = 1.0 / sqrt(2.0 * sm_);
   st->ne = 0;
@@ -768,9 +862,14 @@ static int apply_error_if_due(gs_state *st, const circ *c, uint64_t seed, uint64
   return OR_ST_OK;
 }
 
+/* One shot. In fidelity mode (fid != NULL) every measurement whose record an
+ * OBSERVABLE reads is projected onto +1 and *fid accumulates the product of
+ * their conditional probabilities p_+; when +1 is impossible *fid = 0 and the
+ * shot ends there (kept). */
 static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, uint64_t *rec, uint32_t rw,
-                    int *logical, size_t stop_after, trace_buf *tb, or_counts *cnt) {
+                    int *logical, size_t stop_after, trace_buf *tb, or_counts *cnt, double *fid) {
   init_state(st, c->n);
+  if (fid) *fid = 1.0;
   if (rec) memset(rec, 0, rw * sizeof(uint64_t));
   noise_stream ns = {0, 0, UINT32_MAX, 0};
   next_error(c, seed, shot, &ns);
@@ -822,10 +921,12 @@ static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, u
         if (r) return r;
         break;
       }
-      case OR_M: case OR_R: case OR_MR: {
-        pauli Z = pauli_single(3, (int)o->q0);
+      case OR_M: case OR_R: case OR_MR: case OR_MPP: {
+        if (op == OR_MPP && (o->flags & OR_MPP_MORE)) break; /* the chain's last op measures */
+        pauli P = (op == OR_MPP) ? mpp_product(c->ops, mpp_chain_start(c->ops, i), i) : pauli_single(3, (int)o->q0);
+        const int force = fid && op != OR_R && c->observed[nrec];
         meas_info mi;
-        int r = measure(st, c, &Z, seed, shot, ordinal, &mi, cnt);
+        int r = measure(st, c, &P, seed, shot, ordinal, force, &mi, cnt);
         if (r) return r;
         or_event e;
         memset(&e, 0, sizeof e);
@@ -843,7 +944,14 @@ static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, u
         e.norm = map_norm(st);
         push_ev(tb, &e);
         ordinal++;
-        if (op == OR_M || op == OR_MR) {
+        if (force) {
+          if (mi.m == -1) {
+            *fid = 0.0;
+            return OR_ST_OK;
+          }
+          *fid *= mi.p_plus;
+        }
+        if (op != OR_R) {
           if (mi.m == -1) flipbit(rb, (int)nrec);
           nrec++;
         }
@@ -896,6 +1004,9 @@ typedef struct {
   uint64_t *records;
   uint32_t rw;
   uint64_t tally[5];
+  double fsum[2];
+  double *fid;
+  int fid_mode;
   or_counts cnt;
   int err;
 } worker_arg;
@@ -908,11 +1019,14 @@ static void *worker(void *p) {
     return NULL;
   }
   memset(a->tally, 0, sizeof a->tally);
+  a->fsum[0] = a->fsum[1] = 0.0;
   for (uint64_t t = 0; t < a->count; ++t) {
     uint64_t shot = a->first + t;
     int logical = 0;
     uint64_t *rec = a->records ? a->records + (shot - a->shot0) * a->rw : NULL;
-    int s = run_shot(a->c, st, a->seed, shot, rec, a->rw, &logical, (size_t)-1, NULL, &a->cnt);
+    double f = 0.0;
+    int s = run_shot(a->c, st, a->seed, shot, rec, a->rw, &logical, (size_t)-1, NULL, &a->cnt,
+                     a->fid_mode ? &f : NULL);
     if (a->status) a->status[shot - a->shot0] = (uint8_t)s;
     a->tally[0]++;
     if (s == OR_ST_DISCARDED) a->tally[1]++;
@@ -920,7 +1034,12 @@ static void *worker(void *p) {
     else if (s == OR_ST_OK) {
       a->tally[3]++;
       if (logical) a->tally[4]++;
+      if (a->fid_mode) {
+        a->fsum[0] += f;
+        a->fsum[1] += 1.0;
+      }
     }
+    if (a->fid) a->fid[shot - a->shot0] = (s == OR_ST_OK) ? f : 0.0;
     a->cnt.shots++;
   }
   free(st->e);
@@ -931,11 +1050,23 @@ static void *worker(void *p) {
 int or_run(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t cap, uint64_t seed,
            uint64_t first_shot, uint64_t n_shots, int n_threads, uint8_t *status, uint64_t *records, uint32_t rw,
            uint64_t tally[5], or_counts *counts) {
+  return or_run_ex(ops, n_ops, n_qubits, noise, cap, seed, first_shot, n_shots, n_threads, 0, status, records, rw,
+                   tally, NULL, NULL, counts);
+}
+
+int or_run_ex(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t cap, uint64_t seed,
+              uint64_t first_shot, uint64_t n_shots, int n_threads, int flags, uint8_t *status, uint64_t *records,
+              uint32_t rw, uint64_t tally[5], double fsum[2], double *fid, or_counts *counts) {
   circ c;
   int rc = circ_build(&c, ops, n_ops, n_qubits, noise, cap);
   if (rc) {
     circ_free(&c);
     return rc;
+  }
+  const int fid_mode = (flags & OR_RUN_FIDELITY) != 0;
+  if (fid_mode && !c.fid_ok) {
+    circ_free(&c);
+    return OR_E_ARG;
   }
   if (records && rw * 64u < c.n_records) {
     circ_free(&c);
@@ -959,6 +1090,8 @@ int or_run(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *no
     args[t].status = status;
     args[t].records = records;
     args[t].rw = rw;
+    args[t].fid_mode = fid_mode;
+    args[t].fid = fid;
     at += args[t].count;
   }
   if (n_threads == 1) worker(&args[0]);
@@ -968,10 +1101,15 @@ int or_run(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *no
   }
   memset(tally, 0, 5 * sizeof(uint64_t));
   if (counts) memset(counts, 0, sizeof *counts);
+  if (fsum) fsum[0] = fsum[1] = 0.0;
   rc = OR_OK;
   for (int t = 0; t < n_threads; ++t) {
     if (args[t].err) rc = args[t].err;
     for (int k = 0; k < 5; ++k) tally[k] += args[t].tally[k];
+    if (fsum) {
+      fsum[0] += args[t].fsum[0];
+      fsum[1] += args[t].fsum[1];
+    }
     if (counts) {
       counts->shots += args[t].cnt.shots;
       counts->t_out_entries += args[t].cnt.t_out_entries;
@@ -1007,7 +1145,7 @@ int or_trace(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *
     circ_free(&c);
     return OR_E_ARG;
   }
-  int s = run_shot(&c, st, seed, shot, records, rw, &logical, stop_after, &tb, NULL);
+  int s = run_shot(&c, st, seed, shot, records, rw, &logical, stop_after, &tb, NULL, NULL);
   *status_out = s;
   *logical_out = logical;
   *n_events = tb.n_ev;
@@ -1248,8 +1386,9 @@ int or_project(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise
         if (r) status = r;
         break;
       }
-      case OR_M: case OR_R: case OR_MR: {
-        pauli Z = pauli_single(3, (int)o->q0);
+      case OR_M: case OR_R: case OR_MR: case OR_MPP: {
+        if (op == OR_MPP && (o->flags & OR_MPP_MORE)) break;
+        pauli Z = (op == OR_MPP) ? mpp_product(ops, mpp_chain_start(ops, i), i) : pauli_single(3, (int)o->q0);
         int m;
         if (op == OR_R) {
           m = deterministic_outcome(st, &Z);
@@ -1327,9 +1466,7 @@ int or_errors(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise 
   next_error(&c, seed, pattern, &ns);
   uint32_t k = 0;
   while (ns.site != UINT32_MAX) {
-    uint32_t code;
-    if (c.site_two[ns.site]) code = (uint32_t)(((uint64_t)ns.word2 * 15u) >> 32) + 1u;
-    else code = (uint32_t)(((uint64_t)ns.word2 * 3u) >> 32) + 1u;
+    uint32_t code = (uint32_t)error_code(&c, ns.site, ns.word2);
     if (k < max_out) {
       sites[k] = ns.site;
       codes[k] = code;

@@ -18,9 +18,18 @@ extern "C" {
 enum {
   OR_H = 0, OR_S = 1, OR_SDAG = 2, OR_X = 3, OR_Y = 4, OR_Z = 5, OR_CX = 6, OR_CZ = 7,
   OR_T = 8, OR_TDAG = 9, OR_RZ = 10, OR_M = 11, OR_R = 12, OR_MR = 13, OR_CPAULI = 14,
-  OR_DETECTOR = 15, OR_OBSERVABLE = 16, OR_NOISELESS_BEGIN = 17, OR_NOISELESS_END = 18
+  OR_DETECTOR = 15, OR_OBSERVABLE = 16, OR_NOISELESS_BEGIN = 17, OR_NOISELESS_END = 18, OR_MPP = 19
 };
 enum { OR_FLAG_INVERT = 1, OR_FLAG_CHAIN = 2 };
+/* MPP (Pauli-product measurement): flags bits 0-1 = Pauli on q0 (1 X, 2 Y,
+ * 3 Z), bits 2-3 = Pauli on q1 (0: no second factor), OR_MPP_MORE = the
+ * product continues in the next op, which must be an MPP. The chain's last
+ * op measures the product and appends one record. */
+enum { OR_MPP_MORE = 16 };
+/* or_run_ex flags: OR_RUN_FIDELITY projects every measurement whose record an
+ * OBSERVABLE reads onto outcome +1 and accumulates the product of their
+ * conditional probabilities. */
+enum { OR_RUN_FIDELITY = 1 };
 
 /* 32-byte op: rec[] are absolute record indices (-1 = unused). */
 typedef struct {
@@ -71,6 +80,13 @@ uint64_t or_gap_threshold(double p, uint64_t g);
 int or_run(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t cap, uint64_t seed,
            uint64_t first_shot, uint64_t n_shots, int n_threads, uint8_t *status, uint64_t *records, uint32_t rw,
            uint64_t tally[5], or_counts *counts);
+
+/* or_run with run flags. fsum (may be NULL) receives {sum of F over kept
+ * shots, number of kept shots}; fid (may be NULL, one per shot) receives each
+ * shot's F (0 for shots that are not kept). */
+int or_run_ex(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t cap, uint64_t seed,
+              uint64_t first_shot, uint64_t n_shots, int n_threads, int flags, uint8_t *status, uint64_t *records,
+              uint32_t rw, uint64_t tally[5], double fsum[2], double *fid, or_counts *counts);
 
 int or_trace(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise *noise, uint32_t cap, uint64_t seed,
              uint64_t shot, size_t stop_after, or_event *events, size_t events_cap, size_t *n_events,

@@ -15,8 +15,9 @@ plain runs, and gradient runs substitute the parameter vector.
 Noise model (uniform depolarizing, Sec. III of arxiv 2512.23037): DEPOL1(p1)
 after every one-qubit gate (T/T^dagger/Rz included), DEPOL2(p2) after every
 two-qubit gate, an X flip with p_meas before every M/MR and with p_reset
-after every R/MR. Ops between NOISELESS_BEGIN and NOISELESS_END carry none.
-Idle noise is not modelled (p_idle must be 0).
+after every R/MR; before an MPP chain the flip is the Pauli on the chain's
+first qubit that anticommutes with its first factor (Z for X, X for Y and Z).
+Ops between NOISELESS_BEGIN and NOISELESS_END carry none. Idle noise is not modelled (p_idle must be 0).
 """
 from __future__ import annotations
 
@@ -27,11 +28,14 @@ import numpy as np
 
 # ---------------------------------------------------------------- op codes
 H, S, S_DAG, X, Y, Z, CX, CZ, T, T_DAG, RZ, M, R, MR, CPAULI, DETECTOR, OBSERVABLE, \
-    NOISELESS_BEGIN, NOISELESS_END = range(19)
+    NOISELESS_BEGIN, NOISELESS_END, MPP = range(20)
 OP_NAMES = ["H", "S", "S_DAG", "X", "Y", "Z", "CX", "CZ", "T", "T_DAG", "RZ", "M", "R", "MR",
-            "CPAULI", "DETECTOR", "OBSERVABLE", "NOISELESS_BEGIN", "NOISELESS_END"]
+            "CPAULI", "DETECTOR", "OBSERVABLE", "NOISELESS_BEGIN", "NOISELESS_END", "MPP"]
 FLAG_INVERT = 1
 FLAG_CHAIN = 2
+# MPP: flags bits 0-1 Pauli on q0 (1 X, 2 Y, 3 Z), bits 2-3 Pauli on q1 (0 none),
+# MPP_MORE = the product continues in the next op; the chain's last op records.
+MPP_MORE = 16
 ONE_Q = (H, S, S_DAG, X, Y, Z, T, T_DAG, RZ)
 TWO_Q = (CX, CZ)
 CLIFFORD_1Q = (H, S, S_DAG, X, Y, Z)
@@ -83,6 +87,21 @@ class Circuit:
         self.n_records += 1
         return r
 
+    def mpp(self, terms) -> int:
+        """Measure the Pauli product of `terms` = [(pauli_code, qubit), ...]
+        (codes 1 X, 2 Y, 3 Z; distinct qubits) as one record."""
+        terms = list(terms)
+        assert terms, "empty Pauli product"
+        pairs = [terms[i:i + 2] for i in range(0, len(terms), 2)]
+        for i, pr in enumerate(pairs):
+            (pa, qa) = pr[0]
+            pb, qb = pr[1] if len(pr) > 1 else (0, 0)
+            fl = (pa & 3) | ((pb & 3) << 2) | (MPP_MORE if i < len(pairs) - 1 else 0)
+            self._add(MPP, qa, qb, flags=fl)
+        r = self.n_records
+        self.n_records += 1
+        return r
+
     def reset(self, q):
         self._add(R, q)
 
@@ -119,8 +138,26 @@ class Circuit:
 
     def prefix(self, k: int) -> "Circuit":
         c = Circuit(self.n, list(self.ops[:k]), 0, self.cap, self.name)
-        c.n_records = sum(1 for o in c.ops if o[0] in (M, MR))
+        c.n_records = sum(1 for o in c.ops if records_outcome(o))
         return c
+
+
+def records_outcome(o) -> bool:
+    """True for an op tuple that appends a record: M, MR, the last op of an MPP chain."""
+    return o[0] in (M, MR) or (o[0] == MPP and not (o[1] & MPP_MORE))
+
+
+def mpp_chain_terms(ops, i):
+    """[(pauli_code, qubit), ...] of the MPP chain whose last op is ops[i]."""
+    j = i
+    while j > 0 and ops[j - 1][0] == MPP and (ops[j - 1][1] & MPP_MORE):
+        j -= 1
+    out = []
+    for o in ops[j:i + 1]:
+        out.append((o[1] & 3, o[2]))
+        if (o[1] >> 2) & 3:
+            out.append(((o[1] >> 2) & 3, o[3]))
+    return out
 
 
 # ------------------------------------------------ Pauli strings (generator only)
@@ -497,8 +534,9 @@ def random_param_circuit(seed: int, n: int, n_ops: int, n_params: int, n_checks:
 
 
 def random_circuit(seed: int, n: int, n_ops: int, t_frac=0.15, meas_frac=0.1, rz=True,
-                   resets=True, feedback=True, detectors=False) -> Circuit:
-    """Random op mix over every op kind, for differential tests on small n."""
+                   resets=True, feedback=True, detectors=False, mpp_frac=0.0) -> Circuit:
+    """Random op mix over every op kind, for differential tests on small n.
+    mpp_frac > 0 adds Pauli-product measurements of weight 1..4."""
     rng = np.random.default_rng(seed)
     c = Circuit(n, name=f"random_circuit(n={n},ops={n_ops},seed={seed})", cap=1 << 16)
     for _ in range(n_ops):
@@ -521,12 +559,16 @@ def random_circuit(seed: int, n: int, n_ops: int, t_frac=0.15, meas_frac=0.1, rz
                 c.reset(q)
             else:
                 c.measure(q, reset=True)
-        elif feedback and u < t_frac + meas_frac + 0.03 and c.n_records > 0:
+        elif u < t_frac + meas_frac + mpp_frac:
+            w = int(rng.integers(1, min(4, n) + 1))
+            qs = [int(v) for v in rng.choice(n, size=w, replace=False)]
+            c.mpp([(int(rng.integers(1, 4)), q) for q in qs])
+        elif feedback and u < t_frac + meas_frac + mpp_frac + 0.03 and c.n_records > 0:
             recs = [int(rng.integers(c.n_records))]
             if rng.random() < 0.5:
                 recs.append(int(rng.integers(c.n_records)))
             c.cpauli(int(rng.integers(n)), int(rng.integers(1, 4)), recs)
-        elif detectors and u < t_frac + meas_frac + 0.05 and c.n_records > 0:
+        elif detectors and u < t_frac + meas_frac + mpp_frac + 0.05 and c.n_records > 0:
             recs = [int(rng.integers(c.n_records)) for _ in range(int(rng.integers(1, 4)))]
             c.observable(recs, invert=bool(rng.integers(2)))
         else:

@@ -53,10 +53,25 @@ def apply_pauli_code(psi, n, code, q):
     return apply_1q(psi, n, q, PAULI[code])
 
 
+def apply_pauli_terms(psi, n, terms):
+    """prod of single-qubit Paulis [(code, qubit), ...] on distinct qubits."""
+    for code, q in terms:
+        psi = apply_1q(psi, n, q, PAULI[code])
+    return psi
+
+
+def mpp_first(circ_ops, i):
+    o = circ_ops[i]
+    if o[0] != C.MPP:
+        return False
+    return i == 0 or not (circ_ops[i - 1][0] == C.MPP and (circ_ops[i - 1][1] & C.MPP_MORE))
+
+
 def site_layout(circ_ops, noise):
     """Noise sites of the uniform depolarizing model, numbered in op order:
-    the flip before M/MR, then the site after the op (depolarizing after a
-    gate, flip after R/MR). Returns {site: (op_index, 'pre'|'post')}."""
+    the flip before M/MR (and before the first op of an MPP chain), then the
+    site after the op (depolarizing after a gate, flip after R/MR).
+    Returns {site: (op_index, 'pre'|'post')}."""
     out = {}
     ns = 0
     noiseless = False
@@ -69,7 +84,7 @@ def site_layout(circ_ops, noise):
             noiseless = False
         if noiseless:
             continue
-        if op in (C.M, C.MR) and pm > 0:
+        if (op in (C.M, C.MR) or mpp_first(circ_ops, i)) and pm > 0:
             out[ns] = (i, "pre")
             ns += 1
         if op in C.ONE_Q and p1 > 0:
@@ -150,6 +165,27 @@ def replay(circ: C.Circuit, noise: C.Noise, events, stop_after=None, band=1e-9):
                 recs.append(0 if m == 1 else 1)
             if op in (C.R, C.MR) and m == -1:
                 psi = apply_1q(psi, n, q0, PAULI[1])
+        elif op == C.MPP:
+            if fl & C.MPP_MORE:
+                err(i, "post", o)
+                continue
+            ppsi = apply_pauli_terms(psi, n, C.mpp_chain_terms(circ.ops, i))
+            tot = float(np.sum(np.abs(psi) ** 2))
+            pp = 0.5 * (1.0 + float(np.real(np.vdot(psi, ppsi))) / tot)
+            if pp < 1e-12:
+                pp = 0.0
+            if pp > 1 - 1e-12:
+                pp = 1.0
+            u, m_or, p_or = meas[i]
+            p_err = max(p_err, abs(pp - p_or))
+            m = 1 if u < pp else -1
+            if m != m_or:
+                if abs(pp - u) > band:
+                    mism += 1
+                m = m_or
+            psi = (psi + m * ppsi) / 2
+            psi = psi / np.linalg.norm(psi)
+            recs.append(0 if m == 1 else 1)
         elif op == C.CPAULI:
             par = 0
             for r in rec:
@@ -246,7 +282,7 @@ def record_distribution(circ: C.Circuit, noise: C.Noise):
     branches = [((), np.zeros((1 << n, 1 << n), complex))]
     branches[0][1][0, 0] = 1
     noiseless = False
-    for o in circ.ops:
+    for oi, o in enumerate(circ.ops):
         op, fl, q0, q1, _, ang, rec = o
         if op == C.NOISELESS_BEGIN:
             noiseless = True
@@ -259,6 +295,10 @@ def record_distribution(circ: C.Circuit, noise: C.Noise):
             if op in (C.M, C.MR) and pm > 0 and not noiseless:
                 Xq = _full_1q(n, q0, PAULI[1])
                 rho = _kraus_apply(rho, n, [(1 - pm, np.eye(1 << n)), (pm, Xq)])
+            if op == C.MPP and pm > 0 and not noiseless and mpp_first(circ.ops, oi):
+                # the flip anticommutes with the chain's first factor
+                Fq = _full_1q(n, q0, PAULI[3 if (fl & 3) == 1 else 1])
+                rho = _kraus_apply(rho, n, [(1 - pm, np.eye(1 << n)), (pm, Fq)])
             if op in C.ONE_Q:
                 U = _full_1q(n, q0, one_q_matrix(op, ang))
                 rho = U @ rho @ U.conj().T
@@ -284,8 +324,20 @@ def record_distribution(circ: C.Circuit, noise: C.Noise):
                     r2 = Pm @ rho @ Pm
                     if np.real(np.trace(r2)) > 1e-15:
                         nb.append((bits + (m,), r2))
+            elif op == C.MPP:
+                if fl & C.MPP_MORE:
+                    nb.append((bits, rho))
+                    continue
+                Pf = np.eye(1 << n, dtype=complex)
+                for code, q in C.mpp_chain_terms(circ.ops, oi):
+                    Pf = _full_1q(n, q, PAULI[code]) @ Pf
+                for m in (0, 1):
+                    Pm = (np.eye(1 << n) + (1 - 2 * m) * Pf) / 2
+                    r2 = Pm @ rho @ Pm
+                    if np.real(np.trace(r2)) > 1e-15:
+                        nb.append((bits + (m,), r2))
             else:
-                raise ValueError("record_distribution handles gates and M only")
+                raise ValueError("record_distribution handles gates, M and MPP only")
         branches = nb
     return {bits: float(np.real(np.trace(rho))) for bits, rho in branches}
 
@@ -363,6 +415,20 @@ def project_pattern(circ: C.Circuit, noise: C.Noise, sites, codes, theta=None):
                 rec_i += 1
             if op in (C.R, C.MR) and bit == 1:
                 psi = apply_1q(psi, n, q0, PAULI[1])
+        elif op == C.MPP and not (fl & C.MPP_MORE):
+            rl = role.get(rec_i, 0)
+            if rl == 1:
+                bit = target[rec_i]
+            elif rl == 2:
+                if n_acc is None:
+                    n_acc = float(np.sum(np.abs(psi) ** 2))
+                bit = 0
+            else:
+                return None
+            ppsi = apply_pauli_terms(psi, n, C.mpp_chain_terms(circ.ops, i))
+            psi = (psi + (1 - 2 * bit) * ppsi) / 2
+            bits[rec_i] = bit
+            rec_i += 1
         elif op == C.CPAULI:
             par = 0
             for r in rec:
