@@ -58,15 +58,25 @@ enum { SOFT_SHOT_KEPT = 0, SOFT_SHOT_DISCARDED = 1, SOFT_SHOT_OVERFLOW = 2, SOFT
  * 2 Y, 3 Z on q0 applied when the parity of rec[0], rec[1] is 1),
  * DETECTOR (parity of rec[] xor INVERT = 1 => shot discarded, the early
  * discard of Sec. V-C), OBSERVABLE (parity = 1 => logical error flag),
- * NOISELESS_BEGIN/END (ops in between carry no noise). */
+ * NOISELESS_BEGIN/END (ops in between carry no noise), MPP (a factor pair of
+ * a Pauli-product measurement, the general Pauli measurement of Theorem 1 (2);
+ * see SOFT_MPP_MORE). */
 enum {
   SOFT_H = 0, SOFT_S = 1, SOFT_S_DAG = 2, SOFT_X = 3, SOFT_Y = 4, SOFT_Z = 5, SOFT_CX = 6, SOFT_CZ = 7,
   SOFT_T = 8, SOFT_T_DAG = 9, SOFT_RZ = 10, SOFT_M = 11, SOFT_R = 12, SOFT_MR = 13, SOFT_CPAULI = 14,
-  SOFT_DETECTOR = 15, SOFT_OBSERVABLE = 16, SOFT_NOISELESS_BEGIN = 17, SOFT_NOISELESS_END = 18
+  SOFT_DETECTOR = 15, SOFT_OBSERVABLE = 16, SOFT_NOISELESS_BEGIN = 17, SOFT_NOISELESS_END = 18, SOFT_MPP = 19
 };
 /* DETECTOR / OBSERVABLE flags: INVERT xors 1 into the parity; CHAIN carries
  * the parity into the next DETECTOR / OBSERVABLE instead of testing it. */
 enum { SOFT_FLAG_INVERT = 1, SOFT_FLAG_CHAIN = 2 };
+/* MPP flags: bits 0-1 = Pauli on q0 (1 X, 2 Y, 3 Z, never 0), bits 2-3 =
+ * Pauli on q1 (0: no second factor), SOFT_MPP_MORE = the product continues in
+ * the next op, which must be an MPP. The chain's last op measures the product
+ * of all its factors (distinct qubits) and appends one record. With p_meas > 0
+ * a flip precedes the chain: the Pauli on its first qubit that anticommutes
+ * with the first factor (Z for X; X for Y and Z). Before M/MR the flip is X,
+ * and after R/MR an X with p_reset. */
+enum { SOFT_MPP_MORE = 16 };
 
 /* 32-byte op record. q1 only for CX (control q0, target q1) and CZ. rec[] are
  * absolute record indices (0 = first M/MR of the circuit), -1 = unused. */
@@ -145,7 +155,16 @@ typedef struct {
                             device-side advance of the chunk base) in a CUDA graph and
                             replay it for every full chunk; needs a non-NULL stream */
 } soft_run_opts;
-enum { SOFT_RUN_GRAPH = 1 };
+/* SOFT_RUN_FIDELITY: every measurement whose record an OBSERVABLE reads is
+ * projected onto +1 instead of sampled, and each kept shot adds F, the
+ * product of those measurements' conditional probabilities of +1, to the
+ * tally's sum_fidelity (F = |<0..0|phi>|^2 on the observed qubits, the exact
+ * fidelity of the final chain of Sec. V; E[1 - F | kept] is the sampled
+ * logical-error rate, estimated with lower variance). A shot for which +1 is
+ * impossible ends there, kept, with F = 0. Observed records then read 0.
+ * Needs every DETECTOR before the first observed measurement (SOFT_E_ARG
+ * otherwise). */
+enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
  * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all
@@ -161,7 +180,7 @@ int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint6
 
 typedef struct {
   uint64_t shots, discarded, overflow, kept, logical_errors;
-  double sum_fidelity, sum_weight; /* reserved accumulators (0 here) */
+  double sum_fidelity, sum_weight; /* SOFT_RUN_FIDELITY: sum of F over kept shots, and kept; else 0 */
 } soft_tally_t;
 
 /* One persistent launch sequence over up to 64 compiled circuits (shots and

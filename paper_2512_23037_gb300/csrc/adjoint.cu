@@ -359,7 +359,7 @@ struct GradWarp {
   __device__ void error_pauli(uint32_t s, uint32_t code, const uint64_t *esd, const uint64_t *ess, uint64_t *beta,
                               uint64_t *gamma, uint32_t *e) const {
     const Site *S = P.sites + s;
-    const uint32_t two = __ldg(&S->two);
+    const uint32_t two = (__ldg(&S->kind) & 3u) == SITE_DEPOL2;
     const uint32_t pa = two ? (code >> 2) : code, pb = two ? (code & 3u) : 0u;
     uint32_t q = 0;
 #pragma unroll
@@ -498,8 +498,10 @@ struct GradWarp {
           esd[w] = sd[w] ^ __ldg(&S->dsd[w]);
           ess[w] = ss[w] ^ __ldg(&S->dss[w]);
         }
-        const uint32_t code =
-            __ldg(&S->two) ? (uint32_t)(((uint64_t)w2 * 15u) >> 32) + 1u : (uint32_t)(((uint64_t)w2 * 3u) >> 32) + 1u;
+        const uint32_t kind = __ldg(&S->kind);
+        const uint32_t code = (kind & 3u) == SITE_DEPOL2 ? (uint32_t)(((uint64_t)w2 * 15u) >> 32) + 1u
+                              : (kind & 3u) == SITE_FLIP ? (kind >> 2) & 3u
+                                                         : (uint32_t)(((uint64_t)w2 * 3u) >> 32) + 1u;
         uint32_t e;
         error_pauli(nxt, code, esd, ess, b, g, &e);
         pauli(phi, b, g, e);

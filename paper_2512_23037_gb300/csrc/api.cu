@@ -40,6 +40,8 @@ struct soft_run {
   std::vector<soft_circuit *> circs;       // borrowed: must outlive the run's stream work
   std::vector<uint64_t> n_shots;
   unsigned long long *d_tally = nullptr;   // 5 counters per circuit
+  double *d_fsum = nullptr;                // fidelity mode: sum of F per circuit
+  bool fid_mode = false;
   unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4]
   uint32_t *d_rerun = nullptr;
   unsigned char *d_slab = nullptr;         // global-memory state for large-cap reruns
@@ -150,6 +152,7 @@ void soft_run_free(soft_run *r) {
   if (r->stream) cudaStreamSynchronize(r->stream);
   else cudaDeviceSynchronize();
   cudaFree(r->d_tally);
+  cudaFree(r->d_fsum);
   cudaFree(r->d_work);
   cudaFree(r->d_rerun);
   cudaFree(r->d_slab);
@@ -201,6 +204,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   if (n_circ > 1 && (o.record_mode != SOFT_REC_NONE || o.capture_k))
     return fail(SOFT_E_ARG, "records and state capture are per single-circuit run");
   const bool use_graph = (o.flags & SOFT_RUN_GRAPH) != 0;
+  const bool fid_mode = (o.flags & SOFT_RUN_FIDELITY) != 0;
+  if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY)) return fail(SOFT_E_ARG, "unknown run flags");
   if (use_graph && !o.stream) return fail(SOFT_E_ARG, "graph replay needs a non-default stream");
   const int fp32 = o.precision == SOFT_FP32;
   uint32_t W = 0, cap_max = 0, rw_max = 1;
@@ -209,6 +214,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     if (!circs[i]) return fail(SOFT_E_ARG, "null circuit");
     if (W && circs[i]->hp.W != W) return fail(SOFT_E_ARG, "all circuits of a batch need n <= 64 or all n > 64");
     if (circs[i]->device != circs[0]->device) return fail(SOFT_E_ARG, "all circuits of a batch must be on one device");
+    if (fid_mode && !circs[i]->hp.fid_ok)
+      return fail(SOFT_E_ARG, "fidelity mode needs every DETECTOR before the first observed measurement");
     W = circs[i]->hp.W;
     cap_max = std::max(cap_max, circs[i]->hp.cap);
     rw_max = std::max(rw_max, circs[i]->hp.rw);
@@ -251,6 +258,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     }                                                                                           \
   } while (0)
   SOFT_ALLOC(r->d_tally, 5 * n_circ * sizeof(unsigned long long));
+  r->fid_mode = fid_mode;
+  if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
   SOFT_ALLOC(r->d_work, 8 * sizeof(unsigned long long));
   if (two_pass) SOFT_ALLOC(r->d_rerun, chunk * sizeof(uint32_t));
   uint32_t slab_blocks = 0;
@@ -284,7 +293,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     return cuda_fail(e, "cudaEventCreate");
   }
   if ((e = cudaMemsetAsync(r->d_tally, 0, 5 * n_circ * sizeof(unsigned long long), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(r->d_work, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess) {
+      (e = cudaMemsetAsync(r->d_work, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (fid_mode && (e = cudaMemsetAsync(r->d_fsum, 0, n_circ * sizeof(double), st)) != cudaSuccess)) {
     soft_run_free(r);
     return cuda_fail(e, "cudaMemsetAsync");
   }
@@ -298,6 +308,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.circ[i].n_shots = n_shots[i];
     p.circ[i].first_shot = first_shots[i];
     p.circ[i].tally = r->d_tally + 5 * i;
+    p.circ[i].fsum = fid_mode ? r->d_fsum + i : nullptr;
     begin += n_shots[i];
   }
   p.circ[0].status = r->d_status;
@@ -312,6 +323,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   p.n_rerun = r->d_work + 2;
   p.diag = r->d_work + 4;
   p.groups_per_block = o.groups_per_block;
+  p.fid_mode = fid_mode ? 1 : 0;
   if (r->st_limit) {
     p.st_limit = r->st_limit;
     p.st_signs = r->d_st_signs;
@@ -428,13 +440,19 @@ int soft_tally_batch(soft_run *r, uint32_t index, soft_tally_t *out) {
   cudaError_t e = cudaMemcpyAsync(t, r->d_tally + 5 * index, sizeof t, cudaMemcpyDeviceToHost, r->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
   if (e != cudaSuccess) return cuda_fail(e, "tally copy");
+  double f = 0.0;
+  if (r->fid_mode) {
+    e = cudaMemcpyAsync(&f, r->d_fsum + index, sizeof f, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fidelity sum copy");
+  }
   out->shots = t[0];
   out->discarded = t[1];
   out->overflow = t[2];
   out->kept = t[3];
   out->logical_errors = t[4];
-  out->sum_fidelity = 0.0;
-  out->sum_weight = 0.0;
+  out->sum_fidelity = f;
+  out->sum_weight = r->fid_mode ? (double)t[3] : 0.0;
   return SOFT_OK;
 }
 
@@ -447,13 +465,21 @@ int soft_tally(soft_run *r, soft_tally_t *out) {
   if (e != cudaSuccess) return cuda_fail(e, "tally copy");
   uint64_t s[5] = {0, 0, 0, 0, 0};
   for (size_t i = 0; i < t.size(); ++i) s[i % 5] += t[i];
+  double f = 0.0;
+  if (r->fid_mode) {
+    std::vector<double> fs(r->n_circ);
+    e = cudaMemcpyAsync(fs.data(), r->d_fsum, fs.size() * sizeof(double), cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fidelity sum copy");
+    for (double v : fs) f += v;
+  }
   out->shots = s[0];
   out->discarded = s[1];
   out->overflow = s[2];
   out->kept = s[3];
   out->logical_errors = s[4];
-  out->sum_fidelity = 0.0;
-  out->sum_weight = 0.0;
+  out->sum_fidelity = f;
+  out->sum_weight = r->fid_mode ? (double)s[3] : 0.0;
   return SOFT_OK;
 }
 

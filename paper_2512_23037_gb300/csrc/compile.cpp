@@ -285,13 +285,15 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
   bool noiseless = false;
   uint32_t nrec = 0, ord = 0;
 
-  auto add_site = [&](uint32_t q0, uint32_t q1, bool two, double p) -> bool {
+  // kind: SITE_DEPOL1, SITE_DEPOL2, or SITE_FLIP | code << 2
+  auto add_site = [&](uint32_t q0, uint32_t q1, uint32_t kind, double p) -> bool {
+    const bool two = (kind & 3u) == SITE_DEPOL2;
     Site s{};
     s.dsd[0] = tb.pend_d[0];
     s.dsd[1] = tb.pend_d[1];
     s.dss[0] = tb.pend_s[0];
     s.dss[1] = tb.pend_s[1];
-    s.two = two ? 1u : 0u;
+    s.kind = kind;
     for (int k = 0; k < (two ? 2 : 1); ++k) {
       uint32_t q = k == 0 ? q0 : q1;
       uint32_t e;
@@ -363,7 +365,7 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
     uint32_t nr = 0;
     for (size_t i = 0; i < n_ops; ++i) {
       int op = ops[i].op;
-      if (op == SOFT_M || op == SOFT_MR) nr++;
+      if (op == SOFT_M || op == SOFT_MR || (op == SOFT_MPP && !(ops[i].flags & SOFT_MPP_MORE))) nr++;
       if (op == SOFT_OBSERVABLE)
         for (int k = 0; k < 2; ++k)
           if (ops[i].rec[k] >= 0 && (uint32_t)ops[i].rec[k] < nr) {
@@ -373,14 +375,89 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
     }
   }
 
+  // One Pauli measurement of P (Theorem 1 (2)): case A when P commutes with
+  // every stabilizer row, else case B with its row operations and
+  // replacement constants. Returns false on an internal inconsistency.
+  auto meas_event = [&](const Pz &Pm, bool recd) -> bool {
+    uint64_t beta[2], gamma[2];
+    uint32_t e0;
+    if (!tb.decompose(Pm, beta, gamma, &e0)) return false;
+    const uint32_t fidf = (recd && nrec < observed.size() && observed[nrec]) ? F_FIDELITY : 0u;
+    if ((beta[0] | beta[1]) == 0) {
+      Ev<2> &e = new_event(EV_MEAS_A, (recd ? F_RECORD : 0) | fidf, e0, 0);
+      std::memcpy(e.gamma, gamma, sizeof gamma);
+      e.a = ord;
+      e.b = recd ? nrec : 0;
+      return true;
+    }
+    CaseB cb{};
+    uint32_t p = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
+    cb.p = p;
+    cb.J[0] = beta[0];
+    cb.J[1] = beta[1];
+    flip(cb.J, p);
+    // s_j <- s_j s_p
+    for (uint32_t j = 0; j < n; ++j)
+      if (bit(cb.J, j)) {
+        Pz prod = pmul(herm(tb.s[j]), herm(tb.s[p]));
+        int sb = sign_bit(prod);
+        if (sb < 0) return false;
+        if (sb) flip(cb.Hs, j);
+        tb.s[j] = row_of(prod);
+      }
+    // d_p <- d_p prod_{j in J} d_j
+    {
+      Pz acc = herm(tb.d[p]);
+      for (uint32_t j = 0; j < n; ++j)
+        if (bit(cb.J, j)) acc = pmul(acc, herm(tb.d[j]));
+      int sb = sign_bit(acc);
+      if (sb < 0) return false;
+      cb.hdp = (uint32_t)sb;
+      tb.d[p] = row_of(acc);
+    }
+    uint64_t b2[2];
+    if (!tb.decompose(Pm, b2, cb.gamma2, &cb.e0b)) return false;
+    if (b2[0] != (p < 64 ? (1ull << p) : 0) || b2[1] != (p >= 64 ? (1ull << (p - 64)) : 0)) return false;
+    Row old_sp = tb.s[p];
+    for (uint32_t j = 0; j < n; ++j)
+      if (j != p && bit(cb.gamma2, j)) {
+        flip(cb.G, j);
+        Pz prod = pmul(herm(tb.d[j]), herm(old_sp));
+        int sb = sign_bit(prod);
+        if (sb < 0) return false;
+        if (sb) flip(cb.Hd, j);
+        tb.d[j] = row_of(prod);
+      }
+    tb.d[p] = old_sp;
+    // s_p <- m P: the row of P with P's own sign bit, flipped on the device when m = -1
+    const int rp = sign_bit(Pm);
+    if (rp < 0) return false;
+    tb.s[p] = row_of(Pm);
+    cb.rP = (uint32_t)rp;
+    Ev<2> &e = new_event(EV_MEAS_B, (recd ? F_RECORD : 0) | fidf, 0, 0);
+    e.a = ord;
+    e.b = recd ? nrec : 0;
+    e.beta[0] = P.cb.size();
+    P.cb.push_back(cb);
+    return true;
+  };
+
+  Pz mpp_acc;                     // product of the open MPP chain's factors
+  uint64_t mpp_q[2] = {0, 0};     // its qubits
+  bool mpp_open = false, seen_observed = false;
   for (size_t i = 0; i < n_ops; ++i) {
     const soft_op &o = ops[i];
     int op = o.op;
-    if (op > SOFT_NOISELESS_END) {
+    if (op > SOFT_MPP) {
       err = "unknown op code at op " + std::to_string(i);
       return SOFT_E_UNSUPPORTED_OP;
     }
-    bool needs_q = is1q(op) || is2q(op) || op == SOFT_M || op == SOFT_R || op == SOFT_MR || op == SOFT_CPAULI;
+    if (mpp_open && op != SOFT_MPP) {
+      err = "an MPP chain is continued by a non-MPP op at op " + std::to_string(i);
+      return SOFT_E_ARG;
+    }
+    bool needs_q = is1q(op) || is2q(op) || op == SOFT_M || op == SOFT_R || op == SOFT_MR || op == SOFT_CPAULI ||
+                   op == SOFT_MPP;
     if (needs_q && o.q0 >= n) {
       err = "qubit out of range at op " + std::to_string(i);
       return SOFT_E_QUBIT_RANGE;
@@ -389,6 +466,27 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
       err = "bad second qubit at op " + std::to_string(i);
       return SOFT_E_QUBIT_RANGE;
     }
+    const bool mpp_first = op == SOFT_MPP && !mpp_open;
+    if (op == SOFT_MPP) {
+      const int pa = o.flags & 3, pb = (o.flags >> 2) & 3;
+      if (pa == 0 || (o.flags & ~(uint32_t)(15 | SOFT_MPP_MORE))) {
+        err = "bad MPP flags at op " + std::to_string(i);
+        return SOFT_E_ARG;
+      }
+      if (pb && (o.q1 >= n || o.q1 == o.q0)) {
+        err = "bad second MPP qubit at op " + std::to_string(i);
+        return SOFT_E_QUBIT_RANGE;
+      }
+      if (bit(mpp_q, o.q0) || (pb && bit(mpp_q, o.q1))) {
+        err = "MPP chain repeats a qubit at op " + std::to_string(i);
+        return SOFT_E_ARG;
+      }
+      if ((o.flags & SOFT_MPP_MORE) && i + 1 == n_ops) {
+        err = "MPP chain left open at the end of the circuit";
+        return SOFT_E_ARG;
+      }
+    }
+    if (op == SOFT_DETECTOR && seen_observed) P.fid_ok = false;
     if (op == SOFT_DETECTOR || op == SOFT_OBSERVABLE || op == SOFT_CPAULI) {
       for (int k = 0; k < 2; ++k)
         if (o.rec[k] >= 0 && (uint32_t)o.rec[k] >= nrec) {
@@ -399,8 +497,14 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
     if (op == SOFT_NOISELESS_BEGIN) noiseless = true;
     if (op == SOFT_NOISELESS_END) noiseless = false;
 
-    if ((op == SOFT_M || op == SOFT_MR) && !noiseless && noise->p_meas > 0)
-      if (!add_site(o.q0, 0, false, noise->p_meas)) goto internal;
+    if (!noiseless && noise->p_meas > 0) {
+      if (op == SOFT_M || op == SOFT_MR) {
+        if (!add_site(o.q0, 0, SITE_FLIP | (1u << 2), noise->p_meas)) goto internal;
+      } else if (mpp_first) {
+        const uint32_t fc = (o.flags & 3) == 1 ? 3u : 1u;  // anticommutes with the first factor
+        if (!add_site(o.q0, 0, SITE_FLIP | (fc << 2), noise->p_meas)) goto internal;
+      }
+    }
 
     if (isclifford(op)) {
       if (!tb.gate(op, o.q0, o.q1)) goto internal;
@@ -438,70 +542,29 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
       std::memcpy(e.beta, beta, sizeof beta);
       std::memcpy(e.gamma, gamma, sizeof gamma);
     } else if (op == SOFT_M || op == SOFT_R || op == SOFT_MR) {
-      uint64_t beta[2], gamma[2];
-      uint32_t e0;
-      Pz Zq = single(3, o.q0);
-      if (!tb.decompose(Zq, beta, gamma, &e0)) goto internal;
       bool recd = (op != SOFT_R);
-      if ((beta[0] | beta[1]) == 0) {
-        const uint32_t fidf = (recd && nrec < observed.size() && observed[nrec]) ? F_FIDELITY : 0u;
-        Ev<2> &e = new_event(EV_MEAS_A, (recd ? F_RECORD : 0) | fidf, e0, 0);
-        std::memcpy(e.gamma, gamma, sizeof gamma);
-        e.a = ord;
-        e.b = recd ? nrec : 0;
-      } else {
-        CaseB cb{};
-        uint32_t p = beta[0] ? (uint32_t)__builtin_ctzll(beta[0]) : 64u + (uint32_t)__builtin_ctzll(beta[1]);
-        cb.p = p;
-        cb.J[0] = beta[0];
-        cb.J[1] = beta[1];
-        flip(cb.J, p);
-        // s_j <- s_j s_p
-        for (uint32_t j = 0; j < n; ++j)
-          if (bit(cb.J, j)) {
-            Pz prod = pmul(herm(tb.s[j]), herm(tb.s[p]));
-            int sb = sign_bit(prod);
-            if (sb < 0) goto internal;
-            if (sb) flip(cb.Hs, j);
-            tb.s[j] = row_of(prod);
-          }
-        // d_p <- d_p prod_{j in J} d_j
-        {
-          Pz acc = herm(tb.d[p]);
-          for (uint32_t j = 0; j < n; ++j)
-            if (bit(cb.J, j)) acc = pmul(acc, herm(tb.d[j]));
-          int sb = sign_bit(acc);
-          if (sb < 0) goto internal;
-          cb.hdp = (uint32_t)sb;
-          tb.d[p] = row_of(acc);
-        }
-        uint64_t b2[2];
-        if (!tb.decompose(Zq, b2, cb.gamma2, &cb.e0b)) goto internal;
-        if (b2[0] != (p < 64 ? (1ull << p) : 0) || b2[1] != (p >= 64 ? (1ull << (p - 64)) : 0)) goto internal;
-        Row old_sp = tb.s[p];
-        for (uint32_t j = 0; j < n; ++j)
-          if (j != p && bit(cb.gamma2, j)) {
-            flip(cb.G, j);
-            Pz prod = pmul(herm(tb.d[j]), herm(old_sp));
-            int sb = sign_bit(prod);
-            if (sb < 0) goto internal;
-            if (sb) flip(cb.Hd, j);
-            tb.d[j] = row_of(prod);
-          }
-        tb.d[p] = old_sp;
-        tb.s[p] = row_of(Zq);
-        cb.rP = 0;
-        const uint32_t fidf = (recd && nrec < observed.size() && observed[nrec]) ? F_FIDELITY : 0u;
-        Ev<2> &e = new_event(EV_MEAS_B, (recd ? F_RECORD : 0) | fidf, 0, 0);
-        e.a = ord;
-        e.b = recd ? nrec : 0;
-        e.beta[0] = P.cb.size();
-        P.cb.push_back(cb);
-      }
+      if (recd && nrec < observed.size() && observed[nrec]) seen_observed = true;
+      if (!meas_event(single(3, o.q0), recd)) goto internal;
       ord++;
       if (recd) nrec++;
       if (op == SOFT_R || op == SOFT_MR)
         if (!pauli_event(single(1, o.q0), F_COND_LAST, -1, -1)) goto internal;
+    } else if (op == SOFT_MPP) {
+      if (!mpp_open) mpp_acc = Pz{};
+      mpp_acc = pmul(mpp_acc, single(o.flags & 3, o.q0));
+      flip(mpp_q, o.q0);
+      if ((o.flags >> 2) & 3) {
+        mpp_acc = pmul(mpp_acc, single((o.flags >> 2) & 3, o.q1));
+        flip(mpp_q, o.q1);
+      }
+      mpp_open = (o.flags & SOFT_MPP_MORE) != 0;
+      if (!mpp_open) {
+        mpp_q[0] = mpp_q[1] = 0;
+        if (nrec < observed.size() && observed[nrec]) seen_observed = true;
+        if (!meas_event(mpp_acc, true)) goto internal;
+        ord++;
+        nrec++;
+      }
     } else if (op == SOFT_CPAULI) {
       int code = o.flags & 3;
       if (code) {
@@ -517,11 +580,11 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
 
     if (!noiseless) {
       if (is1q(op) && noise->p1 > 0) {
-        if (!add_site(o.q0, 0, false, noise->p1)) goto internal;
+        if (!add_site(o.q0, 0, SITE_DEPOL1, noise->p1)) goto internal;
       } else if (is2q(op) && noise->p2 > 0) {
-        if (!add_site(o.q0, o.q1, true, noise->p2)) goto internal;
+        if (!add_site(o.q0, o.q1, SITE_DEPOL2, noise->p2)) goto internal;
       } else if ((op == SOFT_R || op == SOFT_MR) && noise->p_reset > 0) {
-        if (!add_site(o.q0, 0, false, noise->p_reset)) goto internal;
+        if (!add_site(o.q0, 0, SITE_FLIP | (1u << 2), noise->p_reset)) goto internal;
       }
     }
   }

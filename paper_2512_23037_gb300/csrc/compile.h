@@ -23,6 +23,7 @@ struct HostProgram {
   std::vector<uint64_t> thr;     // gap thresholds, one per site
   std::vector<uint64_t> fin_x;   // final X words, 2n rows x 2 words
   std::vector<uint64_t> fin_z;
+  bool fid_ok = true;  // no DETECTOR at or after the first measurement an OBSERVABLE reads
 };
 
 // Returns SOFT_OK or a SOFT_E_* code with a message in `err`.

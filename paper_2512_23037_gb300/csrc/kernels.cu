@@ -62,6 +62,8 @@ struct Shot {
   uint64_t sd[W], ss[W];
   uint32_t nxt, cur, kblk, w2;
   int status, chain, logical, lastm;
+  bool force = false;  // fidelity mode: this measurement projects onto +1
+  double fid = 1.0;    // fidelity mode: product of the projected measurements' p_+
   // register mode (G = 32 only): while |v| <= 32, lane i < nnz holds entry i
   static constexpr bool kRegCapable = (G == 32);
   bool reg;
@@ -224,11 +226,16 @@ struct Shot {
       return;
     }
     const Site *S = C->sites + s;
-    uint32_t two = __ldg(&S->two), code, pa, pb;
-    if (two) {
+    const uint32_t kind = __ldg(&S->kind);
+    uint32_t code, pa, pb;
+    if ((kind & 3u) == SITE_DEPOL2) {
       code = (uint32_t)(((uint64_t)w2 * 15u) >> 32) + 1u;
       pa = code >> 2;
       pb = code & 3u;
+    } else if ((kind & 3u) == SITE_FLIP) {
+      code = (kind >> 2) & 3u;
+      pa = code;
+      pb = 0;
     } else {
       code = (uint32_t)(((uint64_t)w2 * 3u) >> 32) + 1u;
       pa = code;
@@ -396,6 +403,19 @@ struct Shot {
     if (t.any(valid && norm2(rv) < tau)) reg_compact(valid && norm2(rv) >= tau);
   }
 
+  // Outcome of a non-deterministic measurement with p_+ = pp: sampled from the
+  // stream, or in fidelity mode +1 (weight pp) unless +1 is impossible.
+  __device__ __forceinline__ int pick(uint32_t ord, double pp) {
+    if (force) {
+      if (pp > 0.0) {
+        fid *= pp;
+        return 1;
+      }
+      return -1;
+    }
+    return uniform(ord) < pp ? 1 : -1;
+  }
+
   __device__ int reg_meas_a(uint32_t sgn, uint32_t ord, const uint64_t *gamma) {
     const bool valid = lane < nnz;
     const bool neg = valid && (kpar(rk, gamma) ^ sgn);
@@ -404,7 +424,7 @@ struct Shot {
     const double a2 = valid ? norm2d(rv) : 0.0;
     const double sp = tile_sum(neg ? 0.0 : a2), sm = tile_sum(neg ? a2 : 0.0);
     const double pp = snap01(sp / (sp + sm));
-    const int m = uniform(ord) < pp ? 1 : -1;
+    const int m = pick(ord, pp);
     const R sc = (R)(1.0 / sqrt(m == 1 ? sp : sm));
     bool keep = valid && (neg == (m == -1));
     if (keep) rv = cscale(rv, sc);
@@ -432,7 +452,7 @@ struct Shot {
     const double sp = tile_sum(owner ? 0.5 * norm2d(cadd(v0, x1)) : 0.0);
     const double sm = tile_sum(owner ? 0.5 * norm2d(csub(v0, x1)) : 0.0);
     const double pp = snap01(sp / (sp + sm));
-    const int m = uniform(ord) < pp ? 1 : -1;
+    const int m = pick(ord, pp);
     const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
     if (owner) {
       rv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
@@ -606,7 +626,7 @@ struct Shot {
     sp = tile_sum(sp);
     sm = tile_sum(sm);
     const double pp = snap01(sp / (sp + sm));
-    const int m = uniform(ord) < pp ? 1 : -1;
+    const int m = pick(ord, pp);
     const R sc = (R)(1.0 / sqrt(m == 1 ? sp : sm));
     const uint32_t want = (m == 1) ? 0u : 1u;
     const R tau = (R)P.tau;
@@ -695,7 +715,7 @@ struct Shot {
       return 1;
     }
     const double pp = snap01(sp / (sp + sm));
-    const int m = uniform(ord) < pp ? 1 : -1;
+    const int m = pick(ord, pp);
     const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
     // stage the paired values in slots [cap, cap + nnz)
     for (uint32_t i = lane; i < nnz; i += G) {
@@ -760,6 +780,8 @@ struct Shot {
     }
     cur = 0;
     kblk = 0;
+    fid = 1.0;
+    force = false;
     draw_next();
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
     const uint32_t n_events = C->n_events;
@@ -794,7 +816,13 @@ struct Shot {
         case EV_ROT_DIAG: rot_diag(w0, hdr.z, gamma); break;
         case EV_MEAS_A:
         case EV_MEAS_B: {
+          force = P.fid_mode && (flags & F_FIDELITY);
           int m = (type == EV_MEAS_A) ? meas_a(w0, hdr.z, gamma) : meas_b(hdr.z, (uint32_t)beta[0]);
+          if (force && m == -1 && status == ST_RUN) {  // +1 impossible: F = 0, the shot ends kept
+            fid = 0.0;
+            status = ST_KEPT;
+            break;
+          }
           lastm = m;
           if (flags & F_RECORD) set_record(hdr.w, m);
           if ((flags & F_COND_LAST) && m == -1 && status == ST_RUN) {  // fused reset correction
@@ -858,6 +886,7 @@ struct Shot {
       else if (status == ST_KEPT) {
         atomicAdd(&btally[ci][3], 1ull);
         if (logical) atomicAdd(&btally[ci][4], 1ull);
+        if (P.fid_mode && C->fsum) atomicAdd(C->fsum, fid);
       }
       if (off < C->out_limit && C->status) C->status[off] = (uint8_t)status;
     }

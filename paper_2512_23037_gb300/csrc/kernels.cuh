@@ -23,6 +23,7 @@ struct CircDev {
   uint32_t n_coef, n_cb, pad0, pad1;
   uint64_t item_begin, n_shots, first_shot;
   unsigned long long *tally;  // [5]: shots, discarded, overflow, kept, logical
+  double *fsum;               // fidelity mode: sum of F over kept shots (may be null)
   uint8_t *status;            // per shot offset < out_limit
   uint64_t *records;          // rw words per shot offset < out_limit
   uint64_t out_limit;
@@ -59,6 +60,9 @@ struct ShotParams {
   uint32_t groups_per_block;  // 0 = 4 (block of 128 threads for 32-lane groups)
   // first failed in-kernel check: [0] count, [1] code << 32 | event, [2] shot, [3] value
   unsigned long long *diag;
+  // fidelity mode: measurements flagged F_FIDELITY project onto +1 and each
+  // kept shot adds the product of their conditional probabilities to fsum
+  int fid_mode;
   CircDev circ[kMaxCirc];
 };
 

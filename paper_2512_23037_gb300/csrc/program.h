@@ -92,10 +92,13 @@ struct alignas(16) CaseB {
 
 // One noise site. X_q / Z_q of the site's qubits (index 0 = q0, 1 = q1)
 // carry beta/gamma words; c0 holds 2 bits per Pauli code (code 1..15).
+// kind: bits 0-1 = SITE_DEPOL1 (X, Y, Z uniform), SITE_DEPOL2 (15 Paulis
+// uniform) or SITE_FLIP (the one-qubit Pauli code in bits 2-3).
+enum : uint32_t { SITE_DEPOL1 = 0, SITE_DEPOL2 = 1, SITE_FLIP = 2 };
 struct alignas(16) Site {
   uint64_t dsd[2], dss[2];  // sign XOR since the previous event
   uint64_t bx[2][2], gx[2][2], bz[2][2], gz[2][2];
-  uint32_t two, thin, always, c0;
+  uint32_t kind, thin, always, c0;
 };
 
 constexpr uint32_t kNoRec = 0xFFFFFFFFu;
