@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--graph", action="store_true", help="replay chunks from a captured CUDA graph")
     ap.add_argument("--chunk", type=int, default=0, help="shots per chunk (0 = library default)")
     ap.add_argument("--autotune", action="store_true", help="time launch-shape candidates first")
+    ap.add_argument("--grad-patterns", type=int, default=100000,
+                    help="error patterns per step of the gradient leg (0 = skip it)")
+    ap.add_argument("--no-fidelity", action="store_true", help="skip the exact-fidelity leg")
     return ap.parse_args()
 
 
@@ -184,6 +187,44 @@ def ops_per_shot_items(items):
     return tot_ops / tot_w, None
 
 
+def grad_bench(S, C, torch, stream, n_pat, steps, warmup):
+    """Patterns/s of the fidelity gradient (forward projection + two adjoint
+    sweeps per pattern) on the 42-qubit workload with every T/T^dag pair as
+    Rz(+-theta_i), 72 angles theta_i = pi/4 + N(0, 0.01), p = 1e-3."""
+    circ, noise = C.workload("w42rz")
+    theta = C.rz_thetas(1, 72)
+    h = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    out = {"workload": "w42rz: the w42 circuit with T/T^dag -> Rz(+theta_i)/Rz(-theta_i), 72 angles "
+                       "theta_i = pi/4 + N(0, 0.01) (seed 1), error patterns of p=1e-3, Philox seed 0",
+           "patterns_per_step": n_pat, "params": 72}
+    for prec in ("fp64", "fp32"):
+        for w in range(warmup):
+            S.soft_fidelity_grad(h, theta, n_pat, (1 << 40) + w * n_pat, 0, prec, stream=stream)
+        torch.cuda.synchronize()
+        ms = 0.0
+        counts = [0, 0, 0, 0]
+        sums = None
+        for k in range(steps):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            fid, pacc, grad, st, sm = S.soft_fidelity_grad(h, theta, n_pat, k * n_pat, 0, prec, stream=stream,
+                                                           sums=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            binc = torch.bincount(st.long(), minlength=4).cpu().tolist()
+            counts = [a + b for a, b in zip(counts, binc[:4])]
+            sm = sm.cpu().tolist()
+            sums = sm if sums is None else [a + b for a, b in zip(sums, sm)]
+        out[prec] = {"value": n_pat * steps / (ms / 1000), "unit": "patterns/s", "ms_per_step": ms / steps,
+                     "status_counts": {"ok": counts[0], "zero_acceptance": counts[1], "unsupported": counts[2],
+                                       "error": counts[3]},
+                     "ratio_estimator": (sums[1] / sums[0]) if sums and sums[0] > 0 else None}
+    h.free()
+    return out
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -248,17 +289,17 @@ def main():
     def compile_all():
         return [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz, _ in items]
 
-    def launch(handles, first, precision):
+    def launch(handles, first, precision, fidelity=False):
         if len(handles) == 1:
             return S.soft_run_shots(handles[0], items[0][2], first, 0, precision=precision, stream=stream,
-                                    graph=args.graph, **tune)
+                                    graph=args.graph, fidelity=fidelity, **tune)
         return S.soft_run_batch(handles, [s for _, _, s in items], [first] * len(handles), 0, precision=precision,
-                                stream=stream, graph=args.graph, **tune)
+                                stream=stream, graph=args.graph, fidelity=fidelity, **tune)
 
-    def time_path(precision, steps, warmup):
+    def time_path(precision, steps, warmup, fidelity=False):
         hs = compile_all()
         for w in range(warmup):
-            r = launch(hs, base_shot + (1 << 36) + w * n, precision)
+            r = launch(hs, base_shot + (1 << 36) + w * n, precision, fidelity)
             S.soft_tally(r)
             r.free()
         barrier()
@@ -270,7 +311,7 @@ def main():
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            r = launch(hs, base_shot + k * n, precision)
+            r = launch(hs, base_shot + k * n, precision, fidelity)
             ev1.record(stream)
             tallies.append(S.soft_tally(r))
             ms, nl = S.soft_run_timing(r)
@@ -297,6 +338,23 @@ def main():
     ms64 = None
     if not args.no_fp64:
         ms64, launches64, kms64, tal64, _ = time_path("fp64", args.steps, args.warmup)
+
+    # exact-fidelity mode: the same shots with the final chain projected (variance-reduced LER)
+    fid_leg = None
+    if not args.no_fidelity:
+        msf, _, _, talf, _ = time_path("fp32", max(1, args.steps // 2), 1, fidelity=True)
+        sf = sum(t["sum_fidelity"] for t in talf)
+        sw = sum(t["sum_weight"] for t in talf)
+        kept = sum(t["kept"] for t in tal32[:len(talf)])
+        le = sum(t["logical_errors"] for t in tal32[:len(talf)])
+        fid_leg = {"value": n * world * len(talf) / (msf / 1000), "unit": "shots/s", "dtype": "f32",
+                   "ler_fidelity_estimate": (1 - sf / sw) if sw else None,
+                   "ler_sampled_same_shots": (le / kept) if kept else None, "kept": int(sw)}
+
+    # Rz adjoint gradient: fixed error patterns of the 42-qubit workload with 72 Rz angles
+    grad_leg = None
+    if args.grad_patterns > 0 and world == 1:
+        grad_leg = grad_bench(S, C, torch, stream, args.grad_patterns, max(2, args.steps // 2), 1)
 
     # end to end through the C ABI: host op lists -> compile + upload -> run -> tally to host
     barrier()
@@ -353,6 +411,10 @@ def main():
                 "d2h_bytes_per_step": 56},
         "clocks": clock_info,
     }
+    if fid_leg:
+        line["fidelity_mode"] = fid_leg
+    if grad_leg:
+        line["gradient"] = grad_leg
     if tuned:
         line["autotune"] = tuned
     if not args.no_cpu_baseline:

@@ -271,12 +271,15 @@ int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_sho
  *   (n_patterns x n_params doubles, row-major), d_status (n_patterns bytes:
  *   0 ok, 1 zero acceptance (skipped, F = 0), 2 unsupported (a map above 32
  *   entries, an undecided reset, a multi-record detector), 3 error).
+ *   d_sums (may be NULL): 3 doubles, zeroed by the call, receiving the sums
+ *   over ok patterns of N_acc and of N_fid = N_acc F, and their count; the
+ *   ratio estimator of the post-selected fidelity is d_sums[1] / d_sums[0].
  * Synchronous: returns after the work on `stream` finished. Scratch (the
  * per-warp tape) is allocated and freed inside the call.
  * Errors: SOFT_E_ARG, SOFT_E_OOM, SOFT_E_CUDA. */
 int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t n_params, uint64_t n_patterns,
                        uint64_t first_pattern, uint64_t seed, int32_t precision, void *stream, double *d_fid,
-                       double *d_pacc, double *d_grad, uint8_t *d_status);
+                       double *d_pacc, double *d_grad, uint8_t *d_status, double *d_sums);
 
 const char *soft_last_error(void);
 

@@ -100,7 +100,7 @@ def load(build_if_missing: bool = True):
         L.soft_run_diagnostics.argtypes = [vp, vp]
         L.soft_run_batch.argtypes = [vp, vp, vp, u32, u64, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
         L.soft_tally_batch.argtypes = [vp, u32, ctypes.POINTER(_Tally)]
-        L.soft_fidelity_grad.argtypes = [vp, vp, u32, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp, vp]
+        L.soft_fidelity_grad.argtypes = [vp, vp, u32, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp, vp, vp]
         L.soft_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -300,10 +300,12 @@ def soft_run_shots_noalloc(circ: Circuit, n_shots: int, first_shot: int, seed: i
 
 
 def soft_fidelity_grad(circ: Circuit, theta, n_patterns: int, first_pattern: int = 0, seed: int = 0,
-                       precision="fp64", stream=None):
+                       precision="fp64", stream=None, sums=False):
     """Post-selected fidelity F, acceptance N_acc, dF/dtheta and status of
     fixed error patterns (see include/soft.h). Returns torch tensors on the
-    current CUDA device: F (n,), p_acc (n,), grad (n, n_params), status (n,)."""
+    current CUDA device: F (n,), p_acc (n,), grad (n, n_params), status (n,),
+    and with sums=True also (3,) = [sum N_acc, sum N_acc F, ok count] over ok
+    patterns (the ratio estimator is sums[1] / sums[0])."""
     import torch
     th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
     n = int(n_patterns)
@@ -312,6 +314,7 @@ def soft_fidelity_grad(circ: Circuit, theta, n_patterns: int, first_pattern: int
     pacc = torch.zeros(n, dtype=torch.float64, device=dev)
     grad = torch.zeros((n, len(th)), dtype=torch.float64, device=dev)
     status = torch.zeros(n, dtype=torch.uint8, device=dev)
+    s3 = torch.zeros(3, dtype=torch.float64, device=dev) if sums else None
     if stream is None:
         stream = torch.cuda.current_stream()
     if hasattr(stream, "cuda_stream"):
@@ -319,5 +322,8 @@ def soft_fidelity_grad(circ: Circuit, theta, n_patterns: int, first_pattern: int
     _check(load().soft_fidelity_grad(circ.h, th.ctypes.data if len(th) else None, len(th), n, int(first_pattern),
                                      int(seed) & (2 ** 64 - 1), FP32 if precision in ("fp32", FP32) else FP64,
                                      ctypes.c_void_p(int(stream) if stream else 0), fid.data_ptr(),
-                                     pacc.data_ptr(), grad.data_ptr() if len(th) else None, status.data_ptr()))
+                                     pacc.data_ptr(), grad.data_ptr() if len(th) else None, status.data_ptr(),
+                                     s3.data_ptr() if s3 is not None else None))
+    if sums:
+        return fid, pacc, grad, status, s3
     return fid, pacc, grad, status

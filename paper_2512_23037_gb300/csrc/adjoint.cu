@@ -669,6 +669,11 @@ struct GradWarp {
       P.status[off] = status;
       P.fid[off] = status == G_OK ? F : 0.0;
       P.pacc[off] = status == G_OK ? n_acc : 0.0;
+      if (P.sums && status == G_OK) {  // ratio estimator sum N_fid / sum N_acc = sum p_acc F / sum p_acc
+        atomicAdd(&P.sums[0], n_acc);
+        atomicAdd(&P.sums[1], n_fid);
+        atomicAdd(&P.sums[2], 1.0);
+      }
     }
     if (status != G_OK)
       for (uint32_t k = lane; k < P.n_params; k += 32) grad[k] = 0.0;

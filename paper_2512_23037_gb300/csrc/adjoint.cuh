@@ -20,6 +20,7 @@ struct GradParams {
   unsigned long long *next;  // work counter (zeroed before launch)
   double *fid, *pacc, *grad;  // per pattern: F, N_acc, dF/dtheta (n_params)
   uint8_t *status;            // per pattern: 0 ok, 1 zero acceptance, 2 unsupported, 3 error
+  double *sums;               // optional: sum of N_acc, sum of N_fid, count over ok patterns
   unsigned char *tape;        // one slot of tape_stride bytes per resident warp
   size_t tape_stride;
 };

@@ -12,7 +12,8 @@
 
 extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t n_params, uint64_t n_patterns,
                                   uint64_t first_pattern, uint64_t seed, int32_t precision, void *stream,
-                                  double *d_fid, double *d_pacc, double *d_grad, uint8_t *d_status) {
+                                  double *d_fid, double *d_pacc, double *d_grad, uint8_t *d_status,
+                                  double *d_sums) {
   if (!c || !d_fid || !d_pacc || !d_status || (n_params && (!theta || !d_grad)))
     return soft::set_error(SOFT_E_ARG, "null argument");
   if (precision != SOFT_FP64 && precision != SOFT_FP32) return soft::set_error(SOFT_E_ARG, "bad precision");
@@ -54,7 +55,8 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   }
   if ((!coefs.empty() && (e = cudaMemcpyAsync(d_coef, coefs.data(), coefs.size() * sizeof(soft::Coef),
                                               cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
-      (e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st)) != cudaSuccess) {
+      (e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+      (d_sums && (e = cudaMemsetAsync(d_sums, 0, 3 * sizeof(double), st)) != cudaSuccess)) {
     cleanup();
     return soft::set_error(SOFT_E_CUDA, "upload failed");
   }
@@ -79,6 +81,7 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   p.pacc = d_pacc;
   p.grad = d_grad;
   p.status = d_status;
+  p.sums = d_sums;
   p.tape = d_tape;
   p.tape_stride = stride;
   if ((e = soft::launch_grad(p, fp32, hp.W, st)) != cudaSuccess) {

@@ -78,6 +78,18 @@ def test_w42_rz_patterns(soft, precision):
     theta = C.rz_thetas(1, 72)
     ok, status = _compare(soft, circ, noise, theta, 300, 0, precision)
     assert ok > 5 and np.sum(status == 1) > 100
+    # ratio estimator sum N_acc F / sum N_acc over the ok patterns, reduced on the device
+    c = soft.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    _, _, _, st, sums = soft.soft_fidelity_grad(c, theta, 300, 0, 0, precision, sums=True)
+    st, sums = st.cpu().numpy(), sums.cpu().numpy()
+    na = nf = 0.0
+    for i in np.nonzero(st == 0)[0]:
+        _, a, f, _ = oracle.fidelity_grad(circ, circ.n, noise, circ.cap, 0, int(i), theta)
+        na += a
+        nf += f
+    assert sums[2] == np.sum(st == 0)
+    assert abs(sums[0] - na) <= FTOL[precision] * max(1.0, na)
+    assert abs(sums[1] / sums[0] - nf / na) <= FTOL[precision]
 
 
 def test_gpu_gradient_matches_finite_differences(soft):
