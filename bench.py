@@ -142,7 +142,7 @@ def profile_traffic(kernel_src_hash):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "program.h"):
+    for f in ("kernels.cu", "kernels.cuh", "program.h", "device_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2512_23037_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

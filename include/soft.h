@@ -274,8 +274,10 @@ int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_sho
  *   d_sums (may be NULL): 3 doubles, zeroed by the call, receiving the sums
  *   over ok patterns of N_acc and of N_fid = N_acc F, and their count; the
  *   ratio estimator of the post-selected fidelity is d_sums[1] / d_sums[0].
- * Synchronous: returns after the work on `stream` finished. Scratch (the
- * per-warp tape) is allocated and freed inside the call.
+ * Synchronous: returns after the work on `stream` finished. The scratch
+ * (per-warp tapes: forward coefficient maps after every rotation, sign words
+ * per event) is allocated by the first call on a handle, grown when a later
+ * call needs more and kept until soft_circuit_free.
  * Errors: SOFT_E_ARG, SOFT_E_OOM, SOFT_E_CUDA. */
 int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t n_params, uint64_t n_patterns,
                        uint64_t first_pattern, uint64_t seed, int32_t precision, void *stream, double *d_fid,

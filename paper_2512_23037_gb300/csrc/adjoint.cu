@@ -475,10 +475,10 @@ struct GradWarp {
     draw_next();
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(P.ev);
     uint32_t r = 0, ev_f = 0xFFFFFFFFu, rot_before_f = 0;
-    bool seen_f = false;
+    bool seen_f = false, done_empty = false;
     double n_acc = 0.0;
     int lastm = 1;
-    for (uint32_t ev = 0; ev < P.n_events && status == G_OK; ++ev) {
+    for (uint32_t ev = 0; ev < P.n_events && status == G_OK && !done_empty; ++ev) {
       const Ev<W> *E = evs + ev;
       const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
       uint64_t body[4 * W];
@@ -611,6 +611,12 @@ struct GradWarp {
             caseb_signs(B, mm);
           }
           lastm = mm;
+          if (phi.n == 0u) {
+            // the projection annihilated the state: N_acc = 0 (before the first fidelity
+            // measurement) or N_fid = 0 (after it); nothing later changes either
+            done_empty = true;
+            break;
+          }
           if ((flags & F_RECORD) && mm < 0 && lane == 0) rec[hdr.w >> 6] |= 1ull << (hdr.w & 63);
           if (mm == -1) tape_bit_set(ev);  // the outcome, for the reverse sweep
           t.sync();
@@ -658,7 +664,7 @@ struct GradWarp {
       if (!(n_acc > 0.0)) status = G_ZERO;
       else F = n_fid / n_acc;
     }
-    if (status == G_OK) {
+    if (status == G_OK && n_fid > 0.0) {  // N_fid = 0: F = 0 and dF/dtheta = 0 exactly
       // sweep 1: N_fid from the end; sweep 2: N_acc from just before the first fidelity measurement
       if (!sweep(phi, P.n_events, r, grad, 1.0)) status = G_UNSUPPORTED;
       if (status == G_OK && !sweep(pre, ev_f, rot_before_f, grad, -F)) status = G_UNSUPPORTED;

@@ -144,6 +144,9 @@ void soft_circuit_free(soft_circuit *c) {
   cudaFree(c->d_cb);
   cudaFree(c->d_sites);
   cudaFree(c->d_thr);
+  cudaFree(c->d_gcoef);
+  cudaFree(c->d_gnext);
+  cudaFree(c->d_gtape);
   delete c;
 }
 

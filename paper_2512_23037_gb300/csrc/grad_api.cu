@@ -39,25 +39,27 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   uint64_t blocks = (uint64_t)(sms > 0 ? sms : 1) * 4;
   blocks = std::min<uint64_t>(blocks, (n_patterns + wpb - 1) / wpb);
   const size_t stride = soft::grad_tape_bytes(fp32, hp.W, hp.n_rot, (uint32_t)hp.ev.size());
-  soft::Coef *d_coef = nullptr;
-  unsigned long long *d_next = nullptr;
-  unsigned char *d_tape = nullptr;
-  auto cleanup = [&]() {
-    cudaFree(d_coef);
-    cudaFree(d_next);
-    cudaFree(d_tape);
-  };
-  if ((e = cudaMalloc(&d_coef, std::max<size_t>(1, coefs.size()) * sizeof(soft::Coef))) != cudaSuccess ||
-      (e = cudaMalloc(&d_next, sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMalloc(&d_tape, stride * blocks * wpb)) != cudaSuccess) {
-    cleanup();
+  // workspace kept in the handle between calls; the tape grows to the largest launch seen
+  const size_t tape_need = stride * blocks * wpb;
+  if (!c->d_gcoef && (e = cudaMalloc(&c->d_gcoef, std::max<size_t>(1, coefs.size()) * sizeof(soft::Coef))) != cudaSuccess)
     return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
+  if (!c->d_gnext && (e = cudaMalloc(&c->d_gnext, sizeof(unsigned long long))) != cudaSuccess)
+    return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
+  if (c->gtape_bytes < tape_need) {
+    cudaFree(c->d_gtape);
+    c->d_gtape = nullptr;
+    c->gtape_bytes = 0;
+    if ((e = cudaMalloc(&c->d_gtape, tape_need)) != cudaSuccess)
+      return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
+    c->gtape_bytes = tape_need;
   }
+  soft::Coef *d_coef = c->d_gcoef;
+  unsigned long long *d_next = c->d_gnext;
+  unsigned char *d_tape = c->d_gtape;
   if ((!coefs.empty() && (e = cudaMemcpyAsync(d_coef, coefs.data(), coefs.size() * sizeof(soft::Coef),
                                               cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
       (e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
       (d_sums && (e = cudaMemsetAsync(d_sums, 0, 3 * sizeof(double), st)) != cudaSuccess)) {
-    cleanup();
     return soft::set_error(SOFT_E_CUDA, "upload failed");
   }
   soft::GradParams p{};
@@ -84,12 +86,9 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   p.sums = d_sums;
   p.tape = d_tape;
   p.tape_stride = stride;
-  if ((e = soft::launch_grad(p, fp32, hp.W, st)) != cudaSuccess) {
-    cleanup();
+  if ((e = soft::launch_grad(p, fp32, hp.W, st)) != cudaSuccess)
     return soft::set_error(SOFT_E_CUDA, "gradient kernel launch failed");
-  }
-  e = cudaStreamSynchronize(st);
-  cleanup();
-  if (e != cudaSuccess) return soft::set_error(SOFT_E_CUDA, "gradient kernel failed");
+  // synchronous: the host coefficient table and the handle's workspace are reused by the next call
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return soft::set_error(SOFT_E_CUDA, "gradient kernel failed");
   return SOFT_OK;
 }

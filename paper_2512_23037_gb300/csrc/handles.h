@@ -24,4 +24,10 @@ struct soft_circuit {
   soft::Site *d_sites = nullptr;
   uint64_t *d_thr = nullptr;
   uint64_t bytes = 0;
+  // fidelity-gradient workspace, kept between calls (they are synchronous):
+  // per-parameter coefficient table, work counter, per-warp tapes
+  soft::Coef *d_gcoef = nullptr;
+  unsigned long long *d_gnext = nullptr;
+  unsigned char *d_gtape = nullptr;
+  size_t gtape_bytes = 0;
 };
