@@ -142,7 +142,7 @@ typedef struct {
   int32_t record_mode;   /* which shots' records and status bytes are kept */
   uint64_t record_k;     /* K for SOFT_REC_FIRST_K */
   void *stream;          /* cudaStream_t to launch on; NULL = legacy default stream */
-  uint32_t group_size;   /* lanes per shot: 0 = auto, else 8 or 32 */
+  uint32_t group_size;   /* lanes per shot: 0 = 32, else 16 (two shots per warp) or 32 */
   uint32_t blocks_per_sm;/* 0 = as many as fit */
   uint64_t chunk_shots;  /* shots per launch; 0 = auto */
   uint32_t first_cap;    /* capacity of the first pass (0 = auto); shots that exceed
@@ -150,7 +150,8 @@ typedef struct {
   uint32_t capture_k;    /* keep the final GS state of the first capture_k shots */
   uint64_t *d_records;   /* optional caller device buffer, record_words per kept shot */
   uint8_t *d_status;     /* optional caller device buffer, one byte per kept shot */
-  uint32_t groups_per_block; /* shots resident per 128-thread block: 0 = 4, else 1..4 */
+  uint32_t groups_per_block; /* shots resident per 128-thread block: 0 = 128 / group lanes,
+                                else 1..that number */
   uint32_t flags;        /* SOFT_RUN_GRAPH: capture one chunk (counter reset, both passes,
                             device-side advance of the chunk base) in a CUDA graph and
                             replay it for every full chunk; needs a non-NULL stream */
@@ -164,7 +165,14 @@ typedef struct {
  * impossible ends there, kept, with F = 0. Observed records then read 0.
  * Needs every DETECTOR before the first observed measurement (SOFT_E_ARG
  * otherwise). */
-enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2 };
+/* SOFT_RUN_NO_PREFIX: run every shot from the first event. By default a shot
+ * starts at the event that applies its first error (or at the end of the
+ * circuit's decided noiseless prefix, if earlier), from the state the noiseless
+ * run reached there: soft_compile_circuit records that run once per precision
+ * (the state at the top of each event, while every outcome is decided, no
+ * fidelity measurement is reached and the map has at most 32 entries). Both
+ * give the same results; the flag is for comparison. */
+enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
  * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all

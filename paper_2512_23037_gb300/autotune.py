@@ -5,8 +5,9 @@ caller will run, so nothing is reused) for every candidate of
 
   - first_cap: capacity of the first pass's on-chip map (shots above it and
     below their circuit's cap rerun at the full cap),
-  - groups_per_block: shots resident per 128-thread block (1, 2 or 4),
-  - group_size: lanes per shot (32 = one warp per shot, 8 = four shots per warp),
+  - groups_per_block: shots resident per 128-thread block (2 or 4 for 32-lane
+    groups, 8 for 16-lane groups),
+  - group_size: lanes per shot (32 = one warp per shot, 16 = two shots per warp),
 
 and keeps the fastest. Results are cached per circuit signature.
 """
@@ -19,7 +20,7 @@ from . import soft_run_batch, soft_run_timing, soft_tally
 
 _CACHE: dict = {}
 
-DEFAULT_SPACE = {"first_cap": [16, 32, 64], "groups_per_block": [2, 4], "group_size": [32, 8]}
+DEFAULT_SPACE = {"first_cap": [16, 32, 64], "groups_per_block": [2, 4, 8], "group_size": [32, 16]}
 
 
 def signature(circs, precision):
@@ -39,8 +40,11 @@ def autotune(circs, precision="fp32", sample_shots=1 << 18, space=None, seed=0x5
     results = []
     for values in itertools.product(*[space[k] for k in names]):
         kw = dict(zip(names, values))
-        if kw.get("group_size") == 8 and kw.get("groups_per_block", 4) != 4:
-            continue  # 8-lane groups always fill a 32-lane warp with four shots
+        gs, gpb = kw.get("group_size", 32), kw.get("groups_per_block", 0)
+        if gpb and gpb > 128 // gs:
+            continue  # more groups than a 128-thread block holds
+        if gs == 16 and gpb and gpb != 8:
+            continue  # 16-lane groups run full blocks
         best = None
         for rep in range(repeats + 1):
             first = [(1 << 50) + rep * per] * n

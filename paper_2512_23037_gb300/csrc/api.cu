@@ -60,6 +60,45 @@ struct soft_run {
   uint32_t launches = 0;
 };
 
+// Records both precisions' noiseless runs of a freshly uploaded circuit (the
+// prefix every shot shares until its first error). Synchronous.
+static cudaError_t build_prefixes(soft_circuit *c) {
+  const auto &hp = c->hp;
+  const size_t n_snap = hp.ev.size() + 1;
+  uint32_t *d_stop = nullptr;
+  cudaError_t e = cudaMalloc(&d_stop, 2 * sizeof(uint32_t));
+  if (e != cudaSuccess) return e;
+  for (int fp32 = 0; fp32 < 2 && e == cudaSuccess; ++fp32) {
+    const size_t stride = soft::prefix_stride(fp32, hp.W, hp.rw);
+    if ((e = cudaMalloc(&c->d_traj[fp32], n_snap * stride)) != cudaSuccess) break;
+    c->traj_stride[fp32] = (uint32_t)stride;
+    soft::ShotParams p{};
+    p.n_circ = 1;
+    soft::CircDev &d = p.circ[0];
+    d.ev = c->d_ev;
+    d.coef = c->d_coef;
+    d.cb = c->d_cb;
+    d.sites = c->d_sites;
+    d.thr = c->d_thr;
+    d.n_events = (uint32_t)hp.ev.size();
+    d.n_sites = hp.n_sites;
+    d.rw = hp.rw;
+    d.cap = hp.cap;
+    d.n_coef = (uint32_t)hp.coefs.size();
+    d.n_cb = (uint32_t)hp.cb.size();
+    p.cap = std::min(hp.cap, soft::kDefaultFirstCap);
+    p.rw_max = hp.rw;
+    p.tau = fp32 ? kTauFp32 : kTauFp64;
+    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + fp32, nullptr);
+  }
+  uint32_t stop[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(stop, d_stop, sizeof stop, cudaMemcpyDeviceToHost);
+  cudaFree(d_stop);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < 2; ++k) c->traj_stop[k] = std::min<uint32_t>(stop[k], (uint32_t)hp.ev.size());
+  return cudaSuccess;
+}
+
 extern "C" {
 
 const char *soft_last_error(void) { return g_err.c_str(); }
@@ -114,6 +153,11 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
     return cuda_fail(e, "cudaMemcpy (program upload)");
   }
   c->bytes = b_ev + b_cf + b_cb + b_st + b_thr;
+  if ((e = build_prefixes(c)) != cudaSuccess) {
+    soft_circuit_free(c);
+    return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed")
+                                          : cuda_fail(e, "noiseless prefix run");
+  }
   *out = c;
   return SOFT_OK;
 }
@@ -144,6 +188,8 @@ void soft_circuit_free(soft_circuit *c) {
   cudaFree(c->d_cb);
   cudaFree(c->d_sites);
   cudaFree(c->d_thr);
+  cudaFree(c->d_traj[0]);
+  cudaFree(c->d_traj[1]);
   cudaFree(c->d_gcoef);
   cudaFree(c->d_gnext);
   cudaFree(c->d_gtape);
@@ -176,8 +222,13 @@ void soft_run_free(soft_run *r) {
 
 namespace {
 
-soft::CircDev circ_desc(const soft_circuit *c) {
+soft::CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix) {
   soft::CircDev d{};
+  if (prefix && c->d_traj[fp32]) {
+    d.traj = c->d_traj[fp32];
+    d.traj_stop = c->traj_stop[fp32];
+    d.traj_stride = c->traj_stride[fp32];
+  }
   d.ev = c->d_ev;
   d.coef = c->d_coef;
   d.cb = c->d_cb;
@@ -202,13 +253,16 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   if (opts) o = *opts;
   if (o.precision != SOFT_FP64 && o.precision != SOFT_FP32) return fail(SOFT_E_ARG, "bad precision");
   if (o.record_mode < SOFT_REC_NONE || o.record_mode > SOFT_REC_ALL) return fail(SOFT_E_ARG, "bad record mode");
-  if (o.group_size != 0 && o.group_size != 8 && o.group_size != 32) return fail(SOFT_E_ARG, "group_size must be 0, 8 or 32");
-  if (o.groups_per_block > 4) return fail(SOFT_E_ARG, "groups_per_block must be 0..4");
+  if (o.group_size != 0 && o.group_size != 16 && o.group_size != 32)
+    return fail(SOFT_E_ARG, "group_size must be 0, 16 or 32");
+  if (o.groups_per_block > 128u / (o.group_size ? o.group_size : 32u))
+    return fail(SOFT_E_ARG, "groups_per_block must be 0..128/group_size");
   if (n_circ > 1 && (o.record_mode != SOFT_REC_NONE || o.capture_k))
     return fail(SOFT_E_ARG, "records and state capture are per single-circuit run");
   const bool use_graph = (o.flags & SOFT_RUN_GRAPH) != 0;
   const bool fid_mode = (o.flags & SOFT_RUN_FIDELITY) != 0;
-  if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY)) return fail(SOFT_E_ARG, "unknown run flags");
+  if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY | SOFT_RUN_NO_PREFIX))
+    return fail(SOFT_E_ARG, "unknown run flags");
   if (use_graph && !o.stream) return fail(SOFT_E_ARG, "graph replay needs a non-default stream");
   const int fp32 = o.precision == SOFT_FP32;
   uint32_t W = 0, cap_max = 0, rw_max = 1;
@@ -306,7 +360,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   p.n_circ = n_circ;
   uint64_t begin = 0;
   for (uint32_t i = 0; i < n_circ; ++i) {
-    p.circ[i] = circ_desc(circs[i]);
+    p.circ[i] = circ_desc(circs[i], fp32, !(o.flags & SOFT_RUN_NO_PREFIX));
     p.circ[i].item_begin = begin;
     p.circ[i].n_shots = n_shots[i];
     p.circ[i].first_shot = first_shots[i];

@@ -24,6 +24,11 @@ struct soft_circuit {
   soft::Site *d_sites = nullptr;
   uint64_t *d_thr = nullptr;
   uint64_t bytes = 0;
+  // the noiseless run's snapshot table per precision (index 0 FP64, 1 FP32),
+  // built at compile time; traj_stop = last valid event
+  unsigned char *d_traj[2] = {nullptr, nullptr};
+  uint32_t traj_stop[2] = {0, 0};
+  uint32_t traj_stride[2] = {0, 0};
   // fidelity-gradient workspace, kept between calls (they are synchronous):
   // per-parameter coefficient table, work counter, per-warp tapes
   soft::Coef *d_gcoef = nullptr;

@@ -1,6 +1,6 @@
 // kernels.cu -- persistent shot kernel for sm_103a.
 //
-// One tile of G lanes (G = 8 or 32) owns one shot at a time and walks the
+// One tile of G lanes (G = 16 or 32) owns one shot at a time and walks the
 // compiled event list of program.h. Per shot it holds, on chip:
 //   - the 2n tableau sign bits (registers; the X/Z words are shot-invariant
 //     and folded into the program),
@@ -63,9 +63,11 @@ struct Shot {
   uint32_t nxt, cur, kblk, w2;
   int status, chain, logical, lastm;
   bool force = false;  // fidelity mode: this measurement projects onto +1
+  bool undecided = false;  // set when an outcome depended on the uniform (0 < p_+ < 1)
   double fid = 1.0;    // fidelity mode: product of the projected measurements' p_+
-  // register mode (G = 32 only): while |v| <= 32, lane i < nnz holds entry i
-  static constexpr bool kRegCapable = (G == 32);
+  // register mode: while |v| <= G, lane i < nnz holds entry i
+  static constexpr bool kRegCapable = (G == 32 || G == 16);
+  static constexpr uint32_t kTileFull = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
   bool reg;
   Key<W> rk;
   Cx<R> rv;
@@ -274,10 +276,11 @@ struct Shot {
   }
 
   // ---------------------------------------------------------------- register mode
-  __device__ __forceinline__ uint32_t vmask() const { return nnz >= 32u ? 0xFFFFFFFFu : ((1u << nnz) - 1u); }
+  // masks below are tile-relative: bit i = lane i of this G-lane tile
+  __device__ __forceinline__ uint32_t vmask() const { return nnz >= (uint32_t)G ? kTileFull : ((1u << nnz) - 1u); }
   __device__ __forceinline__ uint32_t match_key(const Key<W> &k) const {
-    uint32_t m = __match_any_sync(0xFFFFFFFFu, (unsigned long long)k.w[0]);
-    if (W == 2) m &= __match_any_sync(0xFFFFFFFFu, (unsigned long long)k.w[W - 1]);
+    uint32_t m = t.match_any((unsigned long long)k.w[0]);
+    if (W == 2) m &= t.match_any((unsigned long long)k.w[W - 1]);
     return m;
   }
   __device__ __forceinline__ Cx<R> shfl_c(Cx<R> v, uint32_t src) const {
@@ -353,7 +356,7 @@ struct Shot {
       fail_check(CHK_STAGE, nnz + nA);
       return;
     }
-    if (nnz + nA <= 32u) {
+    if (nnz + nA <= (uint32_t)G) {
       if (nA) {
         if (app) {
           const uint32_t d = lanes_below(ab);
@@ -375,7 +378,7 @@ struct Shot {
       if (nnz > ecap) fail_capacity();
       return;
     }
-    // more than 32 entries: continue in shared memory with the hash index
+    // more than G entries: continue in shared memory with the hash index
     if (valid) {
       set_key(lane, rk);
       vals[lane] = nv;
@@ -406,6 +409,7 @@ struct Shot {
   // Outcome of a non-deterministic measurement with p_+ = pp: sampled from the
   // stream, or in fidelity mode +1 (weight pp) unless +1 is impossible.
   __device__ __forceinline__ int pick(uint32_t ord, double pp) {
+    if (pp > 0.0 && pp < 1.0) undecided = true;
     if (force) {
       if (pp > 0.0) {
         fid *= pp;
@@ -749,7 +753,101 @@ struct Shot {
     return (r < 0 || (uint32_t)r >= 64u * C->rw) ? 0u : (uint32_t)((rec[r >> 6] >> (r & 63)) & 1ull);
   }
 
-  __device__ void run(uint64_t s) {
+  // Shot state at the top of event `ev` of the circuit's noiseless run, when that
+  // run has one (traj_stop > ev): written by trace_prefix, read by load_prefix.
+  struct SnapHdr {
+    uint32_t nnz, chain, logical, lastm;
+    double fid;
+    uint64_t sd[2], ss[2];
+    uint64_t pad[2];
+  };
+  __host__ __device__ static constexpr size_t snap_stride(uint32_t rw) {
+    return (sizeof(SnapHdr) + (size_t)rw * 8 + 32 * (size_t)W * 8 + 32 * sizeof(Cx<R>) + 15) & ~(size_t)15;
+  }
+  __device__ void save_snapshot(unsigned char *out) {
+    SnapHdr *h = reinterpret_cast<SnapHdr *>(out);
+    uint64_t *rw_out = reinterpret_cast<uint64_t *>(out + sizeof(SnapHdr));
+    uint64_t *k_out = rw_out + C->rw;
+    Cx<R> *v_out = reinterpret_cast<Cx<R> *>(k_out + 32 * W);
+    if (lane == 0) {
+      h->nnz = nnz;
+      h->chain = (uint32_t)chain;
+      h->logical = (uint32_t)logical;
+      h->lastm = (uint32_t)lastm;
+      h->fid = fid;
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        h->sd[w] = w < W ? sd[w < W ? w : 0] : 0ull;
+        h->ss[w] = w < W ? ss[w < W ? w : 0] : 0ull;
+      }
+    }
+    for (uint32_t w = lane; w < C->rw; w += G) rw_out[w] = rec[w];
+    if (lane < nnz) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) k_out[lane * W + w] = rk.w[w];
+      v_out[lane] = rv;
+    }
+  }
+  // First event whose errors the shot must apply itself: the event that applies
+  // its first error (the first with site_begin > nxt), capped at the end of the
+  // noiseless run's valid prefix. Loads the snapshot there and returns it.
+  __device__ uint32_t load_prefix() {
+    const uint32_t stop = C->traj_stop;
+    const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
+    uint32_t lo = 0, hi = stop;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&evs[mid].site_begin) > nxt) hi = mid;
+      else lo = mid + 1u;
+    }
+    const unsigned char *in = C->traj + (size_t)lo * C->traj_stride;
+    const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);
+    const uint64_t *r_in = reinterpret_cast<const uint64_t *>(in + sizeof(SnapHdr));
+    const uint64_t *k_in = r_in + C->rw;
+    const Cx<R> *v_in = reinterpret_cast<const Cx<R> *>(k_in + 32 * W);
+    nnz = __ldg(&h->nnz);
+    chain = (int)__ldg(&h->chain);
+    logical = (int)__ldg(&h->logical);
+    lastm = (int)__ldg(&h->lastm);
+    fid = __ldg(&h->fid);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      sd[w] = __ldg(&h->sd[w]);
+      ss[w] = __ldg(&h->ss[w]);
+    }
+    for (uint32_t w = lane; w < C->rw; w += G) rec[w] = __ldg(&r_in[w]);
+    if (nnz > 32u) {  // a snapshot never holds more than 32 entries
+      fail_check(CHK_NNZ, nnz);
+      return lo;
+    }
+    if (nnz > ecap) {  // the uninterrupted run would have outgrown this pass's capacity too
+      fail_capacity();
+      return lo;
+    }
+    if (kRegCapable && nnz <= (uint32_t)G) {
+      reg = true;
+      if (lane < nnz) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) rk.w[w] = __ldg(&k_in[lane * W + w]);
+        rv = v_in[lane];
+      }
+      t.sync();
+    } else {
+      for (uint32_t i = lane; i < nnz; i += G) {
+        Key<W> k;
+#pragma unroll
+        for (int w = 0; w < W; ++w) k.w[w] = __ldg(&k_in[i * W + w]);
+        set_key(i, k);
+        vals[i] = v_in[i];
+      }
+      t.sync();
+      reg = false;
+      rebuild();
+    }
+    return lo;
+  }
+
+  __device__ void init_shot(uint64_t s) {
     shot = s;
     status = ST_RUN;
     bad_slot = 0;
@@ -782,10 +880,45 @@ struct Shot {
     kblk = 0;
     fid = 1.0;
     force = false;
+  }
+
+  __device__ void run(uint64_t s) {
+    init_shot(s);
     draw_next();
+    uint32_t ev0 = 0;
+    if (C->traj) ev0 = load_prefix();  // every event before the first error is the noiseless run's
+    const uint32_t n_events = C->n_events;
+    for (uint32_t ev = ev0; ev < n_events && status == ST_RUN; ++ev) step(ev);
+    if (status == ST_RUN) status = ST_KEPT;
+  }
+
+  // The circuit's noiseless run, recording the state at the top of every event
+  // until an outcome is not decided (it would depend on the shot's uniform), a
+  // fidelity measurement, the map leaving register mode, or the end. Event
+  // `stop` is the last valid snapshot: shots resume there at the latest.
+  __device__ uint32_t trace_prefix(unsigned char *out, size_t stride) {
+    init_shot(0);
+    cur = C->n_sites;
+    nxt = 0xFFFFFFFFu;
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
     const uint32_t n_events = C->n_events;
-    for (uint32_t ev = 0; ev < n_events && status == ST_RUN; ++ev) {
+    uint32_t ev = 0;
+    for (; ev <= n_events; ++ev) {
+      save_snapshot(out + (size_t)ev * stride);
+      if (ev == n_events) break;
+      const uint32_t w0 = __ldg(&evs[ev].w0), type = ev_type(w0);
+      if ((type == EV_MEAS_A || type == EV_MEAS_B) && (ev_flags(w0) & F_FIDELITY)) break;
+      undecided = false;
+      step(ev);
+      if (status != ST_RUN || undecided || !reg) break;
+    }
+    t.sync();
+    return ev;
+  }
+
+  __device__ __forceinline__ void step(uint32_t ev) {
+    const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
+    {
       cur_ev = ev;
       const Ev<W> *E = evs + ev;
       const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
@@ -799,12 +932,12 @@ struct Shot {
         body[2 * k + 1] = v.y;
       }
       const uint64_t *dsd = body, *dss = body + W, *beta = body + 2 * W, *gamma = body + 3 * W;
-      if (kRegCapable && !reg && nnz <= 32u) reg_load();
+      if (kRegCapable && !reg && nnz <= (uint32_t)G) reg_load();
       while (nxt < hdr.y && status == ST_RUN) {
         apply_error(nxt);
         draw_next();
       }
-      if (status != ST_RUN) break;
+      if (status != ST_RUN) return;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         sd[w] ^= dsd[w];
@@ -867,7 +1000,6 @@ struct Shot {
         default: break;
       }
     }
-    if (status == ST_RUN) status = ST_KEPT;
   }
 
   __device__ void finish(uint64_t local, uint64_t off, uint32_t ci, unsigned long long (*btally)[5]) {
@@ -968,6 +1100,28 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 :
 
 __global__ void advance_kernel(unsigned long long *item_base, unsigned long long step) { *item_base += step; }
 
+// One warp records the noiseless run of circuit 0 (see Shot::trace_prefix).
+template <typename R, int W>
+__global__ void __launch_bounds__(32) prefix_kernel(const __grid_constant__ ShotParams P, unsigned char *out,
+                                                    size_t stride, uint32_t *stop) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto tile = cg::tiled_partition<32>(cg::this_thread_block());
+  Shot<R, W, 32> s(tile, P, smem);
+  s.C = &P.circ[0];
+  const uint32_t ev = s.trace_prefix(out, stride);
+  if (tile.thread_rank() == 0) *stop = ev;
+}
+
+template <typename R, int W>
+cudaError_t prefix_t(const ShotParams &p, unsigned char *out, uint32_t *stop, cudaStream_t st) {
+  const size_t gb = group_bytes<R, W>(p.cap, p.rw_max);
+  auto kern = prefix_kernel<R, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gb);
+  if (e != cudaSuccess) return e;
+  kern<<<1, 32, gb, st>>>(p, out, Shot<R, W, 32>::snap_stride(p.circ[0].rw), stop);
+  return cudaGetLastError();
+}
+
 template <typename R, int W, int G>
 cudaError_t prepare_t(const ShotParams &p, int blocks_per_sm, LaunchCfg *cfg) {
   auto kern = shot_kernel<R, W, G>;
@@ -1033,17 +1187,17 @@ cudaError_t prepare_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t gr
 #define SOFT_DISPATCH(R, WW, GG) return prepare_t<R, WW, GG>(p, blocks_per_sm, cfg)
   if (fp32) {
     if (W == 1) {
-      if (group == 8) SOFT_DISPATCH(float, 1, 8);
+      if (group == 16) SOFT_DISPATCH(float, 1, 16);
       SOFT_DISPATCH(float, 1, 32);
     }
-    if (group == 8) SOFT_DISPATCH(float, 2, 8);
+    if (group == 16) SOFT_DISPATCH(float, 2, 16);
     SOFT_DISPATCH(float, 2, 32);
   }
   if (W == 1) {
-    if (group == 8) SOFT_DISPATCH(double, 1, 8);
+    if (group == 16) SOFT_DISPATCH(double, 1, 16);
     SOFT_DISPATCH(double, 1, 32);
   }
-  if (group == 8) SOFT_DISPATCH(double, 2, 8);
+  if (group == 16) SOFT_DISPATCH(double, 2, 16);
   SOFT_DISPATCH(double, 2, 32);
 #undef SOFT_DISPATCH
 }
@@ -1065,5 +1219,18 @@ cudaError_t launch_shots(const ShotParams &p, int fp32, uint32_t W, uint32_t gro
 }
 
 uint32_t hash_slots_for(uint32_t cap) { return hash_slots(cap); }
+
+size_t prefix_stride(int fp32, uint32_t W, uint32_t rw) {
+  if (fp32) return W == 1 ? Shot<float, 1, 32>::snap_stride(rw) : Shot<float, 2, 32>::snap_stride(rw);
+  return W == 1 ? Shot<double, 1, 32>::snap_stride(rw) : Shot<double, 2, 32>::snap_stride(rw);
+}
+
+cudaError_t launch_prefix(const ShotParams &p, int fp32, uint32_t W, unsigned char *out, uint32_t *stop,
+                          cudaStream_t st) {
+  ShotParams q = p;
+  q.hs_max = hash_slots(q.cap);
+  if (fp32) return W == 1 ? prefix_t<float, 1>(q, out, stop, st) : prefix_t<float, 2>(q, out, stop, st);
+  return W == 1 ? prefix_t<double, 1>(q, out, stop, st) : prefix_t<double, 2>(q, out, stop, st);
+}
 
 }  // namespace soft

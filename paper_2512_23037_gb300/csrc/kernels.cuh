@@ -27,6 +27,10 @@ struct CircDev {
   uint8_t *status;            // per shot offset < out_limit
   uint64_t *records;          // rw words per shot offset < out_limit
   uint64_t out_limit;
+  // the noiseless run's state at the top of events [0, traj_stop] (null: none);
+  // a shot starts at the event that applies its first error, or at traj_stop
+  const unsigned char *traj;
+  uint32_t traj_stop, traj_stride;
 };
 
 struct ShotParams {
@@ -72,6 +76,13 @@ enum : uint32_t {
   CHK_HASH_SLOT = 1, CHK_STAGE = 2, CHK_SLOTS = 3, CHK_RECORD = 4, CHK_SITE = 5, CHK_COEF = 6,
   CHK_CASEB = 7, CHK_RERUN = 8, CHK_LIST = 9, CHK_PHASE = 10, CHK_NNZ = 11
 };
+
+// Bytes per event of a noiseless-run snapshot table (see CircDev::traj).
+size_t prefix_stride(int fp32, uint32_t W, uint32_t rw);
+// Record circuit p.circ[0]'s noiseless run into `out` ((n_events + 1) snapshots);
+// *stop receives the last valid event. One warp; p.cap is the map capacity used.
+cudaError_t launch_prefix(const ShotParams &p, int fp32, uint32_t W, unsigned char *out, uint32_t *stop,
+                          cudaStream_t st);
 
 // Bytes of shared memory one shot group needs for capacity `cap`.
 size_t group_smem_bytes(int fp32, uint32_t W, uint32_t cap, uint32_t rw);

@@ -143,11 +143,27 @@ def test_rerun_pass_matches_single_pass(soft):
         assert compare_records(circ, noise, 3, 0, rec, st, ref, "fp64") == 0
 
 
-@pytest.mark.parametrize("group", [8, 32])
-def test_group_sizes(soft, group):
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("group", [16, 32])
+def test_group_sizes(soft, group, precision):
     circ, noise = C.workload("w42")
-    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 2000, 5, "fp32", group=group)
-    assert compare_records(circ, noise, 5, 0, rec, st, ref, "fp32") <= 2
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 2000, 5, precision, group=group, capture=64)
+    assert compare_records(circ, noise, 5, 0, rec, st, ref, precision) <= 2
+    compare_states(soft, c, r, circ, noise, 5, 0, 64, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("seed", range(4))
+def test_two_shots_per_warp_random_circuits(soft, precision, seed):
+    """16-lane groups: register maps of up to 16 entries, spills to the shared
+    hash beyond, two shots of one warp on different paths."""
+    n = [4, 9, 30, 80][seed]
+    circ = C.random_circuit(3000 + seed, n, 60 + 8 * n, t_frac=0.22, detectors=True, mpp_frac=0.05)
+    circ.cap = 256
+    noise = C.Noise(0.01, 0.01, 0.01, 0.01)
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 900, seed, precision, capture=48, group=16)
+    assert compare_records(circ, noise, seed, 0, rec, st, ref, precision) <= 3
+    compare_states(soft, c, r, circ, noise, seed, 0, 48, precision)
 
 
 def test_overflow_status(soft):
@@ -288,3 +304,39 @@ def test_graph_replayed_chunks(soft, precision):
     assert launches >= 5 * 2
     ref = oracle.run(circ, circ.n, noise, circ.cap, 4, 77, n, threads=8)
     assert compare_records(circ, noise, 4, 77, rec, st, ref, precision) <= 1
+
+
+def _run_prefix(S, c, n, seed, precision, prefix, **kw):
+    r = S.soft_run_shots(c, n, 0, seed, precision=precision, record_mode=S.REC_ALL, capture_k=48, prefix=prefix,
+                         **kw)
+    rec, st = S.soft_get_records(r, n)
+    states = [S.soft_get_state(r, off) for off in range(48)]
+    return rec, st, S.soft_tally(r), states
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["w42", "tiny6", "random40", "w42_rerun"])
+def test_prefix_start_is_bit_identical(soft, precision, case):
+    """Starting each shot from the noiseless run's state at its first error
+    (the default) gives exactly the records, statuses, tallies and final states
+    of running it from the first event."""
+    S = soft
+    kw = {}
+    if case in ("w42", "w42_rerun"):
+        circ, noise = C.workload("w42")
+        if case == "w42_rerun":
+            kw = {"first_cap": 8}
+    elif case == "tiny6":
+        circ, noise = C.workload("tiny6")
+        noise = C.Noise.uniform(0.02)
+    else:
+        circ = C.random_circuit(4040, 40, 400, t_frac=0.2, detectors=True, mpp_frac=0.05)
+        circ.cap = 256
+        noise = C.Noise(0.005, 0.005, 0.005, 0.005)
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    a = _run_prefix(S, c, 3000, 9, precision, True, **kw)
+    b = _run_prefix(S, c, 3000, 9, precision, False, **kw)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert a[2] == b[2]
+    for (s1, k1, v1), (s2, k2, v2) in zip(a[3], b[3]):
+        assert np.array_equal(s1, s2) and np.array_equal(k1, k2) and np.array_equal(v1, v2)
