@@ -43,7 +43,9 @@ assert EVENT_DTYPE.itemsize == 64
 class _Counts(ctypes.Structure):
     _fields_ = [("shots", ctypes.c_uint64), ("t_out_entries", ctypes.c_uint64),
                 ("t_diag_entries", ctypes.c_uint64), ("meas_entries", ctypes.c_uint64),
-                ("noise_entries", ctypes.c_uint64), ("errors", ctypes.c_uint64)]
+                ("noise_entries", ctypes.c_uint64), ("errors", ctypes.c_uint64),
+                ("post_t_out", ctypes.c_uint64), ("post_t_diag", ctypes.c_uint64),
+                ("post_meas", ctypes.c_uint64), ("post_noise", ctypes.c_uint64)]
 
 
 def build(force: bool = False) -> str:

@@ -862,6 +862,14 @@ static int apply_error_if_due(gs_state *st, const circ *c, uint64_t seed, uint64
   return OR_ST_OK;
 }
 
+/* Adds the work counted since `c0` to the post-prefix counters. */
+static void add_post(or_counts *cnt, const or_counts *c0) {
+  cnt->post_t_out += cnt->t_out_entries - c0->t_out_entries;
+  cnt->post_t_diag += cnt->t_diag_entries - c0->t_diag_entries;
+  cnt->post_meas += cnt->meas_entries - c0->meas_entries;
+  cnt->post_noise += cnt->noise_entries - c0->noise_entries;
+}
+
 /* One shot. In fidelity mode (fid != NULL) every measurement whose record an
  * OBSERVABLE reads is projected onto +1 and *fid accumulates the product of
  * their conditional probabilities p_+; when +1 is impossible *fid = 0 and the
@@ -884,11 +892,20 @@ static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, u
     rb = recbits_local;
   }
   size_t lim = stop_after < c->n_ops ? stop_after : c->n_ops;
+  int live = 0; /* past the noiseless-run prefix (see or_counts) */
+  or_counts c0;
+  memset(&c0, 0, sizeof c0);
   for (size_t i = 0; i < lim; ++i) {
     const or_op *o = &c->ops[i];
     int op = o->op;
+    if (cnt) c0 = *cnt;
     int stt = apply_error_if_due(st, c, seed, shot, &ns, c->pre_site[i], i, tb, cnt);
     if (stt) return stt;
+    if (cnt) {
+      if (cnt->errors != c0.errors) live = 1;
+      if (live) add_post(cnt, &c0);
+      c0 = *cnt;
+    }
     size_t nb = st->ne;
     switch (op) {
       case OR_H: case OR_S: case OR_SDAG: case OR_X: case OR_Y: case OR_Z: case OR_CX: case OR_CZ:
@@ -925,9 +942,11 @@ static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, u
         if (op == OR_MPP && (o->flags & OR_MPP_MORE)) break; /* the chain's last op measures */
         pauli P = (op == OR_MPP) ? mpp_product(c->ops, mpp_chain_start(c->ops, i), i) : pauli_single(3, (int)o->q0);
         const int force = fid && op != OR_R && c->observed[nrec];
+        if (op != OR_R && c->observed[nrec]) live = 1;
         meas_info mi;
         int r = measure(st, c, &P, seed, shot, ordinal, force, &mi, cnt);
         if (r) return r;
+        if (mi.p_plus > 0.0 && mi.p_plus < 1.0) live = 1;
         or_event e;
         memset(&e, 0, sizeof e);
         e.kind = OR_EV_MEAS;
@@ -988,8 +1007,17 @@ static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, u
       default:
         break;
     }
+    if (cnt) {
+      if (st->ne > 32) live = 1;
+      if (live) add_post(cnt, &c0);
+      c0 = *cnt;
+    }
     stt = apply_error_if_due(st, c, seed, shot, &ns, c->post_site[i], i, tb, cnt);
     if (stt) return stt;
+    if (cnt) {
+      if (cnt->errors != c0.errors) live = 1;
+      if (live) add_post(cnt, &c0);
+    }
   }
   return OR_ST_OK;
 }
@@ -1117,6 +1145,10 @@ int or_run_ex(const or_op *ops, size_t n_ops, uint32_t n_qubits, const or_noise 
       counts->meas_entries += args[t].cnt.meas_entries;
       counts->noise_entries += args[t].cnt.noise_entries;
       counts->errors += args[t].cnt.errors;
+      counts->post_t_out += args[t].cnt.post_t_out;
+      counts->post_t_diag += args[t].cnt.post_t_diag;
+      counts->post_meas += args[t].cnt.post_meas;
+      counts->post_noise += args[t].cnt.post_noise;
     }
   }
   free(args); free(th); circ_free(&c);

@@ -71,6 +71,11 @@ typedef struct {
   uint64_t meas_entries;   /* entries visited by measurements */
   uint64_t noise_entries;  /* entries touched by applied Paulis */
   uint64_t errors;         /* sampled errors applied */
+  /* The same four counts restricted to the part of each shot that differs from
+   * the circuit's noiseless run: from the earliest of the first applied error,
+   * the first measurement an OBSERVABLE reads, the first outcome with
+   * 0 < p_+ < 1 and the first map above 32 entries, to the end of the shot. */
+  uint64_t post_t_out, post_t_diag, post_meas, post_noise;
 } or_counts;
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -342,3 +342,38 @@ def test_malformed_inputs_rejected():
     c.detector([0])
     with pytest.raises(RuntimeError):
         oracle.run(c, 2, C.Noise(), 16, 0, 0, 1)
+
+
+# ------------------------------------------------------------------ post-prefix work counters
+def _counts(circ, noise, shots=300, seed=0):
+    return oracle.run(circ, circ.n, noise, circ.cap, seed, 0, shots, threads=4, records=False)["counts"]
+
+
+def test_post_prefix_counts_bounded_by_full():
+    circ, noise = C.windowed(3, n_data=10, n_anc=2, blocks=4, w=3, n_cliff=16, checks=2, p=0.01)
+    k = _counts(circ, noise)
+    for a, b in (("post_t_out", "t_out_entries"), ("post_t_diag", "t_diag_entries"),
+                 ("post_meas", "meas_entries"), ("post_noise", "noise_entries")):
+        assert 0 < k[a] <= k[b]
+
+
+def test_post_prefix_noiseless_counts_only_the_observed_chain():
+    """Noiselessly every outcome of the windowed circuit is decided and the map
+    stays <= 16: only the final observed measurements are past the prefix."""
+    circ, _ = C.windowed(3, n_data=10, n_anc=2, blocks=4, w=3, n_cliff=16, checks=2, p=0.0)
+    k = _counts(circ, C.Noise(), shots=20)
+    assert k["post_t_out"] == 0 and k["post_t_diag"] == 0 and k["post_noise"] == 0
+    n_final = 10  # one measurement per data qubit, one entry each
+    assert k["post_meas"] == 20 * n_final
+
+
+def test_post_prefix_undecided_first_outcome_counts_everything():
+    c = C.Circuit(3)
+    c.gate(C.H, 0)
+    c.measure(0)  # p_+ = 1/2: every shot differs from here on
+    for q in range(3):
+        c.gate(C.H, q)
+        c.gate(C.T, q)
+    c.measure(1)
+    k = _counts(c, C.Noise(), shots=50)
+    assert k["post_t_out"] == k["t_out_entries"] > 0 and k["post_meas"] == k["meas_entries"]
