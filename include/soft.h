@@ -170,7 +170,7 @@ typedef struct {
  * circuit's decided noiseless prefix, if earlier), from the state the noiseless
  * run reached there: soft_compile_circuit records that run once per precision
  * (the state at the top of each event, while every outcome is decided, no
- * fidelity measurement is reached and the map has at most 32 entries). Both
+ * fidelity measurement is reached and the map has at most 64 entries). Both
  * give the same results; the flag is for comparison. */
 enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4 };
 

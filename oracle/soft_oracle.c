@@ -1008,7 +1008,7 @@ static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, u
         break;
     }
     if (cnt) {
-      if (st->ne > 32) live = 1;
+      if (st->ne > 64) live = 1;
       if (live) add_post(cnt, &c0);
       c0 = *cnt;
     }

@@ -74,7 +74,7 @@ typedef struct {
   /* The same four counts restricted to the part of each shot that differs from
    * the circuit's noiseless run: from the earliest of the first applied error,
    * the first measurement an OBSERVABLE reads, the first outcome with
-   * 0 < p_+ < 1 and the first map above 32 entries, to the end of the shot. */
+   * 0 < p_+ < 1 and the first map above 64 entries, to the end of the shot. */
   uint64_t post_t_out, post_t_diag, post_meas, post_noise;
 } or_counts;
 

@@ -761,14 +761,16 @@ struct Shot {
     uint64_t sd[2], ss[2];
     uint64_t pad[2];
   };
+  static constexpr uint32_t kSnapMax = 64;  // entries a snapshot holds (registers or shared memory)
   __host__ __device__ static constexpr size_t snap_stride(uint32_t rw) {
-    return (sizeof(SnapHdr) + (size_t)rw * 8 + 32 * (size_t)W * 8 + 32 * sizeof(Cx<R>) + 15) & ~(size_t)15;
+    return (sizeof(SnapHdr) + (size_t)rw * 8 + kSnapMax * (size_t)W * 8 + kSnapMax * sizeof(Cx<R>) + 15) &
+           ~(size_t)15;
   }
   __device__ void save_snapshot(unsigned char *out) {
     SnapHdr *h = reinterpret_cast<SnapHdr *>(out);
     uint64_t *rw_out = reinterpret_cast<uint64_t *>(out + sizeof(SnapHdr));
     uint64_t *k_out = rw_out + C->rw;
-    Cx<R> *v_out = reinterpret_cast<Cx<R> *>(k_out + 32 * W);
+    Cx<R> *v_out = reinterpret_cast<Cx<R> *>(k_out + kSnapMax * W);
     if (lane == 0) {
       h->nnz = nnz;
       h->chain = (uint32_t)chain;
@@ -782,10 +784,19 @@ struct Shot {
       }
     }
     for (uint32_t w = lane; w < C->rw; w += G) rw_out[w] = rec[w];
-    if (lane < nnz) {
+    if (reg) {
+      if (lane < nnz) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) k_out[lane * W + w] = rk.w[w];
-      v_out[lane] = rv;
+        for (int w = 0; w < W; ++w) k_out[lane * W + w] = rk.w[w];
+        v_out[lane] = rv;
+      }
+    } else {
+      for (uint32_t i = lane; i < nnz && i < kSnapMax; i += G) {
+        const Key<W> k = key(i);
+#pragma unroll
+        for (int w = 0; w < W; ++w) k_out[i * W + w] = k.w[w];
+        v_out[i] = vals[i];
+      }
     }
   }
   // First event whose errors the shot must apply itself: the event that applies
@@ -804,7 +815,7 @@ struct Shot {
     const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);
     const uint64_t *r_in = reinterpret_cast<const uint64_t *>(in + sizeof(SnapHdr));
     const uint64_t *k_in = r_in + C->rw;
-    const Cx<R> *v_in = reinterpret_cast<const Cx<R> *>(k_in + 32 * W);
+    const Cx<R> *v_in = reinterpret_cast<const Cx<R> *>(k_in + kSnapMax * W);
     nnz = __ldg(&h->nnz);
     chain = (int)__ldg(&h->chain);
     logical = (int)__ldg(&h->logical);
@@ -816,7 +827,7 @@ struct Shot {
       ss[w] = __ldg(&h->ss[w]);
     }
     for (uint32_t w = lane; w < C->rw; w += G) rec[w] = __ldg(&r_in[w]);
-    if (nnz > 32u) {  // a snapshot never holds more than 32 entries
+    if (nnz > kSnapMax) {  // a snapshot never holds more than kSnapMax entries
       fail_check(CHK_NNZ, nnz);
       return lo;
     }
@@ -894,7 +905,7 @@ struct Shot {
 
   // The circuit's noiseless run, recording the state at the top of every event
   // until an outcome is not decided (it would depend on the shot's uniform), a
-  // fidelity measurement, the map leaving register mode, or the end. Event
+  // fidelity measurement, a map above kSnapMax entries, or the end. Event
   // `stop` is the last valid snapshot: shots resume there at the latest.
   __device__ uint32_t trace_prefix(unsigned char *out, size_t stride) {
     init_shot(0);
@@ -910,7 +921,7 @@ struct Shot {
       if ((type == EV_MEAS_A || type == EV_MEAS_B) && (ev_flags(w0) & F_FIDELITY)) break;
       undecided = false;
       step(ev);
-      if (status != ST_RUN || undecided || !reg) break;
+      if (status != ST_RUN || undecided || nnz > kSnapMax) break;
     }
     t.sync();
     return ev;

@@ -315,7 +315,7 @@ def _run_prefix(S, c, n, seed, precision, prefix, **kw):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["w42", "tiny6", "random40", "w42_rerun"])
+@pytest.mark.parametrize("case", ["w42", "tiny6", "random40", "w42_rerun", "w97"])
 def test_prefix_start_is_bit_identical(soft, precision, case):
     """Starting each shot from the noiseless run's state at its first error
     (the default) gives exactly the records, statuses, tallies and final states
@@ -326,6 +326,8 @@ def test_prefix_start_is_bit_identical(soft, precision, case):
         circ, noise = C.workload("w42")
         if case == "w42_rerun":
             kw = {"first_cap": 8}
+    elif case == "w97":  # two-word keys, snapshots above 32 entries held in shared memory
+        circ, noise = C.workload("w97")
     elif case == "tiny6":
         circ, noise = C.workload("tiny6")
         noise = C.Noise.uniform(0.02)
