@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -133,7 +134,8 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
   }
   size_t b_cf = std::max<size_t>(1, hp.coefs.size()) * sizeof(soft::Coef),
          b_cb = std::max<size_t>(1, hp.cb.size()) * sizeof(soft::CaseB),
-         b_st = std::max<size_t>(1, hp.sites.size()) * sizeof(soft::Site), b_thr = hp.thr.size() * sizeof(uint64_t);
+         b_st = std::max<size_t>(1, hp.sites.size()) * sizeof(soft::Site),
+         b_thr0 = hp.thr.size() * sizeof(uint64_t), b_thr = b_thr0 + hp.site_ev.size() * sizeof(uint32_t);
   cudaError_t e;
   if ((e = cudaMalloc(&c->d_ev, b_ev)) != cudaSuccess || (e = cudaMalloc(&c->d_coef, b_cf)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_cb, b_cb)) != cudaSuccess || (e = cudaMalloc(&c->d_sites, b_st)) != cudaSuccess ||
@@ -148,7 +150,9 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
                                          cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (!hp.sites.empty() && (e = cudaMemcpy(c->d_sites, hp.sites.data(), hp.sites.size() * sizeof(soft::Site),
                                             cudaMemcpyHostToDevice)) != cudaSuccess) ||
-      (e = cudaMemcpy(c->d_thr, hp.thr.data(), b_thr, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      (e = cudaMemcpy(c->d_thr, hp.thr.data(), b_thr0, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(reinterpret_cast<unsigned char *>(c->d_thr) + b_thr0, hp.site_ev.data(),
+                      hp.site_ev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
     soft_circuit_free(c);
     return cuda_fail(e, "cudaMemcpy (program upload)");
   }
@@ -224,6 +228,7 @@ namespace {
 
 soft::CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix) {
   soft::CircDev d{};
+  d.site_ev = reinterpret_cast<const uint32_t *>(c->d_thr + c->hp.thr.size());
   if (prefix && c->d_traj[fp32]) {
     d.traj = c->d_traj[fp32];
     d.traj_stop = c->traj_stop[fp32];

@@ -599,6 +599,14 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
   P.n_sites = (uint32_t)P.sites.size();
   P.thr.resize(P.n_sites ? P.n_sites : 1);
   for (uint32_t g = 0; g < P.n_sites; ++g) P.thr[g] = gap_thr(P.pmax, g);
+  P.site_ev.assign(P.thr.size(), (uint32_t)P.ev.size());
+  {
+    uint32_t e = 0;
+    for (uint32_t s = 0; s < P.n_sites; ++s) {
+      while (e < P.ev.size() && P.ev[e].site_begin <= s) ++e;
+      P.site_ev[s] = e;
+    }
+  }
   P.fin_x.assign(4 * (size_t)n, 0);
   P.fin_z.assign(4 * (size_t)n, 0);
   for (uint32_t i = 0; i < n; ++i)

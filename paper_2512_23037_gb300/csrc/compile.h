@@ -21,6 +21,7 @@ struct HostProgram {
   std::vector<CaseB> cb;
   std::vector<Site> sites;
   std::vector<uint64_t> thr;     // gap thresholds, one per site
+  std::vector<uint32_t> site_ev; // per site: the first event whose site_begin exceeds it (applies its error)
   std::vector<uint64_t> fin_x;   // final X words, 2n rows x 2 words
   std::vector<uint64_t> fin_z;
   bool fid_ok = true;  // no DETECTOR at or after the first measurement an OBSERVABLE reads

@@ -181,7 +181,8 @@ struct Shot {
       }
       uint4 w = philox(P.seed, shot, 0u, kblk++);
       uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
-      uint32_t rem = n_sites - cur, lo = 0, hi = rem;
+      const uint32_t rem = n_sites - cur;
+      uint32_t lo = 0, hi = rem;  // the gap: the smallest g < rem with U < thr[g] (rem if none)
       while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
         if (U < __ldg(&thr[mid])) hi = mid;
@@ -804,12 +805,10 @@ struct Shot {
   // noiseless run's valid prefix. Loads the snapshot there and returns it.
   __device__ uint32_t load_prefix() {
     const uint32_t stop = C->traj_stop;
-    const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
-    uint32_t lo = 0, hi = stop;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (__ldg(&evs[mid].site_begin) > nxt) hi = mid;
-      else lo = mid + 1u;
+    uint32_t lo = stop;
+    if (nxt < C->n_sites) {
+      const uint32_t e = __ldg(&C->site_ev[nxt]);
+      lo = e < stop ? e : stop;
     }
     const unsigned char *in = C->traj + (size_t)lo * C->traj_stride;
     const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);

@@ -31,6 +31,7 @@ struct CircDev {
   // a shot starts at the event that applies its first error, or at traj_stop
   const unsigned char *traj;
   uint32_t traj_stop, traj_stride;
+  const uint32_t *site_ev;  // per site: the event that applies its error
 };
 
 struct ShotParams {
