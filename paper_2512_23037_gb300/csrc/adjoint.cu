@@ -89,6 +89,13 @@ struct GradWarp {
   uint64_t sd[W], ss[W];
   uint32_t nxt, cur, kblk, w2, n_err;
   uint8_t status;
+  // forward projection run
+  RMap<R, W> phi, pre;
+  uint32_t r, ev_f, rot_before_f;
+  bool seen_f, done_empty;
+  double n_acc;
+  int lastm;
+  uint32_t ev0 = 0, r0 = 0;  // first event / rotation this pattern computes itself
 
   __device__ GradWarp(const Tile &tile, const GradParams &p, unsigned char *smem_base, unsigned char *tape_base)
       : t(tile), P(p), lane(tile.thread_rank()), L(p.n_rot, p.n_events) {
@@ -387,10 +394,19 @@ struct GradWarp {
     }
     if (lane == 0) reinterpret_cast<uint32_t *>(tape + L.nnz)[r] = m.n;
   }
-  __device__ void tape_load_phi(uint32_t r, RMap<R, W> &m) const {
-    const uint64_t *tk = reinterpret_cast<const uint64_t *>(tape + L.keys);
-    const Cx<R> *tv = reinterpret_cast<const Cx<R> *>(tape + L.vals);
-    m.n = reinterpret_cast<const uint32_t *>(tape + L.nnz)[r];
+  // the shared noiseless tape holds what precedes this pattern's first error
+  __device__ __forceinline__ const unsigned char *tape_for_rot(uint32_t rr) const {
+    return rr < r0 ? P.ptape : tape;
+  }
+  __device__ __forceinline__ const unsigned char *tape_for_ev(uint32_t ev) const {
+    return ev < ev0 ? P.ptape : tape;
+  }
+  __device__ void tape_load_phi(uint32_t rr, RMap<R, W> &m) const {
+    const unsigned char *tp = tape_for_rot(rr);
+    const uint64_t *tk = reinterpret_cast<const uint64_t *>(tp + L.keys);
+    const Cx<R> *tv = reinterpret_cast<const Cx<R> *>(tp + L.vals);
+    const uint32_t r = rr;
+    m.n = reinterpret_cast<const uint32_t *>(tp + L.nnz)[r];
     if (lane < m.n) {
 #pragma unroll
       for (int w = 0; w < W; ++w) m.k.w[w] = tk[((size_t)r * 32 + lane) * W + w];
@@ -408,7 +424,7 @@ struct GradWarp {
     }
   }
   __device__ void tape_signs_load(uint32_t ev) {
-    const uint64_t *ts = reinterpret_cast<const uint64_t *>(tape + L.signs) + (size_t)ev * 2 * W;
+    const uint64_t *ts = reinterpret_cast<const uint64_t *>(tape_for_ev(ev) + L.signs) + (size_t)ev * 2 * W;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       sd[w] = ts[w];
@@ -419,7 +435,7 @@ struct GradWarp {
     if (lane == 0) reinterpret_cast<uint64_t *>(tape + L.bits)[ev >> 6] |= 1ull << (ev & 63);
   }
   __device__ bool tape_bit(uint32_t ev) const {
-    return (reinterpret_cast<const uint64_t *>(tape + L.bits)[ev >> 6] >> (ev & 63)) & 1ull;
+    return (reinterpret_cast<const uint64_t *>(tape_for_ev(ev) + L.bits)[ev >> 6] >> (ev & 63)) & 1ull;
   }
   __device__ ErrRec<W> *errs() const { return reinterpret_cast<ErrRec<W> *>(tape + L.errs); }
 
@@ -465,20 +481,50 @@ struct GradWarp {
     double *grad = P.grad + off * P.n_params;
     for (uint32_t k = lane; k < P.n_params; k += 32) grad[k] = 0.0;
     t.sync();
-    RMap<R, W> phi, pre;
-    for (int w = 0; w < W; ++w) phi.k.w[w] = 0ull;
-    phi.v = Cx<R>{(R)(lane == 0 ? 1 : 0), (R)0};
-    phi.n = 1;
-    pre = phi;
+    fwd_init();
     cur = 0;
     kblk = 0;
     draw_next();
+    if (P.psnap) load_prefix();  // every event before the first error is the noiseless run's
+    for (uint32_t ev = ev0; ev < P.n_events && status == G_OK && !done_empty; ++ev) fwd_step(ev);
+    double n_fid = 0.0, F = 0.0;
+    if (status == G_OK) {
+      n_fid = norm2_map(phi);
+      if (!seen_f) {
+        n_acc = n_fid;
+        pre = phi;
+        ev_f = P.n_events;
+        rot_before_f = r;
+      }
+      if (!(n_acc > 0.0)) status = G_ZERO;
+      else F = n_fid / n_acc;
+    }
+    if (status == G_OK && n_fid > 0.0) {  // N_fid = 0: F = 0 and dF/dtheta = 0 exactly
+      // sweep 1: N_fid from the end; sweep 2: N_acc from just before the first fidelity measurement
+      if (!sweep(phi, P.n_events, r, grad, 1.0)) status = G_UNSUPPORTED;
+      if (status == G_OK && !sweep(pre, ev_f, rot_before_f, grad, -F)) status = G_UNSUPPORTED;
+      t.sync();
+      for (uint32_t k = lane; k < P.n_params; k += 32) grad[k] /= n_acc;
+    }
+    if (lane == 0) {
+      P.status[off] = status;
+      P.fid[off] = status == G_OK ? F : 0.0;
+      P.pacc[off] = status == G_OK ? n_acc : 0.0;
+      if (P.sums && status == G_OK) {  // ratio estimator sum N_fid / sum N_acc = sum p_acc F / sum p_acc
+        atomicAdd(&P.sums[0], n_acc);
+        atomicAdd(&P.sums[1], n_fid);
+        atomicAdd(&P.sums[2], 1.0);
+      }
+    }
+    if (status != G_OK)
+      for (uint32_t k = lane; k < P.n_params; k += 32) grad[k] = 0.0;
+    t.sync();
+  }
+
+  // One forward event of the projection run: its due errors, then the event.
+  __device__ void fwd_step(uint32_t ev) {
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(P.ev);
-    uint32_t r = 0, ev_f = 0xFFFFFFFFu, rot_before_f = 0;
-    bool seen_f = false, done_empty = false;
-    double n_acc = 0.0;
-    int lastm = 1;
-    for (uint32_t ev = 0; ev < P.n_events && status == G_OK && !done_empty; ++ev) {
+    {
       const Ev<W> *E = evs + ev;
       const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
       uint64_t body[4 * W];
@@ -523,7 +569,7 @@ struct GradWarp {
         n_err++;
         draw_next();
       }
-      if (status != G_OK) break;
+      if (status != G_OK) return;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         sd[w] ^= dsd[w];
@@ -652,38 +698,115 @@ struct GradWarp {
           break;
       }
     }
-    double n_fid = 0.0, F = 0.0;
-    if (status == G_OK) {
-      n_fid = norm2_map(phi);
-      if (!seen_f) {
-        n_acc = n_fid;
-        pre = phi;
-        ev_f = P.n_events;
-        rot_before_f = r;
-      }
-      if (!(n_acc > 0.0)) status = G_ZERO;
-      else F = n_fid / n_acc;
-    }
-    if (status == G_OK && n_fid > 0.0) {  // N_fid = 0: F = 0 and dF/dtheta = 0 exactly
-      // sweep 1: N_fid from the end; sweep 2: N_acc from just before the first fidelity measurement
-      if (!sweep(phi, P.n_events, r, grad, 1.0)) status = G_UNSUPPORTED;
-      if (status == G_OK && !sweep(pre, ev_f, rot_before_f, grad, -F)) status = G_UNSUPPORTED;
-      t.sync();
-      for (uint32_t k = lane; k < P.n_params; k += 32) grad[k] /= n_acc;
-    }
-    if (lane == 0) {
-      P.status[off] = status;
-      P.fid[off] = status == G_OK ? F : 0.0;
-      P.pacc[off] = status == G_OK ? n_acc : 0.0;
-      if (P.sums && status == G_OK) {  // ratio estimator sum N_fid / sum N_acc = sum p_acc F / sum p_acc
-        atomicAdd(&P.sums[0], n_acc);
-        atomicAdd(&P.sums[1], n_fid);
-        atomicAdd(&P.sums[2], 1.0);
-      }
-    }
-    if (status != G_OK)
-      for (uint32_t k = lane; k < P.n_params; k += 32) grad[k] = 0.0;
+  }
+
+  __device__ void fwd_init() {
+#pragma unroll
+    for (int w = 0; w < W; ++w) sd[w] = ss[w] = 0ull;
+    for (uint32_t w = lane; w < P.rw; w += 32) rec[w] = 0ull;
+    for (int w = 0; w < W; ++w) phi.k.w[w] = 0ull;
+    phi.v = Cx<R>{(R)(lane == 0 ? 1 : 0), (R)0};
+    phi.n = 1;
+    pre = phi;
+    r = 0;
+    ev_f = 0xFFFFFFFFu;
+    rot_before_f = 0;
+    seen_f = done_empty = false;
+    n_acc = 0.0;
+    lastm = 1;
+    ev0 = r0 = 0;
     t.sync();
+  }
+
+  // --------------------------------------------------------- shared noiseless prefix
+  // Until its first error a pattern's projection run is the pattern-independent
+  // noiseless one (projections included). A tracing warp records it once per call:
+  // its tape (maps after each rotation, signs, outcome bits) and, per event, the
+  // state at the top of the event. Patterns start at the event that applies their
+  // first error and read the shared tape below it in the reverse sweeps.
+  struct SnapHdr {
+    uint32_t nnz, r, lastm, pad;
+    uint64_t sd[2], ss[2];
+  };
+  __host__ __device__ static constexpr size_t snap_stride(uint32_t rw) {
+    return (sizeof(SnapHdr) + (size_t)rw * 8 + 32 * (size_t)W * 8 + 32 * sizeof(Cx<R>) + 15) & ~(size_t)15;
+  }
+  __device__ void save_snapshot(unsigned char *out) {
+    SnapHdr *h = reinterpret_cast<SnapHdr *>(out);
+    uint64_t *r_out = reinterpret_cast<uint64_t *>(out + sizeof(SnapHdr));
+    uint64_t *k_out = r_out + P.rw;
+    Cx<R> *v_out = reinterpret_cast<Cx<R> *>(k_out + 32 * W);
+    if (lane == 0) {
+      h->nnz = phi.n;
+      h->r = r;
+      h->lastm = (uint32_t)lastm;
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        h->sd[w] = w < W ? sd[w < W ? w : 0] : 0ull;
+        h->ss[w] = w < W ? ss[w < W ? w : 0] : 0ull;
+      }
+    }
+    for (uint32_t w = lane; w < P.rw; w += 32) r_out[w] = rec[w];
+    if (lane < phi.n) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) k_out[lane * W + w] = phi.k.w[w];
+      v_out[lane] = phi.v;
+    }
+  }
+  __device__ void load_prefix() {
+    const uint32_t stop = *P.pstop;
+    ev0 = stop;
+    if (nxt < P.n_sites) {
+      const uint32_t e = __ldg(&P.site_ev[nxt]);
+      ev0 = e < stop ? e : stop;
+    }
+    const unsigned char *in = P.psnap + (size_t)ev0 * P.psnap_stride;
+    const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);
+    const uint64_t *r_in = reinterpret_cast<const uint64_t *>(in + sizeof(SnapHdr));
+    const uint64_t *k_in = r_in + P.rw;
+    const Cx<R> *v_in = reinterpret_cast<const Cx<R> *>(k_in + 32 * W);
+    phi.n = h->nnz;
+    r0 = r = h->r;
+    lastm = (int)h->lastm;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      sd[w] = h->sd[w];
+      ss[w] = h->ss[w];
+    }
+    for (uint32_t w = lane; w < P.rw; w += 32) rec[w] = r_in[w];
+    if (lane < phi.n) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) phi.k.w[w] = k_in[lane * W + w];
+      phi.v = v_in[lane];
+    }
+    pre = phi;
+    t.sync();
+  }
+  // The noiseless projection run from event 0, into this warp's tape (the shared
+  // tape) and `snaps`; returns the last event a pattern may start at.
+  __device__ uint32_t trace_prefix(unsigned char *snaps, size_t stride) {
+    shot = 0;
+    status = G_OK;
+    n_err = 0;
+    {
+      uint64_t *bits = reinterpret_cast<uint64_t *>(tape + L.bits);
+      for (uint32_t w = lane; w < (P.n_events + 63) / 64; w += 32) bits[w] = 0ull;
+    }
+    fwd_init();
+    cur = P.n_sites;
+    nxt = 0xFFFFFFFFu;
+    const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(P.ev);
+    uint32_t ev = 0;
+    for (; ev <= P.n_events; ++ev) {
+      save_snapshot(snaps + (size_t)ev * stride);
+      if (ev == P.n_events) break;
+      const uint32_t w0 = __ldg(&evs[ev].w0), type = ev_type(w0);
+      if ((type == EV_MEAS_A || type == EV_MEAS_B) && (ev_flags(w0) & F_FIDELITY)) break;
+      fwd_step(ev);
+      if (status != G_OK || done_empty) break;
+    }
+    t.sync();
+    return ev;
   }
 
   // Reverse sweep from just before event `ev_end` (its errors included): the
@@ -821,6 +944,27 @@ __global__ void __launch_bounds__(kGradBlock) grad_kernel(const __grid_constant_
 }
 
 template <typename R, int W>
+__global__ void __launch_bounds__(32) grad_prefix_kernel(const __grid_constant__ GradParams P, unsigned char *tape,
+                                                         unsigned char *snaps, uint32_t *stop) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto tile = cg::tiled_partition<32>(cg::this_thread_block());
+  GradWarp<R, W> g(tile, P, smem, tape);
+  const uint32_t ev = g.trace_prefix(snaps, GradWarp<R, W>::snap_stride(P.rw));
+  if (tile.thread_rank() == 0) *stop = ev;
+}
+
+template <typename R, int W>
+cudaError_t launch_grad_prefix_t(const GradParams &p, unsigned char *tape, unsigned char *snaps, uint32_t *stop,
+                                 cudaStream_t st) {
+  GradParams q = p;
+  q.psnap = nullptr;  // the tracer itself starts at event 0
+  q.ptape = nullptr;
+  const size_t smem = smem_per_warp(sizeof(R) == 4, W, p.rw);
+  grad_prefix_kernel<R, W><<<1, 32, smem, st>>>(q, tape, snaps, stop);
+  return cudaGetLastError();
+}
+
+template <typename R, int W>
 cudaError_t launch_grad_t(const GradParams &p, cudaStream_t st) {
   const size_t smem = (kGradBlock / 32) * smem_per_warp(sizeof(R) == 4, W, p.rw);
   grad_kernel<R, W><<<p.blocks, kGradBlock, smem, st>>>(p);
@@ -837,6 +981,20 @@ size_t grad_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events) 
 }
 
 uint32_t grad_warps_per_block() { return kGradBlock / 32; }
+
+size_t grad_prefix_stride(int fp32, uint32_t W, uint32_t rw) {
+  if (fp32) return W == 1 ? GradWarp<float, 1>::snap_stride(rw) : GradWarp<float, 2>::snap_stride(rw);
+  return W == 1 ? GradWarp<double, 1>::snap_stride(rw) : GradWarp<double, 2>::snap_stride(rw);
+}
+
+cudaError_t launch_grad_prefix(const GradParams &p, int fp32, uint32_t W, unsigned char *tape, unsigned char *snaps,
+                               uint32_t *stop, cudaStream_t st) {
+  if (fp32)
+    return W == 1 ? launch_grad_prefix_t<float, 1>(p, tape, snaps, stop, st)
+                  : launch_grad_prefix_t<float, 2>(p, tape, snaps, stop, st);
+  return W == 1 ? launch_grad_prefix_t<double, 1>(p, tape, snaps, stop, st)
+                : launch_grad_prefix_t<double, 2>(p, tape, snaps, stop, st);
+}
 
 cudaError_t launch_grad(const GradParams &p, int fp32, uint32_t W, cudaStream_t st) {
   if (fp32) return W == 1 ? launch_grad_t<float, 1>(p, st) : launch_grad_t<float, 2>(p, st);

@@ -23,11 +23,22 @@ struct GradParams {
   double *sums;               // optional: sum of N_acc, sum of N_fid, count over ok patterns
   unsigned char *tape;        // one slot of tape_stride bytes per resident warp
   size_t tape_stride;
+  // shared noiseless prefix (null psnap: patterns start at event 0)
+  const unsigned char *ptape;  // the tracing warp's tape (same layout as a warp's)
+  const unsigned char *psnap;  // state at the top of each event, psnap_stride bytes each
+  size_t psnap_stride;
+  const uint32_t *pstop;       // last event a pattern may start at (device)
+  const uint32_t *site_ev;     // per site: the event that applies its error
 };
 
 size_t grad_smem_per_warp(int fp32, uint32_t W, uint32_t rw);
 size_t grad_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events);
 uint32_t grad_warps_per_block();
 cudaError_t launch_grad(const GradParams &p, int fp32, uint32_t W, cudaStream_t st);
+// Per-event snapshot bytes of the noiseless prefix, and its tracing launch (one
+// warp): tape -> p.ptape (writable here), snapshots -> p.psnap, last event -> *stop.
+size_t grad_prefix_stride(int fp32, uint32_t W, uint32_t rw);
+cudaError_t launch_grad_prefix(const GradParams &p, int fp32, uint32_t W, unsigned char *tape, unsigned char *snaps,
+                               uint32_t *stop, cudaStream_t st);
 
 }  // namespace soft

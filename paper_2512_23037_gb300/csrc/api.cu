@@ -197,6 +197,7 @@ void soft_circuit_free(soft_circuit *c) {
   cudaFree(c->d_gcoef);
   cudaFree(c->d_gnext);
   cudaFree(c->d_gtape);
+  cudaFree(c->d_gprefix);
   delete c;
 }
 

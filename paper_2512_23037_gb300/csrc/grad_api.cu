@@ -53,6 +53,19 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
       return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
     c->gtape_bytes = tape_need;
   }
+  // shared noiseless prefix: one tape slot, (events + 1) snapshots, the stop index
+  const size_t snap_stride = soft::grad_prefix_stride(fp32, hp.W, hp.rw);
+  const size_t snap_off = (stride + 255) & ~(size_t)255;
+  const size_t stop_off = (snap_off + (hp.ev.size() + 1) * snap_stride + 255) & ~(size_t)255;
+  const size_t prefix_need = stop_off + 256;
+  if (c->gprefix_bytes < prefix_need) {
+    cudaFree(c->d_gprefix);
+    c->d_gprefix = nullptr;
+    c->gprefix_bytes = 0;
+    if ((e = cudaMalloc(&c->d_gprefix, prefix_need)) != cudaSuccess)
+      return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
+    c->gprefix_bytes = prefix_need;
+  }
   soft::Coef *d_coef = c->d_gcoef;
   unsigned long long *d_next = c->d_gnext;
   unsigned char *d_tape = c->d_gtape;
@@ -86,6 +99,15 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   p.sums = d_sums;
   p.tape = d_tape;
   p.tape_stride = stride;
+  unsigned char *ptape = c->d_gprefix, *psnap = c->d_gprefix + snap_off;
+  uint32_t *pstop = reinterpret_cast<uint32_t *>(c->d_gprefix + stop_off);
+  p.site_ev = reinterpret_cast<const uint32_t *>(c->d_thr + hp.thr.size());
+  if ((e = soft::launch_grad_prefix(p, fp32, hp.W, ptape, psnap, pstop, st)) != cudaSuccess)
+    return soft::set_error(SOFT_E_CUDA, "prefix kernel launch failed");
+  p.ptape = ptape;
+  p.psnap = psnap;
+  p.psnap_stride = snap_stride;
+  p.pstop = pstop;
   if ((e = soft::launch_grad(p, fp32, hp.W, st)) != cudaSuccess)
     return soft::set_error(SOFT_E_CUDA, "gradient kernel launch failed");
   // synchronous: the host coefficient table and the handle's workspace are reused by the next call

@@ -35,4 +35,6 @@ struct soft_circuit {
   unsigned long long *d_gnext = nullptr;
   unsigned char *d_gtape = nullptr;
   size_t gtape_bytes = 0;
+  unsigned char *d_gprefix = nullptr;  // shared noiseless prefix: tape, snapshots, stop index
+  size_t gprefix_bytes = 0;
 };
