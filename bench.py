@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--grad-patterns", type=int, default=100000,
                     help="error patterns per step of the gradient leg (0 = skip it)")
     ap.add_argument("--no-fidelity", action="store_true", help="skip the exact-fidelity leg")
+    ap.add_argument("--sweep", action="store_true",
+                    help="w42 sweeps instead of the bench line: noise p in {5e-4, 1e-3, 2e-3} and shots resident "
+                         "per SM (one JSON line per point)")
     return ap.parse_args()
 
 
@@ -224,6 +227,52 @@ def grad_bench(S, C, torch, stream, n_pat, steps, warmup):
     return out
 
 
+def sweep(args):
+    """Throughput of the 42-qubit workload against the noise rate (discard
+    rate grows with p) and against the shots resident per SM (blocks per SM x
+    groups per block), FP32 and FP64, CUDA events over K steps of --shots."""
+    import torch
+    import paper_2512_23037_gb300 as S
+    from paper_2512_23037_gb300 import circuits as C
+    S.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def rate(h, precision, **kw):
+        for w in range(args.warmup):
+            S.soft_tally(S.soft_run_shots(h, args.shots, (1 << 36) + w * args.shots, 0, precision=precision,
+                                          stream=stream, **kw))
+        ms, tal = 0.0, None
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = S.soft_run_shots(h, args.shots, k * args.shots, 0, precision=precision, stream=stream, **kw)
+            e1.record(stream)
+            tal = S.soft_tally(r)
+            ms += e0.elapsed_time(e1)
+        return args.shots * args.steps / (ms / 1000), tal
+
+    for p in (5e-4, 1e-3, 2e-3):
+        circ, noise = C.windowed(1, p=p)
+        h = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+        v32, tal = rate(h, "fp32")
+        v64, _ = rate(h, "fp64")
+        print(json.dumps({"sweep": "noise", "workload": "w42", "p": p, "fp32_shots_per_s": v32,
+                          "fp64_shots_per_s": v64, "discard_rate": tal["discarded"] / tal["shots"],
+                          "ler_kept": tal["logical_errors"] / max(tal["kept"], 1)}))
+    circ, noise = C.workload("w42")
+    h = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    for bps in (1, 2, 4, 6):
+        for gpb in (1, 2, 4):
+            v32, _ = rate(h, "fp32", blocks_per_sm=bps, groups_per_block=gpb)
+            print(json.dumps({"sweep": "shots_per_sm", "workload": "w42", "blocks_per_sm": bps,
+                              "groups_per_block": gpb, "shots_resident_per_sm": bps * gpb,
+                              "fp32_shots_per_s": v32}))
+    return 0
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -258,6 +307,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.sweep:
+        return sweep(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
