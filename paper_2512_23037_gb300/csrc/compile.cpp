@@ -294,18 +294,50 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
     s.dss[0] = tb.pend_s[0];
     s.dss[1] = tb.pend_s[1];
     s.kind = kind;
+    // X_q and Z_q of each site qubit: Q = i^e d_beta s_gamma at zero signs
+    uint32_t ex[2] = {0, 0}, ez[2] = {0, 0};
     for (int k = 0; k < (two ? 2 : 1); ++k) {
       uint32_t q = k == 0 ? q0 : q1;
-      uint32_t e;
-      if (!tb.decompose(single(1, q), s.bx[k], s.gx[k], &e)) return false;
-      if (!tb.decompose(single(3, q), s.bz[k], s.gz[k], &e)) return false;
+      if (!tb.decompose(single(1, q), s.bx[k], s.gx[k], &ex[k])) return false;
+      if (!tb.decompose(single(3, q), s.bz[k], s.gz[k], &ez[k])) return false;
     }
-    uint32_t c0 = 0;
-    for (int code = 1; code <= (two ? 15 : 3); ++code) {
-      Pz Q = two ? pmul(single(code >> 2, q0), single(code & 3, q1)) : single(code, q0);
+    // Phases of the other Paulis by composition. With P = i^a d_b s_c and
+    // Q = i^a' d_b' s_c', PQ = i^(a + a' + 2 |c & b'|) d_(b^b') s_(c^c'): s_j
+    // anticommutes with d_j only, and the d's (and the s's) commute and square to I.
+    auto comp = [&](uint32_t a, const uint64_t *c, const uint64_t *b2, uint32_t a2) {
+      return (a + a2 + 2u * (uint32_t)(pc(c[0] & b2[0]) + pc(c[1] & b2[1]))) & 3u;
+    };
+    struct One {
       uint64_t b[2], g[2];
       uint32_t e;
-      if (!tb.decompose(Q, b, g, &e)) return false;
+    };
+    auto one = [&](int code, int k) -> One {  // 1 X, 2 Y = i X Z, 3 Z on site qubit k
+      One o{};
+      if (code == 1) o = One{{s.bx[k][0], s.bx[k][1]}, {s.gx[k][0], s.gx[k][1]}, ex[k]};
+      else if (code == 3) o = One{{s.bz[k][0], s.bz[k][1]}, {s.gz[k][0], s.gz[k][1]}, ez[k]};
+      else if (code == 2) {
+        for (int w = 0; w < 2; ++w) {
+          o.b[w] = s.bx[k][w] ^ s.bz[k][w];
+          o.g[w] = s.gx[k][w] ^ s.gz[k][w];
+        }
+        o.e = comp(1u + ex[k], s.gx[k], s.bz[k], ez[k]);
+      }
+      return o;
+    };
+    uint32_t c0 = 0;
+    for (int code = 1; code <= (two ? 15 : 3); ++code) {
+      uint32_t e;
+      if (!two) {
+        e = one(code, 0).e;
+      } else {
+        const int pa = code >> 2, pb = code & 3;
+        if (!pa) e = one(pb, 1).e;
+        else if (!pb) e = one(pa, 0).e;
+        else {
+          const One A = one(pa, 0), B = one(pb, 1);
+          e = comp(A.e, A.g, B.b, B.e);
+        }
+      }
       c0 |= (e & 3u) << (2 * code);
     }
     s.c0 = c0;
