@@ -17,9 +17,13 @@
 // vectors live in the same GS basis at every step (Sec. II-C): the basis is
 // orthonormal, so adjoints are conjugate transposes of the coefficient maps.
 //
-// The map of both vectors stays in registers (lane i holds entry i) and is
-// limited to 32 entries; a pattern that needs more ends UNSUPPORTED.
+// The maps live in registers (lane i holds entry i) while they have at most
+// 32 entries. A pattern that needs more is listed and rerun by a second launch
+// whose maps live in shared memory (up to kWideCap entries); beyond that it
+// ends UNSUPPORTED.
 #include <cooperative_groups.h>
+
+#include <type_traits>
 
 #include "adjoint.cuh"
 #include "device_common.cuh"
@@ -31,7 +35,8 @@ namespace {
 
 using namespace dev;
 
-enum : uint8_t { G_OK = 0, G_ZERO = 1, G_UNSUPPORTED = 2, G_ERROR = 3 };
+enum : uint8_t { G_OK = 0, G_ZERO = 1, G_UNSUPPORTED = 2, G_ERROR = 3, G_WIDE = 4 /* rerun wide */ };
+constexpr uint32_t kWideCap = 256;  // entries of a shared-memory map
 
 // shared memory per warp: 64 staging keys and values, the record words
 __host__ __device__ inline size_t smem_per_warp(int fp32, uint32_t W, uint32_t rw) {
@@ -46,15 +51,19 @@ struct ErrRec {
   uint64_t sd[W], ss[W];
 };
 
+// Per-warp tape: the map after every rotation (`slot` entries each), the sign
+// words after every event's Clifford XOR, outcome bits, the applied errors.
 template <typename R, int W>
 struct TapeLayout {
   size_t keys, vals, nnz, signs, bits, errs, total;
-  __host__ __device__ TapeLayout(uint32_t n_rot, uint32_t n_events) {
+  uint32_t slot;
+  __host__ __device__ TapeLayout(uint32_t n_rot, uint32_t n_events, uint32_t slot_entries = 32) {
+    slot = slot_entries;
     size_t o = 0;
     keys = o;
-    o += (size_t)n_rot * 32 * W * 8;
+    o += (size_t)n_rot * slot * W * 8;
     vals = o;
-    o += (size_t)n_rot * 32 * sizeof(Cx<R>);
+    o += (size_t)n_rot * slot * sizeof(Cx<R>);
     nnz = o;
     o += ((size_t)n_rot * 4 + 15) & ~(size_t)15;
     signs = o;
@@ -73,24 +82,42 @@ struct RMap {
   Cx<R> v;
   uint32_t n;
 };
-
+// A map in shared memory: n entries, key i at k[i * W ...], value v[i].
 template <typename R, int W>
+struct SMap {
+  uint64_t *k;
+  Cx<R> *v;
+  uint32_t n;
+};
+// Wide mode shared memory per warp: four maps (phi, pre, lambda, a tape read),
+// 2 kWideCap staging entries, the record words.
+__host__ __device__ inline size_t wide_entry_bytes(int fp32, uint32_t W) { return (size_t)W * 8 + (fp32 ? 8 : 16); }
+__host__ __device__ inline size_t wide_smem_per_warp(int fp32, uint32_t W, uint32_t rw) {
+  return ((6 * (size_t)kWideCap * wide_entry_bytes(fp32, W) + (size_t)rw * 8) + 15) & ~(size_t)15;
+}
+
+template <typename R, int W, bool Wide = false>
 struct GradWarp {
   using Tile = cg::thread_block_tile<32>;
+  using Map = typename std::conditional<Wide, SMap<R, W>, RMap<R, W>>::type;
+  // a capacity failure: listed for the wide rerun, or final in wide mode
+  static constexpr uint8_t kCapFail = Wide ? G_UNSUPPORTED : G_WIDE;
   const Tile &t;
   const GradParams &P;
   const uint32_t lane;
-  uint64_t *skeys;  // staging: 64 keys x W words (shared)
-  Cx<R> *svals;     // staging: 64 values (shared)
+  uint64_t *skeys;  // staging: 64 (wide: 2 kWideCap) keys x W words (shared)
+  Cx<R> *svals;     // staging values (shared)
   uint64_t *rec;    // record bits (shared)
   unsigned char *tape;
-  TapeLayout<R, W> L;
+  TapeLayout<R, W> L;   // this warp's tape
+  TapeLayout<R, W> PL;  // the shared noiseless prefix tape (32-entry slots)
   uint64_t shot;
   uint64_t sd[W], ss[W];
   uint32_t nxt, cur, kblk, w2, n_err;
   uint8_t status;
   // forward projection run
-  RMap<R, W> phi, pre;
+  Map phi, pre;
+  Map lam_store, phk_store;  // wide mode: the sweep's adjoint map and tape reads
   uint32_t r, ev_f, rot_before_f;
   bool seen_f, done_empty;
   double n_acc;
@@ -98,11 +125,296 @@ struct GradWarp {
   uint32_t ev0 = 0, r0 = 0;  // first event / rotation this pattern computes itself
 
   __device__ GradWarp(const Tile &tile, const GradParams &p, unsigned char *smem_base, unsigned char *tape_base)
-      : t(tile), P(p), lane(tile.thread_rank()), L(p.n_rot, p.n_events) {
-    svals = reinterpret_cast<Cx<R> *>(smem_base);
-    skeys = reinterpret_cast<uint64_t *>(smem_base + 64 * sizeof(Cx<R>));
-    rec = reinterpret_cast<uint64_t *>(smem_base + 64 * sizeof(Cx<R>) + 64 * W * 8);
+      : t(tile), P(p), lane(tile.thread_rank()), L(p.n_rot, p.n_events, Wide ? kWideCap : 32u),
+        PL(p.n_rot, p.n_events, 32u) {
+    if constexpr (Wide) {
+      const size_t kb = (size_t)kWideCap * W * 8, vb = (size_t)kWideCap * sizeof(Cx<R>);
+      unsigned char *b = smem_base;
+      Map *maps[4] = {&phi, &pre, &lam_store, &phk_store};
+      for (int m = 0; m < 4; ++m) {
+        maps[m]->k = reinterpret_cast<uint64_t *>(b);
+        maps[m]->v = reinterpret_cast<Cx<R> *>(b + kb);
+        maps[m]->n = 0;
+        b += kb + vb;
+      }
+      skeys = reinterpret_cast<uint64_t *>(b);
+      svals = reinterpret_cast<Cx<R> *>(b + 2 * kb);
+      rec = reinterpret_cast<uint64_t *>(b + 2 * kb + 2 * vb);
+    } else {
+      svals = reinterpret_cast<Cx<R> *>(smem_base);
+      skeys = reinterpret_cast<uint64_t *>(smem_base + 64 * sizeof(Cx<R>));
+      rec = reinterpret_cast<uint64_t *>(smem_base + 64 * sizeof(Cx<R>) + 64 * W * 8);
+    }
     tape = tape_base;
+  }
+
+  // ------------------------------------------------------------- shared-memory maps (wide mode)
+  // Every lane walks entries lane, lane + 32, ...; lookups scan the map.
+  __device__ __forceinline__ Key<W> smk(const SMap<R, W> &m, uint32_t i) const {
+    Key<W> k;
+#pragma unroll
+    for (int w = 0; w < W; ++w) k.w[w] = m.k[(size_t)i * W + w];
+    return k;
+  }
+  __device__ __forceinline__ void smk_set(SMap<R, W> &m, uint32_t i, const Key<W> &k) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) m.k[(size_t)i * W + w] = k.w[w];
+  }
+  __device__ int sfind(const SMap<R, W> &m, const Key<W> &k) const {
+    for (uint32_t j = 0; j < m.n; ++j)
+      if (keq(smk(m, j), k)) return (int)j;
+    return -1;
+  }
+  __device__ void copy_map(SMap<R, W> &d, const SMap<R, W> &s_) {
+    for (uint32_t i = lane; i < s_.n; i += 32) {
+      smk_set(d, i, smk(s_, i));
+      d.v[i] = s_.v[i];
+    }
+    d.n = s_.n;
+    t.sync();
+  }
+  __device__ void copy_map(RMap<R, W> &d, const RMap<R, W> &s_) { d = s_; }
+  __device__ double norm2_map(const SMap<R, W> &m) const {
+    double a = 0.0;
+    for (uint32_t i = lane; i < m.n; i += 32) a += norm2d(m.v[i]);
+    return wsum(a);
+  }
+  // stable compaction of the staged entries [0, n) with keep(i) into map m
+  template <typename Keep>
+  __device__ void sm_from_stage(SMap<R, W> &m, uint32_t n, Keep keep) {
+    uint32_t out = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+      const uint32_t i = base + lane;
+      const bool kp = i < n && keep(i);
+      const uint32_t b = t.ballot(kp);
+      if (kp) {
+        const uint32_t d = out + lanes_below(b);
+        smk_set(m, d, skey2(i));
+        m.v[d] = svals[i];
+      }
+      out += __popc(b);
+    }
+    m.n = out;
+    t.sync();
+  }
+  __device__ __forceinline__ void skey2_set(uint32_t i, const Key<W> &k) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) skeys[(size_t)w * 2 * kWideCap + i] = k.w[w];
+  }
+  __device__ __forceinline__ Key<W> skey2(uint32_t i) const {
+    Key<W> r_;
+#pragma unroll
+    for (int w = 0; w < W; ++w) r_.w[w] = skeys[(size_t)w * 2 * kWideCap + i];
+    return r_;
+  }
+  // map -> stage (all entries), then back with the relative prune
+  __device__ void prune_rel(SMap<R, W> &m) {
+    const double thr = P.tau_rel * norm2_map(m);
+    for (uint32_t i = lane; i < m.n; i += 32) {
+      skey2_set(i, smk(m, i));
+      svals[i] = m.v[i];
+    }
+    t.sync();
+    sm_from_stage(m, m.n, [&](uint32_t i) { return norm2d(svals[i]) >= thr; });
+  }
+  __device__ void pauli(SMap<R, W> &m, const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+    for (uint32_t i = lane; i < m.n; i += 32) {
+      const Key<W> k = smk(m, i);
+      m.v[i] = ipow(m.v[i], e + 2u * kpar(k, gamma));
+      smk_set(m, i, kxor(k, beta));
+    }
+    t.sync();
+  }
+  __device__ void pauli_adj(SMap<R, W> &m, const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+    for (uint32_t i = lane; i < m.n; i += 32) {
+      const Key<W> a = kxor(smk(m, i), beta);
+      m.v[i] = ipow(m.v[i], (4u - (e & 3u)) + 2u * kpar(a, gamma));
+      smk_set(m, i, a);
+    }
+    t.sync();
+  }
+  // a I + b Z_q (beta != 0): stage [0, n) the updated old entries, [n, n + nA) the new ones
+  __device__ bool rot(SMap<R, W> &m, uint32_t e, uint32_t lowbit, Cx<R> a, Cx<R> b, const uint64_t *beta,
+                      const uint64_t *gamma) {
+    (void)lowbit;
+    const uint32_t n = m.n;
+    uint32_t nA = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+      const uint32_t i = base + lane;
+      bool app = false;
+      Key<W> pk;
+      Cx<R> tb{0, 0};
+      if (i < n) {
+        const Key<W> k = smk(m, i);
+        pk = kxor(k, beta);
+        const int j = sfind(m, pk);
+        Cx<R> nv = cmul(a, m.v[i]);
+        if (j >= 0) nv = cadd(nv, cmul(b, ipow(m.v[j], e + 2u * kpar(pk, gamma))));
+        else {
+          tb = cmul(b, ipow(m.v[i], e + 2u * kpar(k, gamma)));
+          app = true;
+        }
+        skey2_set(i, k);
+        svals[i] = nv;
+      }
+      const uint32_t bal = t.ballot(app);
+      if (app) {
+        const uint32_t d = n + nA + lanes_below(bal);
+        if (d < 2 * kWideCap) {
+          skey2_set(d, pk);
+          svals[d] = tb;
+        }
+      }
+      nA += __popc(bal);
+    }
+    t.sync();
+    if (n + nA > kWideCap) return false;
+    double tot = 0.0;
+    for (uint32_t i = lane; i < n + nA; i += 32) tot += norm2d(svals[i]);
+    const double thr = P.tau_rel * wsum(tot);
+    sm_from_stage(m, n + nA, [&](uint32_t i) { return norm2d(svals[i]) >= thr; });
+    return true;
+  }
+  __device__ void rot_diag(SMap<R, W> &m, uint32_t e, Cx<R> a, Cx<R> b, const uint64_t *gamma) {
+    for (uint32_t i = lane; i < m.n; i += 32)
+      m.v[i] = cadd(cmul(a, m.v[i]), cmul(b, ipow(m.v[i], e + 2u * kpar(smk(m, i), gamma))));
+    t.sync();
+    prune_rel(m);
+  }
+  __device__ void project_a(SMap<R, W> &m, const uint64_t *gamma, uint32_t sgn, int mm) {
+    for (uint32_t i = lane; i < m.n; i += 32) {
+      skey2_set(i, smk(m, i));
+      svals[i] = m.v[i];
+    }
+    t.sync();
+    sm_from_stage(m, m.n, [&](uint32_t i) { return ((kpar(skey2(i), gamma) ^ sgn) != 0u) == (mm == -1); });
+    prune_rel(m);
+  }
+  // relabel a_j ^= a_p (j in J), then v''_{a0} = (v_{a0} + m xi_{a1} v_{a1}) / sqrt(2)
+  __device__ void project_b(SMap<R, W> &m, uint32_t p, const uint64_t *J, const uint64_t *ep, const uint64_t *g2,
+                            uint32_t e2, int mm) {
+    for (uint32_t i = lane; i < m.n; i += 32) {
+      const Key<W> k = smk(m, i);
+      if (kbit(k, p)) smk_set(m, i, kxor(k, J));
+    }
+    t.sync();
+    const R rs = (R)0.70710678118654752440;
+    uint32_t out = 0;
+    for (uint32_t base = 0; base < m.n; base += 32) {
+      const uint32_t i = base + lane;
+      bool own = false;
+      Key<W> a0;
+      Cx<R> nv{0, 0};
+      if (i < m.n) {
+        const Key<W> k = smk(m, i);
+        const uint32_t hi = kbit(k, p);
+        a0 = hi ? kxor(k, ep) : k;
+        const int j = sfind(m, hi ? a0 : kxor(k, ep));
+        Cx<R> v0{0, 0}, v1{0, 0};
+        if (hi) {
+          v1 = m.v[i];
+          own = j < 0;  // else the a0 entry combines the pair
+        } else {
+          v0 = m.v[i];
+          if (j >= 0) v1 = m.v[j];
+          own = true;
+        }
+        const Cx<R> x1 = ipow(v1, e2 + 2u * kpar(kxor(a0, ep), g2));
+        nv = cscale(mm == 1 ? cadd(v0, x1) : csub(v0, x1), rs);
+      }
+      const uint32_t b = t.ballot(own);
+      if (own) {
+        const uint32_t d = out + lanes_below(b);
+        skey2_set(d, a0);
+        svals[d] = nv;
+      }
+      out += __popc(b);
+    }
+    t.sync();
+    sm_from_stage(m, out, [&](uint32_t) { return true; });
+    prune_rel(m);
+  }
+  // adjoint of project_b: drop keys with bit p set, split each into (a0, a1), undo the relabel
+  __device__ bool project_b_adj(SMap<R, W> &m, uint32_t p, const uint64_t *J, const uint64_t *ep,
+                                const uint64_t *g2, uint32_t e2, int mm) {
+    for (uint32_t i = lane; i < m.n; i += 32) {
+      skey2_set(i, smk(m, i));
+      svals[i] = m.v[i];
+    }
+    t.sync();
+    sm_from_stage(m, m.n, [&](uint32_t i) { return !kbit(skey2(i), p); });
+    if (2 * m.n > 2 * kWideCap) return false;
+    const R rs = (R)0.70710678118654752440;
+    const uint32_t n = m.n;
+    for (uint32_t i = lane; i < n; i += 32) {
+      Key<W> k0 = smk(m, i), k1 = kxor(k0, ep);
+      const Cx<R> u0 = cscale(m.v[i], rs);
+      const Cx<R> u1 = ipow(u0, (4u - (e2 & 3u)) + 2u * kpar(k1, g2) + (mm == -1 ? 2u : 0u));
+      if (kbit(k1, p)) k1 = kxor(k1, J);
+      if (kbit(k0, p)) k0 = kxor(k0, J);
+      skey2_set(i, k0);
+      svals[i] = u0;
+      skey2_set(n + i, k1);
+      svals[n + i] = u1;
+    }
+    t.sync();
+    double tot = 0.0;
+    for (uint32_t i = lane; i < 2 * n; i += 32) tot += norm2d(svals[i]);
+    const double thr = P.tau_rel * wsum(tot);
+    uint32_t keep_n = 0;
+    for (uint32_t base = 0; base < 2 * n; base += 32) {
+      const uint32_t i = base + lane;
+      keep_n += __popc(t.ballot(i < 2 * n && norm2d(svals[i]) >= thr && norm2d(svals[i]) > 0.0));
+    }
+    if (keep_n > kWideCap) return false;
+    sm_from_stage(m, 2 * n, [&](uint32_t i) { return norm2d(svals[i]) >= thr && norm2d(svals[i]) > 0.0; });
+    return true;
+  }
+  // <lambda| Z_q |phi> = sum_a conj(lambda_{a^beta}) xi_a phi_a
+  __device__ void zexp(const SMap<R, W> &lam, const SMap<R, W> &ph, const uint64_t *beta, const uint64_t *gamma,
+                       uint32_t e, double *re, double *im) {
+    double cr = 0.0, ci = 0.0;
+    for (uint32_t i = lane; i < ph.n; i += 32) {
+      const Key<W> k = smk(ph, i);
+      const int j = sfind(lam, kxor(k, beta));
+      if (j < 0) continue;
+      const Cx<R> xp = ipow(ph.v[i], e + 2u * kpar(k, gamma));
+      const Cx<R> l = lam.v[j];
+      cr += (double)l.x * (double)xp.x + (double)l.y * (double)xp.y;
+      ci += (double)l.x * (double)xp.y - (double)l.y * (double)xp.x;
+    }
+    *re = wsum(cr);
+    *im = wsum(ci);
+  }
+  __device__ void reset_sides(const SMap<R, W> &m, const uint64_t *gamma, uint32_t sgn, bool &h0, bool &h1) {
+    bool a0 = false, a1 = false;
+    for (uint32_t i = lane; i < m.n; i += 32) {
+      if (kpar(smk(m, i), gamma) ^ sgn) a1 = true;
+      else a0 = true;
+    }
+    h0 = t.any(a0);
+    h1 = t.any(a1);
+  }
+  __device__ void reset_sides(const RMap<R, W> &m, const uint64_t *gamma, uint32_t sgn, bool &h0, bool &h1) {
+    const bool neg = (kpar(m.k, gamma) ^ sgn) != 0u;
+    h1 = t.any(lane < m.n && neg);
+    h0 = t.any(lane < m.n && !neg);
+  }
+  __device__ void map_init_one(SMap<R, W> &m) {
+    if (lane == 0) {
+      Key<W> z;
+#pragma unroll
+      for (int w = 0; w < W; ++w) z.w[w] = 0ull;
+      smk_set(m, 0, z);
+      m.v[0] = Cx<R>{(R)1, (R)0};
+    }
+    m.n = 1;
+    t.sync();
+  }
+  __device__ void map_init_one(RMap<R, W> &m) {
+    for (int w = 0; w < W; ++w) m.k.w[w] = 0ull;
+    m.v = Cx<R>{(R)(lane == 0 ? 1 : 0), (R)0};
+    m.n = 1;
   }
 
   // ------------------------------------------------------------- helpers
@@ -389,29 +701,54 @@ struct GradWarp {
     Cx<R> *tv = reinterpret_cast<Cx<R> *>(tape + L.vals);
     if (lane < m.n) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) tk[((size_t)r * 32 + lane) * W + w] = m.k.w[w];
-      tv[(size_t)r * 32 + lane] = m.v;
+      for (int w = 0; w < W; ++w) tk[((size_t)r * L.slot + lane) * W + w] = m.k.w[w];
+      tv[(size_t)r * L.slot + lane] = m.v;
     }
     if (lane == 0) reinterpret_cast<uint32_t *>(tape + L.nnz)[r] = m.n;
   }
-  // the shared noiseless tape holds what precedes this pattern's first error
+  __device__ void tape_store_phi(uint32_t r, const SMap<R, W> &m) {
+    uint64_t *tk = reinterpret_cast<uint64_t *>(tape + L.keys);
+    Cx<R> *tv = reinterpret_cast<Cx<R> *>(tape + L.vals);
+    for (uint32_t i = lane; i < m.n; i += 32) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) tk[((size_t)r * L.slot + i) * W + w] = m.k[(size_t)i * W + w];
+      tv[(size_t)r * L.slot + i] = m.v[i];
+    }
+    if (lane == 0) reinterpret_cast<uint32_t *>(tape + L.nnz)[r] = m.n;
+  }
+  // the shared noiseless tape (32-entry slots) holds what precedes this pattern's first error
   __device__ __forceinline__ const unsigned char *tape_for_rot(uint32_t rr) const {
     return rr < r0 ? P.ptape : tape;
   }
+  __device__ __forceinline__ const TapeLayout<R, W> &lay_for_rot(uint32_t rr) const { return rr < r0 ? PL : L; }
   __device__ __forceinline__ const unsigned char *tape_for_ev(uint32_t ev) const {
     return ev < ev0 ? P.ptape : tape;
   }
-  __device__ void tape_load_phi(uint32_t rr, RMap<R, W> &m) const {
-    const unsigned char *tp = tape_for_rot(rr);
-    const uint64_t *tk = reinterpret_cast<const uint64_t *>(tp + L.keys);
-    const Cx<R> *tv = reinterpret_cast<const Cx<R> *>(tp + L.vals);
-    const uint32_t r = rr;
-    m.n = reinterpret_cast<const uint32_t *>(tp + L.nnz)[r];
+  __device__ __forceinline__ const TapeLayout<R, W> &lay_for_ev(uint32_t ev) const { return ev < ev0 ? PL : L; }
+  __device__ void tape_load_phi(uint32_t r, RMap<R, W> &m) const {
+    const unsigned char *tp = tape_for_rot(r);
+    const TapeLayout<R, W> &ly = lay_for_rot(r);
+    const uint64_t *tk = reinterpret_cast<const uint64_t *>(tp + ly.keys);
+    const Cx<R> *tv = reinterpret_cast<const Cx<R> *>(tp + ly.vals);
+    m.n = reinterpret_cast<const uint32_t *>(tp + ly.nnz)[r];
     if (lane < m.n) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) m.k.w[w] = tk[((size_t)r * 32 + lane) * W + w];
-      m.v = tv[(size_t)r * 32 + lane];
+      for (int w = 0; w < W; ++w) m.k.w[w] = tk[((size_t)r * ly.slot + lane) * W + w];
+      m.v = tv[(size_t)r * ly.slot + lane];
     }
+  }
+  __device__ void tape_load_phi(uint32_t r, SMap<R, W> &m) {
+    const unsigned char *tp = tape_for_rot(r);
+    const TapeLayout<R, W> &ly = lay_for_rot(r);
+    const uint64_t *tk = reinterpret_cast<const uint64_t *>(tp + ly.keys);
+    const Cx<R> *tv = reinterpret_cast<const Cx<R> *>(tp + ly.vals);
+    m.n = reinterpret_cast<const uint32_t *>(tp + ly.nnz)[r];
+    for (uint32_t i = lane; i < m.n; i += 32) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) m.k[(size_t)i * W + w] = tk[((size_t)r * ly.slot + i) * W + w];
+      m.v[i] = tv[(size_t)r * ly.slot + i];
+    }
+    t.sync();
   }
   __device__ void tape_signs_store(uint32_t ev) {
     if (lane == 0) {
@@ -424,7 +761,8 @@ struct GradWarp {
     }
   }
   __device__ void tape_signs_load(uint32_t ev) {
-    const uint64_t *ts = reinterpret_cast<const uint64_t *>(tape_for_ev(ev) + L.signs) + (size_t)ev * 2 * W;
+    const uint64_t *ts =
+        reinterpret_cast<const uint64_t *>(tape_for_ev(ev) + lay_for_ev(ev).signs) + (size_t)ev * 2 * W;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       sd[w] = ts[w];
@@ -435,7 +773,8 @@ struct GradWarp {
     if (lane == 0) reinterpret_cast<uint64_t *>(tape + L.bits)[ev >> 6] |= 1ull << (ev & 63);
   }
   __device__ bool tape_bit(uint32_t ev) const {
-    return (reinterpret_cast<const uint64_t *>(tape_for_ev(ev) + L.bits)[ev >> 6] >> (ev & 63)) & 1ull;
+    return (reinterpret_cast<const uint64_t *>(tape_for_ev(ev) + lay_for_ev(ev).bits)[ev >> 6] >> (ev & 63)) &
+           1ull;
   }
   __device__ ErrRec<W> *errs() const { return reinterpret_cast<ErrRec<W> *>(tape + L.errs); }
 
@@ -492,7 +831,7 @@ struct GradWarp {
       n_fid = norm2_map(phi);
       if (!seen_f) {
         n_acc = n_fid;
-        pre = phi;
+        copy_map(pre, phi);
         ev_f = P.n_events;
         rot_before_f = r;
       }
@@ -501,10 +840,17 @@ struct GradWarp {
     }
     if (status == G_OK && n_fid > 0.0) {  // N_fid = 0: F = 0 and dF/dtheta = 0 exactly
       // sweep 1: N_fid from the end; sweep 2: N_acc from just before the first fidelity measurement
-      if (!sweep(phi, P.n_events, r, grad, 1.0)) status = G_UNSUPPORTED;
-      if (status == G_OK && !sweep(pre, ev_f, rot_before_f, grad, -F)) status = G_UNSUPPORTED;
+      if (!sweep(phi, P.n_events, r, grad, 1.0)) status = kCapFail;
+      if (status == G_OK && !sweep(pre, ev_f, rot_before_f, grad, -F)) status = kCapFail;
       t.sync();
       for (uint32_t k = lane; k < P.n_params; k += 32) grad[k] /= n_acc;
+    }
+    if (status == G_WIDE) {  // rerun by the shared-memory pass; UNSUPPORTED unless it succeeds
+      if (lane == 0) {
+        const unsigned long long i = atomicAdd(P.wide_n, 1ull);
+        if (i < P.wide_cap) P.wide_list[i] = (uint32_t)off;
+      }
+      status = G_UNSUPPORTED;
     }
     if (lane == 0) {
       P.status[off] = status;
@@ -591,7 +937,7 @@ struct GradWarp {
             b = Cx<R>{(R)__ldg(&C->b_re), (R)__ldg(&C->b_im)};
           }
           if (type == EV_ROT) {
-            if (!rot(phi, e, ev_lowbit(w0), a, b, beta, gamma)) status = G_UNSUPPORTED;
+            if (!rot(phi, e, ev_lowbit(w0), a, b, beta, gamma)) status = kCapFail;
           } else {
             rot_diag(phi, e, a, b, gamma);
           }
@@ -606,7 +952,7 @@ struct GradWarp {
             if (!seen_f) {
               seen_f = true;
               n_acc = norm2_map(phi);
-              pre = phi;
+              copy_map(pre, phi);
               ev_f = ev;
               rot_before_f = r;
             }
@@ -616,8 +962,8 @@ struct GradWarp {
           } else if (!(flags & F_RECORD) && type == EV_MEAS_A) {
             // a reset: its outcome must be decided by the integer test
             const uint32_t sgn = ((ev_e0(w0) + 2u * pe(beta, gamma)) >> 1) & 1u;
-            const bool neg = (kpar(phi.k, gamma) ^ sgn) != 0u;
-            const bool h1 = t.any(lane < phi.n && neg), h0 = t.any(lane < phi.n && !neg);
+            bool h0, h1;
+            reset_sides(phi, gamma, sgn, h0, h1);
             if (h0 && h1) status = G_UNSUPPORTED;
             mm = h1 ? -1 : 1;
           } else {
@@ -704,10 +1050,8 @@ struct GradWarp {
 #pragma unroll
     for (int w = 0; w < W; ++w) sd[w] = ss[w] = 0ull;
     for (uint32_t w = lane; w < P.rw; w += 32) rec[w] = 0ull;
-    for (int w = 0; w < W; ++w) phi.k.w[w] = 0ull;
-    phi.v = Cx<R>{(R)(lane == 0 ? 1 : 0), (R)0};
-    phi.n = 1;
-    pre = phi;
+    map_init_one(phi);
+    copy_map(pre, phi);
     r = 0;
     ev_f = 0xFFFFFFFFu;
     rot_before_f = 0;
@@ -774,13 +1118,21 @@ struct GradWarp {
       ss[w] = h->ss[w];
     }
     for (uint32_t w = lane; w < P.rw; w += 32) rec[w] = r_in[w];
-    if (lane < phi.n) {
+    if constexpr (Wide) {
+      for (uint32_t i = lane; i < phi.n; i += 32) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) phi.k.w[w] = k_in[lane * W + w];
-      phi.v = v_in[lane];
+        for (int w = 0; w < W; ++w) phi.k[(size_t)i * W + w] = k_in[i * W + w];
+        phi.v[i] = v_in[i];
+      }
+    } else {
+      if (lane < phi.n) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) phi.k.w[w] = k_in[lane * W + w];
+        phi.v = v_in[lane];
+      }
     }
-    pre = phi;
     t.sync();
+    copy_map(pre, phi);
   }
   // The noiseless projection run from event 0, into this warp's tape (the shared
   // tape) and `snaps`; returns the last event a pattern may start at.
@@ -812,7 +1164,10 @@ struct GradWarp {
   // Reverse sweep from just before event `ev_end` (its errors included): the
   // adjoint starts as `lam` (the state there) and every parameterised rotation
   // adds weight * s * Im <lambda| Z_q |phi> to grad[k].
-  __device__ bool sweep(RMap<R, W> lam, uint32_t ev_end, uint32_t r_end, double *grad, double weight) {
+  __device__ bool sweep(const Map &src, uint32_t ev_end, uint32_t r_end, double *grad, double weight) {
+    Map lam_local{};
+    Map &lam = Wide ? lam_store : lam_local;  // registers, or the warp's shared-memory map
+    copy_map(lam, src);
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(P.ev);
     int64_t ei = (int64_t)n_err - 1;
     while (ei >= 0 && errs()[ei].ev > ev_end) --ei;  // errors after the sweep's start point
@@ -837,7 +1192,8 @@ struct GradWarp {
           --r;
           const uint32_t e = (ev_e0(w0) + 2u * pe(beta, gamma)) & 3u;
           if (hdr.w != kNoRec) {
-            RMap<R, W> phk;
+            Map phk_local{};
+            Map &phk = Wide ? phk_store : phk_local;
             tape_load_phi(r, phk);
             double zr, zi;
             zexp(lam, phk, beta, gamma, e, &zr, &zi);
@@ -943,6 +1299,24 @@ __global__ void __launch_bounds__(kGradBlock) grad_kernel(const __grid_constant_
   }
 }
 
+// The patterns the register pass listed, with shared-memory maps (one warp per block).
+template <typename R, int W>
+__global__ void __launch_bounds__(32) grad_wide_kernel(const __grid_constant__ GradParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto tile = cg::tiled_partition<32>(cg::this_thread_block());
+  GradWarp<R, W, true> g(tile, P, smem, P.wide_tape + (size_t)blockIdx.x * P.wide_tape_stride);
+  const unsigned long long n = *P.wide_n < P.wide_cap ? *P.wide_n : P.wide_cap;
+  for (;;) {
+    unsigned long long i = 0;
+    if (tile.thread_rank() == 0) i = atomicAdd(P.wide_next, 1ull);
+    i = tile.shfl(i, 0);
+    if (i >= n) break;
+    const uint32_t off = P.wide_list[i];
+    if (off >= P.n_patterns) break;
+    g.run(P.first_pattern + off, off);
+  }
+}
+
 template <typename R, int W>
 __global__ void __launch_bounds__(32) grad_prefix_kernel(const __grid_constant__ GradParams P, unsigned char *tape,
                                                          unsigned char *snaps, uint32_t *stop) {
@@ -968,6 +1342,12 @@ template <typename R, int W>
 cudaError_t launch_grad_t(const GradParams &p, cudaStream_t st) {
   const size_t smem = (kGradBlock / 32) * smem_per_warp(sizeof(R) == 4, W, p.rw);
   grad_kernel<R, W><<<p.blocks, kGradBlock, smem, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !p.wide_list || !p.wide_blocks) return e;
+  const size_t wsmem = wide_smem_per_warp(sizeof(R) == 4, W, p.rw);
+  e = cudaFuncSetAttribute(grad_wide_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+  if (e != cudaSuccess) return e;
+  grad_wide_kernel<R, W><<<p.wide_blocks, 32, wsmem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -981,6 +1361,14 @@ size_t grad_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events) 
 }
 
 uint32_t grad_warps_per_block() { return kGradBlock / 32; }
+
+size_t grad_wide_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events) {
+  if (fp32)
+    return W == 1 ? TapeLayout<float, 1>(n_rot, n_events, kWideCap).total
+                  : TapeLayout<float, 2>(n_rot, n_events, kWideCap).total;
+  return W == 1 ? TapeLayout<double, 1>(n_rot, n_events, kWideCap).total
+                : TapeLayout<double, 2>(n_rot, n_events, kWideCap).total;
+}
 
 size_t grad_prefix_stride(int fp32, uint32_t W, uint32_t rw) {
   if (fp32) return W == 1 ? GradWarp<float, 1>::snap_stride(rw) : GradWarp<float, 2>::snap_stride(rw);

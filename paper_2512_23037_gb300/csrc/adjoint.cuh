@@ -29,11 +29,19 @@ struct GradParams {
   size_t psnap_stride;
   const uint32_t *pstop;       // last event a pattern may start at (device)
   const uint32_t *site_ev;     // per site: the event that applies its error
+  // patterns whose maps outgrow 32 entries: listed by the register pass, rerun
+  // with shared-memory maps (null wide_list: none)
+  uint32_t *wide_list;
+  unsigned long long *wide_n, *wide_next;
+  uint32_t wide_cap, wide_blocks;
+  unsigned char *wide_tape;  // one slot of wide_tape_stride bytes per wide block
+  size_t wide_tape_stride;
 };
 
 size_t grad_smem_per_warp(int fp32, uint32_t W, uint32_t rw);
 size_t grad_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events);
 uint32_t grad_warps_per_block();
+size_t grad_wide_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events);
 cudaError_t launch_grad(const GradParams &p, int fp32, uint32_t W, cudaStream_t st);
 // Per-event snapshot bytes of the noiseless prefix, and its tracing launch (one
 // warp): tape -> p.ptape (writable here), snapshots -> p.psnap, last event -> *stop.

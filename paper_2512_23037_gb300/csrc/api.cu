@@ -198,6 +198,7 @@ void soft_circuit_free(soft_circuit *c) {
   cudaFree(c->d_gnext);
   cudaFree(c->d_gtape);
   cudaFree(c->d_gprefix);
+  cudaFree(c->d_gwide);
   delete c;
 }
 

@@ -66,6 +66,22 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
       return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
     c->gprefix_bytes = prefix_need;
   }
+  // wide rerun (maps above 32 entries): list of up to n_patterns offsets, two counters, and
+  // one shared-memory-map tape per block (SMs x 2 blocks of one warp)
+  const uint32_t wide_blocks = (uint32_t)(sms > 0 ? sms : 1) * 2;
+  const size_t wstride = soft::grad_wide_tape_bytes(fp32, hp.W, hp.n_rot, (uint32_t)hp.ev.size());
+  const size_t list_bytes = ((size_t)std::min<uint64_t>(n_patterns, 0xFFFFFFFFull) * 4 + 255) & ~(size_t)255;
+  const size_t wide_need = 256 + list_bytes + (size_t)wide_blocks * wstride;
+  if (c->gwide_bytes < wide_need) {
+    cudaFree(c->d_gwide);
+    c->d_gwide = nullptr;
+    c->gwide_bytes = 0;
+    if ((e = cudaMalloc(&c->d_gwide, wide_need)) != cudaSuccess)
+      return soft::set_error(e == cudaErrorMemoryAllocation ? SOFT_E_OOM : SOFT_E_CUDA, "device allocation failed");
+    c->gwide_bytes = wide_need;
+  }
+  if ((e = cudaMemsetAsync(c->d_gwide, 0, 256, st)) != cudaSuccess)
+    return soft::set_error(SOFT_E_CUDA, "memset failed");
   soft::Coef *d_coef = c->d_gcoef;
   unsigned long long *d_next = c->d_gnext;
   unsigned char *d_tape = c->d_gtape;
@@ -104,6 +120,13 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   p.site_ev = reinterpret_cast<const uint32_t *>(c->d_thr + hp.thr.size());
   if ((e = soft::launch_grad_prefix(p, fp32, hp.W, ptape, psnap, pstop, st)) != cudaSuccess)
     return soft::set_error(SOFT_E_CUDA, "prefix kernel launch failed");
+  p.wide_n = reinterpret_cast<unsigned long long *>(c->d_gwide);
+  p.wide_next = p.wide_n + 1;
+  p.wide_list = reinterpret_cast<uint32_t *>(c->d_gwide + 256);
+  p.wide_cap = (uint32_t)std::min<uint64_t>(n_patterns, 0xFFFFFFFFull);
+  p.wide_blocks = wide_blocks;
+  p.wide_tape = c->d_gwide + 256 + list_bytes;
+  p.wide_tape_stride = wstride;
   p.ptape = ptape;
   p.psnap = psnap;
   p.psnap_stride = snap_stride;

@@ -37,4 +37,6 @@ struct soft_circuit {
   size_t gtape_bytes = 0;
   unsigned char *d_gprefix = nullptr;  // shared noiseless prefix: tape, snapshots, stop index
   size_t gprefix_bytes = 0;
+  unsigned char *d_gwide = nullptr;    // wide rerun: list, counters, tapes
+  size_t gwide_bytes = 0;
 };

@@ -60,15 +60,18 @@ def test_random_param_circuits(soft, precision, seed):
     assert ok >= 3
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("n", [6, 7])
-def test_oversize_map_reports_unsupported(soft, n):
-    """Random Rz angles on n >= 6 qubits fill 2^n > 32 map entries: every
-    pattern the oracle accepts must come back UNSUPPORTED (or match), never
-    with a wrong value."""
+def test_wide_maps_match_oracle(soft, n, precision):
+    """Random Rz angles on 6 and 7 qubits fill 64 and 128 map entries, beyond
+    the 32-entry register maps: the shared-memory rerun must give every
+    accepted pattern, matching the oracle."""
     circ, noise = C.random_param_circuit(700 + n - 3, n, 50 + 6 * n, n_params=6, p=0.02)
     theta = C.rz_thetas(n - 3, 6, sigma=0.5)
-    ok, status = _compare(soft, circ, noise, theta, 20, n + 2, "fp64")
-    assert np.sum(status == 2) > 0
+    ok, status = _compare(soft, circ, noise, theta, 24, n + 2, precision)
+    n_ok = sum(1 for i in range(24)
+               if oracle.fidelity_grad(circ, circ.n, noise, circ.cap, n + 2, i, theta)[0] == oracle.PROJ_OK)
+    assert ok == n_ok and ok >= 3 and not np.any(status == 2)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
