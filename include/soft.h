@@ -277,8 +277,10 @@ int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_sho
  *   Patterns [first_pattern, first_pattern + n_patterns), key `seed`.
  *   Caller device buffers: d_fid, d_pacc (n_patterns doubles), d_grad
  *   (n_patterns x n_params doubles, row-major), d_status (n_patterns bytes:
- *   0 ok, 1 zero acceptance (skipped, F = 0), 2 unsupported (a map above 32
- *   entries, an undecided reset, a multi-record detector), 3 error).
+ *   0 ok, 1 zero acceptance (skipped, F = 0), 2 unsupported (a map above 256
+ *   entries, an undecided reset, a multi-record detector), 3 error). Maps of
+ *   up to 32 entries stay in registers; patterns that need more are rerun by a
+ *   second launch inside the call with maps in shared memory.
  *   d_sums (may be NULL): 3 doubles, zeroed by the call, receiving the sums
  *   over ok patterns of N_acc and of N_fid = N_acc F, and their count; the
  *   ratio estimator of the post-selected fidelity is d_sums[1] / d_sums[0].
