@@ -169,9 +169,10 @@ typedef struct {
  * starts at the event that applies its first error (or at the end of the
  * circuit's decided noiseless prefix, if earlier), from the state the noiseless
  * run reached there: soft_compile_circuit records that run once per precision
- * (the state at the top of each event, while every outcome is decided, no
- * fidelity measurement is reached and the map has at most 64 entries). Both
- * give the same results; the flag is for comparison. */
+ * (the state at the top of each event, while every outcome is decided and the
+ * map has at most 64 entries; with SOFT_RUN_FIDELITY, only up to the first
+ * observed measurement). Both give the same results; the flag is for
+ * comparison. */
 enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,

@@ -942,7 +942,7 @@ static int run_shot(const circ *c, gs_state *st, uint64_t seed, uint64_t shot, u
         if (op == OR_MPP && (o->flags & OR_MPP_MORE)) break; /* the chain's last op measures */
         pauli P = (op == OR_MPP) ? mpp_product(c->ops, mpp_chain_start(c->ops, i), i) : pauli_single(3, (int)o->q0);
         const int force = fid && op != OR_R && c->observed[nrec];
-        if (op != OR_R && c->observed[nrec]) live = 1;
+        if (fid && op != OR_R && c->observed[nrec]) live = 1;
         meas_info mi;
         int r = measure(st, c, &P, seed, shot, ordinal, force, &mi, cnt);
         if (r) return r;

@@ -73,8 +73,9 @@ typedef struct {
   uint64_t errors;         /* sampled errors applied */
   /* The same four counts restricted to the part of each shot that differs from
    * the circuit's noiseless run: from the earliest of the first applied error,
-   * the first measurement an OBSERVABLE reads, the first outcome with
-   * 0 < p_+ < 1 and the first map above 64 entries, to the end of the shot. */
+   * the first outcome with 0 < p_+ < 1, the first map above 64 entries and, in
+   * fidelity mode, the first measurement an OBSERVABLE reads, to the end of the
+   * shot. */
   uint64_t post_t_out, post_t_diag, post_meas, post_noise;
 } or_counts;
 

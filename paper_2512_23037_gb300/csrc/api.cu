@@ -67,7 +67,7 @@ static cudaError_t build_prefixes(soft_circuit *c) {
   const auto &hp = c->hp;
   const size_t n_snap = hp.ev.size() + 1;
   uint32_t *d_stop = nullptr;
-  cudaError_t e = cudaMalloc(&d_stop, 2 * sizeof(uint32_t));
+  cudaError_t e = cudaMalloc(&d_stop, 4 * sizeof(uint32_t));
   if (e != cudaSuccess) return e;
   for (int fp32 = 0; fp32 < 2 && e == cudaSuccess; ++fp32) {
     const size_t stride = soft::prefix_stride(fp32, hp.W, hp.rw);
@@ -90,13 +90,16 @@ static cudaError_t build_prefixes(soft_circuit *c) {
     p.cap = std::min(hp.cap, soft::kDefaultFirstCap);
     p.rw_max = hp.rw;
     p.tau = fp32 ? kTauFp32 : kTauFp64;
-    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + fp32, nullptr);
+    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + 2 * fp32, nullptr);
   }
-  uint32_t stop[2] = {0, 0};
+  uint32_t stop[4] = {0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(stop, d_stop, sizeof stop, cudaMemcpyDeviceToHost);
   cudaFree(d_stop);
   if (e != cudaSuccess) return e;
-  for (int k = 0; k < 2; ++k) c->traj_stop[k] = std::min<uint32_t>(stop[k], (uint32_t)hp.ev.size());
+  for (int k = 0; k < 2; ++k) {
+    c->traj_stop[k] = std::min<uint32_t>(stop[2 * k], (uint32_t)hp.ev.size());
+    c->traj_fid_stop[k] = std::min<uint32_t>(stop[2 * k + 1], (uint32_t)hp.ev.size());
+  }
   return cudaSuccess;
 }
 
@@ -234,6 +237,7 @@ soft::CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix) {
   if (prefix && c->d_traj[fp32]) {
     d.traj = c->d_traj[fp32];
     d.traj_stop = c->traj_stop[fp32];
+    d.traj_fid_stop = c->traj_fid_stop[fp32];
     d.traj_stride = c->traj_stride[fp32];
   }
   d.ev = c->d_ev;

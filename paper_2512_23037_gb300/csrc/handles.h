@@ -28,6 +28,7 @@ struct soft_circuit {
   // built at compile time; traj_stop = last valid event
   unsigned char *d_traj[2] = {nullptr, nullptr};
   uint32_t traj_stop[2] = {0, 0};
+  uint32_t traj_fid_stop[2] = {0, 0};
   uint32_t traj_stride[2] = {0, 0};
   // fidelity-gradient workspace, kept between calls (they are synchronous):
   // per-parameter coefficient table, work counter, per-warp tapes

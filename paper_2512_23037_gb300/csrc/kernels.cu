@@ -804,7 +804,8 @@ struct Shot {
   // its first error (the first with site_begin > nxt), capped at the end of the
   // noiseless run's valid prefix. Loads the snapshot there and returns it.
   __device__ uint32_t load_prefix() {
-    const uint32_t stop = C->traj_stop;
+    // fidelity mode projects observed measurements: the shared run ends before the first
+    const uint32_t stop = P.fid_mode && C->traj_fid_stop < C->traj_stop ? C->traj_fid_stop : C->traj_stop;
     uint32_t lo = stop;
     if (nxt < C->n_sites) {
       const uint32_t e = __ldg(&C->site_ev[nxt]);
@@ -902,27 +903,30 @@ struct Shot {
     if (status == ST_RUN) status = ST_KEPT;
   }
 
-  // The circuit's noiseless run, recording the state at the top of every event
-  // until an outcome is not decided (it would depend on the shot's uniform), a
-  // fidelity measurement, a map above kSnapMax entries, or the end. Event
-  // `stop` is the last valid snapshot: shots resume there at the latest.
-  __device__ uint32_t trace_prefix(unsigned char *out, size_t stride) {
+  // The circuit's noiseless run (sampling semantics), recording the state at the
+  // top of every event until an outcome is not decided (it would depend on the
+  // shot's uniform), a map above kSnapMax entries, or the end. Event `stop` is the
+  // last valid snapshot: shots resume there at the latest. *fid_stop receives the
+  // first fidelity measurement's event (fidelity-mode shots resume there at the
+  // latest), or the number of events.
+  __device__ uint32_t trace_prefix(unsigned char *out, size_t stride, uint32_t *fid_stop) {
     init_shot(0);
     cur = C->n_sites;
     nxt = 0xFFFFFFFFu;
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
     const uint32_t n_events = C->n_events;
-    uint32_t ev = 0;
+    uint32_t ev = 0, fs = n_events;
     for (; ev <= n_events; ++ev) {
       save_snapshot(out + (size_t)ev * stride);
       if (ev == n_events) break;
       const uint32_t w0 = __ldg(&evs[ev].w0), type = ev_type(w0);
-      if ((type == EV_MEAS_A || type == EV_MEAS_B) && (ev_flags(w0) & F_FIDELITY)) break;
+      if ((type == EV_MEAS_A || type == EV_MEAS_B) && (ev_flags(w0) & F_FIDELITY) && fs == n_events) fs = ev;
       undecided = false;
       step(ev);
       if (status != ST_RUN || undecided || nnz > kSnapMax) break;
     }
     t.sync();
+    *fid_stop = fs;
     return ev;
   }
 
@@ -1118,8 +1122,12 @@ __global__ void __launch_bounds__(32) prefix_kernel(const __grid_constant__ Shot
   auto tile = cg::tiled_partition<32>(cg::this_thread_block());
   Shot<R, W, 32> s(tile, P, smem);
   s.C = &P.circ[0];
-  const uint32_t ev = s.trace_prefix(out, stride);
-  if (tile.thread_rank() == 0) *stop = ev;
+  uint32_t fs = 0;
+  const uint32_t ev = s.trace_prefix(out, stride, &fs);
+  if (tile.thread_rank() == 0) {
+    stop[0] = ev;
+    stop[1] = fs;
+  }
 }
 
 template <typename R, int W>

@@ -31,6 +31,7 @@ struct CircDev {
   // a shot starts at the event that applies its first error, or at traj_stop
   const unsigned char *traj;
   uint32_t traj_stop, traj_stride;
+  uint32_t traj_fid_stop, pad_traj;  // first fidelity measurement's event (fidelity mode stops there)
   const uint32_t *site_ev;  // per site: the event that applies its error
 };
 
@@ -81,7 +82,8 @@ enum : uint32_t {
 // Bytes per event of a noiseless-run snapshot table (see CircDev::traj).
 size_t prefix_stride(int fp32, uint32_t W, uint32_t rw);
 // Record circuit p.circ[0]'s noiseless run into `out` ((n_events + 1) snapshots);
-// *stop receives the last valid event. One warp; p.cap is the map capacity used.
+// stop[0] receives the last valid event, stop[1] the first fidelity measurement's
+// event (or n_events). One warp; p.cap is the map capacity used.
 cudaError_t launch_prefix(const ShotParams &p, int fp32, uint32_t W, unsigned char *out, uint32_t *stop,
                           cudaStream_t st);
 

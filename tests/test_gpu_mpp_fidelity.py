@@ -108,6 +108,18 @@ def test_fidelity_w42_prefix_and_graph(soft, precision):
     assert abs(t2["sum_fidelity"] - tal["sum_fidelity"]) <= 1e-9 * max(1, tal["kept"])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fidelity_prefix_start_is_exact(soft, precision):
+    """Fidelity mode stops the shared noiseless run at the first observed
+    measurement: with and without the prefix start the sums are identical."""
+    S = soft
+    circ, noise = C.workload("w42")
+    h = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    a = S.soft_tally(S.soft_run_shots(h, 20000, 0, 4, precision=precision, fidelity=True))
+    b = S.soft_tally(S.soft_run_shots(h, 20000, 0, 4, precision=precision, fidelity=True, prefix=False))
+    assert a == b
+
+
 def test_fidelity_estimator_vs_sampling_on_gpu(soft):
     """Same shots sampled and in fidelity mode: identical kept counts; the
     sampled logical-error rate within 5 sigma of 1 - mean F."""

@@ -357,14 +357,17 @@ def test_post_prefix_counts_bounded_by_full():
         assert 0 < k[a] <= k[b]
 
 
-def test_post_prefix_noiseless_counts_only_the_observed_chain():
+def test_post_prefix_noiseless_counts_only_the_observed_chain_in_fidelity_mode():
     """Noiselessly every outcome of the windowed circuit is decided and the map
-    stays <= 16: only the final observed measurements are past the prefix."""
+    stays <= 16: a sampled shot never leaves the prefix; in fidelity mode the
+    final observed measurements are past it."""
     circ, _ = C.windowed(3, n_data=10, n_anc=2, blocks=4, w=3, n_cliff=16, checks=2, p=0.0)
     k = _counts(circ, C.Noise(), shots=20)
-    assert k["post_t_out"] == 0 and k["post_t_diag"] == 0 and k["post_noise"] == 0
+    assert k["post_t_out"] == k["post_t_diag"] == k["post_meas"] == k["post_noise"] == 0
+    kf = oracle.run(circ, circ.n, C.Noise(), circ.cap, 0, 0, 20, threads=4, records=False, fidelity=True)["counts"]
+    assert kf["post_t_out"] == 0 and kf["post_t_diag"] == 0 and kf["post_noise"] == 0
     n_final = 10  # one measurement per data qubit, one entry each
-    assert k["post_meas"] == 20 * n_final
+    assert kf["post_meas"] == 20 * n_final
 
 
 def test_post_prefix_undecided_first_outcome_counts_everything():
