@@ -37,7 +37,9 @@ WORKLOADS = {
                 "6..24 blocks, p log-uniform in [1e-4, 3e-3], shots per circuit geometric with mean 1e6 "
                 "(77.1 M shots per step), generator seed 2"),
 }
-# Algorithmic work per counted unit (lane ops: FP + integer), see the design doc
+# Algorithmic work per counted unit (lane ops, FP + integer): a T/Rz output entry (two complex
+# multiply-adds and the key XOR/parity), a diagonal T/Rz entry, a measurement entry visit
+# (norm and filter or pairing), a noise entry touch (key XOR and phase)
 OPS_T_OUT, OPS_T_DIAG, OPS_MEAS, OPS_NOISE = 18, 9, 8, 3
 
 
@@ -81,9 +83,8 @@ class Clocks:
 
     def __init__(self, index):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(ROOT, f".clocks_{os.getpid()}.csv")  # removed after reading
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
                                        "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
@@ -102,7 +103,13 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        for line in lines:
             parts = [t.strip() for t in line.split(",")]
             if len(parts) < 9:
                 continue
