@@ -1281,8 +1281,11 @@ struct GradWarp {
 
 constexpr int kGradBlock = 128;
 
+#ifndef SOFT_GRAD_MIN_BLOCKS
+#define SOFT_GRAD_MIN_BLOCKS 4
+#endif
 template <typename R, int W>
-__global__ void __launch_bounds__(kGradBlock) grad_kernel(const __grid_constant__ GradParams P) {
+__global__ void __launch_bounds__(kGradBlock, SOFT_GRAD_MIN_BLOCKS) grad_kernel(const __grid_constant__ GradParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   auto block = cg::this_thread_block();
   auto tile = cg::tiled_partition<32>(block);
@@ -1361,6 +1364,7 @@ size_t grad_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events) 
 }
 
 uint32_t grad_warps_per_block() { return kGradBlock / 32; }
+uint32_t grad_blocks_per_sm() { return SOFT_GRAD_MIN_BLOCKS; }
 
 size_t grad_wide_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events) {
   if (fp32)

@@ -41,6 +41,7 @@ struct GradParams {
 size_t grad_smem_per_warp(int fp32, uint32_t W, uint32_t rw);
 size_t grad_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events);
 uint32_t grad_warps_per_block();
+uint32_t grad_blocks_per_sm();  // resident blocks per SM the register budget allows
 size_t grad_wide_tape_bytes(int fp32, uint32_t W, uint32_t n_rot, uint32_t n_events);
 cudaError_t launch_grad(const GradParams &p, int fp32, uint32_t W, cudaStream_t st);
 // Per-event snapshot bytes of the noiseless prefix, and its tracing launch (one

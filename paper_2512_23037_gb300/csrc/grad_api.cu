@@ -36,7 +36,7 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const uint32_t wpb = soft::grad_warps_per_block();
-  uint64_t blocks = (uint64_t)(sms > 0 ? sms : 1) * 4;
+  uint64_t blocks = (uint64_t)(sms > 0 ? sms : 1) * soft::grad_blocks_per_sm();
   blocks = std::min<uint64_t>(blocks, (n_patterns + wpb - 1) / wpb);
   const size_t stride = soft::grad_tape_bytes(fp32, hp.W, hp.n_rot, (uint32_t)hp.ev.size());
   // workspace kept in the handle between calls; the tape grows to the largest launch seen
