@@ -44,6 +44,17 @@ __host__ __device__ inline size_t group_bytes(uint32_t cap, uint32_t rw) {
   return (b + 15) & ~(size_t)15;
 }
 
+// 1/sqrt(x) in the coefficient type: FP64 maps compute it in FP64, FP32 maps
+// with the FP32 reciprocal square root (the scale is rounded to FP32 anyway).
+template <typename R>
+__device__ __forceinline__ R inv_sqrt_as(double x) {
+  return (R)(1.0 / sqrt(x));
+}
+template <>
+__device__ __forceinline__ float inv_sqrt_as<float>(double x) {
+  return rsqrtf((float)x);
+}
+
 template <typename R, int W, int G>
 struct Shot {
   using Tile = cg::thread_block_tile<G>;
@@ -430,7 +441,7 @@ struct Shot {
     const double sp = tile_sum(neg ? 0.0 : a2), sm = tile_sum(neg ? a2 : 0.0);
     const double pp = snap01(sp / (sp + sm));
     const int m = pick(ord, pp);
-    const R sc = (R)(1.0 / sqrt(m == 1 ? sp : sm));
+    const R sc = inv_sqrt_as<R>(m == 1 ? sp : sm);
     bool keep = valid && (neg == (m == -1));
     if (keep) rv = cscale(rv, sc);
     reg_compact(keep && norm2(rv) >= (R)P.tau);
@@ -458,7 +469,7 @@ struct Shot {
     const double sm = tile_sum(owner ? 0.5 * norm2d(csub(v0, x1)) : 0.0);
     const double pp = snap01(sp / (sp + sm));
     const int m = pick(ord, pp);
-    const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
+    const R sc = inv_sqrt_as<R>(2.0 * (m == 1 ? sp : sm));
     if (owner) {
       rv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
       rk = a0;
@@ -632,7 +643,7 @@ struct Shot {
     sm = tile_sum(sm);
     const double pp = snap01(sp / (sp + sm));
     const int m = pick(ord, pp);
-    const R sc = (R)(1.0 / sqrt(m == 1 ? sp : sm));
+    const R sc = inv_sqrt_as<R>(m == 1 ? sp : sm);
     const uint32_t want = (m == 1) ? 0u : 1u;
     const R tau = (R)P.tau;
     t.sync();
@@ -721,7 +732,7 @@ struct Shot {
     }
     const double pp = snap01(sp / (sp + sm));
     const int m = pick(ord, pp);
-    const R sc = (R)(1.0 / sqrt(2.0 * (m == 1 ? sp : sm)));
+    const R sc = inv_sqrt_as<R>(2.0 * (m == 1 ? sp : sm));
     // stage the paired values in slots [cap, cap + nnz)
     for (uint32_t i = lane; i < nnz; i += G) {
       Key<W> k = key(i);
