@@ -342,3 +342,73 @@ def test_prefix_start_is_bit_identical(soft, precision, case):
     assert a[2] == b[2]
     for (s1, k1, v1), (s2, k2, v2) in zip(a[3], b[3]):
         assert np.array_equal(s1, s2) and np.array_equal(k1, k2) and np.array_equal(v1, v2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_maximum_qubits_128(soft, precision):
+    """n = 128, the largest register the two-word keys hold."""
+    circ = C.random_circuit(6128, 128, 700, t_frac=0.04, meas_frac=0.2, detectors=True, mpp_frac=0.04)
+    circ.cap = 256
+    noise = C.Noise(0.004, 0.004, 0.004, 0.004)
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 400, 3, precision, capture=24)
+    assert compare_records(circ, noise, 3, 0, rec, st, ref, precision) <= 2
+    compare_states(soft, c, r, circ, noise, 3, 0, 24, precision)
+
+
+def _many_records(n_rounds):
+    rng = np.random.default_rng(77)
+    c = C.Circuit(12, cap=256)
+    for _ in range(n_rounds):
+        for q in range(12):
+            c.gate([C.H, C.S, C.T, C.T_DAG][int(rng.integers(4))], q)
+        a, b = (int(v) for v in rng.choice(12, size=2, replace=False))
+        c.gate(C.CX, a, b)
+        for q in range(12):
+            c.measure(q, reset=bool(rng.integers(2)))
+    return c
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_maximum_records_1020(soft, precision):
+    """85 rounds of 12 measurements: 1020 records, 16 record words per shot."""
+    circ = _many_records(85)
+    assert circ.n_records == 1020
+    noise = C.Noise(0.01, 0.01, 0.01, 0.01)
+    c, r, rec, st, tal, ref = run_both(soft, circ, noise, 300, 4, precision)
+    assert rec.shape[1] == 16
+    assert compare_records(circ, noise, 4, 0, rec, st, ref, precision) <= 2
+
+
+def test_more_than_1024_records_rejected(soft):
+    circ = _many_records(86)  # 1032 records
+    with pytest.raises(soft.SoftError):
+        soft.soft_compile_circuit(circ.array(), circ.n, C.Noise(), circ.cap)
+
+
+@pytest.mark.parametrize("case", ["empty", "clifford_only", "no_measurements", "one_qubit"])
+def test_degenerate_circuits(soft, case):
+    """An empty op list, a Clifford-only circuit (the map stays one entry), a
+    circuit without measurements, a one-qubit circuit: tallies and records
+    equal the oracle's."""
+    n = 1 if case == "one_qubit" else 5
+    c = C.Circuit(n, cap=16)
+    rng = np.random.default_rng(5)
+    if case != "empty":
+        for _ in range(40):
+            q = int(rng.integers(n))
+            if case == "clifford_only" or n == 1:
+                c.gate([C.H, C.S, C.X, C.Z, C.S_DAG][int(rng.integers(5))], q)
+            elif rng.random() < 0.3:
+                c.gate(C.CX, q, (q + 1) % n)
+            else:
+                c.gate([C.H, C.T, C.S][int(rng.integers(3))], q)
+        if case == "one_qubit":
+            c.gate(C.T, 0)
+            c.measure(0)
+        elif case == "clifford_only":
+            for q in range(n):
+                c.measure(q)
+    noise = C.Noise(0.05, 0.05, 0.05, 0.05)
+    cc, r, rec, st, tal, ref = run_both(soft, c, noise, 500, 2, "fp64")
+    assert [tal["shots"], tal["discarded"], tal["overflow"], tal["kept"], tal["logical_errors"]] == ref["tally"]
+    assert compare_records(c, noise, 2, 0, rec, st, ref, "fp64") == 0
