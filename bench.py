@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer between steps (0 = none)")
     ap.add_argument("--workload", default="w42", choices=["w42", "w97", "batch64"])
     ap.add_argument("--graph", action="store_true", help="replay chunks from a captured CUDA graph")
+    ap.add_argument("--warp-per-shot", action="store_true",
+                    help="a warp per shot even where the library would run a lane per shot")
     ap.add_argument("--chunk", type=int, default=0, help="shots per chunk (0 = library default)")
     ap.add_argument("--autotune", action="store_true", help="time launch-shape candidates first")
     ap.add_argument("--grad-patterns", type=int, default=100000,
@@ -349,7 +351,7 @@ def main():
     def launch(handles, first, precision, fidelity=False):
         if len(handles) == 1:
             return S.soft_run_shots(handles[0], items[0][2], first, 0, precision=precision, stream=stream,
-                                    graph=args.graph, fidelity=fidelity, **tune)
+                                    graph=args.graph, fidelity=fidelity, lanes=not args.warp_per_shot, **tune)
         return S.soft_run_batch(handles, [s for _, _, s in items], [first] * len(handles), 0, precision=precision,
                                 stream=stream, graph=args.graph, fidelity=fidelity, **tune)
 

@@ -173,7 +173,15 @@ typedef struct {
  * map has at most 64 entries; with SOFT_RUN_FIDELITY, only up to the first
  * observed measurement). Both give the same results; the flag is for
  * comparison. */
-enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4 };
+/* Lane-per-shot scheduling (the default where it applies): one shot per lane,
+ * 32 shots per warp. Shots are bucketed by the event they start at, and each
+ * warp executes one event at a time for all its lanes, each lane updating its
+ * own shot's map (up to 16 entries; larger maps finish in the rerun pass). It
+ * applies to single-circuit runs without state capture or a forced group size,
+ * when every map of the circuit's noiseless run fits (at most 16 entries);
+ * otherwise a warp (group) runs each shot. SOFT_RUN_NO_LANES always uses the
+ * warp per shot. Same results either way, another order. */
+enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_RUN_NO_LANES = 8 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
  * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsoft.so")
-SOURCES = ["compile.cpp", "kernels.cu", "api.cu", "noalloc.cu", "adjoint.cu", "grad_api.cu"]
+SOURCES = ["compile.cpp", "kernels.cu", "lanes.cu", "api.cu", "noalloc.cu", "adjoint.cu", "grad_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 for _v in ("SOFT_MIN_BLOCKS_F32", "SOFT_MIN_BLOCKS_F64", "SOFT_GRAD_MIN_BLOCKS"):  # register-budget experiments

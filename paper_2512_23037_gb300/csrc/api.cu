@@ -42,6 +42,7 @@ struct soft_run {
   std::vector<uint64_t> n_shots;
   unsigned long long *d_tally = nullptr;   // 5 counters per circuit
   double *d_fsum = nullptr;                // fidelity mode: sum of F per circuit
+  uint32_t *d_al = nullptr;                // lane-per-shot bucketing buffers
   bool fid_mode = false;
   unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4]
   uint32_t *d_rerun = nullptr;
@@ -67,7 +68,7 @@ static cudaError_t build_prefixes(soft_circuit *c) {
   const auto &hp = c->hp;
   const size_t n_snap = hp.ev.size() + 1;
   uint32_t *d_stop = nullptr;
-  cudaError_t e = cudaMalloc(&d_stop, 4 * sizeof(uint32_t));
+  cudaError_t e = cudaMalloc(&d_stop, 6 * sizeof(uint32_t));
   if (e != cudaSuccess) return e;
   for (int fp32 = 0; fp32 < 2 && e == cudaSuccess; ++fp32) {
     const size_t stride = soft::prefix_stride(fp32, hp.W, hp.rw);
@@ -90,15 +91,16 @@ static cudaError_t build_prefixes(soft_circuit *c) {
     p.cap = std::min(hp.cap, soft::kDefaultFirstCap);
     p.rw_max = hp.rw;
     p.tau = fp32 ? kTauFp32 : kTauFp64;
-    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + 2 * fp32, nullptr);
+    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + 3 * fp32, nullptr);
   }
-  uint32_t stop[4] = {0, 0, 0, 0};
+  uint32_t stop[6] = {0, 0, 0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(stop, d_stop, sizeof stop, cudaMemcpyDeviceToHost);
   cudaFree(d_stop);
   if (e != cudaSuccess) return e;
   for (int k = 0; k < 2; ++k) {
-    c->traj_stop[k] = std::min<uint32_t>(stop[2 * k], (uint32_t)hp.ev.size());
-    c->traj_fid_stop[k] = std::min<uint32_t>(stop[2 * k + 1], (uint32_t)hp.ev.size());
+    c->traj_stop[k] = std::min<uint32_t>(stop[3 * k], (uint32_t)hp.ev.size());
+    c->traj_fid_stop[k] = std::min<uint32_t>(stop[3 * k + 1], (uint32_t)hp.ev.size());
+    c->traj_max_n[k] = stop[3 * k + 2];
   }
   return cudaSuccess;
 }
@@ -211,6 +213,7 @@ void soft_run_free(soft_run *r) {
   else cudaDeviceSynchronize();
   cudaFree(r->d_tally);
   cudaFree(r->d_fsum);
+  cudaFree(r->d_al);
   cudaFree(r->d_work);
   cudaFree(r->d_rerun);
   cudaFree(r->d_slab);
@@ -272,7 +275,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     return fail(SOFT_E_ARG, "records and state capture are per single-circuit run");
   const bool use_graph = (o.flags & SOFT_RUN_GRAPH) != 0;
   const bool fid_mode = (o.flags & SOFT_RUN_FIDELITY) != 0;
-  if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY | SOFT_RUN_NO_PREFIX))
+  if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY | SOFT_RUN_NO_PREFIX | SOFT_RUN_NO_LANES))
     return fail(SOFT_E_ARG, "unknown run flags");
   if (use_graph && !o.stream) return fail(SOFT_E_ARG, "graph replay needs a non-default stream");
   const int fp32 = o.precision == SOFT_FP32;
@@ -290,7 +293,14 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     total += n_shots[i];
   }
   const uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap_max) : std::min(kDefaultFirstCap, cap_max);
-  const bool two_pass = cap1 < cap_max;
+  // lane-per-shot scheduling: one circuit, the noiseless prefix, no state capture, group size
+  // not forced, and a noiseless run whose maps fit a lane's map
+  const int pk = o.precision == SOFT_FP32 ? 1 : 0;
+  const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && n_circ == 1 && !(o.flags & SOFT_RUN_NO_PREFIX) &&
+                     o.capture_k == 0 && o.group_size == 0 && circs[0]->d_traj[pk] &&
+                     circs[0]->traj_max_n[pk] <= soft::lane_map_cap();
+  // a rerun pass finishes the shots whose maps outgrow the first pass (a lane's map, or cap1)
+  const bool two_pass = (lanes ? soft::lane_map_cap() : cap1) < cap_max;
   const uint32_t g1 = o.group_size ? o.group_size : 32u;
   const uint32_t g2 = 32;
   const size_t smem_limit = 227 * 1024 - 5 * sizeof(unsigned long long) * soft::kMaxCirc;
@@ -326,6 +336,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     }                                                                                           \
   } while (0)
   SOFT_ALLOC(r->d_tally, 5 * n_circ * sizeof(unsigned long long));
+  const uint32_t n_ev0 = (uint32_t)circs[0]->hp.ev.size();
+  if (lanes) SOFT_ALLOC(r->d_al, (2 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
   r->fid_mode = fid_mode;
   if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
   SOFT_ALLOC(r->d_work, 8 * sizeof(unsigned long long));
@@ -416,9 +428,17 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     q.gslab = r->d_slab;
     q.gslab_blocks = slab_blocks;
   }
+  if (lanes) {  // start events, order, bucket starts, then the two counter arrays (zeroed per chunk)
+    p.al_ev = r->d_al;
+    p.al_order = r->d_al + chunk;
+    p.al_start = r->d_al + 2 * chunk;
+    p.al_count = r->d_al + 2 * chunk + (n_ev0 + 2);
+    p.al_next = p.al_count + (n_ev0 + 1);
+  }
   soft::LaunchCfg c1{}, c2{};
   p.n_items = std::min(chunk, total);
-  if ((e = soft::prepare_shots(p, fp32, W, g1, (int)o.blocks_per_sm, &c1)) != cudaSuccess ||
+  if ((e = lanes ? soft::prepare_lanes(p, fp32, W, (int)o.blocks_per_sm, &c1)
+                 : soft::prepare_shots(p, fp32, W, g1, (int)o.blocks_per_sm, &c1)) != cudaSuccess ||
       (two_pass && (e = soft::prepare_shots(q, fp32, W, g2, (int)o.blocks_per_sm, &c2)) != cudaSuccess)) {
     soft_run_free(r);
     return cuda_fail(e, "shot kernel configuration");
@@ -432,6 +452,12 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     a.n_items = b.n_items = cnt;
     a.item_base = b.item_base = base;
     if (dev_base) a.item_base_dev = b.item_base_dev = r->d_work + 3;
+    if (lanes) {
+      if ((err = cudaMemsetAsync(a.al_count, 0, 2 * (size_t)(n_ev0 + 1) * sizeof(uint32_t), st)) != cudaSuccess ||
+          (err = soft::launch_lane_prepass(a, st)) != cudaSuccess)
+        return err;
+      r->launches += 3;
+    }
     if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
     r->launches++;
     if (two_pass) {

@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include "device_common.cuh"
+#include "shot_common.cuh"
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -183,37 +184,7 @@ struct Shot {
 
   // ---- noise: next accepted error site (geometric gaps, then thinning)
   __device__ void draw_next() {
-    const uint32_t n_sites = C->n_sites;
-    const uint64_t *thr = C->thr;
-    for (uint32_t guard = 0; guard <= n_sites; ++guard) {
-      if (cur >= n_sites) {
-        nxt = 0xFFFFFFFFu;
-        return;
-      }
-      uint4 w = philox(P.seed, shot, 0u, kblk++);
-      uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
-      const uint32_t rem = n_sites - cur;
-      uint32_t lo = 0, hi = rem;  // the gap: the smallest g < rem with U < thr[g] (rem if none)
-      while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (U < __ldg(&thr[mid])) hi = mid;
-        else lo = mid + 1u;
-      }
-      if (lo == rem) {
-        cur = n_sites;
-        nxt = 0xFFFFFFFFu;
-        return;
-      }
-      uint32_t s = cur + lo;
-      cur = s + 1u;
-      const Site *st = C->sites + s;
-      if (!__ldg(&st->always) && !(w.w < __ldg(&st->thin))) continue;
-      nxt = s;
-      w2 = w.z;
-      return;
-    }
-    nxt = 0xFFFFFFFFu;
-    status = ST_ERR;
+    if (!next_site(C, P.seed, shot, cur, kblk, nxt, w2)) status = ST_ERR;
   }
 
   // v'_{a^beta} = i^{e + 2 gamma.a} v_a
@@ -767,17 +738,7 @@ struct Shot {
 
   // Shot state at the top of event `ev` of the circuit's noiseless run, when that
   // run has one (traj_stop > ev): written by trace_prefix, read by load_prefix.
-  struct SnapHdr {
-    uint32_t nnz, chain, logical, lastm;
-    double fid;
-    uint64_t sd[2], ss[2];
-    uint64_t pad[2];
-  };
-  static constexpr uint32_t kSnapMax = 64;  // entries a snapshot holds (registers or shared memory)
-  __host__ __device__ static constexpr size_t snap_stride(uint32_t rw) {
-    return (sizeof(SnapHdr) + (size_t)rw * 8 + kSnapMax * (size_t)W * 8 + kSnapMax * sizeof(Cx<R>) + 15) &
-           ~(size_t)15;
-  }
+  __host__ __device__ static constexpr size_t snap_stride(uint32_t rw) { return dev::snap_stride<R, W>(rw); }
   __device__ void save_snapshot(unsigned char *out) {
     SnapHdr *h = reinterpret_cast<SnapHdr *>(out);
     uint64_t *rw_out = reinterpret_cast<uint64_t *>(out + sizeof(SnapHdr));
@@ -815,13 +776,7 @@ struct Shot {
   // its first error (the first with site_begin > nxt), capped at the end of the
   // noiseless run's valid prefix. Loads the snapshot there and returns it.
   __device__ uint32_t load_prefix() {
-    // fidelity mode projects observed measurements: the shared run ends before the first
-    const uint32_t stop = P.fid_mode && C->traj_fid_stop < C->traj_stop ? C->traj_fid_stop : C->traj_stop;
-    uint32_t lo = stop;
-    if (nxt < C->n_sites) {
-      const uint32_t e = __ldg(&C->site_ev[nxt]);
-      lo = e < stop ? e : stop;
-    }
+    const uint32_t lo = first_event(C, P.fid_mode, nxt);
     const unsigned char *in = C->traj + (size_t)lo * C->traj_stride;
     const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);
     const uint64_t *r_in = reinterpret_cast<const uint64_t *>(in + sizeof(SnapHdr));
@@ -920,15 +875,16 @@ struct Shot {
   // last valid snapshot: shots resume there at the latest. *fid_stop receives the
   // first fidelity measurement's event (fidelity-mode shots resume there at the
   // latest), or the number of events.
-  __device__ uint32_t trace_prefix(unsigned char *out, size_t stride, uint32_t *fid_stop) {
+  __device__ uint32_t trace_prefix(unsigned char *out, size_t stride, uint32_t *fid_stop, uint32_t *max_n) {
     init_shot(0);
     cur = C->n_sites;
     nxt = 0xFFFFFFFFu;
     const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
     const uint32_t n_events = C->n_events;
-    uint32_t ev = 0, fs = n_events;
+    uint32_t ev = 0, fs = n_events, mx = 0;
     for (; ev <= n_events; ++ev) {
       save_snapshot(out + (size_t)ev * stride);
+      mx = nnz > mx ? nnz : mx;
       if (ev == n_events) break;
       const uint32_t w0 = __ldg(&evs[ev].w0), type = ev_type(w0);
       if ((type == EV_MEAS_A || type == EV_MEAS_B) && (ev_flags(w0) & F_FIDELITY) && fs == n_events) fs = ev;
@@ -938,6 +894,7 @@ struct Shot {
     }
     t.sync();
     *fid_stop = fs;
+    *max_n = mx;
     return ev;
   }
 
@@ -1133,11 +1090,12 @@ __global__ void __launch_bounds__(32) prefix_kernel(const __grid_constant__ Shot
   auto tile = cg::tiled_partition<32>(cg::this_thread_block());
   Shot<R, W, 32> s(tile, P, smem);
   s.C = &P.circ[0];
-  uint32_t fs = 0;
-  const uint32_t ev = s.trace_prefix(out, stride, &fs);
+  uint32_t fs = 0, mx = 0;
+  const uint32_t ev = s.trace_prefix(out, stride, &fs, &mx);
   if (tile.thread_rank() == 0) {
     stop[0] = ev;
     stop[1] = fs;
+    stop[2] = mx;
   }
 }
 

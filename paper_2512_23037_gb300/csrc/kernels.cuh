@@ -69,6 +69,10 @@ struct ShotParams {
   // fidelity mode: measurements flagged F_FIDELITY project onto +1 and each
   // kept shot adds the product of their conditional probabilities to fsum
   int fid_mode;
+  // lane-per-shot scheduling of circuit 0 (lane_kernel): per item its start event;
+  // bucket e = al_order[al_start[e] .. al_start[e + 1]); claims per bucket
+  uint32_t *al_ev, *al_order, *al_start;
+  unsigned int *al_count, *al_next;
   CircDev circ[kMaxCirc];
 };
 
@@ -83,7 +87,8 @@ enum : uint32_t {
 size_t prefix_stride(int fp32, uint32_t W, uint32_t rw);
 // Record circuit p.circ[0]'s noiseless run into `out` ((n_events + 1) snapshots);
 // stop[0] receives the last valid event, stop[1] the first fidelity measurement's
-// event (or n_events). One warp; p.cap is the map capacity used.
+// event (or n_events), stop[2] the largest map of the recorded snapshots. One
+// warp; p.cap is the map capacity used.
 cudaError_t launch_prefix(const ShotParams &p, int fp32, uint32_t W, unsigned char *out, uint32_t *stop,
                           cudaStream_t st);
 
@@ -99,6 +104,12 @@ struct LaunchCfg {
   unsigned grid, block;
   size_t smem;
 };
+
+// Lane-per-shot kernel (lanes.cu): the bucketing pre-pass (start events, bucket
+// starts, order), its launch shape, and its map capacity per shot.
+cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st);
+cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg);
+uint32_t lane_map_cap();
 
 // Resolve the launch (sets the kernel's shared-memory attribute, queries
 // occupancy). `p.hs_max` must already be hash_slots_for(p.cap). Not a stream

@@ -1,0 +1,690 @@
+// lanes.cu -- shot kernel with one shot per lane, 32 shots per warp, all at the
+// same event.
+//
+// Shots are first bucketed by the event they start at (the event that applies
+// their first error, capped at the end of the circuit's recorded noiseless run).
+// Every warp then walks the events in order. Its idle lanes claim shots from the
+// bucket of the event it is at, load the noiseless run's state there, and the
+// warp executes each event once for all its lanes: the event is decoded once,
+// and every lane updates its own shot's coefficient map, kept in shared memory
+// (entry i of lane l at row i, column l). A map that outgrows kLaneCap entries
+// ends the shot as a rerun; the rerun pass of the warp-per-shot kernel finishes
+// it at the full capacity. The per-shot arithmetic is that of the warp-per-shot
+// kernel (the same formulas, pruning thresholds and outcome rule), entry by entry.
+#include <cooperative_groups.h>
+
+#include "device_common.cuh"
+#include "kernels.cuh"
+#include "shot_common.cuh"
+
+namespace soft {
+namespace {
+
+using namespace dev;
+namespace cg = cooperative_groups;
+
+enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_RERUN = 4 };
+constexpr uint32_t kLaneCap = 16;  // map entries per lane
+constexpr int kLaneBlock = 128;
+
+template <typename R, int W>
+__host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
+  // map keys and values; the pairing output (keys, values); record words
+  return 2 * ((size_t)kLaneCap * W * 8 * 32 + (size_t)kLaneCap * sizeof(Cx<R>) * 32) + (size_t)rw * 8 * 32;
+}
+
+template <typename R, int W>
+struct LaneShot {
+  const ShotParams &P;
+  const CircDev *C;
+  uint32_t lane;
+  uint64_t *keys, *tkeys;  // [i][w][lane]
+  Cx<R> *vals, *tvals;     // [i][lane]
+  uint64_t *rec;           // [w][lane]
+  // per-lane shot state
+  uint64_t shot;
+  uint32_t n;
+  uint64_t sd[W], ss[W];
+  uint32_t nxt, cur, kblk, w2;
+  int status, chain, logical, lastm;
+  double fid;
+  bool force;
+
+  __device__ LaneShot(const ShotParams &p, unsigned char *base) : P(p), C(&p.circ[0]) {
+    lane = threadIdx.x & 31u;
+    const size_t kb = (size_t)kLaneCap * W * 8 * 32, vb = (size_t)kLaneCap * sizeof(Cx<R>) * 32;
+    keys = reinterpret_cast<uint64_t *>(base);
+    vals = reinterpret_cast<Cx<R> *>(base + kb);
+    tkeys = reinterpret_cast<uint64_t *>(base + kb + vb);
+    tvals = reinterpret_cast<Cx<R> *>(base + 2 * kb + vb);
+    rec = reinterpret_cast<uint64_t *>(base + 2 * kb + 2 * vb);
+  }
+
+  __device__ __forceinline__ Key<W> key(uint32_t i) const {
+    Key<W> k;
+#pragma unroll
+    for (int w = 0; w < W; ++w) k.w[w] = keys[((size_t)i * W + w) * 32 + lane];
+    return k;
+  }
+  __device__ __forceinline__ void set_key(uint32_t i, const Key<W> &k) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) keys[((size_t)i * W + w) * 32 + lane] = k.w[w];
+  }
+  __device__ __forceinline__ Cx<R> val(uint32_t i) const { return vals[(size_t)i * 32 + lane]; }
+  __device__ __forceinline__ void set_val(uint32_t i, Cx<R> v) { vals[(size_t)i * 32 + lane] = v; }
+  __device__ __forceinline__ void set_tkey(uint32_t i, const Key<W> &k) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) tkeys[((size_t)i * W + w) * 32 + lane] = k.w[w];
+  }
+  __device__ __forceinline__ Key<W> tkey(uint32_t i) const {
+    Key<W> k;
+#pragma unroll
+    for (int w = 0; w < W; ++w) k.w[w] = tkeys[((size_t)i * W + w) * 32 + lane];
+    return k;
+  }
+  __device__ int find(const Key<W> &k, uint32_t lim) const {
+    for (uint32_t j = 0; j < lim; ++j)
+      if (keq(key(j), k)) return (int)j;
+    return -1;
+  }
+  __device__ void fail_capacity() { status = (P.small_pass && C->cap > kLaneCap) ? LS_RERUN : LS_OVF; }
+  __device__ void fail_check(uint32_t code, uint64_t value) {
+    status = LS_ERR;
+    if (P.diag && atomicAdd(&P.diag[0], 1ull) == 0ull) {
+      P.diag[1] = ((unsigned long long)code << 32);
+      P.diag[2] = shot;
+      P.diag[3] = value;
+    }
+  }
+  // keep the entries with |v|^2 >= tau, in order
+  __device__ void prune() {
+    const R tau = (R)P.tau;
+    uint32_t o = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      const Cx<R> v = val(i);
+      if (norm2(v) >= tau) {
+        if (o != i) {
+          set_key(o, key(i));
+          set_val(o, v);
+        }
+        ++o;
+      }
+    }
+    n = o;
+  }
+
+  __device__ double uniform(uint32_t ord) const {
+    uint4 w = philox(P.seed, shot, 1u, ord);
+    uint64_t m = ((uint64_t)w.x << 21) ^ (uint64_t)(w.y >> 11);
+    return (double)m * 0x1p-53;
+  }
+  __device__ __forceinline__ int pick(uint32_t ord, double pp) {
+    if (force) {
+      if (pp > 0.0) {
+        fid *= pp;
+        return 1;
+      }
+      return -1;
+    }
+    return uniform(ord) < pp ? 1 : -1;
+  }
+  __device__ __forceinline__ R inv_sqrt(double x) const {
+    if (sizeof(R) == 4) return (R)rsqrtf((float)x);
+    return (R)(1.0 / sqrt(x));
+  }
+
+  // ---- start: shot s at event e of the noiseless run
+  __device__ void begin(uint64_t s, uint32_t e) {
+    shot = s;
+    status = LS_RUN;
+    force = false;
+    cur = 0;
+    kblk = 0;
+    if (!next_site(C, P.seed, shot, cur, kblk, nxt, w2)) {
+      status = LS_ERR;
+      return;
+    }
+    const unsigned char *in = C->traj + (size_t)e * C->traj_stride;
+    const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);
+    const uint64_t *r_in = reinterpret_cast<const uint64_t *>(in + sizeof(SnapHdr));
+    const uint64_t *k_in = r_in + C->rw;
+    const Cx<R> *v_in = reinterpret_cast<const Cx<R> *>(k_in + kSnapMax * W);
+    n = __ldg(&h->nnz);
+    chain = (int)__ldg(&h->chain);
+    logical = (int)__ldg(&h->logical);
+    lastm = (int)__ldg(&h->lastm);
+    fid = __ldg(&h->fid);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      sd[w] = __ldg(&h->sd[w]);
+      ss[w] = __ldg(&h->ss[w]);
+    }
+    for (uint32_t w = 0; w < C->rw; ++w) rec[(size_t)w * 32 + lane] = __ldg(&r_in[w]);
+    if (n > kLaneCap) {
+      fail_capacity();
+      return;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+      Key<W> k;
+#pragma unroll
+      for (int w = 0; w < W; ++w) k.w[w] = __ldg(&k_in[i * W + w]);
+      set_key(i, k);
+      set_val(i, v_in[i]);
+    }
+  }
+
+  // ---- Paulis: v'_{a^beta} = i^{e + 2 gamma.a} v_a
+  __device__ void apply_pauli(const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+    for (uint32_t i = 0; i < n; ++i) {
+      const Key<W> k = key(i);
+      set_val(i, ipow(val(i), e + 2u * kpar(k, gamma)));
+      set_key(i, kxor(k, beta));
+    }
+  }
+  __device__ void apply_error(uint32_t s) {
+    if (s >= C->n_sites) {
+      fail_check(CHK_SITE, s);
+      return;
+    }
+    const Site *S = C->sites + s;
+    const uint32_t kind = __ldg(&S->kind);
+    uint32_t code, pa, pb;
+    if ((kind & 3u) == SITE_DEPOL2) {
+      code = (uint32_t)(((uint64_t)w2 * 15u) >> 32) + 1u;
+      pa = code >> 2;
+      pb = code & 3u;
+    } else if ((kind & 3u) == SITE_FLIP) {
+      code = (kind >> 2) & 3u;
+      pa = code;
+      pb = 0;
+    } else {
+      code = (uint32_t)(((uint64_t)w2 * 3u) >> 32) + 1u;
+      pa = code;
+      pb = 0;
+    }
+    uint64_t beta[W], gamma[W];
+    uint32_t pe = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint64_t b = 0, g = 0;
+      if (pa == 1u || pa == 2u) { b ^= __ldg(&S->bx[0][w]); g ^= __ldg(&S->gx[0][w]); }
+      if (pa == 3u || pa == 2u) { b ^= __ldg(&S->bz[0][w]); g ^= __ldg(&S->gz[0][w]); }
+      if (pb == 1u || pb == 2u) { b ^= __ldg(&S->bx[1][w]); g ^= __ldg(&S->gx[1][w]); }
+      if (pb == 3u || pb == 2u) { b ^= __ldg(&S->bz[1][w]); g ^= __ldg(&S->gz[1][w]); }
+      beta[w] = b;
+      gamma[w] = g;
+      pe += __popcll((sd[w] ^ __ldg(&S->dsd[w])) & b) + __popcll((ss[w] ^ __ldg(&S->dss[w])) & g);
+    }
+    apply_pauli(beta, gamma, ((__ldg(&S->c0) >> (2u * code)) + 2u * pe) & 3u);
+  }
+
+  // ---- a I + b Z_q: paired entries (a, a^beta) mix, an unpaired entry gains its partner
+  __device__ void rot(uint32_t w0, uint32_t ci, const uint64_t *beta, const uint64_t *gamma, bool diag) {
+    uint32_t pe = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) pe += diag ? __popcll(ss[w] & gamma[w]) : __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
+    const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
+    if (ci >= C->n_coef) {
+      fail_check(CHK_COEF, ci);
+      return;
+    }
+    const Coef *cf = C->coef + ci;
+    Cx<R> a, b;
+    if (sizeof(R) == 4) {
+      const float4 f = __ldg(reinterpret_cast<const float4 *>(&cf->fa_re));
+      a = Cx<R>{(R)f.x, (R)f.y};
+      b = Cx<R>{(R)f.z, (R)f.w};
+    } else {
+      const double2 d0 = __ldg(reinterpret_cast<const double2 *>(&cf->a_re));
+      const double2 d1 = __ldg(reinterpret_cast<const double2 *>(&cf->b_re));
+      a = Cx<R>{(R)d0.x, (R)d0.y};
+      b = Cx<R>{(R)d1.x, (R)d1.y};
+    }
+    const R tau = (R)P.tau;
+    bool small = false;
+    if (diag) {
+      for (uint32_t i = 0; i < n; ++i) {
+        const Cx<R> v = val(i);
+        const Cx<R> nv = cadd(cmul(a, v), cmul(b, ipow(v, e + 2u * kpar(key(i), gamma))));
+        set_val(i, nv);
+        small = small || norm2(nv) < tau;
+      }
+      if (small) prune();
+      return;
+    }
+    const uint32_t lowbit = ev_lowbit(w0);
+    const uint32_t n0 = n;
+    uint32_t na = 0;
+    for (uint32_t i = 0; i < n0; ++i) {
+      const Key<W> k = key(i);
+      const Key<W> pk = kxor(k, beta);
+      const int j = find(pk, n0);
+      const Cx<R> v = val(i);
+      if (j >= 0) {
+        if (kbit(k, lowbit)) continue;  // the pair's member with bit lowbit clear updates both
+        const Cx<R> vj = val((uint32_t)j);
+        const Cx<R> ni = cadd(cmul(a, v), cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
+        const Cx<R> nj = cadd(cmul(a, vj), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
+        set_val(i, ni);
+        set_val((uint32_t)j, nj);
+        small = small || norm2(ni) < tau || norm2(nj) < tau;
+      } else {
+        const Cx<R> ni = cmul(a, v);
+        const Cx<R> av = cmul(b, ipow(v, e + 2u * kpar(k, gamma)));
+        set_val(i, ni);
+        if (n0 + na >= kLaneCap) {
+          fail_capacity();
+          return;
+        }
+        set_key(n0 + na, pk);
+        set_val(n0 + na, av);
+        ++na;
+        small = small || norm2(ni) < tau || norm2(av) < tau;
+      }
+    }
+    n = n0 + na;
+    if (small) prune();
+  }
+
+  // ---- measurement of P, beta = 0: lambda_a = c (-1)^{gamma.a}
+  __device__ int meas_a(uint32_t w0, uint32_t ord, const uint64_t *gamma) {
+    uint32_t pe = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) pe += __popcll(ss[w] & gamma[w]);
+    const uint32_t e = (ev_e0(w0) + 2u * pe) & 3u;
+    if (e & 1u) {
+      fail_check(CHK_PHASE, e);
+      return 1;
+    }
+    const uint32_t sgn = e >> 1;
+    bool h0 = false, h1 = false;
+    for (uint32_t i = 0; i < n; ++i) {
+      if (kpar(key(i), gamma) ^ sgn) h1 = true;
+      else h0 = true;
+    }
+    if (!(h0 && h1)) return h1 ? -1 : 1;
+    double sp = 0.0, sm = 0.0;
+    for (uint32_t i = 0; i < n; ++i) {
+      const double a2 = norm2d(val(i));
+      if (kpar(key(i), gamma) ^ sgn) sm += a2;
+      else sp += a2;
+    }
+    const double pp = snap01(sp / (sp + sm));
+    const int m = pick(ord, pp);
+    const R sc = inv_sqrt(m == 1 ? sp : sm);
+    const uint32_t want = (m == 1) ? 0u : 1u;
+    const R tau = (R)P.tau;
+    uint32_t o = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      const Key<W> k = key(i);
+      if ((kpar(k, gamma) ^ sgn) != want) continue;
+      const Cx<R> v = cscale(val(i), sc);
+      if (norm2(v) < tau) continue;
+      set_key(o, k);
+      set_val(o, v);
+      ++o;
+    }
+    n = o;
+    return m;
+  }
+
+  // Entry i's pair after the relabel: false if i only feeds the pair of its a0
+  // partner; else a0, v0 = v_{a0} and x1 = xi_{a1} v_{a1} (zero when absent).
+  __device__ bool pair_at(uint32_t i, uint32_t p, const uint64_t *ep, const uint64_t *g2, uint32_t e2, Key<W> &a0,
+                          Cx<R> &v0, Cx<R> &x1) const {
+    const Key<W> k = key(i);
+    const uint32_t hi = kbit(k, p);
+    const int j = find(kxor(k, ep), n);
+    if (hi && j >= 0) return false;
+    Cx<R> v1{0, 0};
+    v0 = Cx<R>{0, 0};
+    if (hi) v1 = val(i);
+    else {
+      v0 = val(i);
+      if (j >= 0) v1 = val((uint32_t)j);
+    }
+    a0 = hi ? kxor(k, ep) : k;
+    x1 = ipow(v1, e2 + 2u * kpar(kxor(a0, ep), g2));
+    return true;
+  }
+
+  // ---- measurement of P, beta != 0 (case B): row operations on the signs, relabel,
+  // pairing, replacement
+  __device__ int meas_b(uint32_t ord, uint32_t cbi) {
+    if (cbi >= C->n_cb) {
+      fail_check(CHK_CASEB, cbi);
+      return 1;
+    }
+    const CaseB *B = C->cb + cbi;
+    const uint32_t p = __ldg(&B->p);
+    uint64_t J[W], g2[W], ep[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      J[w] = __ldg(&B->J[w]);
+      g2[w] = __ldg(&B->gamma2[w]);
+      ep[w] = ((int)(p >> 6) == w) ? (1ull << (p & 63)) : 0ull;
+    }
+    const uint32_t ssp = wbit<W>(ss, p);
+    const uint32_t sdJ = wpar<W>(sd, J);
+#pragma unroll
+    for (int w = 0; w < W; ++w) ss[w] ^= (ssp ? J[w] : 0ull) ^ __ldg(&B->Hs[w]);
+    if (sdJ ^ __ldg(&B->hdp)) wflip<W>(sd, p);
+    const uint32_t e2 = (__ldg(&B->e0b) + 2u * (wbit<W>(sd, p) + wpar<W>(ss, g2))) & 3u;
+    // relabel a_j ^= a_p (j in J)
+    for (uint32_t i = 0; i < n; ++i) {
+      const Key<W> k = key(i);
+      if (kbit(k, p)) set_key(i, kxor(k, J));
+    }
+    // pair a0 (bit p clear) with a1 = a0 ^ e_p: first the outcome probabilities, then
+    // the combined values (v0 + m x1) / sqrt(2 p_m) into the pairing buffer
+    double sp = 0.0, sm = 0.0;
+    for (uint32_t i = 0; i < n; ++i) {
+      Key<W> a0;
+      Cx<R> v0, x1;
+      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1)) continue;
+      sp += 0.5 * norm2d(cadd(v0, x1));
+      sm += 0.5 * norm2d(csub(v0, x1));
+    }
+    const double pp = snap01(sp / (sp + sm));
+    const int m = pick(ord, pp);
+    const R sc = inv_sqrt(2.0 * (m == 1 ? sp : sm));
+    const R tau = (R)P.tau;
+    uint32_t o = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      Key<W> a0;
+      Cx<R> v0, x1;
+      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1)) continue;
+      const Cx<R> nv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
+      if (norm2(nv) < tau) continue;
+      set_tkey(o, a0);
+      tvals[(size_t)o * 32 + lane] = nv;
+      ++o;
+    }
+    for (uint32_t t = 0; t < o; ++t) {
+      set_key(t, tkey(t));
+      set_val(t, tvals[(size_t)t * 32 + lane]);
+    }
+    n = o;
+    // replacement: d_j <- d_j s_p (j in G), d_p <- old s_p, s_p <- m P
+#pragma unroll
+    for (int w = 0; w < W; ++w) sd[w] ^= (ssp ? __ldg(&B->G[w]) : 0ull) ^ __ldg(&B->Hd[w]);
+    if (wbit<W>(sd, p) != ssp) wflip<W>(sd, p);
+    const uint32_t newsp = (m == -1 ? 1u : 0u) ^ __ldg(&B->rP);
+    if (wbit<W>(ss, p) != newsp) wflip<W>(ss, p);
+    return m;
+  }
+
+  __device__ uint32_t rec_bit(int32_t r) const {
+    return (r < 0 || (uint32_t)r >= 64u * C->rw) ? 0u : (uint32_t)((rec[(size_t)(r >> 6) * 32 + lane] >> (r & 63)) & 1ull);
+  }
+
+  // one event for this lane's shot
+  __device__ void step(uint32_t ev, const uint4 &hdr, const uint64_t *body, const Ev<W> *E) {
+    while (nxt < hdr.y && status == LS_RUN) {
+      apply_error(nxt);
+      if (!next_site(C, P.seed, shot, cur, kblk, nxt, w2)) status = LS_ERR;
+    }
+    if (status != LS_RUN) return;
+    const uint64_t *dsd = body, *dss = body + W, *beta = body + 2 * W, *gamma = body + 3 * W;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      sd[w] ^= dsd[w];
+      ss[w] ^= dss[w];
+    }
+    const uint32_t w0 = hdr.x, type = ev_type(w0), flags = ev_flags(w0);
+    switch (type) {
+      case EV_ROT: rot(w0, hdr.z, beta, gamma, false); break;
+      case EV_ROT_DIAG: rot(w0, hdr.z, beta, gamma, true); break;
+      case EV_MEAS_A:
+      case EV_MEAS_B: {
+        force = P.fid_mode && (flags & F_FIDELITY);
+        const int m = (type == EV_MEAS_A) ? meas_a(w0, hdr.z, gamma) : meas_b(hdr.z, (uint32_t)beta[0]);
+        if (status != LS_RUN) break;
+        if (force && m == -1) {
+          fid = 0.0;
+          status = LS_KEPT;
+          break;
+        }
+        lastm = m;
+        if (flags & F_RECORD) {
+          const uint32_t r = hdr.w;
+          if (r >= 64u * C->rw) {
+            fail_check(CHK_RECORD, r);
+            break;
+          }
+          if (m < 0) rec[(size_t)(r >> 6) * 32 + lane] |= 1ull << (r & 63);
+        }
+        if ((flags & F_COND_LAST) && m == -1) {
+          uint64_t xb[W], xg[W];
+          uint32_t pe = 0;
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            xb[w] = __ldg(&E->xbeta[w]);
+            xg[w] = __ldg(&E->xgamma[w]);
+            pe += __popcll(sd[w] & xb[w]) + __popcll(ss[w] & xg[w]);
+          }
+          apply_pauli(xb, xg, (ev_xe0(w0) + 2u * pe) & 3u);
+        }
+        if ((flags & F_DETECTOR) && ((m == -1 ? 1u : 0u) ^ ((flags & F_INVERT) ? 1u : 0u))) status = LS_DISC;
+        break;
+      }
+      case EV_PAULI: {
+        uint32_t cond;
+        if (flags & F_COND_LAST) cond = (lastm == -1);
+        else cond = rec_bit((int32_t)hdr.z) ^ rec_bit((int32_t)hdr.w);
+        if (cond) {
+          uint32_t pe = 0;
+#pragma unroll
+          for (int w = 0; w < W; ++w) pe += __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
+          apply_pauli(beta, gamma, (ev_e0(w0) + 2u * pe) & 3u);
+        }
+        break;
+      }
+      case EV_PARITY: {
+        const int par = chain ^ (int)rec_bit((int32_t)hdr.z) ^ (int)rec_bit((int32_t)hdr.w) ^
+                        ((flags & F_INVERT) ? 1 : 0);
+        if (flags & F_CHAIN) {
+          chain = par;
+        } else {
+          chain = 0;
+          if ((flags & F_DETECTOR) && par) status = LS_DISC;
+          if ((flags & F_OBSERVABLE) && par) logical = 1;
+        }
+        break;
+      }
+      default: break;
+    }
+    (void)ev;
+  }
+};
+
+// ---- bucketing pre-pass: start event per item, bucket sizes, starts, order
+__global__ void lane_count_kernel(const __grid_constant__ ShotParams P) {
+  const CircDev *C = &P.circ[0];
+  const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
+  const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_items;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    uint32_t cur = 0, kblk = 0, nxt = 0, w2 = 0;
+    next_site(C, P.seed, C->first_shot + base + i, cur, kblk, nxt, w2);
+    const uint32_t e = first_event(C, P.fid_mode, nxt);
+    P.al_ev[i] = e;
+    atomicAdd(&P.al_count[e], 1u);
+  }
+}
+__global__ void lane_scan_kernel(const __grid_constant__ ShotParams P) {
+  __shared__ uint32_t part[1024];
+  const uint32_t nb = P.circ[0].n_events + 1, tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t per = (nb + nt - 1) / nt, lo = tid * per < nb ? tid * per : nb, hi = lo + per < nb ? lo + per : nb;
+  uint32_t sum = 0;
+  for (uint32_t k = lo; k < hi; ++k) sum += P.al_count[k];
+  part[tid] = sum;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (uint32_t k = 0; k < nt; ++k) {
+      const uint32_t v = part[k];
+      part[k] = run;
+      run += v;
+    }
+    P.al_start[nb] = run;
+  }
+  __syncthreads();
+  uint32_t run = part[tid];
+  for (uint32_t k = lo; k < hi; ++k) {
+    P.al_start[k] = run;
+    run += P.al_count[k];
+  }
+  __syncthreads();
+  for (uint32_t k = lo; k < hi; ++k) P.al_count[k] = 0u;  // reused as fill counters
+}
+__global__ void lane_scatter_kernel(const __grid_constant__ ShotParams P) {
+  const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_items;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t e = P.al_ev[i];
+    P.al_order[P.al_start[e] + atomicAdd(&P.al_count[e], 1u)] = (uint32_t)i;
+  }
+}
+
+template <typename R, int W>
+__global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant__ ShotParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long btally[5];
+  for (uint32_t i = threadIdx.x; i < 5; i += blockDim.x) btally[i] = 0ull;
+  __syncthreads();
+  const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x & 31u;
+  LaneShot<R, W> s(P, smem + (size_t)warp * lane_warp_bytes<R, W>(P.rw_max));
+  const CircDev *C = &P.circ[0];
+  const uint32_t n_ev = C->n_events;
+  const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
+  const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
+  const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
+  bool active = false;
+  uint32_t item = 0, e = 0;
+  const unsigned long long limit = (n_items + 2ull) * (n_ev + 2ull) + 64ull;
+  for (unsigned long long guard = 0; guard < limit; ++guard) {
+    // idle lanes claim shots that start at event e (one atomic per warp)
+    const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
+    if (idle) {
+      const uint32_t b0 = __ldg(&P.al_start[e]), sz = __ldg(&P.al_start[e + 1]) - b0;
+      uint32_t got0 = 0;
+      const uint32_t leader = __ffs(idle) - 1;
+      if (lane == leader) got0 = *(volatile unsigned int *)&P.al_next[e] < sz ? atomicAdd(&P.al_next[e], __popc(idle)) : sz;
+      got0 = __shfl_sync(0xFFFFFFFFu, got0, leader);
+      if (!active) {
+        const uint32_t k = got0 + __popc(idle & ((1u << lane) - 1u));
+        if (k < sz) {
+          item = __ldg(&P.al_order[b0 + k]);
+          if (item < n_items) {
+            active = true;
+            s.begin(C->first_shot + base + item, e);
+          }
+        }
+      }
+    }
+    if (e < n_ev && __any_sync(0xFFFFFFFFu, active && s.status == LS_RUN)) {
+      const Ev<W> *E = evs + e;
+      const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
+      uint64_t body[4 * W];
+      const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(&E->dsd[0]);
+#pragma unroll
+      for (int k = 0; k < 2 * W; ++k) {
+        const ulonglong2 v = __ldg(bp + k);
+        body[2 * k] = v.x;
+        body[2 * k + 1] = v.y;
+      }
+      if (active && s.status == LS_RUN) s.step(e, hdr, body, E);
+    }
+    // finish: ended, or past the last event
+    if (active && (s.status != LS_RUN || e + 1u >= n_ev)) {
+      if (s.status == LS_RUN) s.status = LS_KEPT;
+      const uint64_t off = base + item;
+      if (s.status == LS_RERUN) {
+        const unsigned long long i = atomicAdd(P.n_rerun, 1ull);
+        if (i < P.rerun_cap) P.rerun[i] = item;
+      } else {
+        atomicAdd(&btally[0], 1ull);
+        if (s.status == LS_DISC) atomicAdd(&btally[1], 1ull);
+        else if (s.status == LS_OVF) atomicAdd(&btally[2], 1ull);
+        else if (s.status == LS_KEPT) {
+          atomicAdd(&btally[3], 1ull);
+          if (s.logical) atomicAdd(&btally[4], 1ull);
+          if (P.fid_mode && C->fsum) atomicAdd(C->fsum, s.fid);
+        }
+        if (off < C->out_limit) {
+          if (C->status) C->status[off] = (uint8_t)s.status;
+          if (C->records)
+            for (uint32_t w = 0; w < C->rw; ++w) C->records[off * C->rw + w] = s.rec[(size_t)w * 32 + lane];
+        }
+      }
+      active = false;
+    }
+    uint32_t en = e + 1u > n_ev ? 0u : e + 1u;
+    if (!__any_sync(0xFFFFFFFFu, active)) {
+      // all lanes idle: the next bucket (cyclically) that still has shots, or stop
+      uint32_t found = 0xFFFFFFFFu;
+      if (lane == 0) {
+        for (uint32_t k = 0; k <= n_ev; ++k) {
+          const uint32_t c = (en + k) % (n_ev + 1u);
+          if (*(volatile unsigned int *)&P.al_next[c] < __ldg(&P.al_start[c + 1]) - __ldg(&P.al_start[c])) {
+            found = c;
+            break;
+          }
+        }
+      }
+      found = __shfl_sync(0xFFFFFFFFu, found, 0);
+      if (found == 0xFFFFFFFFu) break;
+      en = found;
+    }
+    e = en;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < 5; i += blockDim.x)
+    if (btally[i]) atomicAdd(&P.circ[0].tally[i], btally[i]);
+}
+
+}  // namespace
+
+size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw) {
+  const size_t per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1>(rw) : lane_warp_bytes<float, 2>(rw))
+                          : (W == 1 ? lane_warp_bytes<double, 1>(rw) : lane_warp_bytes<double, 2>(rw));
+  return per * (kLaneBlock / 32);
+}
+
+uint32_t lane_map_cap() { return kLaneCap; }
+
+cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * 8u;
+  lane_count_kernel<<<grid, 256, 0, st>>>(p);
+  lane_scan_kernel<<<1, 1024, 0, st>>>(p);
+  lane_scatter_kernel<<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg) {
+  const void *kern = fp32 ? (W == 1 ? reinterpret_cast<const void *>(lane_kernel<float, 1>)
+                                    : reinterpret_cast<const void *>(lane_kernel<float, 2>))
+                          : (W == 1 ? reinterpret_cast<const void *>(lane_kernel<double, 1>)
+                                    : reinterpret_cast<const void *>(lane_kernel<double, 2>));
+  const size_t smem = lane_smem_bytes(fp32, W, p.rw_max);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLaneBlock, smem)) != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+  cfg->kern = kern;
+  cfg->grid = (unsigned)(occ * sms);
+  cfg->block = kLaneBlock;
+  cfg->smem = smem;
+  return cudaSuccess;
+}
+
+}  // namespace soft

@@ -1,0 +1,82 @@
+// shot_common.cuh -- per-shot device pieces shared by the shot kernels: the
+// noise stream's next accepted site, the event a shot starts at, and the layout
+// of the noiseless run's snapshots.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "kernels.cuh"
+
+namespace soft {
+namespace dev {
+
+// The next accepted error site at or after `cur` of shot `shot`: geometric gaps
+// of the noise stream against the thresholds thr (the smallest gap g with
+// U < thr[g]), then thinning. nxt = the site (0xFFFFFFFF if none), w2 = its
+// Pauli choice word. False if the guard ran out (impossible for valid tables).
+__device__ __forceinline__ bool next_site(const CircDev *C, uint64_t seed, uint64_t shot, uint32_t &cur,
+                                          uint32_t &kblk, uint32_t &nxt, uint32_t &w2) {
+  const uint32_t n_sites = C->n_sites;
+  const uint64_t *thr = C->thr;
+  for (uint32_t guard = 0; guard <= n_sites; ++guard) {
+    if (cur >= n_sites) {
+      nxt = 0xFFFFFFFFu;
+      return true;
+    }
+    uint4 w = philox(seed, shot, 0u, kblk++);
+    uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
+    const uint32_t rem = n_sites - cur;
+    uint32_t lo = 0, hi = rem;
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (U < __ldg(&thr[mid])) hi = mid;
+      else lo = mid + 1u;
+    }
+    if (lo == rem) {
+      cur = n_sites;
+      nxt = 0xFFFFFFFFu;
+      return true;
+    }
+    uint32_t s = cur + lo;
+    cur = s + 1u;
+    const Site *st = C->sites + s;
+    if (!__ldg(&st->always) && !(w.w < __ldg(&st->thin))) continue;
+    nxt = s;
+    w2 = w.z;
+    return true;
+  }
+  nxt = 0xFFFFFFFFu;
+  return false;
+}
+
+// The event a shot whose first error is at site nxt starts at: the event that
+// applies that error, capped at the last valid event of the noiseless run
+// (fidelity mode: of its part before the first observed measurement).
+__device__ __forceinline__ uint32_t first_event(const CircDev *C, int fid_mode, uint32_t nxt) {
+  const uint32_t stop = fid_mode && C->traj_fid_stop < C->traj_stop ? C->traj_fid_stop : C->traj_stop;
+  if (nxt < C->n_sites) {
+    const uint32_t e = __ldg(&C->site_ev[nxt]);
+    return e < stop ? e : stop;
+  }
+  return stop;
+}
+
+// Snapshot of the noiseless run at the top of an event: header, rw record words,
+// kSnapMax keys (W words each), kSnapMax values.
+struct SnapHdr {
+  uint32_t nnz, chain, logical, lastm;
+  double fid;
+  uint64_t sd[2], ss[2];
+  uint64_t pad[2];
+};
+constexpr uint32_t kSnapMax = 64;
+template <typename R, int W>
+__host__ __device__ constexpr size_t snap_stride(uint32_t rw) {
+  return (sizeof(SnapHdr) + (size_t)rw * 8 + kSnapMax * (size_t)W * 8 + kSnapMax * sizeof(Cx<R>) + 15) &
+         ~(size_t)15;
+}
+
+}  // namespace dev
+}  // namespace soft

@@ -412,3 +412,36 @@ def test_degenerate_circuits(soft, case):
     cc, r, rec, st, tal, ref = run_both(soft, c, noise, 500, 2, "fp64")
     assert [tal["shots"], tal["discarded"], tal["overflow"], tal["kept"], tal["logical_errors"]] == ref["tally"]
     assert compare_records(c, noise, 2, 0, rec, st, ref, "fp64") == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["w42", "w42_rerun_chunks", "tiny6", "random40", "w97"])
+def test_lane_per_shot_matches_oracle(soft, precision, case):
+    """One shot per lane, 32 per warp, event-aligned: records, statuses and
+    tallies against the oracle (and the tallies of the warp-per-shot kernel)."""
+    S = soft
+    kw = {}
+    n_shots = 3000
+    if case.startswith("w42"):
+        circ, noise = C.workload("w42")
+        if case == "w42_rerun_chunks":
+            kw = {"first_cap": 8, "chunk_shots": 1000}
+    elif case == "w97":
+        circ, noise = C.workload("w97")
+        n_shots = 800
+    elif case == "tiny6":
+        circ, noise = C.workload("tiny6")
+        noise = C.Noise.uniform(0.02)
+    else:
+        circ = C.random_circuit(4040, 40, 400, t_frac=0.2, detectors=True, mpp_frac=0.05)
+        circ.cap = 256
+        noise = C.Noise(0.005, 0.005, 0.005, 0.005)
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    r = S.soft_run_shots(c, n_shots, 0, 9, precision=precision, record_mode=S.REC_ALL, **kw)
+    rec, st = S.soft_get_records(r, n_shots)
+    tal = S.soft_tally(r)
+    assert S.soft_run_diagnostics(r)[0] == 0
+    ref = oracle.run(circ, circ.n, noise, circ.cap, 9, 0, n_shots, threads=8)
+    assert compare_records(circ, noise, 9, 0, rec, st, ref, precision) <= 2
+    t2 = S.soft_tally(S.soft_run_shots(c, n_shots, 0, 9, precision=precision, lanes=False, **kw))
+    assert abs(tal["kept"] - t2["kept"]) <= 2 and tal["shots"] == t2["shots"] == n_shots
