@@ -337,7 +337,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   } while (0)
   SOFT_ALLOC(r->d_tally, 5 * n_circ * sizeof(unsigned long long));
   const uint32_t n_ev0 = (uint32_t)circs[0]->hp.ev.size();
-  if (lanes) SOFT_ALLOC(r->d_al, (2 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
+  // lanes: cursors (4 words per item, first: 16-byte aligned), start events, order, bucket starts, counters
+  if (lanes) SOFT_ALLOC(r->d_al, (6 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
   r->fid_mode = fid_mode;
   if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
   SOFT_ALLOC(r->d_work, 8 * sizeof(unsigned long long));
@@ -429,10 +430,11 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     q.gslab_blocks = slab_blocks;
   }
   if (lanes) {  // start events, order, bucket starts, then the two counter arrays (zeroed per chunk)
-    p.al_ev = r->d_al;
-    p.al_order = r->d_al + chunk;
-    p.al_start = r->d_al + 2 * chunk;
-    p.al_count = r->d_al + 2 * chunk + (n_ev0 + 2);
+    p.al_cursor = r->d_al;
+    p.al_ev = r->d_al + 4 * chunk;
+    p.al_order = r->d_al + 5 * chunk;
+    p.al_start = r->d_al + 6 * chunk;
+    p.al_count = r->d_al + 6 * chunk + (n_ev0 + 2);
     p.al_next = p.al_count + (n_ev0 + 1);
   }
   soft::LaunchCfg c1{}, c2{};

@@ -73,6 +73,7 @@ struct ShotParams {
   // bucket e = al_order[al_start[e] .. al_start[e + 1]); claims per bucket
   uint32_t *al_ev, *al_order, *al_start;
   unsigned int *al_count, *al_next;
+  uint32_t *al_cursor;  // per item the noise cursor after its first draw (nxt, cur, kblk, w2), 16-byte aligned
   CircDev circ[kMaxCirc];
 };
 

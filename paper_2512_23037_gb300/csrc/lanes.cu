@@ -134,13 +134,16 @@ struct LaneShot {
   }
 
   // ---- start: shot s at event e of the noiseless run
-  __device__ void begin(uint64_t s, uint32_t e) {
+  // (the pre-pass drew the shot's first error: its noise cursor comes with the item)
+  __device__ void begin(uint64_t s, uint32_t e, uint4 cursor) {
     shot = s;
     status = LS_RUN;
     force = false;
-    cur = 0;
-    kblk = 0;
-    if (!next_site(C, P.seed, shot, cur, kblk, nxt, w2)) {
+    nxt = cursor.x;
+    cur = cursor.y;
+    kblk = cursor.z;
+    w2 = cursor.w;
+    if (kblk == 0xFFFFFFFFu) {
       status = LS_ERR;
       return;
     }
@@ -506,9 +509,10 @@ __global__ void lane_count_kernel(const __grid_constant__ ShotParams P) {
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_items;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     uint32_t cur = 0, kblk = 0, nxt = 0, w2 = 0;
-    next_site(C, P.seed, C->first_shot + base + i, cur, kblk, nxt, w2);
+    if (!next_site(C, P.seed, C->first_shot + base + i, cur, kblk, nxt, w2)) kblk = 0xFFFFFFFFu;  // marks a failure
     const uint32_t e = first_event(C, P.fid_mode, nxt);
     P.al_ev[i] = e;
+    reinterpret_cast<uint4 *>(P.al_cursor)[i] = make_uint4(nxt, cur, kblk, w2);
     atomicAdd(&P.al_count[e], 1u);
   }
 }
@@ -561,7 +565,10 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
   const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
   const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
   bool active = false;
-  uint32_t item = 0, e = 0;
+  // warps start spread evenly over the events, so that they meet buckets that still hold shots
+  const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x / 32) + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x / 32);
+  uint32_t item = 0, e = (uint32_t)((gw * (n_ev + 1ull)) / nw);
   const unsigned long long limit = (n_items + 2ull) * (n_ev + 2ull) + 64ull;
   for (unsigned long long guard = 0; guard < limit; ++guard) {
     // idle lanes claim shots that start at event e (one atomic per warp)
@@ -578,7 +585,7 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
           item = __ldg(&P.al_order[b0 + k]);
           if (item < n_items) {
             active = true;
-            s.begin(C->first_shot + base + item, e);
+            s.begin(C->first_shot + base + item, e, reinterpret_cast<const uint4 *>(P.al_cursor)[item]);
           }
         }
       }
