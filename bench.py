@@ -137,10 +137,10 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel_src_hash):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "shot_kernel_w42.md")
+def profile_traffic(kernel_src_hash, name):
+    """DRAM bytes per launch from the committed ncu summary `name`, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
@@ -154,7 +154,7 @@ def profile_traffic(kernel_src_hash):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "program.h", "device_common.cuh"):
+    for f in ("kernels.cu", "kernels.cuh", "program.h", "device_common.cuh", "lanes.cu", "shot_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2512_23037_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -348,12 +348,13 @@ def main():
     def compile_all():
         return [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz, _ in items]
 
-    def launch(handles, first, precision, fidelity=False):
+    def launch(handles, first, precision, fidelity=False, time_passes=False):
         if len(handles) == 1:
             return S.soft_run_shots(handles[0], items[0][2], first, 0, precision=precision, stream=stream,
-                                    graph=args.graph, fidelity=fidelity, lanes=not args.warp_per_shot, **tune)
+                                    graph=args.graph, fidelity=fidelity, lanes=not args.warp_per_shot,
+                                    time_passes=time_passes, **tune)
         return S.soft_run_batch(handles, [s for _, _, s in items], [first] * len(handles), 0, precision=precision,
-                                stream=stream, graph=args.graph, fidelity=fidelity, **tune)
+                                stream=stream, graph=args.graph, fidelity=fidelity, time_passes=time_passes, **tune)
 
     def time_path(precision, steps, warmup, fidelity=False):
         hs = compile_all()
@@ -370,11 +371,16 @@ def main():
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            r = launch(hs, base_shot + k * n, precision, fidelity)
+            r = launch(hs, base_shot + k * n, precision, fidelity, time_passes=not args.graph)
             ev1.record(stream)
             tallies.append(S.soft_tally(r))
             ms, nl = S.soft_run_timing(r)
-            kernel_ms.append(ms)
+            # per pass (bucketing pre-pass, first pass, rerun pass) when events were recorded between them
+            if args.graph:
+                kernel_ms.append([0.0, ms, 0.0, 0])
+            else:
+                pms, _, n_rr = S.soft_run_pass_timing(r)
+                kernel_ms.append(pms + [n_rr])
             launches += nl
             total_ms += ev0.elapsed_time(ev1)
             r.free()
@@ -444,10 +450,14 @@ def main():
     sm_clock = peaks.get("sm_max_mhz", 2070.0)
     sms = dev_props.multi_processor_count
     peak_ops = sms * 128 * sm_clock * 1e6  # FP32/INT32 lanes x clock
-    # dominant kernel: the first-pass shot kernel; CUDA events around each run
-    avg_launch_ms = sum(kms32) / len(kms32)
+    # dominant kernel: the first-pass shot kernel (lane per shot where it applies), timed with the
+    # passes that finish its work (bucketing pre-pass, rerun of outgrown maps) by CUDA events between
+    # them on the launching stream; the work is every shot's executed lane ops
+    pass_ms = [sum(k[j] for k in kms32) / len(kms32) for j in range(3)]
+    avg_launch_ms = sum(pass_ms)
     achieved = ops_shot * n / (avg_launch_ms / 1000)
-    traffic = profile_traffic(kernel_hash())
+    lane_mode = pass_ms[0] > 0
+    traffic = profile_traffic(kernel_hash(), "lane_kernel_w42.md" if lane_mode else "shot_kernel_w42.md")
     line = {
         "metric": "shots/s", "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -462,6 +472,9 @@ def main():
         "tally_last_step": tal32[-1],
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": "lane_kernel" if lane_mode else "shot_kernel",
+                     "pass_ms_per_step": {"prepass": pass_ms[0], "first_pass": pass_ms[1], "rerun": pass_ms[2]},
+                     "rerun_shots_per_step": sum(k[3] for k in kms32) / len(kms32),
                      "ops_per_shot": ops_shot, "ops_per_shot_whole_method": ops_full,
                      "work": "lane ops a shot executes after the noiseless-run prefix it shares with every "
                              "shot (oracle counters); the whole method per shot is ops_per_shot_whole_method",

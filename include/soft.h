@@ -181,7 +181,10 @@ typedef struct {
  * when every map of the circuit's noiseless run fits (at most 16 entries);
  * otherwise a warp (group) runs each shot. SOFT_RUN_NO_LANES always uses the
  * warp per shot. Same results either way, another order. */
-enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_RUN_NO_LANES = 8 };
+/* SOFT_RUN_TIME_PASSES records CUDA events between the passes of every chunk
+ * (ignored with SOFT_RUN_GRAPH), read back by soft_run_pass_timing. */
+enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_RUN_NO_LANES = 8,
+       SOFT_RUN_TIME_PASSES = 16 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
  * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all
@@ -242,6 +245,16 @@ int soft_run_diagnostics(soft_run *r, uint64_t out[4]);
 /* Device time of the run's kernels in milliseconds (CUDA events on the run's
  * stream), and how many kernels were launched. Waits for the run. */
 int soft_run_timing(soft_run *r, double *ms, uint32_t *n_launches);
+
+/* Device time of each pass, summed over the run's chunks, in milliseconds:
+ * ms[0] the lane-per-shot bucketing pre-pass (0 for warp-per-shot runs),
+ * ms[1] the first pass (the shot kernel of the chosen scheduling), ms[2] the
+ * rerun pass of shots whose maps outgrew the first pass (0 without one).
+ * n_chunks (may be NULL) receives the number of chunks, n_rerun (may be NULL)
+ * the number of shots the rerun pass finished. Waits for the run.
+ * SOFT_E_ARG unless the run was launched with SOFT_RUN_TIME_PASSES and
+ * without SOFT_RUN_GRAPH. */
+int soft_run_pass_timing(soft_run *r, double ms[3], uint32_t *n_chunks, uint64_t *n_rerun);
 
 void soft_run_free(soft_run *r);
 

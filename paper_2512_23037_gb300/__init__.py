@@ -29,7 +29,7 @@ SOFT_OK = 0
 FP64, FP32 = 0, 1
 REC_NONE, REC_FIRST_K, REC_ALL = 0, 1, 2
 SHOT_KEPT, SHOT_DISCARDED, SHOT_OVERFLOW, SHOT_ERROR = 0, 1, 2, 3
-RUN_GRAPH, RUN_FIDELITY, RUN_NO_PREFIX, RUN_NO_LANES = 1, 2, 4, 8
+RUN_GRAPH, RUN_FIDELITY, RUN_NO_PREFIX, RUN_NO_LANES, RUN_TIME_PASSES = 1, 2, 4, 8, 16
 
 
 class SoftError(RuntimeError):
@@ -64,7 +64,7 @@ class _Tally(ctypes.Structure):
 
 
 EXPORTED = ["soft_compile_circuit", "soft_circuit_info", "soft_circuit_tableau", "soft_circuit_free",
-            "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing",
+            "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing", "soft_run_pass_timing",
             "soft_run_free", "soft_run_shots_noalloc", "soft_run_diagnostics", "soft_run_batch",
             "soft_tally_batch", "soft_fidelity_grad", "soft_last_error"]
 
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         L.soft_get_records.argtypes = [vp, vp, sz, vp, sz]
         L.soft_get_state.argtypes = [vp, u64, vp, vp, vp, sz, ctypes.POINTER(sz)]
         L.soft_run_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
+        L.soft_run_pass_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32), ctypes.POINTER(u64)]
         L.soft_run_free.argtypes = [vp]
         L.soft_run_free.restype = None
         L.soft_run_shots_noalloc.argtypes = [vp, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp]
@@ -178,7 +179,7 @@ def soft_compile_circuit(ops, n_qubits: int, noise, coeff_cap: int) -> Circuit:
 
 def _opts(precision="fp64", record_mode=REC_NONE, record_k=0, stream=None, group_size=0, blocks_per_sm=0,
           chunk_shots=0, first_cap=0, capture_k=0, d_records=None, d_status=None, groups_per_block=0,
-          graph=False, fidelity=False, prefix=True, lanes=True) -> _Opts:
+          graph=False, fidelity=False, prefix=True, lanes=True, time_passes=False) -> _Opts:
     o = _Opts()
     o.precision = FP32 if precision in ("fp32", FP32) else FP64
     o.record_mode = int(record_mode)
@@ -202,7 +203,7 @@ def _opts(precision="fp64", record_mode=REC_NONE, record_k=0, stream=None, group
     o.d_status = ctypes.c_void_p(int(d_status) if d_status else 0)
     o.groups_per_block = int(groups_per_block)
     o.flags = ((RUN_GRAPH if graph else 0) | (RUN_FIDELITY if fidelity else 0) | (0 if prefix else RUN_NO_PREFIX)
-               | (0 if lanes else RUN_NO_LANES))
+               | (0 if lanes else RUN_NO_LANES) | (RUN_TIME_PASSES if time_passes else 0))
     return o
 
 
@@ -210,16 +211,18 @@ def soft_run_shots(circ: Circuit, n_shots: int, first_shot: int = 0, seed: int =
                    record_mode=REC_NONE, record_k: int = 0, stream=None, group_size: int = 0,
                    blocks_per_sm: int = 0, chunk_shots: int = 0, first_cap: int = 0, capture_k: int = 0,
                    d_records=None, d_status=None, groups_per_block: int = 0, graph: bool = False,
-                   fidelity: bool = False, prefix: bool = True, lanes: bool = True) -> Run:
+                   fidelity: bool = False, prefix: bool = True, lanes: bool = True,
+                   time_passes: bool = False) -> Run:
     """Launch shots asynchronously on `stream` (a torch.cuda.Stream, a raw
     cudaStream_t int, or None for torch's current stream when torch is
     imported, else the legacy default stream). fidelity=True projects the
     observed measurements onto +1 and sums their exact fidelity F per kept
     shot (tally sum_fidelity / sum_weight). prefix=False runs every shot from
     the first event instead of from the shared noiseless prefix, lanes=False a
-    warp per shot instead of a lane per shot where that applies (same results)."""
+    warp per shot instead of a lane per shot where that applies (same results).
+    time_passes=True records events between passes for soft_run_pass_timing."""
     o = _opts(precision, record_mode, record_k, stream, group_size, blocks_per_sm, chunk_shots, first_cap,
-              capture_k, d_records, d_status, groups_per_block, graph, fidelity, prefix, lanes)
+              capture_k, d_records, d_status, groups_per_block, graph, fidelity, prefix, lanes, time_passes)
     out = ctypes.c_void_p()
     _check(load().soft_run_shots(circ.h, int(n_shots), int(first_shot), int(seed) & (2 ** 64 - 1), ctypes.byref(o),
                                  ctypes.byref(out)))
@@ -287,6 +290,16 @@ def soft_run_timing(run: Run):
     nl = ctypes.c_uint32(0)
     _check(load().soft_run_timing(run.h, ctypes.byref(ms), ctypes.byref(nl)))
     return float(ms.value), int(nl.value)
+
+
+def soft_run_pass_timing(run: Run):
+    """([pre-pass, first pass, rerun pass] ms summed over chunks, chunks, shots
+    finished by the rerun pass) of a run launched with time_passes=True."""
+    ms = (ctypes.c_double * 3)()
+    nc = ctypes.c_uint32(0)
+    nr = ctypes.c_uint64(0)
+    _check(load().soft_run_pass_timing(run.h, ms, ctypes.byref(nc), ctypes.byref(nr)))
+    return [float(v) for v in ms], int(nc.value), int(nr.value)
 
 
 def soft_run_shots_noalloc(circ: Circuit, n_shots: int, first_shot: int, seed: int, precision, stream,

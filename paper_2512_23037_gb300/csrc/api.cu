@@ -44,7 +44,7 @@ struct soft_run {
   double *d_fsum = nullptr;                // fidelity mode: sum of F per circuit
   uint32_t *d_al = nullptr;                // lane-per-shot bucketing buffers
   bool fid_mode = false;
-  unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4]
+  unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4], reruns of all chunks
   uint32_t *d_rerun = nullptr;
   unsigned char *d_slab = nullptr;         // global-memory state for large-cap reruns
   uint8_t *d_status = nullptr;             // circuit 0 only
@@ -59,6 +59,7 @@ struct soft_run {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> pass_ev;        // SOFT_RUN_TIME_PASSES: 4 per chunk around pre-pass, first, rerun
   uint32_t launches = 0;
 };
 
@@ -227,6 +228,8 @@ void soft_run_free(soft_run *r) {
   if (r->graph) cudaGraphDestroy(r->graph);
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
+  for (size_t k = 0; k < r->pass_ev.size(); ++k)
+    if (k == 0 || r->pass_ev[k] != r->pass_ev[k - 1]) cudaEventDestroy(r->pass_ev[k]);
   delete r;
 }
 
@@ -275,7 +278,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     return fail(SOFT_E_ARG, "records and state capture are per single-circuit run");
   const bool use_graph = (o.flags & SOFT_RUN_GRAPH) != 0;
   const bool fid_mode = (o.flags & SOFT_RUN_FIDELITY) != 0;
-  if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY | SOFT_RUN_NO_PREFIX | SOFT_RUN_NO_LANES))
+  if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY | SOFT_RUN_NO_PREFIX | SOFT_RUN_NO_LANES |
+                          SOFT_RUN_TIME_PASSES))
     return fail(SOFT_E_ARG, "unknown run flags");
   if (use_graph && !o.stream) return fail(SOFT_E_ARG, "graph replay needs a non-default stream");
   const int fp32 = o.precision == SOFT_FP32;
@@ -341,7 +345,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   if (lanes) SOFT_ALLOC(r->d_al, (6 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
   r->fid_mode = fid_mode;
   if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
-  SOFT_ALLOC(r->d_work, 8 * sizeof(unsigned long long));
+  SOFT_ALLOC(r->d_work, 9 * sizeof(unsigned long long));
   if (two_pass) SOFT_ALLOC(r->d_rerun, chunk * sizeof(uint32_t));
   uint32_t slab_blocks = 0;
   if (global_rerun) {
@@ -376,7 +380,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     return cuda_fail(e, "cudaEventCreate");
   }
   if ((e = cudaMemsetAsync(r->d_tally, 0, 5 * n_circ * sizeof(unsigned long long), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(r->d_work, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(r->d_work, 0, 9 * sizeof(unsigned long long), st)) != cudaSuccess ||
       (fid_mode && (e = cudaMemsetAsync(r->d_fsum, 0, n_circ * sizeof(double), st)) != cudaSuccess)) {
     soft_run_free(r);
     return cuda_fail(e, "cudaMemsetAsync");
@@ -405,6 +409,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   p.rerun_cap = two_pass ? (uint32_t)chunk : 0u;
   p.n_rerun = r->d_work + 2;
   p.diag = r->d_work + 4;
+  p.n_rerun_total = r->d_work + 8;
   p.groups_per_block = o.groups_per_block;
   p.fid_mode = fid_mode ? 1 : 0;
   if (r->st_limit) {
@@ -447,6 +452,21 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   }
   cudaEventRecord(r->ev0, st);
   // one chunk of items [base, base + cnt): clear counters, first pass, rerun pass
+  const bool time_passes = (o.flags & SOFT_RUN_TIME_PASSES) && !use_graph;
+  // marks the boundary between passes of a chunk when the caller asked for per-pass times
+  // (a pass that does not run repeats the previous event: it reports exactly 0)
+  auto mark = [&](bool ran = true) -> cudaError_t {
+    if (!time_passes) return cudaSuccess;
+    if (!ran && !r->pass_ev.empty()) {
+      r->pass_ev.push_back(r->pass_ev.back());
+      return cudaSuccess;
+    }
+    cudaEvent_t ev;
+    cudaError_t err = cudaEventCreate(&ev);
+    if (err != cudaSuccess) return err;
+    r->pass_ev.push_back(ev);
+    return cudaEventRecord(ev, st);
+  };
   auto enqueue_chunk = [&](uint64_t base, uint64_t cnt, bool dev_base) -> cudaError_t {
     cudaError_t err;
     if ((err = cudaMemsetAsync(r->d_work, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
@@ -454,19 +474,22 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     a.n_items = b.n_items = cnt;
     a.item_base = b.item_base = base;
     if (dev_base) a.item_base_dev = b.item_base_dev = r->d_work + 3;
+    if ((err = mark()) != cudaSuccess) return err;
     if (lanes) {
       if ((err = cudaMemsetAsync(a.al_count, 0, 2 * (size_t)(n_ev0 + 1) * sizeof(uint32_t), st)) != cudaSuccess ||
           (err = soft::launch_lane_prepass(a, st)) != cudaSuccess)
         return err;
       r->launches += 3;
     }
+    if ((err = mark(lanes)) != cudaSuccess) return err;
     if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
     r->launches++;
+    if ((err = mark()) != cudaSuccess) return err;
     if (two_pass) {
       if ((err = soft::launch_prepared(c2, b, st)) != cudaSuccess) return err;
       r->launches++;
     }
-    return cudaSuccess;
+    return mark(two_pass);
   };
   uint64_t s0 = 0;
   const uint64_t n_full = total / chunk;
@@ -640,6 +663,29 @@ int soft_run_timing(soft_run *r, double *ms, uint32_t *n_launches) {
   if ((e = cudaEventElapsedTime(&f, r->ev0, r->ev1)) != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
   if (ms) *ms = (double)f;
   if (n_launches) *n_launches = r->launches;
+  return SOFT_OK;
+}
+
+int soft_run_pass_timing(soft_run *r, double ms[3], uint32_t *n_chunks, uint64_t *n_rerun) {
+  if (!r || !ms) return fail(SOFT_E_ARG, "null argument");
+  if (r->pass_ev.empty()) return fail(SOFT_E_ARG, "run was not launched with SOFT_RUN_TIME_PASSES (or used a graph)");
+  cudaError_t e = cudaEventSynchronize(r->ev1);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+  ms[0] = ms[1] = ms[2] = 0.0;
+  for (size_t k = 0; k + 3 < r->pass_ev.size(); k += 4)
+    for (int j = 0; j < 3; ++j) {
+      float f = 0.f;
+      if ((e = cudaEventElapsedTime(&f, r->pass_ev[k + j], r->pass_ev[k + j + 1])) != cudaSuccess)
+        return cuda_fail(e, "cudaEventElapsedTime");
+      ms[j] += (double)f;
+    }
+  if (n_chunks) *n_chunks = (uint32_t)(r->pass_ev.size() / 4);
+  if (n_rerun) {
+    unsigned long long t = 0;
+    if ((e = cudaMemcpy(&t, r->d_work + 8, sizeof t, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "rerun count copy");
+    *n_rerun = t;
+  }
   return SOFT_OK;
 }
 

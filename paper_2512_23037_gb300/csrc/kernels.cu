@@ -989,6 +989,7 @@ struct Shot {
       if (lane == 0) {
         unsigned long long i = atomicAdd(P.n_rerun, 1ull);
         if (i < P.rerun_cap) P.rerun[i] = (uint32_t)local;
+        if (P.n_rerun_total) atomicAdd(P.n_rerun_total, 1ull);
       }
       t.sync();
       return;

@@ -52,6 +52,7 @@ struct ShotParams {
   uint32_t rerun_cap;
   uint32_t *rerun;                // rerun list of local items (capacity rerun_cap)
   unsigned long long *n_rerun;
+  unsigned long long *n_rerun_total;  // reruns over all chunks of a run (may be null)
   // final GS state of circuit 0's first st_limit shots
   uint64_t *st_signs;  // 4 words per shot
   uint64_t *st_keys;   // st_stride entries x 2 words

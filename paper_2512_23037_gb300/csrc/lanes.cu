@@ -24,13 +24,17 @@ using namespace dev;
 namespace cg = cooperative_groups;
 
 enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_RERUN = 4 };
-constexpr uint32_t kLaneCap = 16;  // map entries per lane
+#ifndef SOFT_LANE_CAP
+#define SOFT_LANE_CAP 16
+#endif
+constexpr uint32_t kLaneCap = SOFT_LANE_CAP;  // map entries per lane
+static_assert(kLaneCap >= 2 && kLaneCap <= 64, "lane map capacity");
 constexpr int kLaneBlock = 128;
 
 template <typename R, int W>
 __host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
-  // map keys and values; the pairing output (keys, values); record words
-  return 2 * ((size_t)kLaneCap * W * 8 * 32 + (size_t)kLaneCap * sizeof(Cx<R>) * 32) + (size_t)rw * 8 * 32;
+  // map keys and values; record words
+  return (size_t)kLaneCap * W * 8 * 32 + (size_t)kLaneCap * sizeof(Cx<R>) * 32 + (size_t)rw * 8 * 32;
 }
 
 template <typename R, int W>
@@ -38,8 +42,8 @@ struct LaneShot {
   const ShotParams &P;
   const CircDev *C;
   uint32_t lane;
-  uint64_t *keys, *tkeys;  // [i][w][lane]
-  Cx<R> *vals, *tvals;     // [i][lane]
+  uint64_t *keys;  // [i][w][lane]
+  Cx<R> *vals;     // [i][lane]
   uint64_t *rec;           // [w][lane]
   // per-lane shot state
   uint64_t shot;
@@ -55,9 +59,7 @@ struct LaneShot {
     const size_t kb = (size_t)kLaneCap * W * 8 * 32, vb = (size_t)kLaneCap * sizeof(Cx<R>) * 32;
     keys = reinterpret_cast<uint64_t *>(base);
     vals = reinterpret_cast<Cx<R> *>(base + kb);
-    tkeys = reinterpret_cast<uint64_t *>(base + kb + vb);
-    tvals = reinterpret_cast<Cx<R> *>(base + 2 * kb + vb);
-    rec = reinterpret_cast<uint64_t *>(base + 2 * kb + 2 * vb);
+    rec = reinterpret_cast<uint64_t *>(base + kb + vb);
   }
 
   __device__ __forceinline__ Key<W> key(uint32_t i) const {
@@ -72,16 +74,6 @@ struct LaneShot {
   }
   __device__ __forceinline__ Cx<R> val(uint32_t i) const { return vals[(size_t)i * 32 + lane]; }
   __device__ __forceinline__ void set_val(uint32_t i, Cx<R> v) { vals[(size_t)i * 32 + lane] = v; }
-  __device__ __forceinline__ void set_tkey(uint32_t i, const Key<W> &k) {
-#pragma unroll
-    for (int w = 0; w < W; ++w) tkeys[((size_t)i * W + w) * 32 + lane] = k.w[w];
-  }
-  __device__ __forceinline__ Key<W> tkey(uint32_t i) const {
-    Key<W> k;
-#pragma unroll
-    for (int w = 0; w < W; ++w) k.w[w] = tkeys[((size_t)i * W + w) * 32 + lane];
-    return k;
-  }
   __device__ int find(const Key<W> &k, uint32_t lim) const {
     for (uint32_t j = 0; j < lim; ++j)
       if (keq(key(j), k)) return (int)j;
@@ -332,12 +324,13 @@ struct LaneShot {
   }
 
   // Entry i's pair after the relabel: false if i only feeds the pair of its a0
-  // partner; else a0, v0 = v_{a0} and x1 = xi_{a1} v_{a1} (zero when absent).
+  // partner; else a0, v0 = v_{a0}, x1 = xi_{a1} v_{a1} (zero when absent) and
+  // the index j of the a1 partner that i consumes (-1 if none).
   __device__ bool pair_at(uint32_t i, uint32_t p, const uint64_t *ep, const uint64_t *g2, uint32_t e2, Key<W> &a0,
-                          Cx<R> &v0, Cx<R> &x1) const {
+                          Cx<R> &v0, Cx<R> &x1, int &j) const {
     const Key<W> k = key(i);
     const uint32_t hi = kbit(k, p);
-    const int j = find(kxor(k, ep), n);
+    j = find(kxor(k, ep), n);
     if (hi && j >= 0) return false;
     Cx<R> v1{0, 0};
     v0 = Cx<R>{0, 0};
@@ -379,35 +372,33 @@ struct LaneShot {
       if (kbit(k, p)) set_key(i, kxor(k, J));
     }
     // pair a0 (bit p clear) with a1 = a0 ^ e_p: first the outcome probabilities, then
-    // the combined values (v0 + m x1) / sqrt(2 p_m) into the pairing buffer
+    // the combined values (v0 + m x1) / sqrt(2 p_m)
     double sp = 0.0, sm = 0.0;
     for (uint32_t i = 0; i < n; ++i) {
       Key<W> a0;
       Cx<R> v0, x1;
-      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1)) continue;
+      int j;
+      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1, j)) continue;
       sp += 0.5 * norm2d(cadd(v0, x1));
       sm += 0.5 * norm2d(csub(v0, x1));
     }
     const double pp = snap01(sp / (sp + sm));
     const int m = pick(ord, pp);
     const R sc = inv_sqrt(2.0 * (m == 1 ? sp : sm));
-    const R tau = (R)P.tau;
-    uint32_t o = 0;
+    // In place: a pair's result goes to the slot of the entry that forms it (the a0
+    // member, or a lone a1), and the consumed a1 partner's value is zeroed. Every other
+    // slot keeps its key, so the partner searches of later entries still hold; the
+    // prune then drops the zeroed and the negligible entries, keeping slot order.
     for (uint32_t i = 0; i < n; ++i) {
       Key<W> a0;
       Cx<R> v0, x1;
-      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1)) continue;
-      const Cx<R> nv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
-      if (norm2(nv) < tau) continue;
-      set_tkey(o, a0);
-      tvals[(size_t)o * 32 + lane] = nv;
-      ++o;
+      int j;
+      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1, j)) continue;
+      set_key(i, a0);
+      set_val(i, cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc));
+      if (j >= 0) set_val((uint32_t)j, Cx<R>{0, 0});  // only an a0 entry has a partner here
     }
-    for (uint32_t t = 0; t < o; ++t) {
-      set_key(t, tkey(t));
-      set_val(t, tvals[(size_t)t * 32 + lane]);
-    }
-    n = o;
+    prune();
     // replacement: d_j <- d_j s_p (j in G), d_p <- old s_p, s_p <- m P
 #pragma unroll
     for (int w = 0; w < W; ++w) sd[w] ^= (ssp ? __ldg(&B->G[w]) : 0ull) ^ __ldg(&B->Hd[w]);
@@ -610,6 +601,7 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
       if (s.status == LS_RERUN) {
         const unsigned long long i = atomicAdd(P.n_rerun, 1ull);
         if (i < P.rerun_cap) P.rerun[i] = item;
+        if (P.n_rerun_total) atomicAdd(P.n_rerun_total, 1ull);
       } else {
         atomicAdd(&btally[0], 1ull);
         if (s.status == LS_DISC) atomicAdd(&btally[1], 1ull);

@@ -306,6 +306,30 @@ def test_graph_replayed_chunks(soft, precision):
     assert compare_records(circ, noise, 4, 77, rec, st, ref, precision) <= 1
 
 
+@pytest.mark.parametrize("lanes", [True, False])
+def test_pass_timing(soft, lanes):
+    """Per-pass events: one set per chunk, each pass non-negative, the sum within
+    the run's own events; the pre-pass runs only with lane-per-shot scheduling;
+    runs without the flag, or replayed from a graph, report SOFT_E_ARG."""
+    S = soft
+    circ, noise = C.workload("w42")
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    r = S.soft_run_shots(c, 30000, 0, 1, precision="fp32", chunk_shots=10000, lanes=lanes, time_passes=True)
+    t = S.soft_tally(r)
+    assert t["shots"] == 30000
+    ms, chunks, n_rerun = S.soft_run_pass_timing(r)
+    total, _ = S.soft_run_timing(r)
+    assert chunks == 3 and min(ms) >= 0.0 and ms[1] > 0.0
+    assert (ms[0] > 0.0) == lanes
+    assert 0 <= n_rerun <= 30000 and (n_rerun == 0 or ms[2] > 0.0)
+    assert sum(ms) <= total * 1.01 + 0.01
+    r.free()
+    r = S.soft_run_shots(c, 1000, 0, 1, precision="fp32")
+    with pytest.raises(S.SoftError):
+        S.soft_run_pass_timing(r)
+    r.free()
+
+
 def _run_prefix(S, c, n, seed, precision, prefix, **kw):
     r = S.soft_run_shots(c, n, 0, seed, precision=precision, record_mode=S.REC_ALL, capture_k=48, prefix=prefix,
                          **kw)
