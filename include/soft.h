@@ -176,7 +176,9 @@ typedef struct {
 /* Lane-per-shot scheduling (the default where it applies): one shot per lane,
  * 32 shots per warp. Shots are bucketed by the event they start at, and each
  * warp executes one event at a time for all its lanes, each lane updating its
- * own shot's map (up to 16 entries; larger maps finish in the rerun pass). It
+ * own shot's map (up to 16 entries). A shot whose map outgrows its lane is
+ * rerun from its start by a warp, with a register map of up to first_cap
+ * entries (default 64), and only beyond that at the circuit's cap. It
  * applies to single-circuit runs without state capture or a forced group size,
  * when every map of the circuit's noiseless run fits (at most 16 entries);
  * otherwise a warp (group) runs each shot. SOFT_RUN_NO_LANES always uses the

@@ -44,7 +44,8 @@ struct soft_run {
   double *d_fsum = nullptr;                // fidelity mode: sum of F per circuit
   uint32_t *d_al = nullptr;                // lane-per-shot bucketing buffers
   bool fid_mode = false;
-  unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4], reruns of all chunks
+  unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4], reruns of all chunks,
+                                           // middle pass: next, n_rerun
   uint32_t *d_rerun = nullptr;
   unsigned char *d_slab = nullptr;         // global-memory state for large-cap reruns
   uint8_t *d_status = nullptr;             // circuit 0 only
@@ -305,6 +306,9 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
                      circs[0]->traj_max_n[pk] <= soft::lane_map_cap();
   // a rerun pass finishes the shots whose maps outgrow the first pass (a lane's map, or cap1)
   const bool two_pass = (lanes ? soft::lane_map_cap() : cap1) < cap_max;
+  // after lanes, a middle pass (a warp per shot, register map up to cap1) takes the shots whose
+  // maps outgrew a lane, and only those that outgrow cap1 go on to the pass at the circuit's cap
+  const bool mid_pass = lanes && soft::lane_map_cap() < cap1 && cap1 < cap_max;
   const uint32_t g1 = o.group_size ? o.group_size : 32u;
   const uint32_t g2 = 32;
   const size_t smem_limit = 227 * 1024 - 5 * sizeof(unsigned long long) * soft::kMaxCirc;
@@ -345,8 +349,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   if (lanes) SOFT_ALLOC(r->d_al, (6 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
   r->fid_mode = fid_mode;
   if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
-  SOFT_ALLOC(r->d_work, 9 * sizeof(unsigned long long));
-  if (two_pass) SOFT_ALLOC(r->d_rerun, chunk * sizeof(uint32_t));
+  SOFT_ALLOC(r->d_work, 11 * sizeof(unsigned long long));
+  if (two_pass) SOFT_ALLOC(r->d_rerun, (mid_pass ? 2 : 1) * chunk * sizeof(uint32_t));
   uint32_t slab_blocks = 0;
   if (global_rerun) {
     int sms = 0;
@@ -380,7 +384,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     return cuda_fail(e, "cudaEventCreate");
   }
   if ((e = cudaMemsetAsync(r->d_tally, 0, 5 * n_circ * sizeof(unsigned long long), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(r->d_work, 0, 9 * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(r->d_work, 0, 11 * sizeof(unsigned long long), st)) != cudaSuccess ||
       (fid_mode && (e = cudaMemsetAsync(r->d_fsum, 0, n_circ * sizeof(double), st)) != cudaSuccess)) {
     soft_run_free(r);
     return cuda_fail(e, "cudaMemsetAsync");
@@ -430,6 +434,18 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   q.list = r->d_rerun;
   q.n_items_dev = r->d_work + 2;
   q.next_item = r->d_work + 1;
+  q.n_rerun_total = nullptr;
+  soft::ShotParams m = q;  // middle pass: first list in, second list out
+  if (mid_pass) {
+    m.cap = cap1;
+    m.hs_max = soft::hash_slots_for(cap1);
+    m.small_pass = 1;
+    m.next_item = r->d_work + 9;
+    m.rerun = r->d_rerun + chunk;
+    m.n_rerun = r->d_work + 10;
+    q.list = m.rerun;
+    q.n_items_dev = m.n_rerun;
+  }
   if (global_rerun) {
     q.gslab = r->d_slab;
     q.gslab_blocks = slab_blocks;
@@ -442,11 +458,12 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.al_count = r->d_al + 6 * chunk + (n_ev0 + 2);
     p.al_next = p.al_count + (n_ev0 + 1);
   }
-  soft::LaunchCfg c1{}, c2{};
+  soft::LaunchCfg c1{}, c2{}, cm{};
   p.n_items = std::min(chunk, total);
   if ((e = lanes ? soft::prepare_lanes(p, fp32, W, (int)o.blocks_per_sm, &c1)
                  : soft::prepare_shots(p, fp32, W, g1, (int)o.blocks_per_sm, &c1)) != cudaSuccess ||
-      (two_pass && (e = soft::prepare_shots(q, fp32, W, g2, (int)o.blocks_per_sm, &c2)) != cudaSuccess)) {
+      (two_pass && (e = soft::prepare_shots(q, fp32, W, g2, (int)o.blocks_per_sm, &c2)) != cudaSuccess) ||
+      (mid_pass && (e = soft::prepare_shots(m, fp32, W, g2, (int)o.blocks_per_sm, &cm)) != cudaSuccess)) {
     soft_run_free(r);
     return cuda_fail(e, "shot kernel configuration");
   }
@@ -470,10 +487,12 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   auto enqueue_chunk = [&](uint64_t base, uint64_t cnt, bool dev_base) -> cudaError_t {
     cudaError_t err;
     if ((err = cudaMemsetAsync(r->d_work, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
-    soft::ShotParams a = p, b = q;
-    a.n_items = b.n_items = cnt;
-    a.item_base = b.item_base = base;
-    if (dev_base) a.item_base_dev = b.item_base_dev = r->d_work + 3;
+    if (mid_pass && (err = cudaMemsetAsync(r->d_work + 9, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+      return err;
+    soft::ShotParams a = p, b = q, c = m;
+    a.n_items = b.n_items = c.n_items = cnt;
+    a.item_base = b.item_base = c.item_base = base;
+    if (dev_base) a.item_base_dev = b.item_base_dev = c.item_base_dev = r->d_work + 3;
     if ((err = mark()) != cudaSuccess) return err;
     if (lanes) {
       if ((err = cudaMemsetAsync(a.al_count, 0, 2 * (size_t)(n_ev0 + 1) * sizeof(uint32_t), st)) != cudaSuccess ||
@@ -485,6 +504,10 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
     r->launches++;
     if ((err = mark()) != cudaSuccess) return err;
+    if (mid_pass) {
+      if ((err = soft::launch_prepared(cm, c, st)) != cudaSuccess) return err;
+      r->launches++;
+    }
     if (two_pass) {
       if ((err = soft::launch_prepared(c2, b, st)) != cudaSuccess) return err;
       r->launches++;

@@ -439,10 +439,13 @@ def test_degenerate_circuits(soft, case):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["w42", "w42_rerun_chunks", "tiny6", "random40", "w97"])
+@pytest.mark.parametrize("case", ["w42", "w42_rerun_chunks", "w42_mid32", "tiny6", "random40", "random40_mid32",
+                                  "w97"])
 def test_lane_per_shot_matches_oracle(soft, precision, case):
     """One shot per lane, 32 per warp, event-aligned: records, statuses and
-    tallies against the oracle (and the tallies of the warp-per-shot kernel)."""
+    tallies against the oracle (and the tallies of the warp-per-shot kernel).
+    Shots whose maps outgrow a lane go through the middle pass (a warp, up to
+    first_cap entries) and the pass at the circuit's cap."""
     S = soft
     kw = {}
     n_shots = 3000
@@ -450,6 +453,8 @@ def test_lane_per_shot_matches_oracle(soft, precision, case):
         circ, noise = C.workload("w42")
         if case == "w42_rerun_chunks":
             kw = {"first_cap": 8, "chunk_shots": 1000}
+        elif case == "w42_mid32":
+            kw = {"first_cap": 32, "chunk_shots": 1000}
     elif case == "w97":
         circ, noise = C.workload("w97")
         n_shots = 800
@@ -460,11 +465,15 @@ def test_lane_per_shot_matches_oracle(soft, precision, case):
         circ = C.random_circuit(4040, 40, 400, t_frac=0.2, detectors=True, mpp_frac=0.05)
         circ.cap = 256
         noise = C.Noise(0.005, 0.005, 0.005, 0.005)
+        if case == "random40_mid32":
+            kw = {"first_cap": 32}
     c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
-    r = S.soft_run_shots(c, n_shots, 0, 9, precision=precision, record_mode=S.REC_ALL, **kw)
+    r = S.soft_run_shots(c, n_shots, 0, 9, precision=precision, record_mode=S.REC_ALL, time_passes=True, **kw)
     rec, st = S.soft_get_records(r, n_shots)
     tal = S.soft_tally(r)
     assert S.soft_run_diagnostics(r)[0] == 0
+    if case.startswith("w42"):
+        assert S.soft_run_pass_timing(r)[2] > 0  # some shots left their lane
     ref = oracle.run(circ, circ.n, noise, circ.cap, 9, 0, n_shots, threads=8)
     assert compare_records(circ, noise, 9, 0, rec, st, ref, precision) <= 2
     t2 = S.soft_tally(S.soft_run_shots(c, n_shots, 0, 9, precision=precision, lanes=False, **kw))
