@@ -345,8 +345,9 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   } while (0)
   SOFT_ALLOC(r->d_tally, 5 * n_circ * sizeof(unsigned long long));
   const uint32_t n_ev0 = (uint32_t)circs[0]->hp.ev.size();
-  // lanes: cursors (4 words per item, first: 16-byte aligned), start events, order, bucket starts, counters
-  if (lanes) SOFT_ALLOC(r->d_al, (6 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
+  // lanes: cursors (4 words per item, first: 16-byte aligned), (start event, rank) pairs, order,
+  // bucket starts, counters
+  if (lanes) SOFT_ALLOC(r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
   r->fid_mode = fid_mode;
   if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
   SOFT_ALLOC(r->d_work, 11 * sizeof(unsigned long long));
@@ -453,9 +454,9 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   if (lanes) {  // start events, order, bucket starts, then the two counter arrays (zeroed per chunk)
     p.al_cursor = r->d_al;
     p.al_ev = r->d_al + 4 * chunk;
-    p.al_order = r->d_al + 5 * chunk;
-    p.al_start = r->d_al + 6 * chunk;
-    p.al_count = r->d_al + 6 * chunk + (n_ev0 + 2);
+    p.al_order = r->d_al + 6 * chunk;
+    p.al_start = r->d_al + 7 * chunk;
+    p.al_count = r->d_al + 7 * chunk + (n_ev0 + 2);
     p.al_next = p.al_count + (n_ev0 + 1);
   }
   soft::LaunchCfg c1{}, c2{}, cm{};

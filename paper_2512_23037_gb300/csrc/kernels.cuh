@@ -72,7 +72,8 @@ struct ShotParams {
   int fid_mode;
   // lane-per-shot scheduling of circuit 0 (lane_kernel): per item its start event;
   // bucket e = al_order[al_start[e] .. al_start[e + 1]); claims per bucket
-  uint32_t *al_ev, *al_order, *al_start;
+  uint32_t *al_ev;  // per item (start event, rank in its bucket), 8-byte aligned
+  uint32_t *al_order, *al_start;
   unsigned int *al_count, *al_next;
   uint32_t *al_cursor;  // per item the noise cursor after its first draw (nxt, cur, kblk, w2), 16-byte aligned
   CircDev circ[kMaxCirc];

@@ -75,6 +75,7 @@ struct LaneShot {
   __device__ __forceinline__ Cx<R> val(uint32_t i) const { return vals[(size_t)i * 32 + lane]; }
   __device__ __forceinline__ void set_val(uint32_t i, Cx<R> v) { vals[(size_t)i * 32 + lane] = v; }
   __device__ int find(const Key<W> &k, uint32_t lim) const {
+#pragma unroll 1
     for (uint32_t j = 0; j < lim; ++j)
       if (keq(key(j), k)) return (int)j;
     return -1;
@@ -92,6 +93,7 @@ struct LaneShot {
   __device__ void prune() {
     const R tau = (R)P.tau;
     uint32_t o = 0;
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       const Cx<R> v = val(i);
       if (norm2(v) >= tau) {
@@ -154,11 +156,13 @@ struct LaneShot {
       sd[w] = __ldg(&h->sd[w]);
       ss[w] = __ldg(&h->ss[w]);
     }
+#pragma unroll 1
     for (uint32_t w = 0; w < C->rw; ++w) rec[(size_t)w * 32 + lane] = __ldg(&r_in[w]);
     if (n > kLaneCap) {
       fail_capacity();
       return;
     }
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       Key<W> k;
 #pragma unroll
@@ -170,6 +174,7 @@ struct LaneShot {
 
   // ---- Paulis: v'_{a^beta} = i^{e + 2 gamma.a} v_a
   __device__ void apply_pauli(const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       const Key<W> k = key(i);
       set_val(i, ipow(val(i), e + 2u * kpar(k, gamma)));
@@ -238,6 +243,7 @@ struct LaneShot {
     const R tau = (R)P.tau;
     bool small = false;
     if (diag) {
+#pragma unroll 1
       for (uint32_t i = 0; i < n; ++i) {
         const Cx<R> v = val(i);
         const Cx<R> nv = cadd(cmul(a, v), cmul(b, ipow(v, e + 2u * kpar(key(i), gamma))));
@@ -250,6 +256,7 @@ struct LaneShot {
     const uint32_t lowbit = ev_lowbit(w0);
     const uint32_t n0 = n;
     uint32_t na = 0;
+#pragma unroll 1
     for (uint32_t i = 0; i < n0; ++i) {
       const Key<W> k = key(i);
       const Key<W> pk = kxor(k, beta);
@@ -293,12 +300,14 @@ struct LaneShot {
     }
     const uint32_t sgn = e >> 1;
     bool h0 = false, h1 = false;
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       if (kpar(key(i), gamma) ^ sgn) h1 = true;
       else h0 = true;
     }
     if (!(h0 && h1)) return h1 ? -1 : 1;
     double sp = 0.0, sm = 0.0;
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       const double a2 = norm2d(val(i));
       if (kpar(key(i), gamma) ^ sgn) sm += a2;
@@ -310,6 +319,7 @@ struct LaneShot {
     const uint32_t want = (m == 1) ? 0u : 1u;
     const R tau = (R)P.tau;
     uint32_t o = 0;
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       const Key<W> k = key(i);
       if ((kpar(k, gamma) ^ sgn) != want) continue;
@@ -367,6 +377,7 @@ struct LaneShot {
     if (sdJ ^ __ldg(&B->hdp)) wflip<W>(sd, p);
     const uint32_t e2 = (__ldg(&B->e0b) + 2u * (wbit<W>(sd, p) + wpar<W>(ss, g2))) & 3u;
     // relabel a_j ^= a_p (j in J)
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       const Key<W> k = key(i);
       if (kbit(k, p)) set_key(i, kxor(k, J));
@@ -374,6 +385,7 @@ struct LaneShot {
     // pair a0 (bit p clear) with a1 = a0 ^ e_p: first the outcome probabilities, then
     // the combined values (v0 + m x1) / sqrt(2 p_m)
     double sp = 0.0, sm = 0.0;
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       Key<W> a0;
       Cx<R> v0, x1;
@@ -389,6 +401,7 @@ struct LaneShot {
     // member, or a lone a1), and the consumed a1 partner's value is zeroed. Every other
     // slot keeps its key, so the partner searches of later entries still hold; the
     // prune then drops the zeroed and the negligible entries, keeping slot order.
+#pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       Key<W> a0;
       Cx<R> v0, x1;
@@ -492,19 +505,32 @@ struct LaneShot {
   }
 };
 
-// ---- bucketing pre-pass: start event per item, bucket sizes, starts, order
+// ---- bucketing pre-pass: start event per item, its rank in the bucket, bucket starts, order
+// (lanes of a warp that share a start event, as the shots that begin at the end of the
+// noiseless prefix do, take their ranks with one atomic)
 __global__ void lane_count_kernel(const __grid_constant__ ShotParams P) {
   const CircDev *C = &P.circ[0];
   const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
   const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_items;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  // the loop bound is warp-uniform: blockDim.x is a multiple of 32
+  for (unsigned long long w0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); w0 < n_items;
+       w0 += stride) {
+    const unsigned long long i = w0 + lane;
+    const bool ok = i < n_items;
+    const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok);
+    if (!ok) continue;
     uint32_t cur = 0, kblk = 0, nxt = 0, w2 = 0;
     if (!next_site(C, P.seed, C->first_shot + base + i, cur, kblk, nxt, w2)) kblk = 0xFFFFFFFFu;  // marks a failure
     const uint32_t e = first_event(C, P.fid_mode, nxt);
-    P.al_ev[i] = e;
     reinterpret_cast<uint4 *>(P.al_cursor)[i] = make_uint4(nxt, cur, kblk, w2);
-    atomicAdd(&P.al_count[e], 1u);
+    const uint32_t peers = __match_any_sync(act, e);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t r0 = 0;
+    if (lane == leader) r0 = atomicAdd(&P.al_count[e], (uint32_t)__popc(peers));
+    r0 = __shfl_sync(peers, r0, leader);
+    reinterpret_cast<uint2 *>(P.al_ev)[i] = make_uint2(e, r0 + __popc(peers & ((1u << lane) - 1u)));
   }
 }
 __global__ void lane_scan_kernel(const __grid_constant__ ShotParams P) {
@@ -530,15 +556,13 @@ __global__ void lane_scan_kernel(const __grid_constant__ ShotParams P) {
     P.al_start[k] = run;
     run += P.al_count[k];
   }
-  __syncthreads();
-  for (uint32_t k = lo; k < hi; ++k) P.al_count[k] = 0u;  // reused as fill counters
 }
 __global__ void lane_scatter_kernel(const __grid_constant__ ShotParams P) {
   const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_items;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    const uint32_t e = P.al_ev[i];
-    P.al_order[P.al_start[e] + atomicAdd(&P.al_count[e], 1u)] = (uint32_t)i;
+    const uint2 er = reinterpret_cast<const uint2 *>(P.al_ev)[i];
+    P.al_order[P.al_start[er.x] + er.y] = (uint32_t)i;
   }
 }
 
@@ -614,6 +638,7 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
         if (off < C->out_limit) {
           if (C->status) C->status[off] = (uint8_t)s.status;
           if (C->records)
+#pragma unroll 1
             for (uint32_t w = 0; w < C->rw; ++w) C->records[off * C->rw + w] = s.rec[(size_t)w * 32 + lane];
         }
       }
