@@ -137,19 +137,24 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel_src_hash, name):
+def profile_traffic(kernel_src_hash, name, shots_per_launch):
     """DRAM bytes per launch from the committed ncu summary `name`, if it was
-    taken on the current kernel source."""
+    taken on the current kernel source: a per-launch figure as it stands, or a
+    per-shot figure (traffic that grows with the shots) times the bench's
+    shots per launch."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernel_src_hash:
+        return None
+    t = re.search(r"dram_bytes_per_shot:\s*([0-9.e+]+)", txt)
+    if t:
+        return float(t.group(1)) * shots_per_launch
     t = re.search(r"dram_bytes_per_launch_full:\s*([0-9.e+]+)", txt)
-    if m and t and m.group(1) == kernel_src_hash:
-        return float(t.group(1))
-    return None
+    return float(t.group(1)) if t else None
 
 
 def kernel_hash():
@@ -457,7 +462,9 @@ def main():
     avg_launch_ms = sum(pass_ms)
     achieved = ops_shot * n / (avg_launch_ms / 1000)
     lane_mode = pass_ms[0] > 0
-    traffic = profile_traffic(kernel_hash(), "lane_kernel_w42.md" if lane_mode else "shot_kernel_w42.md")
+    chunks = -(-n // args.chunk) if args.chunk else -(-n // (1 << 24))
+    traffic = profile_traffic(kernel_hash(), "lane_kernel_w42.md" if lane_mode else "shot_kernel_w42.md",
+                              -(-n // chunks))
     line = {
         "metric": "shots/s", "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -28,7 +28,7 @@ enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_R
 #define SOFT_LANE_CAP 16
 #endif
 constexpr uint32_t kLaneCap = SOFT_LANE_CAP;  // map entries per lane
-static_assert(kLaneCap >= 2 && kLaneCap <= 64, "lane map capacity");
+static_assert(kLaneCap >= 2 && kLaneCap <= 16, "lane map capacity (partner indices are 4-bit)");
 constexpr int kLaneBlock = 128;
 
 template <typename R, int W>
@@ -74,11 +74,32 @@ struct LaneShot {
   }
   __device__ __forceinline__ Cx<R> val(uint32_t i) const { return vals[(size_t)i * 32 + lane]; }
   __device__ __forceinline__ void set_val(uint32_t i, Cx<R> v) { vals[(size_t)i * 32 + lane] = v; }
-  __device__ int find(const Key<W> &k, uint32_t lim) const {
+  // Partners (a, a ^ x) differ in bit `bit`, set in x. Each entry with the bit clear
+  // looks for its partner among the entries with it set (mask `him`). Out: `paired`,
+  // the entries with the bit set that have a partner; `has`, those with it clear that
+  // have one; part, the partner's index (4 bits per entry).
+  __device__ void partners(uint32_t n0, uint32_t bit, const uint64_t *x, uint32_t &paired, uint32_t &has,
+                           uint64_t &part) const {
+    uint32_t him = 0;
 #pragma unroll 1
-    for (uint32_t j = 0; j < lim; ++j)
-      if (keq(key(j), k)) return (int)j;
-    return -1;
+    for (uint32_t i = 0; i < n0; ++i) him |= kbit(key(i), bit) << i;
+    paired = has = 0;
+    part = 0;
+#pragma unroll 1
+    for (uint32_t lo = ~him & ((1u << n0) - 1u); lo; lo &= lo - 1u) {
+      const uint32_t i = __ffs(lo) - 1;
+      const Key<W> pk = kxor(key(i), x);
+#pragma unroll 1
+      for (uint32_t m = him & ~paired; m; m &= m - 1u) {
+        const uint32_t j = __ffs(m) - 1;
+        if (keq(key(j), pk)) {
+          paired |= 1u << j;
+          has |= 1u << i;
+          part |= (uint64_t)j << (4 * i);
+          break;
+        }
+      }
+    }
   }
   __device__ void fail_capacity() { status = (P.small_pass && C->cap > kLaneCap) ? LS_RERUN : LS_OVF; }
   __device__ void fail_check(uint32_t code, uint64_t value) {
@@ -253,18 +274,20 @@ struct LaneShot {
       if (small) prune();
       return;
     }
-    const uint32_t lowbit = ev_lowbit(w0);
     const uint32_t n0 = n;
+    uint32_t paired, has;
+    uint64_t part;
+    partners(n0, ev_lowbit(w0), beta, paired, has, part);
     uint32_t na = 0;
 #pragma unroll 1
     for (uint32_t i = 0; i < n0; ++i) {
+      if ((paired >> i) & 1u) continue;  // the pair's member with bit lowbit clear updates both
       const Key<W> k = key(i);
       const Key<W> pk = kxor(k, beta);
-      const int j = find(pk, n0);
       const Cx<R> v = val(i);
-      if (j >= 0) {
-        if (kbit(k, lowbit)) continue;  // the pair's member with bit lowbit clear updates both
-        const Cx<R> vj = val((uint32_t)j);
+      if ((has >> i) & 1u) {
+        const uint32_t j = (uint32_t)(part >> (4 * i)) & 15u;
+        const Cx<R> vj = val(j);
         const Cx<R> ni = cadd(cmul(a, v), cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
         const Cx<R> nj = cadd(cmul(a, vj), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
         set_val(i, ni);
@@ -333,15 +356,13 @@ struct LaneShot {
     return m;
   }
 
-  // Entry i's pair after the relabel: false if i only feeds the pair of its a0
-  // partner; else a0, v0 = v_{a0}, x1 = xi_{a1} v_{a1} (zero when absent) and
-  // the index j of the a1 partner that i consumes (-1 if none).
-  __device__ bool pair_at(uint32_t i, uint32_t p, const uint64_t *ep, const uint64_t *g2, uint32_t e2, Key<W> &a0,
-                          Cx<R> &v0, Cx<R> &x1, int &j) const {
+  // Entry i's pair after the relabel (entry i is not a paired a1): a0, v0 = v_{a0} and
+  // x1 = xi_{a1} v_{a1} (zero when absent); j, the a1 partner that i consumes (-1 if none).
+  __device__ void pair_at(uint32_t i, uint32_t p, const uint64_t *ep, const uint64_t *g2, uint32_t e2, uint32_t has,
+                          uint64_t part, Key<W> &a0, Cx<R> &v0, Cx<R> &x1, int &j) const {
     const Key<W> k = key(i);
-    const uint32_t hi = kbit(k, p);
-    j = find(kxor(k, ep), n);
-    if (hi && j >= 0) return false;
+    const bool hi = kbit(k, p);
+    j = ((has >> i) & 1u) ? (int)((part >> (4 * i)) & 15u) : -1;
     Cx<R> v1{0, 0};
     v0 = Cx<R>{0, 0};
     if (hi) v1 = val(i);
@@ -351,7 +372,6 @@ struct LaneShot {
     }
     a0 = hi ? kxor(k, ep) : k;
     x1 = ipow(v1, e2 + 2u * kpar(kxor(a0, ep), g2));
-    return true;
   }
 
   // ---- measurement of P, beta != 0 (case B): row operations on the signs, relabel,
@@ -384,13 +404,17 @@ struct LaneShot {
     }
     // pair a0 (bit p clear) with a1 = a0 ^ e_p: first the outcome probabilities, then
     // the combined values (v0 + m x1) / sqrt(2 p_m)
+    uint32_t paired, has;
+    uint64_t part;
+    partners(n, p, ep, paired, has, part);
     double sp = 0.0, sm = 0.0;
 #pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
+      if ((paired >> i) & 1u) continue;  // a paired a1 only feeds its a0's pair
       Key<W> a0;
       Cx<R> v0, x1;
       int j;
-      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1, j)) continue;
+      pair_at(i, p, ep, g2, e2, has, part, a0, v0, x1, j);
       sp += 0.5 * norm2d(cadd(v0, x1));
       sm += 0.5 * norm2d(csub(v0, x1));
     }
@@ -398,15 +422,16 @@ struct LaneShot {
     const int m = pick(ord, pp);
     const R sc = inv_sqrt(2.0 * (m == 1 ? sp : sm));
     // In place: a pair's result goes to the slot of the entry that forms it (the a0
-    // member, or a lone a1), and the consumed a1 partner's value is zeroed. Every other
-    // slot keeps its key, so the partner searches of later entries still hold; the
-    // prune then drops the zeroed and the negligible entries, keeping slot order.
+    // member, or a lone a1), and the consumed a1 partner's value is zeroed (the partners
+    // were found before any write); the prune then drops the zeroed and the negligible
+    // entries, keeping slot order.
 #pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
+      if ((paired >> i) & 1u) continue;
       Key<W> a0;
       Cx<R> v0, x1;
       int j;
-      if (!pair_at(i, p, ep, g2, e2, a0, v0, x1, j)) continue;
+      pair_at(i, p, ep, g2, e2, has, part, a0, v0, x1, j);
       set_key(i, a0);
       set_val(i, cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc));
       if (j >= 0) set_val((uint32_t)j, Cx<R>{0, 0});  // only an a0 entry has a partner here
