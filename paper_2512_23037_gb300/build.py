@@ -12,7 +12,7 @@ LIB = os.path.join(OUT, "libsoft.so")
 SOURCES = ["compile.cpp", "kernels.cu", "lanes.cu", "api.cu", "noalloc.cu", "adjoint.cu", "grad_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-for _v in ("SOFT_MIN_BLOCKS_F32", "SOFT_MIN_BLOCKS_F64", "SOFT_GRAD_MIN_BLOCKS", "SOFT_LANE_CAP"):  # budget experiments
+for _v in ("SOFT_MIN_BLOCKS_F32", "SOFT_MIN_BLOCKS_F64", "SOFT_GRAD_MIN_BLOCKS", "SOFT_LANE_CAP", "SOFT_LANE_EVICT", "SOFT_LANE_ROUNDS"):  # budget experiments
     if os.environ.get(_v):
         FLAGS += [f"-D{_v}={int(os.environ[_v])}"]
 

@@ -43,6 +43,8 @@ struct soft_run {
   unsigned long long *d_tally = nullptr;   // 5 counters per circuit
   double *d_fsum = nullptr;                // fidelity mode: sum of F per circuit
   uint32_t *d_al = nullptr;                // lane-per-shot bucketing buffers
+  unsigned char *d_sp = nullptr;           // lane-per-shot spill pool (shots evicted between rounds)
+  unsigned long long *d_lr = nullptr;      // its record count and each round's record range
   bool fid_mode = false;
   unsigned long long *d_work = nullptr;    // next1, next2, n_rerun, item_base, diag[4], reruns of all chunks,
                                            // middle pass: next, n_rerun
@@ -216,6 +218,8 @@ void soft_run_free(soft_run *r) {
   cudaFree(r->d_tally);
   cudaFree(r->d_fsum);
   cudaFree(r->d_al);
+  cudaFree(r->d_sp);
+  cudaFree(r->d_lr);
   cudaFree(r->d_work);
   cudaFree(r->d_rerun);
   cudaFree(r->d_slab);
@@ -348,6 +352,15 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   // lanes: cursors (4 words per item, first: 16-byte aligned), (start event, rank) pairs, order,
   // bucket starts, counters
   if (lanes) SOFT_ALLOC(r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
+  // spill pool for the shots a sparse warp evicts: a quarter of the chunk (when it is full,
+  // warps keep their shots)
+  const uint32_t rounds = lanes ? soft::lane_rounds() : 1u;
+  const uint32_t sp_cap = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 4);
+  const size_t n_lr = 3 + 2 * (size_t)rounds;
+  if (rounds > 1) {
+    SOFT_ALLOC(r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_cap));
+    SOFT_ALLOC(r->d_lr, n_lr * sizeof(unsigned long long));
+  }
   r->fid_mode = fid_mode;
   if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
   SOFT_ALLOC(r->d_work, 11 * sizeof(unsigned long long));
@@ -458,6 +471,11 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.al_start = r->d_al + 7 * chunk;
     p.al_count = r->d_al + 7 * chunk + (n_ev0 + 2);
     p.al_next = p.al_count + (n_ev0 + 1);
+    p.lane_round = 0;
+    p.lane_evict = rounds > 1 ? 1u : 0u;
+    p.sp = r->d_sp;
+    p.sp_cap = sp_cap;
+    p.lr = r->d_lr;
   }
   soft::LaunchCfg c1{}, c2{}, cm{};
   p.n_items = std::min(chunk, total);
@@ -502,8 +520,22 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
       r->launches += 3;
     }
     if ((err = mark(lanes)) != cudaSuccess) return err;
+    if (rounds > 1 && (err = cudaMemsetAsync(r->d_lr, 0, n_lr * sizeof(unsigned long long), st)) != cudaSuccess)
+      return err;
     if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
     r->launches++;
+    // later rounds: the evicted shots, bucketed by the event they resume at
+    for (uint32_t rd = 1; rd < rounds; ++rd) {
+      soft::ShotParams ar = a;
+      ar.lane_round = rd;
+      ar.lane_evict = rd + 1 < rounds ? 1u : 0u;
+      ar.n_items_dev = r->d_lr + 2 + 2 * rd;
+      if ((err = cudaMemsetAsync(ar.al_count, 0, 2 * (size_t)(n_ev0 + 1) * sizeof(uint32_t), st)) != cudaSuccess ||
+          (err = soft::launch_lane_resume_prepass(ar, fp32, W, st)) != cudaSuccess ||
+          (err = soft::launch_prepared(c1, ar, st)) != cudaSuccess)
+        return err;
+      r->launches += 5;
+    }
     if ((err = mark()) != cudaSuccess) return err;
     if (mid_pass) {
       if ((err = soft::launch_prepared(cm, c, st)) != cudaSuccess) return err;

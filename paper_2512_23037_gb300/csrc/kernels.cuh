@@ -76,6 +76,13 @@ struct ShotParams {
   uint32_t *al_order, *al_start;
   unsigned int *al_count, *al_next;
   uint32_t *al_cursor;  // per item the noise cursor after its first draw (nxt, cur, kblk, w2), 16-byte aligned
+  // lane-per-shot rounds: a warp left with few active lanes evicts their shots to the spill
+  // pool; the next round buckets them by the event they resume at and packs them into warps
+  uint32_t lane_round;        // 0: shots from their start buckets; r >= 1: shots evicted before round r
+  uint32_t lane_evict;        // 1: this round may evict
+  unsigned char *sp;          // spill pool, sp_cap records (layout: lane_spill_bytes)
+  uint32_t sp_cap;
+  unsigned long long *lr;     // [0] records taken; round r >= 1: [1 + 2r] its first record, [2 + 2r] its count
   CircDev circ[kMaxCirc];
 };
 
@@ -111,6 +118,10 @@ struct LaunchCfg {
 // Lane-per-shot kernel (lanes.cu): the bucketing pre-pass (start events, bucket
 // starts, order), its launch shape, and its map capacity per shot.
 cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st);
+// round r >= 1: the range of records evicted before it, then their buckets
+cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W, cudaStream_t st);
+size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap);
+uint32_t lane_rounds();
 cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg);
 uint32_t lane_map_cap();
 

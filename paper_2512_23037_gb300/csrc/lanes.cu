@@ -11,6 +11,14 @@
 // ends the shot as a rerun; the rerun pass of the warp-per-shot kernel finishes
 // it at the full capacity. The per-shot arithmetic is that of the warp-per-shot
 // kernel (the same formulas, pruning thresholds and outcome rule), entry by entry.
+//
+// Most shots end at the first detector after their first error, but a few run to
+// the end of the circuit, and they would hold a warp with a few active lanes. So a
+// warp left with at most kEvictBelow active lanes writes their shots' state to a
+// spill pool and moves on to fresh shots. The next round (another launch) buckets
+// the evicted shots by the event they resume at, and packs them into warps again.
+// The last round evicts nothing. Which lane runs a shot does not change its
+// arithmetic, so the results are those of a single round.
 #include <cooperative_groups.h>
 
 #include "device_common.cuh"
@@ -30,6 +38,50 @@ enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_R
 constexpr uint32_t kLaneCap = SOFT_LANE_CAP;  // map entries per lane
 static_assert(kLaneCap >= 2 && kLaneCap <= 16, "lane map capacity (partner indices are 4-bit)");
 constexpr int kLaneBlock = 128;
+#ifndef SOFT_LANE_EVICT
+#define SOFT_LANE_EVICT 8
+#endif
+constexpr uint32_t kEvictBelow = SOFT_LANE_EVICT;  // a warp with this many active lanes or fewer evicts them
+#ifndef SOFT_LANE_ROUNDS
+#define SOFT_LANE_ROUNDS 2
+#endif
+constexpr uint32_t kLaneRounds = SOFT_LANE_ROUNDS;  // rounds per chunk, the last without eviction
+static_assert(kLaneRounds >= 1 && kLaneRounds <= 8, "lane rounds");
+
+// Spill pool, structure of arrays over cap records: header (item, resume event, n,
+// flags), cursor (nxt, cur, kblk, w2), F, signs, record words, keys, values.
+template <typename R, int W>
+struct Spill {
+  uint4 *ha, *hb;
+  double *fid;
+  uint64_t *sd, *ss, *rec, *keys;
+  Cx<R> *vals;
+  uint32_t cap;
+  __host__ __device__ static size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+  __host__ __device__ static size_t bytes(uint32_t cap, uint32_t rw) {
+    const size_t c = cap;
+    return 2 * al16(c * 16) + al16(c * 8) + 2 * al16(c * 8 * W) + al16(c * 8 * rw) + al16(c * 8 * W * kLaneCap) +
+           al16(c * sizeof(Cx<R>) * kLaneCap);
+  }
+  __device__ Spill(unsigned char *b, uint32_t cap_, uint32_t rw) : cap(cap_) {
+    const size_t c = cap;
+    ha = reinterpret_cast<uint4 *>(b);
+    b += al16(c * 16);
+    hb = reinterpret_cast<uint4 *>(b);
+    b += al16(c * 16);
+    fid = reinterpret_cast<double *>(b);
+    b += al16(c * 8);
+    sd = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * W);
+    ss = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * W);
+    rec = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * rw);
+    keys = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * W * kLaneCap);
+    vals = reinterpret_cast<Cx<R> *>(b);
+  }
+};
 
 template <typename R, int W>
 __host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
@@ -191,6 +243,67 @@ struct LaneShot {
       set_key(i, k);
       set_val(i, v_in[i]);
     }
+  }
+
+  // ---- eviction: the shot's whole state into record r, to resume at event ev
+  __device__ void evict(const Spill<R, W> &S, uint32_t r, uint32_t item, uint32_t ev) const {
+    const size_t c = S.cap;
+    S.ha[r] = make_uint4(item, ev, n, (uint32_t)(chain & 1) | ((uint32_t)(logical & 1) << 1) |
+                                          (((uint32_t)lastm & 255u) << 8));
+    S.hb[r] = make_uint4(nxt, cur, kblk, w2);
+    S.fid[r] = fid;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      S.sd[w * c + r] = sd[w];
+      S.ss[w * c + r] = ss[w];
+    }
+#pragma unroll 1
+    for (uint32_t w = 0; w < C->rw; ++w) S.rec[w * c + r] = rec[(size_t)w * 32 + lane];
+#pragma unroll 1
+    for (uint32_t i = 0; i < n; ++i) {
+      const Key<W> k = key(i);
+#pragma unroll
+      for (int w = 0; w < W; ++w) S.keys[((size_t)i * W + w) * c + r] = k.w[w];
+      S.vals[(size_t)i * c + r] = val(i);
+    }
+  }
+  // ---- resumption from record r; returns the shot's item (chunk-local index)
+  __device__ uint32_t resume(const Spill<R, W> &S, uint32_t r, uint64_t first) {
+    const size_t c = S.cap;
+    const uint4 a = S.ha[r], b = S.hb[r];
+    shot = first + a.x;
+    status = LS_RUN;
+    force = false;
+    n = a.z;
+    chain = (int)(a.w & 1u);
+    logical = (int)((a.w >> 1) & 1u);
+    lastm = (int)(int8_t)((a.w >> 8) & 255u);
+    nxt = b.x;
+    cur = b.y;
+    kblk = b.z;
+    w2 = b.w;
+    fid = S.fid[r];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      sd[w] = S.sd[w * c + r];
+      ss[w] = S.ss[w * c + r];
+    }
+#pragma unroll 1
+    for (uint32_t w = 0; w < C->rw; ++w) rec[(size_t)w * 32 + lane] = S.rec[w * c + r];
+    if (n > kLaneCap) {  // a record never holds more; checked so that a bad record cannot index past the map
+      fail_check(CHK_NNZ, n);
+      n = 0;
+      return a.x;
+    }
+#pragma unroll 1
+    for (uint32_t i = 0; i < n; ++i) {
+      Key<W> k;
+#pragma unroll
+      for (int w = 0; w < W; ++w) k.w[w] = S.keys[((size_t)i * W + w) * c + r];
+      set_key(i, k);
+      set_val(i, S.vals[(size_t)i * c + r]);
+    }
+    return a.x;
   }
 
   // ---- Paulis: v'_{a^beta} = i^{e + 2 gamma.a} v_a
@@ -591,6 +704,40 @@ __global__ void lane_scatter_kernel(const __grid_constant__ ShotParams P) {
   }
 }
 
+// ---- round r >= 1: its records are those taken since round r - 1 began (the pool's
+// count, capped at its capacity: reservations past it were not written)
+__global__ void lane_round_setup_kernel(const __grid_constant__ ShotParams P) {
+  const unsigned long long used = P.lr[0] < P.sp_cap ? P.lr[0] : P.sp_cap;
+  const uint32_t r = P.lane_round;
+  const unsigned long long first = r == 1 ? 0ull : P.lr[1 + 2 * (r - 1)] + P.lr[2 + 2 * (r - 1)];
+  P.lr[1 + 2 * r] = first;
+  P.lr[2 + 2 * r] = used > first ? used - first : 0ull;
+}
+template <typename R, int W>
+__global__ void lane_count_resume_kernel(const __grid_constant__ ShotParams P) {
+  const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
+  const uint32_t n_ev = P.circ[0].n_events;
+  const unsigned long long n_items = P.lr[2 + 2 * P.lane_round];
+  const unsigned long long first = P.lr[1 + 2 * P.lane_round];
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); w0 < n_items;
+       w0 += stride) {
+    const unsigned long long i = w0 + lane;
+    const bool ok = i < n_items;
+    const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok);
+    if (!ok) continue;
+    uint32_t e = S.ha[first + i].y;
+    if (e > n_ev) e = n_ev;  // a record always resumes at an event of the circuit
+    const uint32_t peers = __match_any_sync(act, e);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t r0 = 0;
+    if (lane == leader) r0 = atomicAdd(&P.al_count[e], (uint32_t)__popc(peers));
+    r0 = __shfl_sync(peers, r0, leader);
+    reinterpret_cast<uint2 *>(P.al_ev)[i] = make_uint2(e, r0 + __popc(peers & ((1u << lane) - 1u)));
+  }
+}
+
 template <typename R, int W>
 __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -602,8 +749,11 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
   const CircDev *C = &P.circ[0];
   const uint32_t n_ev = C->n_events;
   const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
-  const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
   const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
+  const unsigned long long n_items =
+      P.lane_round ? P.lr[2 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
+  const unsigned long long rec0 = P.lane_round ? P.lr[1 + 2 * P.lane_round] : 0ull;
+  const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
   bool active = false;
   // warps start spread evenly over the events, so that they meet buckets that still hold shots
   const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x / 32) + warp;
@@ -625,7 +775,8 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
           item = __ldg(&P.al_order[b0 + k]);
           if (item < n_items) {
             active = true;
-            s.begin(C->first_shot + base + item, e, reinterpret_cast<const uint4 *>(P.al_cursor)[item]);
+            if (P.lane_round) item = s.resume(S, (uint32_t)(rec0 + item), C->first_shot + base);
+            else s.begin(C->first_shot + base + item, e, reinterpret_cast<const uint4 *>(P.al_cursor)[item]);
           }
         }
       }
@@ -669,6 +820,24 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
       }
       active = false;
     }
+    // few active lanes: their shots go to the spill pool (when it has room), to resume in
+    // the next round packed with others, and the warp moves on to fresh shots
+    if (P.lane_evict) {
+      const uint32_t am = __ballot_sync(0xFFFFFFFFu, active);
+      if (am && (uint32_t)__popc(am) <= kEvictBelow && e + 1u < n_ev) {
+        const uint32_t leader = __ffs(am) - 1;
+        unsigned long long r0 = 0;
+        if (lane == leader) r0 = atomicAdd(&P.lr[0], (unsigned long long)__popc(am));
+        r0 = __shfl_sync(0xFFFFFFFFu, r0, leader);
+        if (active) {
+          const unsigned long long r = r0 + __popc(am & ((1u << lane) - 1u));
+          if (r < P.sp_cap) {
+            s.evict(S, (uint32_t)r, item, e + 1u);
+            active = false;
+          }
+        }
+      }
+    }
     uint32_t en = e + 1u > n_ev ? 0u : e + 1u;
     if (!__any_sync(0xFFFFFFFFu, active)) {
       // all lanes idle: the next bucket (cyclically) that still has shots, or stop
@@ -702,6 +871,30 @@ size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw) {
 }
 
 uint32_t lane_map_cap() { return kLaneCap; }
+uint32_t lane_rounds() { return kLaneRounds; }
+
+size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap) {
+  return fp32 ? (W == 1 ? Spill<float, 1>::bytes(cap, rw) : Spill<float, 2>::bytes(cap, rw))
+              : (W == 1 ? Spill<double, 1>::bytes(cap, rw) : Spill<double, 2>::bytes(cap, rw));
+}
+
+cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W, cudaStream_t st) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * 8u;
+  lane_round_setup_kernel<<<1, 1, 0, st>>>(p);
+  if (fp32) {
+    if (W == 1) lane_count_resume_kernel<float, 1><<<grid, 256, 0, st>>>(p);
+    else lane_count_resume_kernel<float, 2><<<grid, 256, 0, st>>>(p);
+  } else {
+    if (W == 1) lane_count_resume_kernel<double, 1><<<grid, 256, 0, st>>>(p);
+    else lane_count_resume_kernel<double, 2><<<grid, 256, 0, st>>>(p);
+  }
+  lane_scan_kernel<<<1, 1024, 0, st>>>(p);
+  lane_scatter_kernel<<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st) {
   int dev = 0, sms = 1;
