@@ -352,13 +352,17 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   // lanes: cursors (4 words per item, first: 16-byte aligned), (start event, rank) pairs, order,
   // bucket starts, counters
   if (lanes) SOFT_ALLOC(r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
-  // spill pool for the shots a sparse warp evicts: a quarter of the chunk (when it is full,
-  // warps keep their shots)
+  // spill pool: records for the shots a sparse warp evicts (a quarter of the chunk; when it is
+  // full, warps keep their shots), then records for shots a lane hands to a warp (an eighth;
+  // when full, the warp reruns them from their start). Entries of the rerun list name a record
+  // with their top bit, so a chunk stays below 2^31 items for it.
   const uint32_t rounds = lanes ? soft::lane_rounds() : 1u;
-  const uint32_t sp_cap = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 4);
-  const size_t n_lr = 3 + 2 * (size_t)rounds;
-  if (rounds > 1) {
-    SOFT_ALLOC(r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_cap));
+  const bool spill = lanes && (rounds > 1 || two_pass) && chunk < (1ull << 31);
+  const uint32_t sp_evict = rounds > 1 ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 4) : 0u;
+  const uint32_t sp_hand = two_pass ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 8) : 0u;
+  const size_t n_lr = 4 + 2 * (size_t)rounds;
+  if (spill) {
+    SOFT_ALLOC(r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_evict + sp_hand));
     SOFT_ALLOC(r->d_lr, n_lr * sizeof(unsigned long long));
   }
   r->fid_mode = fid_mode;
@@ -472,10 +476,16 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.al_count = r->d_al + 7 * chunk + (n_ev0 + 2);
     p.al_next = p.al_count + (n_ev0 + 1);
     p.lane_round = 0;
-    p.lane_evict = rounds > 1 ? 1u : 0u;
-    p.sp = r->d_sp;
-    p.sp_cap = sp_cap;
-    p.lr = r->d_lr;
+    p.lane_evict = spill && rounds > 1 ? 1u : 0u;
+    p.sp = spill ? r->d_sp : nullptr;
+    p.sp_cap = spill ? sp_evict + sp_hand : 0u;
+    p.sp_evict_cap = spill ? sp_evict : 0u;
+    p.lr = spill ? r->d_lr : nullptr;
+    // the middle pass (or, without one, the pass at the circuit's cap) resumes handed-over shots
+    soft::ShotParams &h = mid_pass ? m : q;
+    h.sp = p.sp;
+    h.sp_cap = p.sp_cap;
+    h.sp_evict_cap = p.sp_evict_cap;
   }
   soft::LaunchCfg c1{}, c2{}, cm{};
   p.n_items = std::min(chunk, total);
@@ -520,16 +530,16 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
       r->launches += 3;
     }
     if ((err = mark(lanes)) != cudaSuccess) return err;
-    if (rounds > 1 && (err = cudaMemsetAsync(r->d_lr, 0, n_lr * sizeof(unsigned long long), st)) != cudaSuccess)
+    if (spill && (err = cudaMemsetAsync(r->d_lr, 0, n_lr * sizeof(unsigned long long), st)) != cudaSuccess)
       return err;
     if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
     r->launches++;
     // later rounds: the evicted shots, bucketed by the event they resume at
-    for (uint32_t rd = 1; rd < rounds; ++rd) {
+    for (uint32_t rd = 1; spill && rd < rounds; ++rd) {
       soft::ShotParams ar = a;
       ar.lane_round = rd;
       ar.lane_evict = rd + 1 < rounds ? 1u : 0u;
-      ar.n_items_dev = r->d_lr + 2 + 2 * rd;
+      ar.n_items_dev = r->d_lr + 3 + 2 * rd;
       if ((err = cudaMemsetAsync(ar.al_count, 0, 2 * (size_t)(n_ev0 + 1) * sizeof(uint32_t), st)) != cudaSuccess ||
           (err = soft::launch_lane_resume_prepass(ar, fp32, W, st)) != cudaSuccess ||
           (err = soft::launch_prepared(c1, ar, st)) != cudaSuccess)

@@ -859,11 +859,68 @@ struct Shot {
     force = false;
   }
 
-  __device__ void run(uint64_t s) {
+  // A shot handed over by a lane: its whole state at the top of its resume event,
+  // which is returned.
+  __device__ uint32_t load_spill(uint32_t r) {
+    const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
+    const size_t c = S.cap;
+    const uint4 a = S.ha[r], b = S.hb[r];
+    nnz = a.z;
+    chain = (int)(a.w & 1u);
+    logical = (int)((a.w >> 1) & 1u);
+    lastm = (int)(int8_t)((a.w >> 8) & 255u);
+    nxt = b.x;
+    cur = b.y;
+    kblk = b.z;
+    w2 = b.w;
+    fid = S.fid[r];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      sd[w] = S.sd[w * c + r];
+      ss[w] = S.ss[w * c + r];
+    }
+    for (uint32_t w = lane; w < C->rw; w += G) rec[w] = S.rec[w * c + r];
+    if (nnz > kLaneCap || a.y >= C->n_events) {  // a record never holds more, nor resumes past the end
+      fail_check(CHK_NNZ, nnz);
+      return C->n_events;
+    }
+    if (nnz > ecap) {
+      fail_capacity();
+      return a.y;
+    }
+    if (kRegCapable && nnz <= (uint32_t)G) {
+      reg = true;
+      if (lane < nnz) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) rk.w[w] = S.keys[((size_t)lane * W + w) * c + r];
+        rv = S.vals[(size_t)lane * c + r];
+      }
+      t.sync();
+    } else {
+      for (uint32_t i = lane; i < nnz; i += G) {
+        Key<W> k;
+#pragma unroll
+        for (int w = 0; w < W; ++w) k.w[w] = S.keys[((size_t)i * W + w) * c + r];
+        set_key(i, k);
+        vals[i] = S.vals[(size_t)i * c + r];
+      }
+      t.sync();
+      reg = false;
+      rebuild();
+    }
+    return a.y;
+  }
+
+  // rec: a spill record to resume from, or kNoRecord
+  __device__ void run(uint64_t s, uint32_t r = kNoRecord) {
     init_shot(s);
-    draw_next();
     uint32_t ev0 = 0;
-    if (C->traj) ev0 = load_prefix();  // every event before the first error is the noiseless run's
+    if (r != kNoRecord) {
+      ev0 = load_spill(r);
+    } else {
+      draw_next();
+      if (C->traj) ev0 = load_prefix();  // every event before the first error is the noiseless run's
+    }
     const uint32_t n_events = C->n_events;
     for (uint32_t ev = ev0; ev < n_events && status == ST_RUN; ++ev) step(ev);
     if (status == ST_RUN) status = ST_KEPT;
@@ -1062,7 +1119,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 :
     item = tile.shfl(item, 0);
     if (item >= n_items) break;
     if (P.list && item >= P.rerun_cap) break;  // a list never holds more than its capacity
-    const uint64_t local = P.list ? (uint64_t)P.list[item] : (uint64_t)item;
+    uint64_t local = P.list ? (uint64_t)P.list[item] : (uint64_t)item;
+    uint32_t rec = kNoRecord;  // an entry naming a spill record resumes the shot a lane handed over
+    if (P.list && (local & kSpillRef) && P.sp) {
+      rec = (uint32_t)local & ~kSpillRef;
+      if (rec >= P.sp_cap) break;  // never: records are taken below the pool's capacity
+      local = Spill<R, W>(P.sp, P.sp_cap, P.rw_max).ha[rec].x;
+    }
     const uint64_t g = item_base + local;
     // circuit of item g: the last one whose item range starts at or before g
     uint32_t lo = 0, hi = n_circ;
@@ -1073,7 +1136,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? SOFT_MIN_BLOCKS_F32 :
     }
     s.C = &P.circ[lo];
     const uint64_t off = g - s.C->item_begin;
-    s.run(s.C->first_shot + off);
+    s.run(s.C->first_shot + off, rec);
     s.finish(local, off, lo, btally);
   }
   __syncthreads();

@@ -80,9 +80,11 @@ struct ShotParams {
   // pool; the next round buckets them by the event they resume at and packs them into warps
   uint32_t lane_round;        // 0: shots from their start buckets; r >= 1: shots evicted before round r
   uint32_t lane_evict;        // 1: this round may evict
-  unsigned char *sp;          // spill pool, sp_cap records (layout: lane_spill_bytes)
-  uint32_t sp_cap;
-  unsigned long long *lr;     // [0] records taken; round r >= 1: [1 + 2r] its first record, [2 + 2r] its count
+  unsigned char *sp;          // spill pool, sp_cap records (layout: lane_spill_bytes): evictions in
+  uint32_t sp_cap;            // [0, sp_evict_cap), shots handed from a lane to a warp after that
+  uint32_t sp_evict_cap;
+  unsigned long long *lr;     // [0] eviction records taken, [1] handover records taken;
+                              // round r >= 1: [2 + 2r] its first record, [3 + 2r] its count
   CircDev circ[kMaxCirc];
 };
 

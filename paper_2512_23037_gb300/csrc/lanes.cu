@@ -31,12 +31,7 @@ namespace {
 using namespace dev;
 namespace cg = cooperative_groups;
 
-enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_RERUN = 4 };
-#ifndef SOFT_LANE_CAP
-#define SOFT_LANE_CAP 16
-#endif
-constexpr uint32_t kLaneCap = SOFT_LANE_CAP;  // map entries per lane
-static_assert(kLaneCap >= 2 && kLaneCap <= 16, "lane map capacity (partner indices are 4-bit)");
+enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_RERUN = 4, LS_HAND = 5 };
 constexpr int kLaneBlock = 128;
 #ifndef SOFT_LANE_EVICT
 #define SOFT_LANE_EVICT 8
@@ -48,40 +43,6 @@ constexpr uint32_t kEvictBelow = SOFT_LANE_EVICT;  // a warp with this many acti
 constexpr uint32_t kLaneRounds = SOFT_LANE_ROUNDS;  // rounds per chunk, the last without eviction
 static_assert(kLaneRounds >= 1 && kLaneRounds <= 8, "lane rounds");
 
-// Spill pool, structure of arrays over cap records: header (item, resume event, n,
-// flags), cursor (nxt, cur, kblk, w2), F, signs, record words, keys, values.
-template <typename R, int W>
-struct Spill {
-  uint4 *ha, *hb;
-  double *fid;
-  uint64_t *sd, *ss, *rec, *keys;
-  Cx<R> *vals;
-  uint32_t cap;
-  __host__ __device__ static size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
-  __host__ __device__ static size_t bytes(uint32_t cap, uint32_t rw) {
-    const size_t c = cap;
-    return 2 * al16(c * 16) + al16(c * 8) + 2 * al16(c * 8 * W) + al16(c * 8 * rw) + al16(c * 8 * W * kLaneCap) +
-           al16(c * sizeof(Cx<R>) * kLaneCap);
-  }
-  __device__ Spill(unsigned char *b, uint32_t cap_, uint32_t rw) : cap(cap_) {
-    const size_t c = cap;
-    ha = reinterpret_cast<uint4 *>(b);
-    b += al16(c * 16);
-    hb = reinterpret_cast<uint4 *>(b);
-    b += al16(c * 16);
-    fid = reinterpret_cast<double *>(b);
-    b += al16(c * 8);
-    sd = reinterpret_cast<uint64_t *>(b);
-    b += al16(c * 8 * W);
-    ss = reinterpret_cast<uint64_t *>(b);
-    b += al16(c * 8 * W);
-    rec = reinterpret_cast<uint64_t *>(b);
-    b += al16(c * 8 * rw);
-    keys = reinterpret_cast<uint64_t *>(b);
-    b += al16(c * 8 * W * kLaneCap);
-    vals = reinterpret_cast<Cx<R> *>(b);
-  }
-};
 
 template <typename R, int W>
 __host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
@@ -391,6 +352,12 @@ struct LaneShot {
     uint32_t paired, has;
     uint64_t part;
     partners(n0, ev_lowbit(w0), beta, paired, has, part);
+    // every entry without a partner gains one: if that outgrows the lane, nothing has
+    // been written yet, and a warp can take the shot over at the top of this event
+    if (n0 + (n0 - 2u * (uint32_t)__popc(has)) > kLaneCap && P.sp && P.small_pass && C->cap > kLaneCap) {
+      status = LS_HAND;
+      return;
+    }
     uint32_t na = 0;
 #pragma unroll 1
     for (uint32_t i = 0; i < n0; ++i) {
@@ -639,6 +606,13 @@ struct LaneShot {
       }
       default: break;
     }
+    if (status == LS_HAND) {  // back to the top of the event: the signs as before its XOR
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        sd[w] ^= dsd[w];
+        ss[w] ^= dss[w];
+      }
+    }
     (void)ev;
   }
 };
@@ -707,18 +681,18 @@ __global__ void lane_scatter_kernel(const __grid_constant__ ShotParams P) {
 // ---- round r >= 1: its records are those taken since round r - 1 began (the pool's
 // count, capped at its capacity: reservations past it were not written)
 __global__ void lane_round_setup_kernel(const __grid_constant__ ShotParams P) {
-  const unsigned long long used = P.lr[0] < P.sp_cap ? P.lr[0] : P.sp_cap;
+  const unsigned long long used = P.lr[0] < P.sp_evict_cap ? P.lr[0] : P.sp_evict_cap;
   const uint32_t r = P.lane_round;
-  const unsigned long long first = r == 1 ? 0ull : P.lr[1 + 2 * (r - 1)] + P.lr[2 + 2 * (r - 1)];
-  P.lr[1 + 2 * r] = first;
-  P.lr[2 + 2 * r] = used > first ? used - first : 0ull;
+  const unsigned long long first = r == 1 ? 0ull : P.lr[2 + 2 * (r - 1)] + P.lr[3 + 2 * (r - 1)];
+  P.lr[2 + 2 * r] = first;
+  P.lr[3 + 2 * r] = used > first ? used - first : 0ull;
 }
 template <typename R, int W>
 __global__ void lane_count_resume_kernel(const __grid_constant__ ShotParams P) {
   const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
   const uint32_t n_ev = P.circ[0].n_events;
-  const unsigned long long n_items = P.lr[2 + 2 * P.lane_round];
-  const unsigned long long first = P.lr[1 + 2 * P.lane_round];
+  const unsigned long long n_items = P.lr[3 + 2 * P.lane_round];
+  const unsigned long long first = P.lr[2 + 2 * P.lane_round];
   const uint32_t lane = threadIdx.x & 31u;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long w0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); w0 < n_items;
@@ -751,8 +725,8 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
   const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
   const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
   const unsigned long long n_items =
-      P.lane_round ? P.lr[2 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
-  const unsigned long long rec0 = P.lane_round ? P.lr[1 + 2 * P.lane_round] : 0ull;
+      P.lane_round ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
+  const unsigned long long rec0 = P.lane_round ? P.lr[2 + 2 * P.lane_round] : 0ull;
   const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
   bool active = false;
   // warps start spread evenly over the events, so that they meet buckets that still hold shots
@@ -798,9 +772,19 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
     if (active && (s.status != LS_RUN || e + 1u >= n_ev)) {
       if (s.status == LS_RUN) s.status = LS_KEPT;
       const uint64_t off = base + item;
+      uint32_t entry = item;  // a rerun starts the shot again from its start
+      if (s.status == LS_HAND) {  // or a warp resumes it from its state at the top of event e
+        const unsigned long long h = atomicAdd(&P.lr[1], 1ull);
+        if (h < (unsigned long long)(P.sp_cap - P.sp_evict_cap)) {
+          const uint32_t r = P.sp_evict_cap + (uint32_t)h;
+          s.evict(S, r, item, e);
+          entry = kSpillRef | r;
+        }
+        s.status = LS_RERUN;
+      }
       if (s.status == LS_RERUN) {
         const unsigned long long i = atomicAdd(P.n_rerun, 1ull);
-        if (i < P.rerun_cap) P.rerun[i] = item;
+        if (i < P.rerun_cap) P.rerun[i] = entry;
         if (P.n_rerun_total) atomicAdd(P.n_rerun_total, 1ull);
       } else {
         atomicAdd(&btally[0], 1ull);
@@ -831,7 +815,7 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
         r0 = __shfl_sync(0xFFFFFFFFu, r0, leader);
         if (active) {
           const unsigned long long r = r0 + __popc(am & ((1u << lane) - 1u));
-          if (r < P.sp_cap) {
+          if (r < P.sp_evict_cap) {
             s.evict(S, (uint32_t)r, item, e + 1u);
             active = false;
           }

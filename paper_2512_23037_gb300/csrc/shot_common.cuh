@@ -1,6 +1,7 @@
 // shot_common.cuh -- per-shot device pieces shared by the shot kernels: the
-// noise stream's next accepted site, the event a shot starts at, and the layout
-// of the noiseless run's snapshots.
+// noise stream's next accepted site, the event a shot starts at, the layout of
+// the noiseless run's snapshots, and the spill records through which a shot
+// moves between lanes of later rounds, or from a lane to a warp.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -77,6 +78,54 @@ __host__ __device__ constexpr size_t snap_stride(uint32_t rw) {
   return (sizeof(SnapHdr) + (size_t)rw * 8 + kSnapMax * (size_t)W * 8 + kSnapMax * sizeof(Cx<R>) + 15) &
          ~(size_t)15;
 }
+
+#ifndef SOFT_LANE_CAP
+#define SOFT_LANE_CAP 16
+#endif
+constexpr uint32_t kLaneCap = SOFT_LANE_CAP;  // map entries per lane
+static_assert(kLaneCap >= 2 && kLaneCap <= 16, "lane map capacity (partner indices are 4-bit)");
+
+// A rerun-list entry with this bit names a spill record (a shot handed from its
+// lane to a warp) instead of an item.
+constexpr uint32_t kSpillRef = 0x80000000u;
+constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
+
+// A spill record holds one shot's whole state at the top of an event: item,
+// resume event, n and flags (chain, logical, last outcome); the noise cursor
+// (nxt, cur, kblk, w2); F; the signs; the record words; up to kLaneCap entries.
+// Structure of arrays over `cap` records.
+template <typename R, int W>
+struct Spill {
+  uint4 *ha, *hb;
+  double *fid;
+  uint64_t *sd, *ss, *rec, *keys;
+  Cx<R> *vals;
+  uint32_t cap;
+  __host__ __device__ static size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+  __host__ __device__ static size_t bytes(uint32_t cap, uint32_t rw) {
+    const size_t c = cap;
+    return 2 * al16(c * 16) + al16(c * 8) + 2 * al16(c * 8 * W) + al16(c * 8 * rw) + al16(c * 8 * W * kLaneCap) +
+           al16(c * sizeof(Cx<R>) * kLaneCap);
+  }
+  __device__ Spill(unsigned char *b, uint32_t cap_, uint32_t rw) : cap(cap_) {
+    const size_t c = cap;
+    ha = reinterpret_cast<uint4 *>(b);
+    b += al16(c * 16);
+    hb = reinterpret_cast<uint4 *>(b);
+    b += al16(c * 16);
+    fid = reinterpret_cast<double *>(b);
+    b += al16(c * 8);
+    sd = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * W);
+    ss = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * W);
+    rec = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * rw);
+    keys = reinterpret_cast<uint64_t *>(b);
+    b += al16(c * 8 * W * kLaneCap);
+    vals = reinterpret_cast<Cx<R> *>(b);
+  }
+};
 
 }  // namespace dev
 }  // namespace soft
