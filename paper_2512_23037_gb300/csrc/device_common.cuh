@@ -125,11 +125,6 @@ __device__ __forceinline__ uint4 philox(uint64_t seed, uint64_t shot, uint32_t s
   return make_uint4(c0, c1, c2, c3);
 }
 
-__device__ __forceinline__ double snap01(double p) {
-  if (p < 1e-12) return 0.0;
-  if (p > 1.0 - 1e-12) return 1.0;
-  return p;
-}
 
 
 }  // namespace dev

@@ -49,7 +49,7 @@ __host__ __device__ inline size_t group_bytes(uint32_t cap, uint32_t rw) {
 // with the FP32 reciprocal square root (the scale is rounded to FP32 anyway).
 template <typename R>
 __device__ __forceinline__ R inv_sqrt_as(double x) {
-  return (R)(1.0 / sqrt(x));
+  return (R)rsqrt(x);
 }
 template <>
 __device__ __forceinline__ float inv_sqrt_as<float>(double x) {
@@ -391,16 +391,21 @@ struct Shot {
 
   // Outcome of a non-deterministic measurement with p_+ = pp: sampled from the
   // stream, or in fidelity mode +1 (weight pp) unless +1 is impossible.
-  __device__ __forceinline__ int pick(uint32_t ord, double pp) {
-    if (pp > 0.0 && pp < 1.0) undecided = true;
+  // Outcome +1 iff u < p, with p = sp / (sp + sm) snapped to 0 or 1 within 1e-12:
+  // decided as u (sp + sm) < sp, so that only the fidelity mode divides.
+  __device__ __forceinline__ int pick(uint32_t ord, double sp, double sm) {
+    const double tot = sp + sm;
+    if (!(tot > 0.0)) return -1;
+    const bool zero = sp < 1e-12 * tot, one = sp > (1.0 - 1e-12) * tot;
+    if (!zero && !one) undecided = true;
     if (force) {
-      if (pp > 0.0) {
-        fid *= pp;
-        return 1;
-      }
-      return -1;
+      if (zero) return -1;
+      fid *= one ? 1.0 : sp / tot;
+      return 1;
     }
-    return uniform(ord) < pp ? 1 : -1;
+    if (zero) return -1;
+    if (one) return 1;
+    return uniform(ord) * tot < sp ? 1 : -1;
   }
 
   __device__ int reg_meas_a(uint32_t sgn, uint32_t ord, const uint64_t *gamma) {
@@ -410,8 +415,7 @@ struct Shot {
     if (!(h0 && h1)) return h1 ? -1 : 1;
     const double a2 = valid ? norm2d(rv) : 0.0;
     const double sp = tile_sum(neg ? 0.0 : a2), sm = tile_sum(neg ? a2 : 0.0);
-    const double pp = snap01(sp / (sp + sm));
-    const int m = pick(ord, pp);
+    const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt_as<R>(m == 1 ? sp : sm);
     bool keep = valid && (neg == (m == -1));
     if (keep) rv = cscale(rv, sc);
@@ -438,8 +442,7 @@ struct Shot {
     const Cx<R> x1 = ipow(v1, e2 + 2u * kpar(kxor(a0, ep), g2));
     const double sp = tile_sum(owner ? 0.5 * norm2d(cadd(v0, x1)) : 0.0);
     const double sm = tile_sum(owner ? 0.5 * norm2d(csub(v0, x1)) : 0.0);
-    const double pp = snap01(sp / (sp + sm));
-    const int m = pick(ord, pp);
+    const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt_as<R>(2.0 * (m == 1 ? sp : sm));
     if (owner) {
       rv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
@@ -612,8 +615,7 @@ struct Shot {
     }
     sp = tile_sum(sp);
     sm = tile_sum(sm);
-    const double pp = snap01(sp / (sp + sm));
-    const int m = pick(ord, pp);
+    const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt_as<R>(m == 1 ? sp : sm);
     const uint32_t want = (m == 1) ? 0u : 1u;
     const R tau = (R)P.tau;
@@ -701,8 +703,7 @@ struct Shot {
       fail_check(CHK_HASH_SLOT, bad_slot);
       return 1;
     }
-    const double pp = snap01(sp / (sp + sm));
-    const int m = pick(ord, pp);
+    const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt_as<R>(2.0 * (m == 1 ? sp : sm));
     // stage the paired values in slots [cap, cap + nnz)
     for (uint32_t i = lane; i < nnz; i += G) {

@@ -146,19 +146,24 @@ struct LaneShot {
     uint64_t m = ((uint64_t)w.x << 21) ^ (uint64_t)(w.y >> 11);
     return (double)m * 0x1p-53;
   }
-  __device__ __forceinline__ int pick(uint32_t ord, double pp) {
+  // Outcome +1 iff u < p, with p = sp / (sp + sm) snapped to 0 or 1 within 1e-12:
+  // decided as u (sp + sm) < sp, so that only the fidelity mode divides.
+  __device__ __forceinline__ int pick(uint32_t ord, double sp, double sm) {
+    const double tot = sp + sm;
+    if (!(tot > 0.0)) return -1;
+    const bool zero = sp < 1e-12 * tot, one = sp > (1.0 - 1e-12) * tot;
     if (force) {
-      if (pp > 0.0) {
-        fid *= pp;
-        return 1;
-      }
-      return -1;
+      if (zero) return -1;
+      fid *= one ? 1.0 : sp / tot;
+      return 1;
     }
-    return uniform(ord) < pp ? 1 : -1;
+    if (zero) return -1;
+    if (one) return 1;
+    return uniform(ord) * tot < sp ? 1 : -1;
   }
   __device__ __forceinline__ R inv_sqrt(double x) const {
     if (sizeof(R) == 4) return (R)rsqrtf((float)x);
-    return (R)(1.0 / sqrt(x));
+    return (R)rsqrt(x);
   }
 
   // ---- start: shot s at event e of the noiseless run
@@ -416,8 +421,7 @@ struct LaneShot {
       if (kpar(key(i), gamma) ^ sgn) sm += a2;
       else sp += a2;
     }
-    const double pp = snap01(sp / (sp + sm));
-    const int m = pick(ord, pp);
+    const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt(m == 1 ? sp : sm);
     const uint32_t want = (m == 1) ? 0u : 1u;
     const R tau = (R)P.tau;
@@ -498,8 +502,7 @@ struct LaneShot {
       sp += 0.5 * norm2d(cadd(v0, x1));
       sm += 0.5 * norm2d(csub(v0, x1));
     }
-    const double pp = snap01(sp / (sp + sm));
-    const int m = pick(ord, pp);
+    const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt(2.0 * (m == 1 ? sp : sm));
     // In place: a pair's result goes to the slot of the entry that forms it (the a0
     // member, or a lone a1), and the consumed a1 partner's value is zeroed (the partners
