@@ -195,7 +195,11 @@ enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_R
  *   opts may be NULL (FP64, no records, auto tuning, default stream).
  *   out: receives a run handle (freed with soft_run_free) that owns the
  *   device tallies and, unless caller buffers are given, the record/status
- *   buffers.
+ *   buffers. All device buffers a run owns sit in one workspace, borrowed from
+ *   the device's cached workspace when that is idle and large enough; at
+ *   soft_run_free it goes back to the cache (the larger one is kept), so
+ *   repeated runs allocate no device memory. soft_release_workspace frees the
+ *   cache.
  * Errors: SOFT_E_ARG, SOFT_E_OOM, SOFT_E_CUDA. */
 int soft_run_shots(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, const soft_run_opts *opts,
                    soft_run **out);
@@ -258,7 +262,13 @@ int soft_run_timing(soft_run *r, double *ms, uint32_t *n_launches);
  * without SOFT_RUN_GRAPH. */
 int soft_run_pass_timing(soft_run *r, double ms[3], uint32_t *n_chunks, uint64_t *n_rerun);
 
+/* Waits for the run, then hands its workspace back to the device's cache (or
+ * frees it) and releases the handle. */
 void soft_run_free(soft_run *r);
+
+/* Frees the cached run workspace of every device (one per device, the largest
+ * a freed run used). Runs still alive keep theirs until soft_run_free. */
+int soft_release_workspace(void);
 
 /* Run entry point that allocates no device memory. The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc, such as

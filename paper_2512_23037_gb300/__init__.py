@@ -64,7 +64,7 @@ class _Tally(ctypes.Structure):
 
 
 EXPORTED = ["soft_compile_circuit", "soft_circuit_info", "soft_circuit_tableau", "soft_circuit_free",
-            "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing", "soft_run_pass_timing",
+            "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing", "soft_run_pass_timing", "soft_release_workspace",
             "soft_run_free", "soft_run_shots_noalloc", "soft_run_diagnostics", "soft_run_batch",
             "soft_tally_batch", "soft_fidelity_grad", "soft_last_error"]
 
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
         L.soft_run_pass_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32), ctypes.POINTER(u64)]
         L.soft_run_free.argtypes = [vp]
         L.soft_run_free.restype = None
+        L.soft_release_workspace.argtypes = []
         L.soft_run_shots_noalloc.argtypes = [vp, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp]
         L.soft_run_diagnostics.argtypes = [vp, vp]
         L.soft_run_batch.argtypes = [vp, vp, vp, u32, u64, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
@@ -290,6 +291,11 @@ def soft_run_timing(run: Run):
     nl = ctypes.c_uint32(0)
     _check(load().soft_run_timing(run.h, ctypes.byref(ms), ctypes.byref(nl)))
     return float(ms.value), int(nl.value)
+
+
+def soft_release_workspace():
+    """Free every device's cached run workspace (runs still alive keep theirs)."""
+    _check(load().soft_release_workspace())
 
 
 def soft_run_pass_timing(run: Run):

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -52,7 +53,6 @@ struct soft_run {
   unsigned char *d_slab = nullptr;         // global-memory state for large-cap reruns
   uint8_t *d_status = nullptr;             // circuit 0 only
   uint64_t *d_records = nullptr;
-  bool own_status = false, own_records = false;
   uint64_t out_limit = 0;
   uint64_t *d_st_signs = nullptr, *d_st_keys = nullptr;
   double *d_st_vals = nullptr;
@@ -64,7 +64,24 @@ struct soft_run {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> pass_ev;        // SOFT_RUN_TIME_PASSES: 4 per chunk around pre-pass, first, rerun
   uint32_t launches = 0;
+  // every device buffer above that the run owns lives in one arena, borrowed from
+  // the device's cached workspace when it fits
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  int device = 0;
 };
+
+namespace {
+// Per device: the cached run workspace (one arena), lent to a run that fits in it
+// and handed back at soft_run_free; freed by soft_release_workspace.
+struct WsCache {
+  std::mutex mu;
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+constexpr int kMaxDevices = 64;
+WsCache g_ws[kMaxDevices];
+}  // namespace
 
 // Records both precisions' noiseless runs of a freshly uploaded circuit (the
 // prefix every shot shares until its first error). Synchronous.
@@ -74,10 +91,15 @@ static cudaError_t build_prefixes(soft_circuit *c) {
   uint32_t *d_stop = nullptr;
   cudaError_t e = cudaMalloc(&d_stop, 6 * sizeof(uint32_t));
   if (e != cudaSuccess) return e;
-  for (int fp32 = 0; fp32 < 2 && e == cudaSuccess; ++fp32) {
+  // the two precisions' runs are one warp each: they run side by side on two streams
+  cudaStream_t ps[2] = {nullptr, nullptr};
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&ps[k], cudaStreamNonBlocking);
+  for (int fp32 = 0; fp32 < 2 && e == cudaSuccess; ++fp32) {  // (allocations first: they may synchronise)
     const size_t stride = soft::prefix_stride(fp32, hp.W, hp.rw);
     if ((e = cudaMalloc(&c->d_traj[fp32], n_snap * stride)) != cudaSuccess) break;
     c->traj_stride[fp32] = (uint32_t)stride;
+  }
+  for (int fp32 = 0; fp32 < 2 && e == cudaSuccess; ++fp32) {
     soft::ShotParams p{};
     p.n_circ = 1;
     soft::CircDev &d = p.circ[0];
@@ -95,8 +117,14 @@ static cudaError_t build_prefixes(soft_circuit *c) {
     p.cap = std::min(hp.cap, soft::kDefaultFirstCap);
     p.rw_max = hp.rw;
     p.tau = fp32 ? kTauFp32 : kTauFp64;
-    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + 3 * fp32, nullptr);
+    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + 3 * fp32, ps[fp32]);
   }
+  for (int k = 0; k < 2; ++k)
+    if (ps[k]) {
+      const cudaError_t es = cudaStreamSynchronize(ps[k]);
+      if (e == cudaSuccess) e = es;
+      cudaStreamDestroy(ps[k]);
+    }
   uint32_t stop[6] = {0, 0, 0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(stop, d_stop, sizeof stop, cudaMemcpyDeviceToHost);
   cudaFree(d_stop);
@@ -215,20 +243,22 @@ void soft_run_free(soft_run *r) {
   if (!r) return;
   if (r->stream) cudaStreamSynchronize(r->stream);
   else cudaDeviceSynchronize();
-  cudaFree(r->d_tally);
-  cudaFree(r->d_fsum);
-  cudaFree(r->d_al);
-  cudaFree(r->d_sp);
-  cudaFree(r->d_lr);
-  cudaFree(r->d_work);
-  cudaFree(r->d_rerun);
-  cudaFree(r->d_slab);
-  if (r->own_status) cudaFree(r->d_status);
-  if (r->own_records) cudaFree(r->d_records);
-  cudaFree(r->d_st_signs);
-  cudaFree(r->d_st_keys);
-  cudaFree(r->d_st_vals);
-  cudaFree(r->d_st_nnz);
+  // the arena goes back to the circuit's slot (unless the circuit is gone, or keeps a
+  // larger one), else it is freed
+  if (r->arena) {
+    bool kept = false;
+    if (r->device >= 0 && r->device < kMaxDevices) {
+      WsCache &w = g_ws[r->device];
+      std::lock_guard<std::mutex> lk(w.mu);
+      if (!w.p || w.bytes < r->arena_bytes) {
+        cudaFree(w.p);
+        w.p = r->arena;
+        w.bytes = r->arena_bytes;
+        kept = true;
+      }
+    }
+    if (!kept) cudaFree(r->arena);
+  }
   if (r->graph_exec) cudaGraphExecDestroy(r->graph_exec);
   if (r->graph) cudaGraphDestroy(r->graph);
   if (r->ev0) cudaEventDestroy(r->ev0);
@@ -339,19 +369,22 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   r->st_limit = std::min<uint64_t>(o.capture_k, n0);
   r->st_stride = circs[0]->hp.cap;
   cudaStream_t st = r->stream;
-#define SOFT_ALLOC(ptr, bytes)                                                                  \
-  do {                                                                                          \
-    if ((e = cudaMalloc(&(ptr), (bytes))) != cudaSuccess) {                                     \
-      soft_run_free(r);                                                                         \
-      return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed")      \
-                                            : cuda_fail(e, "cudaMalloc");                       \
-    }                                                                                           \
-  } while (0)
-  SOFT_ALLOC(r->d_tally, 5 * n_circ * sizeof(unsigned long long));
+  // every buffer the run owns is carved from one arena (256-byte aligned pieces)
+  struct Piece {
+    void **ptr;
+    size_t bytes;
+  };
+  std::vector<Piece> pieces;
+  size_t arena_bytes = 0;
+  auto need = [&](auto **ptr, size_t bytes) {
+    pieces.push_back(Piece{reinterpret_cast<void **>(ptr), bytes});
+    arena_bytes += (bytes + 255) & ~(size_t)255;
+  };
+  need(&r->d_tally, 5 * n_circ * sizeof(unsigned long long));
   const uint32_t n_ev0 = (uint32_t)circs[0]->hp.ev.size();
   // lanes: cursors (4 words per item, first: 16-byte aligned), (start event, rank) pairs, order,
   // bucket starts, counters
-  if (lanes) SOFT_ALLOC(r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
+  if (lanes) need(&r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
   // spill pool: records for the shots a sparse warp evicts (a quarter of the chunk; when it is
   // full, warps keep their shots), then records for shots a lane hands to a warp (an eighth;
   // when full, the warp reruns them from their start). Entries of the rerun list name a record
@@ -362,13 +395,13 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   const uint32_t sp_hand = two_pass ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 8) : 0u;
   const size_t n_lr = 4 + 2 * (size_t)rounds;
   if (spill) {
-    SOFT_ALLOC(r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_evict + sp_hand));
-    SOFT_ALLOC(r->d_lr, n_lr * sizeof(unsigned long long));
+    need(&r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_evict + sp_hand));
+    need(&r->d_lr, n_lr * sizeof(unsigned long long));
   }
   r->fid_mode = fid_mode;
-  if (fid_mode) SOFT_ALLOC(r->d_fsum, n_circ * sizeof(double));
-  SOFT_ALLOC(r->d_work, 11 * sizeof(unsigned long long));
-  if (two_pass) SOFT_ALLOC(r->d_rerun, (mid_pass ? 2 : 1) * chunk * sizeof(uint32_t));
+  if (fid_mode) need(&r->d_fsum, n_circ * sizeof(double));
+  need(&r->d_work, 11 * sizeof(unsigned long long));
+  if (two_pass) need(&r->d_rerun, (mid_pass ? 2 : 1) * chunk * sizeof(uint32_t));
   uint32_t slab_blocks = 0;
   if (global_rerun) {
     int sms = 0;
@@ -376,27 +409,47 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     // 4 blocks of 4 groups per SM: the rerun pass is latency-bound, so residency pays for the slab
     // memory (1 block/SM: w97 24.5 M shots/s, 4: 26.3 M, 6: 26.4 M)
     slab_blocks = (uint32_t)(sms > 0 ? sms : 1) * 4u;
-    SOFT_ALLOC(r->d_slab, soft::global_slab_bytes(fp32, W, cap_max, rw_max, slab_blocks));
+    need(&r->d_slab, soft::global_slab_bytes(fp32, W, cap_max, rw_max, slab_blocks));
   }
   if (r->out_limit) {
     if (o.d_status) r->d_status = o.d_status;
-    else {
-      SOFT_ALLOC(r->d_status, r->out_limit);
-      r->own_status = true;
-    }
+    else need(&r->d_status, r->out_limit);
     if (o.d_records) r->d_records = o.d_records;
-    else {
-      SOFT_ALLOC(r->d_records, r->out_limit * circs[0]->hp.rw * sizeof(uint64_t));
-      r->own_records = true;
-    }
+    else need(&r->d_records, r->out_limit * circs[0]->hp.rw * sizeof(uint64_t));
   }
   if (r->st_limit) {
-    SOFT_ALLOC(r->d_st_signs, r->st_limit * 4 * sizeof(uint64_t));
-    SOFT_ALLOC(r->d_st_keys, r->st_limit * r->st_stride * 2 * sizeof(uint64_t));
-    SOFT_ALLOC(r->d_st_vals, r->st_limit * r->st_stride * 2 * sizeof(double));
-    SOFT_ALLOC(r->d_st_nnz, r->st_limit * sizeof(uint32_t));
+    need(&r->d_st_signs, r->st_limit * 4 * sizeof(uint64_t));
+    need(&r->d_st_keys, r->st_limit * r->st_stride * 2 * sizeof(uint64_t));
+    need(&r->d_st_vals, r->st_limit * r->st_stride * 2 * sizeof(double));
+    need(&r->d_st_nnz, r->st_limit * sizeof(uint32_t));
   }
-#undef SOFT_ALLOC
+  // borrow the device's cached arena when it is free and large enough
+  r->device = dev;
+  if (dev >= 0 && dev < kMaxDevices) {
+    WsCache &w = g_ws[dev];
+    std::lock_guard<std::mutex> lk(w.mu);
+    if (w.p && w.bytes >= arena_bytes) {
+      r->arena = w.p;
+      r->arena_bytes = w.bytes;
+      w.p = nullptr;
+      w.bytes = 0;
+    }
+  }
+  if (!r->arena) {
+    if ((e = cudaMalloc(&r->arena, arena_bytes)) != cudaSuccess) {
+      r->arena = nullptr;
+      soft_run_free(r);
+      return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed") : cuda_fail(e, "cudaMalloc");
+    }
+    r->arena_bytes = arena_bytes;
+  }
+  {
+    unsigned char *at = static_cast<unsigned char *>(r->arena);
+    for (const Piece &pc : pieces) {
+      *pc.ptr = at;
+      at += (pc.bytes + 255) & ~(size_t)255;
+    }
+  }
   if ((e = cudaEventCreate(&r->ev0)) != cudaSuccess || (e = cudaEventCreate(&r->ev1)) != cudaSuccess) {
     soft_run_free(r);
     return cuda_fail(e, "cudaEventCreate");
@@ -718,6 +771,21 @@ int soft_run_diagnostics(soft_run *r, uint64_t out[4]) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics copy");
   for (int i = 0; i < 4; ++i) out[i] = d[i];
+  return SOFT_OK;
+}
+
+int soft_release_workspace(void) {
+  int prev = 0;
+  cudaGetDevice(&prev);
+  for (int d = 0; d < kMaxDevices; ++d) {
+    std::lock_guard<std::mutex> lk(g_ws[d].mu);
+    if (!g_ws[d].p) continue;
+    cudaSetDevice(d);
+    cudaFree(g_ws[d].p);
+    g_ws[d].p = nullptr;
+    g_ws[d].bytes = 0;
+  }
+  cudaSetDevice(prev);
   return SOFT_OK;
 }
 

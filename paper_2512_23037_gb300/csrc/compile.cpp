@@ -170,21 +170,43 @@ struct Tableau {
   }
 
   // Q = i^e0 d_beta s_gamma at zero signs.
-  bool decompose(const Pz &q, uint64_t beta[2], uint64_t gamma[2], uint32_t *e0) const {
+  // Q = i^e0 d_beta s_gamma at zero signs. NW: the 64-bit words in use. Bits are set
+  // without branches and the product runs over the set bits in increasing order,
+  // accumulating X, Z and the phase in place (the data-dependent branches and the
+  // second word were most of the compile time).
+  template <int NW>
+  bool decompose_w(const Pz &q, uint64_t beta[2], uint64_t gamma[2], uint32_t *e0) const {
     beta[0] = beta[1] = gamma[0] = gamma[1] = 0;
     for (uint32_t i = 0; i < n; ++i) {
-      if (anti(q, s[i])) flip(beta, i);
-      if (anti(q, d[i])) flip(gamma, i);
+      int ts = 0, td = 0;
+      for (int w = 0; w < NW; ++w) {
+        ts += pc((q.x[w] & s[i].z[w]) ^ (q.z[w] & s[i].x[w]));
+        td += pc((q.x[w] & d[i].z[w]) ^ (q.z[w] & d[i].x[w]));
+      }
+      beta[i >> 6] |= (uint64_t)(ts & 1) << (i & 63);
+      gamma[i >> 6] |= (uint64_t)(td & 1) << (i & 63);
     }
-    Pz acc;
-    for (uint32_t i = 0; i < n; ++i)
-      if (bit(beta, i)) acc = pmul(acc, herm(d[i]));
-    for (uint32_t i = 0; i < n; ++i)
-      if (bit(gamma, i)) acc = pmul(acc, herm(s[i]));
+    // acc <- acc * herm(r): phase + herm's own (popc(x & z)) + 2 popc(acc.z & r.x)
+    uint64_t ax[2] = {0, 0}, az[2] = {0, 0};
+    int ae = 0;
+    auto mul = [&](const Row &r) {
+      for (int w = 0; w < NW; ++w) {
+        ae += pc(r.x[w] & r.z[w]) + 2 * pc(az[w] & r.x[w]);
+        ax[w] ^= r.x[w];
+        az[w] ^= r.z[w];
+      }
+    };
+    for (int w = 0; w < NW; ++w)
+      for (uint64_t m = beta[w]; m; m &= m - 1) mul(d[64 * w + __builtin_ctzll(m)]);
+    for (int w = 0; w < NW; ++w)
+      for (uint64_t m = gamma[w]; m; m &= m - 1) mul(s[64 * w + __builtin_ctzll(m)]);
     for (int w = 0; w < 2; ++w)
-      if (acc.x[w] != q.x[w] || acc.z[w] != q.z[w]) return false;
-    *e0 = (uint32_t)((q.e - acc.e) & 3);
+      if (ax[w] != q.x[w] || az[w] != q.z[w]) return false;
+    *e0 = (uint32_t)((q.e - ae) & 3);
     return true;
+  }
+  bool decompose(const Pz &q, uint64_t beta[2], uint64_t gamma[2], uint32_t *e0) const {
+    return n <= 64 ? decompose_w<1>(q, beta, gamma, e0) : decompose_w<2>(q, beta, gamma, e0);
   }
 };
 

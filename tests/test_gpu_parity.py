@@ -306,6 +306,43 @@ def test_graph_replayed_chunks(soft, precision):
     assert compare_records(circ, noise, 4, 77, rec, st, ref, precision) <= 1
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_workspace_reuse_is_clean(soft, precision):
+    """Runs borrow the device's cached workspace, left dirty by the run before
+    (another circuit, other shots, records, captured states): records, statuses,
+    tallies and states equal those of a run on a freshly allocated workspace."""
+    S = soft
+    circ, noise = C.workload("w42")
+    small, nz2 = C.workload("tiny6")
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    c2 = S.soft_compile_circuit(small.array(), small.n, nz2, small.cap)
+
+    def run(cc, n, first, **kw):
+        r = S.soft_run_shots(cc, n, first, 5, precision=precision, record_mode=S.REC_ALL, **kw)
+        rec, st = S.soft_get_records(r, n)
+        states = [S.soft_get_state(r, k) for k in range(kw.get("capture_k", 0))]
+        t = S.soft_tally(r)
+        r.free()
+        return rec, st, t, states
+
+    S.soft_release_workspace()
+    fresh = run(c, 6000, 100, chunk_shots=2000)
+    S.soft_release_workspace()
+    fresh_cap = run(c, 300, 7, capture_k=16)
+    # dirty the cache with other circuits and shots, then repeat both
+    run(c2, 20000, 0)
+    run(c, 9000, 50000, chunk_shots=3000)
+    again = run(c, 6000, 100, chunk_shots=2000)
+    again_cap = run(c, 300, 7, capture_k=16)
+    for a, b in ((fresh, again), (fresh_cap, again_cap)):
+        assert (a[0] == b[0]).all() and (a[1] == b[1]).all() and a[2] == b[2]
+        for (s1, k1, v1), (s2, k2, v2) in zip(a[3], b[3]):
+            assert (s1 == s2).all() and (k1 == k2).all() and (v1 == v2).all()
+    S.soft_release_workspace()
+    c.free()
+    c2.free()
+
+
 @pytest.mark.parametrize("lanes", [True, False])
 def test_pass_timing(soft, lanes):
     """Per-pass events: one set per chunk, each pass non-negative, the sum within
