@@ -654,6 +654,12 @@ struct GradWarp {
       uint4 w = philox(P.seed, shot, 0u, kblk++);
       uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
       uint32_t rem = P.n_sites - cur, lo = 0, hi = rem;
+      if (P.thr_tab) {  // U's bucket bounds the answer
+        const uint32_t b = (uint32_t)(U >> (64 - kThrTabBits));
+        const uint32_t t0 = __ldg(&P.thr_tab[b]), t1 = __ldg(&P.thr_tab[b + 1]);
+        lo = t0 < rem ? t0 : rem;
+        hi = t1 < rem ? t1 : rem;
+      }
       while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
         if (U < __ldg(&P.thr[mid])) hi = mid;

@@ -14,6 +14,7 @@ struct GradParams {
   const CaseB *cb;
   const Site *sites;
   const uint64_t *thr;
+  const uint32_t *thr_tab;  // the gap search's index (program.h; null: plain search)
   uint32_t n_events, n_sites, rw, n_rot, n_params, blocks;
   double tau_rel;  // prune |v|^2 below tau_rel times the squared norm
   uint64_t seed, first_pattern, n_patterns;

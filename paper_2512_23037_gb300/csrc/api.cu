@@ -172,7 +172,8 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
   size_t b_cf = std::max<size_t>(1, hp.coefs.size()) * sizeof(soft::Coef),
          b_cb = std::max<size_t>(1, hp.cb.size()) * sizeof(soft::CaseB),
          b_st = std::max<size_t>(1, hp.sites.size()) * sizeof(soft::Site),
-         b_thr0 = hp.thr.size() * sizeof(uint64_t), b_thr = b_thr0 + hp.site_ev.size() * sizeof(uint32_t);
+         b_thr0 = hp.thr.size() * sizeof(uint64_t), b_thr1 = b_thr0 + hp.site_ev.size() * sizeof(uint32_t),
+         b_thr = b_thr1 + hp.thr_tab.size() * sizeof(uint32_t);
   cudaError_t e;
   if ((e = cudaMalloc(&c->d_ev, b_ev)) != cudaSuccess || (e = cudaMalloc(&c->d_coef, b_cf)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_cb, b_cb)) != cudaSuccess || (e = cudaMalloc(&c->d_sites, b_st)) != cudaSuccess ||
@@ -189,7 +190,9 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
                                             cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (e = cudaMemcpy(c->d_thr, hp.thr.data(), b_thr0, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(reinterpret_cast<unsigned char *>(c->d_thr) + b_thr0, hp.site_ev.data(),
-                      hp.site_ev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+                      hp.site_ev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(reinterpret_cast<unsigned char *>(c->d_thr) + b_thr1, hp.thr_tab.data(),
+                      hp.thr_tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
     soft_circuit_free(c);
     return cuda_fail(e, "cudaMemcpy (program upload)");
   }
@@ -275,6 +278,7 @@ namespace {
 soft::CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix) {
   soft::CircDev d{};
   d.site_ev = reinterpret_cast<const uint32_t *>(c->d_thr + c->hp.thr.size());
+  d.thr_tab = d.site_ev + c->hp.site_ev.size();
   if (prefix && c->d_traj[fp32]) {
     d.traj = c->d_traj[fp32];
     d.traj_stop = c->traj_stop[fp32];

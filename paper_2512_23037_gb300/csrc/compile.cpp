@@ -653,6 +653,13 @@ int compile_program(const soft_op *ops, size_t n_ops, uint32_t n, const soft_noi
   P.n_sites = (uint32_t)P.sites.size();
   P.thr.resize(P.n_sites ? P.n_sites : 1);
   for (uint32_t g = 0; g < P.n_sites; ++g) P.thr[g] = gap_thr(P.pmax, g);
+  // thr increases with g, so the first g with U < thr[g] for every U of a bucket of the top
+  // bits lies between the bucket's entry and the next one's
+  P.thr_tab.assign((1u << kThrTabBits) + 1u, P.n_sites);
+  for (uint32_t b = 0; b < (1u << kThrTabBits); ++b) {
+    const uint64_t U = (uint64_t)b << (64 - kThrTabBits);
+    P.thr_tab[b] = (uint32_t)(std::upper_bound(P.thr.begin(), P.thr.begin() + P.n_sites, U) - P.thr.begin());
+  }
   P.site_ev.assign(P.thr.size(), (uint32_t)P.ev.size());
   {
     uint32_t e = 0;

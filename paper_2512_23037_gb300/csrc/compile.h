@@ -22,6 +22,7 @@ struct HostProgram {
   std::vector<Site> sites;
   std::vector<uint64_t> thr;     // gap thresholds, one per site
   std::vector<uint32_t> site_ev; // per site: the first event whose site_begin exceeds it (applies its error)
+  std::vector<uint32_t> thr_tab; // 2^kThrTabBits + 1 entries: the gap search's index (program.h)
   std::vector<uint64_t> fin_x;   // final X words, 2n rows x 2 words
   std::vector<uint64_t> fin_z;
   bool fid_ok = true;  // no DETECTOR at or after the first measurement an OBSERVABLE reads

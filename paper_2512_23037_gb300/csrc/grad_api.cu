@@ -118,6 +118,7 @@ extern "C" int soft_fidelity_grad(soft_circuit *c, const double *theta, uint32_t
   unsigned char *ptape = c->d_gprefix, *psnap = c->d_gprefix + snap_off;
   uint32_t *pstop = reinterpret_cast<uint32_t *>(c->d_gprefix + stop_off);
   p.site_ev = reinterpret_cast<const uint32_t *>(c->d_thr + hp.thr.size());
+  p.thr_tab = p.site_ev + hp.site_ev.size();
   if ((e = soft::launch_grad_prefix(p, fp32, hp.W, ptape, psnap, pstop, st)) != cudaSuccess)
     return soft::set_error(SOFT_E_CUDA, "prefix kernel launch failed");
   p.wide_n = reinterpret_cast<unsigned long long *>(c->d_gwide);

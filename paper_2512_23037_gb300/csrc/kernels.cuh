@@ -33,6 +33,7 @@ struct CircDev {
   uint32_t traj_stop, traj_stride;
   uint32_t traj_fid_stop, pad_traj;  // first fidelity measurement's event (fidelity mode stops there)
   const uint32_t *site_ev;  // per site: the event that applies its error
+  const uint32_t *thr_tab;  // the gap search's index, 2^kThrTabBits + 1 entries (null: plain search)
 };
 
 struct ShotParams {

@@ -44,6 +44,10 @@ enum : uint32_t {
 };
 
 // Header word 0: type (bits 0-3) | flags (4-11) | e0 (12-13) | lowbit (16-23) | xe0 (24-25).
+// The gap search's index: bucket b of the top kThrTabBits bits of U holds the
+// first gap g with U < thr[g] for the bucket's lowest U (bucket 2^bits: n_sites).
+constexpr uint32_t kThrTabBits = 12;
+
 SOFT_HD inline uint32_t ev_type(uint32_t w0) { return w0 & 15u; }
 SOFT_HD inline uint32_t ev_flags(uint32_t w0) { return (w0 >> 4) & 255u; }
 SOFT_HD inline uint32_t ev_e0(uint32_t w0) { return (w0 >> 12) & 3u; }

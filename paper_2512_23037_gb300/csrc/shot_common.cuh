@@ -30,6 +30,12 @@ __device__ __forceinline__ bool next_site(const CircDev *C, uint64_t seed, uint6
     uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
     const uint32_t rem = n_sites - cur;
     uint32_t lo = 0, hi = rem;
+    if (C->thr_tab) {  // U's bucket bounds the answer: search between its entry and the next
+      const uint32_t b = (uint32_t)(U >> (64 - kThrTabBits));
+      const uint32_t t0 = __ldg(&C->thr_tab[b]), t1 = __ldg(&C->thr_tab[b + 1]);
+      lo = t0 < rem ? t0 : rem;
+      hi = t1 < rem ? t1 : rem;
+    }
     while (lo < hi) {
       uint32_t mid = (lo + hi) >> 1;
       if (U < __ldg(&thr[mid])) hi = mid;
