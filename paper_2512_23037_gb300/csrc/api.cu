@@ -388,7 +388,11 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   const uint32_t n_ev0 = (uint32_t)circs[0]->hp.ev.size();
   // lanes: cursors (4 words per item, first: 16-byte aligned), (start event, rank) pairs, order,
   // bucket starts, counters
-  if (lanes) need(&r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1)) * sizeof(uint32_t));
+  // then the per-block bucket bases of the block-binned pre-pass
+  const uint32_t al_grid = lanes ? soft::lane_prepass_grid() : 0u;
+  if (lanes)
+    need(&r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1) + (size_t)al_grid * (n_ev0 + 1)) *
+                       sizeof(uint32_t));
   // spill pool: records for the shots a sparse warp evicts (a quarter of the chunk; when it is
   // full, warps keep their shots), then records for shots a lane hands to a warp (an eighth;
   // when full, the warp reruns them from their start). Entries of the rerun list name a record
@@ -532,6 +536,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.al_start = r->d_al + 7 * chunk;
     p.al_count = r->d_al + 7 * chunk + (n_ev0 + 2);
     p.al_next = p.al_count + (n_ev0 + 1);
+    p.al_base = p.al_next + (n_ev0 + 1);
+    p.al_grid = al_grid;
     p.lane_round = 0;
     p.lane_evict = spill && rounds > 1 ? 1u : 0u;
     p.sp = spill ? r->d_sp : nullptr;

@@ -33,6 +33,7 @@ namespace cg = cooperative_groups;
 
 enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_RERUN = 4, LS_HAND = 5 };
 constexpr int kLaneBlock = 128;
+constexpr uint32_t kBinMaxEvents = 12287;  // block-binned pre-pass: its histogram fits 48 KB of shared memory
 #ifndef SOFT_LANE_EVICT
 #define SOFT_LANE_EVICT 8
 #endif
@@ -715,6 +716,56 @@ __global__ void lane_count_resume_kernel(const __grid_constant__ ShotParams P) {
   }
 }
 
+// ---- block-binned pre-pass (circuits of at most kBinMaxEvents events): each block
+// ranks its contiguous range of items per bucket with shared-memory atomics, then
+// takes one global atomic per non-empty bucket for its base. The first errors
+// cluster in a few buckets, and global atomics on one address serialise.
+template <bool Resume, typename R, int W>
+__global__ void __launch_bounds__(256) lane_bin_kernel(const __grid_constant__ ShotParams P) {
+  extern __shared__ uint32_t hist[];
+  const CircDev *C = &P.circ[0];
+  const uint32_t n_ev = C->n_events, nb = n_ev + 1;
+  for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) hist[k] = 0u;
+  __syncthreads();
+  const unsigned long long n_items =
+      Resume ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
+  const unsigned long long per = (n_items + gridDim.x - 1) / gridDim.x;
+  const unsigned long long i0 = blockIdx.x * per, i1 = i0 + per < n_items ? i0 + per : n_items;
+  const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
+  for (unsigned long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    uint32_t e;
+    if (Resume) {
+      const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
+      e = S.ha[P.lr[2 + 2 * P.lane_round] + i].y;
+      if (e > n_ev) e = n_ev;  // a record always resumes at an event of the circuit
+    } else {
+      uint32_t cur = 0, kblk = 0, nxt = 0, w2 = 0;
+      if (!next_site(C, P.seed, C->first_shot + base + i, cur, kblk, nxt, w2)) kblk = 0xFFFFFFFFu;  // a failure
+      e = first_event(C, P.fid_mode, nxt);
+      reinterpret_cast<uint4 *>(P.al_cursor)[i] = make_uint4(nxt, cur, kblk, w2);
+    }
+    reinterpret_cast<uint2 *>(P.al_ev)[i] = make_uint2(e, atomicAdd(&hist[e], 1u));
+  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
+    const uint32_t c = hist[k];
+    P.al_base[(size_t)blockIdx.x * nb + k] = c ? atomicAdd(&P.al_count[k], c) : 0u;
+  }
+}
+// (same grid as lane_bin_kernel: it fixes each item's block)
+template <bool Resume>
+__global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_constant__ ShotParams P) {
+  const uint32_t nb = P.circ[0].n_events + 1;
+  const unsigned long long n_items =
+      Resume ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
+  const unsigned long long per = (n_items + gridDim.x - 1) / gridDim.x;
+  const unsigned long long i0 = blockIdx.x * per, i1 = i0 + per < n_items ? i0 + per : n_items;
+  for (unsigned long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint2 er = reinterpret_cast<const uint2 *>(P.al_ev)[i];
+    P.al_order[P.al_start[er.x] + P.al_base[(size_t)blockIdx.x * nb + er.x] + er.y] = (uint32_t)i;
+  }
+}
+
 template <typename R, int W>
 __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -859,6 +910,12 @@ size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw) {
 
 uint32_t lane_map_cap() { return kLaneCap; }
 uint32_t lane_rounds() { return kLaneRounds; }
+uint32_t lane_prepass_grid() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (uint32_t)(sms > 0 ? sms : 1) * 8u;
+}
 
 size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap) {
   return fp32 ? (W == 1 ? Spill<float, 1>::bytes(cap, rw) : Spill<float, 2>::bytes(cap, rw))
@@ -866,11 +923,22 @@ size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap) {
 }
 
 cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W, cudaStream_t st) {
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * 8u;
+  const unsigned grid = p.al_grid;
   lane_round_setup_kernel<<<1, 1, 0, st>>>(p);
+  const uint32_t nb = p.circ[0].n_events + 1;
+  if (nb <= kBinMaxEvents + 1) {
+    const size_t sh = (size_t)nb * sizeof(uint32_t);
+    if (fp32) {
+      if (W == 1) lane_bin_kernel<true, float, 1><<<grid, 256, sh, st>>>(p);
+      else lane_bin_kernel<true, float, 2><<<grid, 256, sh, st>>>(p);
+    } else {
+      if (W == 1) lane_bin_kernel<true, double, 1><<<grid, 256, sh, st>>>(p);
+      else lane_bin_kernel<true, double, 2><<<grid, 256, sh, st>>>(p);
+    }
+    lane_scan_kernel<<<1, 1024, 0, st>>>(p);
+    lane_bin_scatter_kernel<true><<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+  }
   if (fp32) {
     if (W == 1) lane_count_resume_kernel<float, 1><<<grid, 256, 0, st>>>(p);
     else lane_count_resume_kernel<float, 2><<<grid, 256, 0, st>>>(p);
@@ -884,10 +952,14 @@ cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W
 }
 
 cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st) {
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * 8u;
+  const unsigned grid = p.al_grid;
+  const uint32_t nb = p.circ[0].n_events + 1;
+  if (nb <= kBinMaxEvents + 1) {
+    lane_bin_kernel<false, float, 1><<<grid, 256, (size_t)nb * sizeof(uint32_t), st>>>(p);
+    lane_scan_kernel<<<1, 1024, 0, st>>>(p);
+    lane_bin_scatter_kernel<false><<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+  }
   lane_count_kernel<<<grid, 256, 0, st>>>(p);
   lane_scan_kernel<<<1, 1024, 0, st>>>(p);
   lane_scatter_kernel<<<grid, 256, 0, st>>>(p);
