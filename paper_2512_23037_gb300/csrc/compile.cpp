@@ -137,30 +137,34 @@ struct Tableau {
     }
   }
 
-  int apply_row(const GateTab &t, Row &r, uint32_t a, uint32_t b, bool two) {
-    uint32_t in = (uint32_t)bit(r.x, a) | ((uint32_t)bit(r.z, a) << 1);
-    if (two) in |= ((uint32_t)bit(r.x, b) << 2) | ((uint32_t)bit(r.z, b) << 3);
-    uint32_t o = t.out[in];
-    put(r.x, a, (int)(o & 1));
-    put(r.z, a, (int)((o >> 1) & 1));
+  // (bits replaced and sign flips applied without data-dependent branches)
+  static int apply_row(const GateTab &t, Row &r, uint32_t a, uint32_t b, bool two) {
+    const uint32_t wa = a >> 6, sa = a & 63, wb = b >> 6, sb = b & 63;
+    uint32_t in = (uint32_t)((r.x[wa] >> sa) & 1u) | ((uint32_t)((r.z[wa] >> sa) & 1u) << 1);
+    if (two) in |= ((uint32_t)((r.x[wb] >> sb) & 1u) << 2) | ((uint32_t)((r.z[wb] >> sb) & 1u) << 3);
+    const uint64_t o = t.out[in];
+    r.x[wa] = (r.x[wa] & ~(1ull << sa)) | ((o & 1u) << sa);
+    r.z[wa] = (r.z[wa] & ~(1ull << sa)) | (((o >> 1) & 1u) << sa);
     if (two) {
-      put(r.x, b, (int)((o >> 2) & 1));
-      put(r.z, b, (int)((o >> 3) & 1));
+      r.x[wb] = (r.x[wb] & ~(1ull << sb)) | (((o >> 2) & 1u) << sb);
+      r.z[wb] = (r.z[wb] & ~(1ull << sb)) | (((o >> 3) & 1u) << sb);
     }
     return t.flipb[in];
   }
 
+  // false if a row met an odd phase (impossible for a valid tableau; the compile stops)
   bool gate(int op, uint32_t a, uint32_t b) {
     const GateTab &t = tabs().g[op];
-    bool two = (op == SOFT_CX || op == SOFT_CZ);
+    const bool two = (op == SOFT_CX || op == SOFT_CZ);
+    int bad = 0;
     for (uint32_t i = 0; i < n; ++i) {
-      int fd = apply_row(t, d[i], a, b, two);
-      int fs = apply_row(t, s[i], a, b, two);
-      if ((fd | fs) & 0x80) return false;
-      if (fd) flip(pend_d, i);
-      if (fs) flip(pend_s, i);
+      const int fd = apply_row(t, d[i], a, b, two);
+      const int fs = apply_row(t, s[i], a, b, two);
+      bad |= fd | fs;
+      pend_d[i >> 6] ^= (uint64_t)(fd & 1) << (i & 63);
+      pend_s[i >> 6] ^= (uint64_t)(fs & 1) << (i & 63);
     }
-    return true;
+    return !(bad & 0x80);
   }
 
   static bool anti(const Pz &q, const Row &r) {
@@ -169,7 +173,6 @@ struct Tableau {
     return t & 1;
   }
 
-  // Q = i^e0 d_beta s_gamma at zero signs.
   // Q = i^e0 d_beta s_gamma at zero signs. NW: the 64-bit words in use. Bits are set
   // without branches and the product runs over the set bits in increasing order,
   // accumulating X, Z and the phase in place (the data-dependent branches and the
