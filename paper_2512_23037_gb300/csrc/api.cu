@@ -84,13 +84,15 @@ WsCache g_ws[kMaxDevices];
 }  // namespace
 
 // Records both precisions' noiseless runs of a freshly uploaded circuit (the
-// prefix every shot shares until its first error). Synchronous.
-static cudaError_t build_prefixes(soft_circuit *c) {
+// prefix every shot shares until its first error). Synchronous, but on streams
+// of its own: it waits for no other work on the device.
+static cudaError_t build_prefixes(soft_circuit *c, cudaStream_t us) {
   const auto &hp = c->hp;
   const size_t n_snap = hp.ev.size() + 1;
   uint32_t *d_stop = nullptr;
   cudaError_t e = cudaMalloc(&d_stop, 6 * sizeof(uint32_t));
   if (e != cudaSuccess) return e;
+  c->d_stop = d_stop;
   // the two precisions' runs are one warp each: they run side by side on two streams
   cudaStream_t ps[2] = {nullptr, nullptr};
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&ps[k], cudaStreamNonBlocking);
@@ -126,8 +128,8 @@ static cudaError_t build_prefixes(soft_circuit *c) {
       cudaStreamDestroy(ps[k]);
     }
   uint32_t stop[6] = {0, 0, 0, 0, 0, 0};
-  if (e == cudaSuccess) e = cudaMemcpy(stop, d_stop, sizeof stop, cudaMemcpyDeviceToHost);
-  cudaFree(d_stop);
+  if (e == cudaSuccess && (e = cudaMemcpyAsync(stop, d_stop, sizeof stop, cudaMemcpyDeviceToHost, us)) == cudaSuccess)
+    e = cudaStreamSynchronize(us);
   if (e != cudaSuccess) return e;
   for (int k = 0; k < 2; ++k) {
     c->traj_stop[k] = std::min<uint32_t>(stop[3 * k], (uint32_t)hp.ev.size());
@@ -181,23 +183,33 @@ int soft_compile_circuit(const soft_op *ops, size_t n_ops, uint32_t n_qubits, co
     soft_circuit_free(c);
     return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed") : cuda_fail(e, "cudaMalloc");
   }
-  if ((e = cudaMemcpy(c->d_ev, ev_src, b_ev, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (!hp.coefs.empty() && (e = cudaMemcpy(c->d_coef, hp.coefs.data(), hp.coefs.size() * sizeof(soft::Coef),
-                                            cudaMemcpyHostToDevice)) != cudaSuccess) ||
-      (!hp.cb.empty() && (e = cudaMemcpy(c->d_cb, hp.cb.data(), hp.cb.size() * sizeof(soft::CaseB),
-                                         cudaMemcpyHostToDevice)) != cudaSuccess) ||
-      (!hp.sites.empty() && (e = cudaMemcpy(c->d_sites, hp.sites.data(), hp.sites.size() * sizeof(soft::Site),
-                                            cudaMemcpyHostToDevice)) != cudaSuccess) ||
-      (e = cudaMemcpy(c->d_thr, hp.thr.data(), b_thr0, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(reinterpret_cast<unsigned char *>(c->d_thr) + b_thr0, hp.site_ev.data(),
-                      hp.site_ev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(reinterpret_cast<unsigned char *>(c->d_thr) + b_thr1, hp.thr_tab.data(),
-                      hp.thr_tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+  // uploads on a stream of the compile's own (a non-blocking one), so that compiling
+  // waits for no other work on the device, a running batch of shots included
+  cudaStream_t us = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking)) != cudaSuccess) {
     soft_circuit_free(c);
-    return cuda_fail(e, "cudaMemcpy (program upload)");
+    return cuda_fail(e, "cudaStreamCreateWithFlags");
+  }
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, us) : cudaSuccess;
+  };
+  unsigned char *thr_b = reinterpret_cast<unsigned char *>(c->d_thr);
+  if ((e = up(c->d_ev, ev_src, b_ev)) != cudaSuccess ||
+      (e = up(c->d_coef, hp.coefs.data(), hp.coefs.size() * sizeof(soft::Coef))) != cudaSuccess ||
+      (e = up(c->d_cb, hp.cb.data(), hp.cb.size() * sizeof(soft::CaseB))) != cudaSuccess ||
+      (e = up(c->d_sites, hp.sites.data(), hp.sites.size() * sizeof(soft::Site))) != cudaSuccess ||
+      (e = up(c->d_thr, hp.thr.data(), b_thr0)) != cudaSuccess ||
+      (e = up(thr_b + b_thr0, hp.site_ev.data(), hp.site_ev.size() * sizeof(uint32_t))) != cudaSuccess ||
+      (e = up(thr_b + b_thr1, hp.thr_tab.data(), hp.thr_tab.size() * sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaStreamSynchronize(us)) != cudaSuccess) {
+    cudaStreamDestroy(us);
+    soft_circuit_free(c);
+    return cuda_fail(e, "program upload");
   }
   c->bytes = b_ev + b_cf + b_cb + b_st + b_thr;
-  if ((e = build_prefixes(c)) != cudaSuccess) {
+  e = build_prefixes(c, us);
+  cudaStreamDestroy(us);
+  if (e != cudaSuccess) {
     soft_circuit_free(c);
     return e == cudaErrorMemoryAllocation ? fail(SOFT_E_OOM, "device allocation failed")
                                           : cuda_fail(e, "noiseless prefix run");
@@ -234,6 +246,7 @@ void soft_circuit_free(soft_circuit *c) {
   cudaFree(c->d_thr);
   cudaFree(c->d_traj[0]);
   cudaFree(c->d_traj[1]);
+  cudaFree(c->d_stop);
   cudaFree(c->d_gcoef);
   cudaFree(c->d_gnext);
   cudaFree(c->d_gtape);

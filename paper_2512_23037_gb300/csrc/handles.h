@@ -27,6 +27,7 @@ struct soft_circuit {
   // the noiseless run's snapshot table per precision (index 0 FP64, 1 FP32),
   // built at compile time; traj_stop = last valid event
   unsigned char *d_traj[2] = {nullptr, nullptr};
+  uint32_t *d_stop = nullptr;  // where the noiseless runs report their stop events (6 words)
   uint32_t traj_stop[2] = {0, 0};
   uint32_t traj_fid_stop[2] = {0, 0};
   uint32_t traj_max_n[2] = {0, 0};  // largest map of the recorded noiseless run
