@@ -243,8 +243,9 @@ def grad_bench(S, C, torch, stream, n_pat, steps, warmup):
 
 def sweep(args):
     """Throughput of the 42-qubit workload against the noise rate (discard
-    rate grows with p) and against the shots resident per SM (blocks per SM x
-    groups per block), FP32 and FP64, CUDA events over K steps of --shots."""
+    rate grows with p), FP32 and FP64, and against the shots resident per SM:
+    lane-per-shot blocks per SM (128 shots each), and a few warp-per-shot shapes
+    (blocks per SM x groups per block); CUDA events over K steps of --shots."""
     import torch
     import paper_2512_23037_gb300 as S
     from paper_2512_23037_gb300 import circuits as C
@@ -278,12 +279,15 @@ def sweep(args):
                           "ler_kept": tal["logical_errors"] / max(tal["kept"], 1)}))
     circ, noise = C.workload("w42")
     h = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
-    for bps in (1, 2, 4, 6):
-        for gpb in (1, 2, 4):
-            v32, _ = rate(h, "fp32", blocks_per_sm=bps, groups_per_block=gpb)
-            print(json.dumps({"sweep": "shots_per_sm", "workload": "w42", "blocks_per_sm": bps,
-                              "groups_per_block": gpb, "shots_resident_per_sm": bps * gpb,
-                              "fp32_shots_per_s": v32}))
+    for bps in (1, 2, 3, 4, 5, 6):
+        v32, _ = rate(h, "fp32", blocks_per_sm=bps)
+        print(json.dumps({"sweep": "shots_per_sm", "workload": "w42", "scheduling": "lane per shot",
+                          "blocks_per_sm": bps, "shots_resident_per_sm": bps * 128, "fp32_shots_per_s": v32}))
+    for bps, gpb in ((1, 1), (2, 4), (6, 4)):
+        v32, _ = rate(h, "fp32", blocks_per_sm=bps, groups_per_block=gpb, lanes=False)
+        print(json.dumps({"sweep": "shots_per_sm", "workload": "w42", "scheduling": "warp per shot",
+                          "blocks_per_sm": bps, "groups_per_block": gpb, "shots_resident_per_sm": bps * gpb,
+                          "fp32_shots_per_s": v32}))
     return 0
 
 
