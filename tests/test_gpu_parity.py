@@ -197,11 +197,12 @@ def test_zero_and_one_shot(soft):
 
 
 def test_bench_config_sampled(soft):
-    """The bench's launch configuration (w42, FP32, 2^22 shots, default
-    tuning): tallies are consistent and sampled shots match the oracle."""
+    """The bench's launch configuration (w42, FP32, 2^23 shots in one chunk,
+    default tuning: lane per shot, eviction rounds, handover, middle pass):
+    tallies are consistent and sampled shots match the oracle."""
     S = soft
     circ, noise = C.workload("w42")
-    n = 1 << 22
+    n = 1 << 23
     c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
     r = S.soft_run_shots(c, n, 0, 0, precision="fp32", record_mode=S.REC_ALL)
     rec, st = S.soft_get_records(r, n)
@@ -473,6 +474,24 @@ def test_degenerate_circuits(soft, case):
     cc, r, rec, st, tal, ref = run_both(soft, c, noise, 500, 2, "fp64")
     assert [tal["shots"], tal["discarded"], tal["overflow"], tal["kept"], tal["logical_errors"]] == ref["tally"]
     assert compare_records(c, noise, 2, 0, rec, st, ref, "fp64") == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n_data,n_anc", [(72, 4), (120, 8)])
+def test_lane_per_shot_two_word_keys(soft, precision, n_data, n_anc):
+    """Above 64 qubits (two-word keys, signs and spill records) in the lane
+    kernel: windowed circuits of 76 and 128 qubits, whose noiseless maps fit a
+    lane, against the oracle."""
+    S = soft
+    circ, noise = C.windowed(11, n_data=n_data, n_anc=n_anc, blocks=4, p=4e-3)
+    n_shots = 3000
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    r = S.soft_run_shots(c, n_shots, 0, 9, precision=precision, record_mode=S.REC_ALL, time_passes=True)
+    rec, st = S.soft_get_records(r, n_shots)
+    assert S.soft_run_diagnostics(r)[0] == 0
+    assert S.soft_run_pass_timing(r)[0][0] > 0.0  # the lane pre-pass ran
+    ref = oracle.run(circ, circ.n, noise, circ.cap, 9, 0, n_shots, threads=8)
+    assert compare_records(circ, noise, 9, 0, rec, st, ref, precision) <= 2
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
