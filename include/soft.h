@@ -178,9 +178,11 @@ typedef struct {
  * warp executes one event at a time for all its lanes, each lane updating its
  * own shot's map (up to 16 entries). A shot whose map outgrows its lane is
  * rerun from its start by a warp, with a register map of up to first_cap
- * entries (default 64), and only beyond that at the circuit's cap. It
- * applies to single-circuit runs without state capture or a forced group size,
- * when every map of the circuit's noiseless run fits (at most 16 entries);
+ * entries (default 64), and only beyond that at the circuit's cap. In a
+ * batch each circuit has its own buckets, and a warp serves one circuit at a
+ * time. It applies to runs without state capture or a forced group size, when
+ * every map of every circuit's noiseless run fits (at most 16 entries) and the
+ * circuits hold at most 50 000 events (plus one per circuit) together;
  * otherwise a warp (group) runs each shot. SOFT_RUN_NO_LANES always uses the
  * warp per shot. Same results either way, another order. */
 /* SOFT_RUN_TIME_PASSES records CUDA events between the passes of every chunk

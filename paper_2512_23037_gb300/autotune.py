@@ -7,7 +7,9 @@ caller will run, so nothing is reused) for every candidate of
     below their circuit's cap rerun at the full cap),
   - groups_per_block: shots resident per 128-thread block (2 or 4 for 32-lane
     groups, 8 for 16-lane groups),
-  - group_size: lanes per shot (32 = one warp per shot, 16 = two shots per warp),
+  - group_size: lanes per shot (32 = one warp per shot, 16 = two shots per warp;
+    0 = the library default: one shot per lane where that applies, with
+    first_cap the capacity of the warp pass that takes shots outgrowing a lane),
 
 and keeps the fastest. Results are cached per circuit signature.
 """
@@ -20,7 +22,7 @@ from . import soft_run_batch, soft_run_timing, soft_tally
 
 _CACHE: dict = {}
 
-DEFAULT_SPACE = {"first_cap": [16, 32, 64], "groups_per_block": [2, 4, 8], "group_size": [32, 16]}
+DEFAULT_SPACE = {"first_cap": [16, 32, 64], "groups_per_block": [2, 4, 8], "group_size": [0, 32, 16]}
 
 
 def signature(circs, precision):
@@ -37,11 +39,16 @@ def autotune(circs, precision="fp32", sample_shots=1 << 18, space=None, seed=0x5
     n = len(circs)
     per = max(1, sample_shots // n)
     names = list(space)
-    results = []
+    results, seen = [], set()
     for values in itertools.product(*[space[k] for k in names]):
         kw = dict(zip(names, values))
         gs, gpb = kw.get("group_size", 32), kw.get("groups_per_block", 0)
-        if gpb and gpb > 128 // gs:
+        if gs == 0:  # the library default shape: groups per block do not apply
+            kw["groups_per_block"] = 0
+            if tuple(sorted(kw.items())) in seen:
+                continue
+            seen.add(tuple(sorted(kw.items())))
+        elif gpb and gpb > 128 // gs:
             continue  # more groups than a 128-thread block holds
         if gs == 16 and gpb and gpb != 8:
             continue  # 16-lane groups run full blocks

@@ -349,12 +349,19 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     total += n_shots[i];
   }
   const uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap_max) : std::min(kDefaultFirstCap, cap_max);
-  // lane-per-shot scheduling: one circuit, the noiseless prefix, no state capture, group size
-  // not forced, and a noiseless run whose maps fit a lane's map
+  // lane-per-shot scheduling: the noiseless prefix, no state capture, group size not forced,
+  // every circuit's noiseless run with maps that fit a lane's map, and at most
+  // lane_max_buckets buckets (one per event, plus one, per circuit)
   const int pk = o.precision == SOFT_FP32 ? 1 : 0;
-  const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && n_circ == 1 && !(o.flags & SOFT_RUN_NO_PREFIX) &&
-                     o.capture_k == 0 && o.group_size == 0 && circs[0]->d_traj[pk] &&
-                     circs[0]->traj_max_n[pk] <= soft::lane_map_cap();
+  uint64_t n_buckets = 0;
+  bool lanes_fit = true;
+  for (uint32_t i = 0; i < n_circ; ++i) {
+    n_buckets += circs[i]->hp.ev.size() + 1;
+    lanes_fit = lanes_fit && circs[i]->d_traj[pk] && circs[i]->traj_max_n[pk] <= soft::lane_map_cap();
+  }
+  const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && !(o.flags & SOFT_RUN_NO_PREFIX) && o.capture_k == 0 &&
+                     o.group_size == 0 && lanes_fit && n_buckets <= soft::lane_max_buckets();
+  const uint32_t nb = lanes ? (uint32_t)n_buckets : 0u;
   // a rerun pass finishes the shots whose maps outgrow the first pass (a lane's map, or cap1)
   const bool two_pass = (lanes ? soft::lane_map_cap() : cap1) < cap_max;
   // after lanes, a middle pass (a warp per shot, register map up to cap1) takes the shots whose
@@ -398,14 +405,12 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     arena_bytes += (bytes + 255) & ~(size_t)255;
   };
   need(&r->d_tally, 5 * n_circ * sizeof(unsigned long long));
-  const uint32_t n_ev0 = (uint32_t)circs[0]->hp.ev.size();
   // lanes: cursors (4 words per item, first: 16-byte aligned), (start event, rank) pairs, order,
   // bucket starts, counters
   // then the per-block bucket bases of the block-binned pre-pass
   const uint32_t al_grid = lanes ? soft::lane_prepass_grid() : 0u;
   if (lanes)
-    need(&r->d_al, (7 * chunk + (n_ev0 + 2) + 2 * (size_t)(n_ev0 + 1) + (size_t)al_grid * (n_ev0 + 1)) *
-                       sizeof(uint32_t));
+    need(&r->d_al, (7 * chunk + (nb + 1) + 2 * (size_t)nb + (size_t)al_grid * nb) * sizeof(uint32_t));
   // spill pool: records for the shots a sparse warp evicts (a quarter of the chunk; when it is
   // full, warps keep their shots), then records for shots a lane hands to a warp (an eighth;
   // when full, the warp reruns them from their start). Entries of the rerun list name a record
@@ -494,6 +499,10 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.circ[i].fsum = fid_mode ? r->d_fsum + i : nullptr;
     begin += n_shots[i];
   }
+  for (uint32_t i = 0, b = 0; lanes && i < n_circ; ++i) {  // each circuit's buckets, circuit after circuit
+    p.circ[i].bucket0 = b;
+    b += p.circ[i].n_events + 1;
+  }
   p.circ[0].status = r->d_status;
   p.circ[0].records = r->d_records;
   p.circ[0].out_limit = r->out_limit;
@@ -547,9 +556,10 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.al_ev = r->d_al + 4 * chunk;
     p.al_order = r->d_al + 6 * chunk;
     p.al_start = r->d_al + 7 * chunk;
-    p.al_count = r->d_al + 7 * chunk + (n_ev0 + 2);
-    p.al_next = p.al_count + (n_ev0 + 1);
-    p.al_base = p.al_next + (n_ev0 + 1);
+    p.al_count = r->d_al + 7 * chunk + (nb + 1);
+    p.al_next = p.al_count + nb;
+    p.al_base = p.al_next + nb;
+    p.al_nb = nb;
     p.al_grid = al_grid;
     p.lane_round = 0;
     p.lane_evict = spill && rounds > 1 ? 1u : 0u;
@@ -600,7 +610,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     if (dev_base) a.item_base_dev = b.item_base_dev = c.item_base_dev = r->d_work + 3;
     if ((err = mark()) != cudaSuccess) return err;
     if (lanes) {
-      if ((err = cudaMemsetAsync(a.al_count, 0, 2 * (size_t)(n_ev0 + 1) * sizeof(uint32_t), st)) != cudaSuccess ||
+      if ((err = cudaMemsetAsync(a.al_count, 0, 2 * (size_t)nb * sizeof(uint32_t), st)) != cudaSuccess ||
           (err = soft::launch_lane_prepass(a, st)) != cudaSuccess)
         return err;
       r->launches += 3;
@@ -616,7 +626,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
       ar.lane_round = rd;
       ar.lane_evict = rd + 1 < rounds ? 1u : 0u;
       ar.n_items_dev = r->d_lr + 3 + 2 * rd;
-      if ((err = cudaMemsetAsync(ar.al_count, 0, 2 * (size_t)(n_ev0 + 1) * sizeof(uint32_t), st)) != cudaSuccess ||
+      if ((err = cudaMemsetAsync(ar.al_count, 0, 2 * (size_t)nb * sizeof(uint32_t), st)) != cudaSuccess ||
           (err = soft::launch_lane_resume_prepass(ar, fp32, W, st)) != cudaSuccess ||
           (err = soft::launch_prepared(c1, ar, st)) != cudaSuccess)
         return err;

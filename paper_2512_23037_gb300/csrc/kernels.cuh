@@ -20,7 +20,9 @@ struct CircDev {
   const Site *sites;
   const uint64_t *thr;
   uint32_t n_events, n_sites, rw, cap;  // cap: this circuit's coefficient cap
-  uint32_t n_coef, n_cb, pad0, pad1;
+  uint32_t n_coef, n_cb;
+  uint32_t bucket0;  // lane-per-shot scheduling: the circuit's first bucket (one per event, plus one)
+  uint32_t pad1;
   uint64_t item_begin, n_shots, first_shot;
   unsigned long long *tally;  // [5]: shots, discarded, overflow, kept, logical
   double *fsum;               // fidelity mode: sum of F over kept shots (may be null)
@@ -79,6 +81,7 @@ struct ShotParams {
   uint32_t *al_cursor;  // per item the noise cursor after its first draw (nxt, cur, kblk, w2), 16-byte aligned
   uint32_t *al_base;    // per pre-pass block and bucket: the block's first rank in the bucket
   uint32_t al_grid;     // pre-pass blocks (each bins a contiguous range of items)
+  uint32_t al_nb;       // buckets over all circuits of the run
   // lane-per-shot rounds: a warp left with few active lanes evicts their shots to the spill
   // pool; the next round buckets them by the event they resume at and packs them into warps
   uint32_t lane_round;        // 0: shots from their start buckets; r >= 1: shots evicted before round r
@@ -127,6 +130,7 @@ cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st);
 cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W, cudaStream_t st);
 size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap);
 uint32_t lane_rounds();
+uint32_t lane_max_buckets();  // lane-per-shot runs hold at most this many buckets (events + 1 per circuit)
 uint32_t lane_prepass_grid();  // blocks of the bucketing pre-pass (al_base holds this many rows)
 cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg);
 uint32_t lane_map_cap();

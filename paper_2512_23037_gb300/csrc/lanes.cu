@@ -33,7 +33,7 @@ namespace cg = cooperative_groups;
 
 enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_RERUN = 4, LS_HAND = 5 };
 constexpr int kLaneBlock = 128;
-constexpr uint32_t kBinMaxEvents = 12287;  // block-binned pre-pass: its histogram fits 48 KB of shared memory
+constexpr uint32_t kLaneMaxBuckets = 50000;  // the pre-pass histogram of all buckets: 200 KB of shared memory
 #ifndef SOFT_LANE_EVICT
 #define SOFT_LANE_EVICT 8
 #endif
@@ -621,37 +621,31 @@ struct LaneShot {
   }
 };
 
-// ---- bucketing pre-pass: start event per item, its rank in the bucket, bucket starts, order
-// (lanes of a warp that share a start event, as the shots that begin at the end of the
-// noiseless prefix do, take their ranks with one atomic)
-__global__ void lane_count_kernel(const __grid_constant__ ShotParams P) {
-  const CircDev *C = &P.circ[0];
-  const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
-  const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
-  const uint32_t lane = threadIdx.x & 31u;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  // the loop bound is warp-uniform: blockDim.x is a multiple of 32
-  for (unsigned long long w0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); w0 < n_items;
-       w0 += stride) {
-    const unsigned long long i = w0 + lane;
-    const bool ok = i < n_items;
-    const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok);
-    if (!ok) continue;
-    uint32_t cur = 0, kblk = 0, nxt = 0, w2 = 0;
-    if (!next_site(C, P.seed, C->first_shot + base + i, cur, kblk, nxt, w2)) kblk = 0xFFFFFFFFu;  // marks a failure
-    const uint32_t e = first_event(C, P.fid_mode, nxt);
-    reinterpret_cast<uint4 *>(P.al_cursor)[i] = make_uint4(nxt, cur, kblk, w2);
-    const uint32_t peers = __match_any_sync(act, e);
-    const uint32_t leader = __ffs(peers) - 1;
-    uint32_t r0 = 0;
-    if (lane == leader) r0 = atomicAdd(&P.al_count[e], (uint32_t)__popc(peers));
-    r0 = __shfl_sync(peers, r0, leader);
-    reinterpret_cast<uint2 *>(P.al_ev)[i] = make_uint2(e, r0 + __popc(peers & ((1u << lane) - 1u)));
+// ---- bucketing pre-pass. Buckets: per circuit of the run, one per event plus one
+// (shots that start past the end), circuit after circuit from circuit.bucket0.
+// The circuit of item g: the last one whose item range starts at or before g.
+__device__ __forceinline__ uint32_t circ_of_item(const ShotParams &P, uint64_t g) {
+  uint32_t lo = 0, hi = P.n_circ;
+  while (hi - lo > 1u) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (P.circ[mid].item_begin <= g) lo = mid;
+    else hi = mid;
   }
+  return lo;
+}
+// The circuit of bucket g: the last one whose first bucket is at or before g.
+__device__ __forceinline__ uint32_t circ_of_bucket(const ShotParams &P, uint32_t g) {
+  uint32_t lo = 0, hi = P.n_circ;
+  while (hi - lo > 1u) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (P.circ[mid].bucket0 <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 __global__ void lane_scan_kernel(const __grid_constant__ ShotParams P) {
   __shared__ uint32_t part[1024];
-  const uint32_t nb = P.circ[0].n_events + 1, tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t nb = P.al_nb, tid = threadIdx.x, nt = blockDim.x;
   const uint32_t per = (nb + nt - 1) / nt, lo = tid * per < nb ? tid * per : nb, hi = lo + per < nb ? lo + per : nb;
   uint32_t sum = 0;
   for (uint32_t k = lo; k < hi; ++k) sum += P.al_count[k];
@@ -673,15 +667,6 @@ __global__ void lane_scan_kernel(const __grid_constant__ ShotParams P) {
     run += P.al_count[k];
   }
 }
-__global__ void lane_scatter_kernel(const __grid_constant__ ShotParams P) {
-  const unsigned long long n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_items;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    const uint2 er = reinterpret_cast<const uint2 *>(P.al_ev)[i];
-    P.al_order[P.al_start[er.x] + er.y] = (uint32_t)i;
-  }
-}
-
 // ---- round r >= 1: its records are those taken since round r - 1 began (the pool's
 // count, capped at its capacity: reservations past it were not written)
 __global__ void lane_round_setup_kernel(const __grid_constant__ ShotParams P) {
@@ -691,40 +676,14 @@ __global__ void lane_round_setup_kernel(const __grid_constant__ ShotParams P) {
   P.lr[2 + 2 * r] = first;
   P.lr[3 + 2 * r] = used > first ? used - first : 0ull;
 }
-template <typename R, int W>
-__global__ void lane_count_resume_kernel(const __grid_constant__ ShotParams P) {
-  const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
-  const uint32_t n_ev = P.circ[0].n_events;
-  const unsigned long long n_items = P.lr[3 + 2 * P.lane_round];
-  const unsigned long long first = P.lr[2 + 2 * P.lane_round];
-  const uint32_t lane = threadIdx.x & 31u;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long w0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); w0 < n_items;
-       w0 += stride) {
-    const unsigned long long i = w0 + lane;
-    const bool ok = i < n_items;
-    const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok);
-    if (!ok) continue;
-    uint32_t e = S.ha[first + i].y;
-    if (e > n_ev) e = n_ev;  // a record always resumes at an event of the circuit
-    const uint32_t peers = __match_any_sync(act, e);
-    const uint32_t leader = __ffs(peers) - 1;
-    uint32_t r0 = 0;
-    if (lane == leader) r0 = atomicAdd(&P.al_count[e], (uint32_t)__popc(peers));
-    r0 = __shfl_sync(peers, r0, leader);
-    reinterpret_cast<uint2 *>(P.al_ev)[i] = make_uint2(e, r0 + __popc(peers & ((1u << lane) - 1u)));
-  }
-}
-
-// ---- block-binned pre-pass (circuits of at most kBinMaxEvents events): each block
-// ranks its contiguous range of items per bucket with shared-memory atomics, then
-// takes one global atomic per non-empty bucket for its base. The first errors
-// cluster in a few buckets, and global atomics on one address serialise.
+// ---- block-binned pre-pass: each block ranks its contiguous range of items per
+// bucket with shared-memory atomics, then takes one global atomic per non-empty
+// bucket for its base. The first errors cluster in a few buckets, and global
+// atomics on one address serialise.
 template <bool Resume, typename R, int W>
 __global__ void __launch_bounds__(256) lane_bin_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ uint32_t hist[];
-  const CircDev *C = &P.circ[0];
-  const uint32_t n_ev = C->n_events, nb = n_ev + 1;
+  const uint32_t nb = P.al_nb;
   for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) hist[k] = 0u;
   __syncthreads();
   const unsigned long long n_items =
@@ -734,16 +693,21 @@ __global__ void __launch_bounds__(256) lane_bin_kernel(const __grid_constant__ S
   const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
   for (unsigned long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     uint32_t e;
+    const CircDev *C;
     if (Resume) {
       const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
-      e = S.ha[P.lr[2 + 2 * P.lane_round] + i].y;
-      if (e > n_ev) e = n_ev;  // a record always resumes at an event of the circuit
+      const uint4 a = S.ha[P.lr[2 + 2 * P.lane_round] + i];
+      C = &P.circ[circ_of_item(P, base + a.x)];
+      e = a.y < C->n_events ? a.y : C->n_events;  // a record always resumes at an event of its circuit
     } else {
+      C = &P.circ[circ_of_item(P, base + i)];
       uint32_t cur = 0, kblk = 0, nxt = 0, w2 = 0;
-      if (!next_site(C, P.seed, C->first_shot + base + i, cur, kblk, nxt, w2)) kblk = 0xFFFFFFFFu;  // a failure
+      if (!next_site(C, P.seed, C->first_shot + (base + i - C->item_begin), cur, kblk, nxt, w2))
+        kblk = 0xFFFFFFFFu;  // a failure
       e = first_event(C, P.fid_mode, nxt);
       reinterpret_cast<uint4 *>(P.al_cursor)[i] = make_uint4(nxt, cur, kblk, w2);
     }
+    e += C->bucket0;
     reinterpret_cast<uint2 *>(P.al_ev)[i] = make_uint2(e, atomicAdd(&hist[e], 1u));
   }
   __syncthreads();
@@ -755,7 +719,7 @@ __global__ void __launch_bounds__(256) lane_bin_kernel(const __grid_constant__ S
 // (same grid as lane_bin_kernel: it fixes each item's block)
 template <bool Resume>
 __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_constant__ ShotParams P) {
-  const uint32_t nb = P.circ[0].n_events + 1;
+  const uint32_t nb = P.al_nb;
   const unsigned long long n_items =
       Resume ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
   const unsigned long long per = (n_items + gridDim.x - 1) / gridDim.x;
@@ -766,36 +730,53 @@ __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_cons
   }
 }
 
-template <typename R, int W>
+// Multi: the run holds several circuits (a warp serves one at a time); the single-
+// circuit instantiation keeps circuit 0 and bucket offset 0 as constants.
+template <typename R, int W, bool Multi>
 __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long btally[5];
-  for (uint32_t i = threadIdx.x; i < 5; i += blockDim.x) btally[i] = 0ull;
-  __syncthreads();
+  // per warp: tallies of its current circuit, added to the circuit's when the warp moves
+  // to another circuit and at the end
+  __shared__ unsigned long long wt[kLaneBlock / 32][5];
   const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x & 31u;
+  if (lane < 5) wt[warp][lane] = 0ull;
+  __syncwarp();
   LaneShot<R, W> s(P, smem + (size_t)warp * lane_warp_bytes<R, W>(P.rw_max));
-  const CircDev *C = &P.circ[0];
-  const uint32_t n_ev = C->n_events;
-  const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
   const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
   const unsigned long long n_items =
       P.lane_round ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
   const unsigned long long rec0 = P.lane_round ? P.lr[2 + 2 * P.lane_round] : 0ull;
   const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
-  bool active = false;
-  // warps start spread evenly over the events, so that they meet buckets that still hold shots
+  const uint32_t nb = P.al_nb;
+  // warps start spread evenly over all buckets, so that they meet buckets that still hold shots
   const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x / 32) + warp;
   const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x / 32);
-  uint32_t item = 0, e = (uint32_t)((gw * (n_ev + 1ull)) / nw);
-  const unsigned long long limit = (n_items + 2ull) * (n_ev + 2ull) + 64ull;
+  uint32_t g = (uint32_t)((gw * (unsigned long long)nb) / nw);
+  uint32_t ci = Multi ? circ_of_bucket(P, g) : 0u;
+  const CircDev *C = &P.circ[ci];
+  uint32_t n_ev = C->n_events, e = Multi ? g - C->bucket0 : g;
+  const Ev<W> *evs = reinterpret_cast<const Ev<W> *>(C->ev);
+  s.C = C;
+  auto flush = [&]() {  // the warp's tallies into its current circuit's
+    __syncwarp();
+    if (lane < 5 && wt[warp][lane]) {
+      atomicAdd(&C->tally[lane], wt[warp][lane]);
+      wt[warp][lane] = 0ull;
+    }
+    __syncwarp();
+  };
+  bool active = false;
+  uint32_t item = 0;
+  const unsigned long long limit = (n_items + 2ull) * (nb + 2ull) + 64ull;
   for (unsigned long long guard = 0; guard < limit; ++guard) {
-    // idle lanes claim shots that start at event e (one atomic per warp)
+    g = Multi ? C->bucket0 + e : e;
+    // idle lanes claim shots that start at event e of circuit ci (one atomic per warp)
     const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
     if (idle) {
-      const uint32_t b0 = __ldg(&P.al_start[e]), sz = __ldg(&P.al_start[e + 1]) - b0;
+      const uint32_t b0 = __ldg(&P.al_start[g]), sz = __ldg(&P.al_start[g + 1]) - b0;
       uint32_t got0 = 0;
       const uint32_t leader = __ffs(idle) - 1;
-      if (lane == leader) got0 = *(volatile unsigned int *)&P.al_next[e] < sz ? atomicAdd(&P.al_next[e], __popc(idle)) : sz;
+      if (lane == leader) got0 = *(volatile unsigned int *)&P.al_next[g] < sz ? atomicAdd(&P.al_next[g], __popc(idle)) : sz;
       got0 = __shfl_sync(0xFFFFFFFFu, got0, leader);
       if (!active) {
         const uint32_t k = got0 + __popc(idle & ((1u << lane) - 1u));
@@ -803,8 +784,9 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
           item = __ldg(&P.al_order[b0 + k]);
           if (item < n_items) {
             active = true;
-            if (P.lane_round) item = s.resume(S, (uint32_t)(rec0 + item), C->first_shot + base);
-            else s.begin(C->first_shot + base + item, e, reinterpret_cast<const uint4 *>(P.al_cursor)[item]);
+            const uint64_t first = C->first_shot + base - (Multi ? C->item_begin : 0ull);  // shot of item i: first + i
+            if (P.lane_round) item = s.resume(S, (uint32_t)(rec0 + item), first);
+            else s.begin(first + item, e, reinterpret_cast<const uint4 *>(P.al_cursor)[item]);
           }
         }
       }
@@ -825,7 +807,7 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
     // finish: ended, or past the last event
     if (active && (s.status != LS_RUN || e + 1u >= n_ev)) {
       if (s.status == LS_RUN) s.status = LS_KEPT;
-      const uint64_t off = base + item;
+      const uint64_t off = base + item - (Multi ? C->item_begin : 0ull);  // the shot's offset within its circuit
       uint32_t entry = item;  // a rerun starts the shot again from its start
       if (s.status == LS_HAND) {  // or a warp resumes it from its state at the top of event e
         const unsigned long long h = atomicAdd(&P.lr[1], 1ull);
@@ -841,12 +823,12 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
         if (i < P.rerun_cap) P.rerun[i] = entry;
         if (P.n_rerun_total) atomicAdd(P.n_rerun_total, 1ull);
       } else {
-        atomicAdd(&btally[0], 1ull);
-        if (s.status == LS_DISC) atomicAdd(&btally[1], 1ull);
-        else if (s.status == LS_OVF) atomicAdd(&btally[2], 1ull);
+        atomicAdd(&wt[warp][0], 1ull);
+        if (s.status == LS_DISC) atomicAdd(&wt[warp][1], 1ull);
+        else if (s.status == LS_OVF) atomicAdd(&wt[warp][2], 1ull);
         else if (s.status == LS_KEPT) {
-          atomicAdd(&btally[3], 1ull);
-          if (s.logical) atomicAdd(&btally[4], 1ull);
+          atomicAdd(&wt[warp][3], 1ull);
+          if (s.logical) atomicAdd(&wt[warp][4], 1ull);
           if (P.fid_mode && C->fsum) atomicAdd(C->fsum, s.fid);
         }
         if (off < C->out_limit) {
@@ -876,13 +858,14 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
         }
       }
     }
-    uint32_t en = e + 1u > n_ev ? 0u : e + 1u;
+    uint32_t en = e + 1u > n_ev ? 0u : e + 1u;  // (within the circuit, cyclically)
     if (!__any_sync(0xFFFFFFFFu, active)) {
-      // all lanes idle: the next bucket (cyclically) that still has shots, or stop
+      // all lanes idle: the next bucket of any circuit (cyclically) that still has shots, or stop
       uint32_t found = 0xFFFFFFFFu;
       if (lane == 0) {
-        for (uint32_t k = 0; k <= n_ev; ++k) {
-          const uint32_t c = (en + k) % (n_ev + 1u);
+        const uint32_t g1 = (Multi ? C->bucket0 : 0u) + en;
+        for (uint32_t k = 0; k < nb; ++k) {
+          const uint32_t c = (g1 + k) % nb;
           if (*(volatile unsigned int *)&P.al_next[c] < __ldg(&P.al_start[c + 1]) - __ldg(&P.al_start[c])) {
             found = c;
             break;
@@ -891,13 +874,24 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
       }
       found = __shfl_sync(0xFFFFFFFFu, found, 0);
       if (found == 0xFFFFFFFFu) break;
-      en = found;
+      if (Multi) {
+        const uint32_t cn = circ_of_bucket(P, found);
+        if (cn != ci) {
+          flush();
+          ci = cn;
+          C = &P.circ[ci];
+          n_ev = C->n_events;
+          evs = reinterpret_cast<const Ev<W> *>(C->ev);
+          s.C = C;
+        }
+        en = found - C->bucket0;
+      } else {
+        en = found;
+      }
     }
     e = en;
   }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < 5; i += blockDim.x)
-    if (btally[i]) atomicAdd(&P.circ[0].tally[i], btally[i]);
+  flush();
 }
 
 }  // namespace
@@ -910,6 +904,7 @@ size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw) {
 
 uint32_t lane_map_cap() { return kLaneCap; }
 uint32_t lane_rounds() { return kLaneRounds; }
+uint32_t lane_max_buckets() { return kLaneMaxBuckets; }
 uint32_t lane_prepass_grid() {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -922,55 +917,40 @@ size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap) {
               : (W == 1 ? Spill<double, 1>::bytes(cap, rw) : Spill<double, 2>::bytes(cap, rw));
 }
 
-cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W, cudaStream_t st) {
-  const unsigned grid = p.al_grid;
-  lane_round_setup_kernel<<<1, 1, 0, st>>>(p);
-  const uint32_t nb = p.circ[0].n_events + 1;
-  if (nb <= kBinMaxEvents + 1) {
-    const size_t sh = (size_t)nb * sizeof(uint32_t);
-    if (fp32) {
-      if (W == 1) lane_bin_kernel<true, float, 1><<<grid, 256, sh, st>>>(p);
-      else lane_bin_kernel<true, float, 2><<<grid, 256, sh, st>>>(p);
-    } else {
-      if (W == 1) lane_bin_kernel<true, double, 1><<<grid, 256, sh, st>>>(p);
-      else lane_bin_kernel<true, double, 2><<<grid, 256, sh, st>>>(p);
-    }
-    lane_scan_kernel<<<1, 1024, 0, st>>>(p);
-    lane_bin_scatter_kernel<true><<<grid, 256, 0, st>>>(p);
-    return cudaGetLastError();
+// the histogram of all buckets in shared memory (above 48 KB by the opt-in attribute)
+template <bool Resume, typename R, int W>
+static cudaError_t launch_bin(const ShotParams &p, cudaStream_t st) {
+  const size_t sh = (size_t)p.al_nb * sizeof(uint32_t);
+  if (sh > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(lane_bin_kernel<Resume, R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
   }
-  if (fp32) {
-    if (W == 1) lane_count_resume_kernel<float, 1><<<grid, 256, 0, st>>>(p);
-    else lane_count_resume_kernel<float, 2><<<grid, 256, 0, st>>>(p);
-  } else {
-    if (W == 1) lane_count_resume_kernel<double, 1><<<grid, 256, 0, st>>>(p);
-    else lane_count_resume_kernel<double, 2><<<grid, 256, 0, st>>>(p);
-  }
+  lane_bin_kernel<Resume, R, W><<<p.al_grid, 256, sh, st>>>(p);
   lane_scan_kernel<<<1, 1024, 0, st>>>(p);
-  lane_scatter_kernel<<<grid, 256, 0, st>>>(p);
+  lane_bin_scatter_kernel<Resume><<<p.al_grid, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st) {
-  const unsigned grid = p.al_grid;
-  const uint32_t nb = p.circ[0].n_events + 1;
-  if (nb <= kBinMaxEvents + 1) {
-    lane_bin_kernel<false, float, 1><<<grid, 256, (size_t)nb * sizeof(uint32_t), st>>>(p);
-    lane_scan_kernel<<<1, 1024, 0, st>>>(p);
-    lane_bin_scatter_kernel<false><<<grid, 256, 0, st>>>(p);
-    return cudaGetLastError();
-  }
-  lane_count_kernel<<<grid, 256, 0, st>>>(p);
-  lane_scan_kernel<<<1, 1024, 0, st>>>(p);
-  lane_scatter_kernel<<<grid, 256, 0, st>>>(p);
-  return cudaGetLastError();
+cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W, cudaStream_t st) {
+  lane_round_setup_kernel<<<1, 1, 0, st>>>(p);
+  if (fp32) return W == 1 ? launch_bin<true, float, 1>(p, st) : launch_bin<true, float, 2>(p, st);
+  return W == 1 ? launch_bin<true, double, 1>(p, st) : launch_bin<true, double, 2>(p, st);
 }
+
+cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st) { return launch_bin<false, float, 1>(p, st); }
 
 cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg) {
-  const void *kern = fp32 ? (W == 1 ? reinterpret_cast<const void *>(lane_kernel<float, 1>)
-                                    : reinterpret_cast<const void *>(lane_kernel<float, 2>))
-                          : (W == 1 ? reinterpret_cast<const void *>(lane_kernel<double, 1>)
-                                    : reinterpret_cast<const void *>(lane_kernel<double, 2>));
+  const bool multi = p.n_circ > 1;
+  const void *kern =
+      fp32 ? (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<float, 1, true>)
+                              : reinterpret_cast<const void *>(lane_kernel<float, 1, false>))
+                     : (multi ? reinterpret_cast<const void *>(lane_kernel<float, 2, true>)
+                              : reinterpret_cast<const void *>(lane_kernel<float, 2, false>)))
+           : (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<double, 1, true>)
+                              : reinterpret_cast<const void *>(lane_kernel<double, 1, false>))
+                     : (multi ? reinterpret_cast<const void *>(lane_kernel<double, 2, true>)
+                              : reinterpret_cast<const void *>(lane_kernel<double, 2, false>)));
   const size_t smem = lane_smem_bytes(fp32, W, p.rw_max);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

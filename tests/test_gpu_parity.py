@@ -276,6 +276,52 @@ def test_batch_matches_single_runs_and_oracle(soft, precision):
     assert tot["shots"] == sum(shots)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_lane_per_shot(soft, precision):
+    """A batch of windowed circuits of different sizes runs lane per shot (a
+    bucket range per circuit, warps moving between circuits): per-circuit
+    tallies against the warp-per-shot batch, and (FP64) the oracle's."""
+    S = soft
+    batch = [C.windowed(40 + k, blocks=2 + k % 4, n_data=30 + 4 * k, p=3e-3) for k in range(5)]
+    circs = [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz in batch]
+    shots = [3000 + 500 * k for k in range(len(batch))]
+    firsts = [777 * k for k in range(len(batch))]
+    r = S.soft_run_batch(circs, shots, firsts, 8, precision=precision, time_passes=True)
+    assert S.soft_run_pass_timing(r)[0][0] > 0.0  # the lane pre-pass ran
+    rw = S.soft_run_batch(circs, shots, firsts, 8, precision=precision, lanes=False)
+    key = ("shots", "discarded", "overflow", "kept", "logical_errors")
+    for i, ((circ, noise), n) in enumerate(zip(batch, shots)):
+        tb, tw = S.soft_tally_batch(r, i), S.soft_tally_batch(rw, i)
+        assert tb["shots"] == tw["shots"] == n
+        assert all(abs(tb[k] - tw[k]) <= 2 for k in key), (i, tb, tw)
+        if precision == "fp64":
+            ref = oracle.run(circ, circ.n, noise, circ.cap, 8, firsts[i], n, threads=8, records=False)
+            assert all(abs(a - b) <= 2 for a, b in zip([tb[k] for k in key], ref["tally"])), (i, tb, ref["tally"])
+    assert S.soft_tally(r)["shots"] == sum(shots)
+
+
+def test_autotune_choice_is_valid_and_exact(soft):
+    """The autotuner times every candidate shape of a reduced space (the library
+    default, lane per shot, among them) on a batch and returns the fastest; a run
+    with its choice gives the default run's per-circuit tallies (up to outcomes
+    within rounding)."""
+    from paper_2512_23037_gb300.autotune import autotune
+    S = soft
+    batch = [C.windowed(60 + k, blocks=2, n_data=30, p=3e-3) for k in range(3)]
+    circs = [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz in batch]
+    space = {"first_cap": [32, 64], "groups_per_block": [4], "group_size": [0, 32]}
+    res = autotune(circs, precision="fp32", sample_shots=1 << 14, space=space, repeats=1)
+    assert len(res["table"]) == 4 and res["best"] in [kw for _, kw in res["table"]]
+    assert all(ms > 0 for ms, _ in res["table"])
+    shots, firsts = [4000] * 3, [0, 5000, 10000]
+    r = S.soft_run_batch(circs, shots, firsts, 2, precision="fp32", **res["best"])
+    r0 = S.soft_run_batch(circs, shots, firsts, 2, precision="fp32")
+    for i in range(3):
+        a, b = S.soft_tally_batch(r, i), S.soft_tally_batch(r0, i)
+        assert a["shots"] == b["shots"] == 4000
+        assert all(abs(a[k] - b[k]) <= 2 for k in ("discarded", "kept", "logical_errors"))
+
+
 def test_batch_with_global_memory_reruns(soft):
     """A batch where one circuit's cap (2^12) forces global-memory reruns."""
     S = soft
