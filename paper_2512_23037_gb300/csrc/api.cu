@@ -350,17 +350,18 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   }
   const uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap_max) : std::min(kDefaultFirstCap, cap_max);
   // lane-per-shot scheduling: the noiseless prefix, no state capture, group size not forced,
-  // every circuit's noiseless run with maps that fit a lane's map, and at most
-  // lane_max_buckets buckets (one per event, plus one, per circuit)
+  // a circuit whose noiseless run's maps fit a lane's map, and at most lane_max_buckets
+  // buckets (one per event, plus one, per such circuit). The shots of the other circuits of a
+  // batch go straight to the warp pass that follows the lanes.
   const int pk = o.precision == SOFT_FP32 ? 1 : 0;
   uint64_t n_buckets = 0;
-  bool lanes_fit = true;
+  std::vector<char> fits(n_circ);
   for (uint32_t i = 0; i < n_circ; ++i) {
-    n_buckets += circs[i]->hp.ev.size() + 1;
-    lanes_fit = lanes_fit && circs[i]->d_traj[pk] && circs[i]->traj_max_n[pk] <= soft::lane_map_cap();
+    fits[i] = circs[i]->d_traj[pk] && circs[i]->traj_max_n[pk] <= soft::lane_map_cap();
+    if (fits[i]) n_buckets += circs[i]->hp.ev.size() + 1;
   }
   const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && !(o.flags & SOFT_RUN_NO_PREFIX) && o.capture_k == 0 &&
-                     o.group_size == 0 && lanes_fit && n_buckets <= soft::lane_max_buckets();
+                     o.group_size == 0 && n_buckets > 0 && n_buckets <= soft::lane_max_buckets();
   const uint32_t nb = lanes ? (uint32_t)n_buckets : 0u;
   // a rerun pass finishes the shots whose maps outgrow the first pass (a lane's map, or cap1)
   const bool two_pass = (lanes ? soft::lane_map_cap() : cap1) < cap_max;
@@ -410,7 +411,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   // then the per-block bucket bases of the block-binned pre-pass
   const uint32_t al_grid = lanes ? soft::lane_prepass_grid() : 0u;
   if (lanes)
-    need(&r->d_al, (7 * chunk + (nb + 1) + 2 * (size_t)nb + (size_t)al_grid * nb) * sizeof(uint32_t));
+    need(&r->d_al, (7 * chunk + (nb + 1) + 2 * (size_t)nb + (size_t)al_grid * (nb + 1)) * sizeof(uint32_t));
   // spill pool: records for the shots a sparse warp evicts (a quarter of the chunk; when it is
   // full, warps keep their shots), then records for shots a lane hands to a warp (an eighth;
   // when full, the warp reruns them from their start). Entries of the rerun list name a record
@@ -501,7 +502,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   }
   for (uint32_t i = 0, b = 0; lanes && i < n_circ; ++i) {  // each circuit's buckets, circuit after circuit
     p.circ[i].bucket0 = b;
-    b += p.circ[i].n_events + 1;
+    p.circ[i].lanes_off = fits[i] ? 0u : 1u;
+    if (fits[i]) b += p.circ[i].n_events + 1;
   }
   p.circ[0].status = r->d_status;
   p.circ[0].records = r->d_records;

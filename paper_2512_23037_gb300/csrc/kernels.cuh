@@ -21,8 +21,8 @@ struct CircDev {
   const uint64_t *thr;
   uint32_t n_events, n_sites, rw, cap;  // cap: this circuit's coefficient cap
   uint32_t n_coef, n_cb;
-  uint32_t bucket0;  // lane-per-shot scheduling: the circuit's first bucket (one per event, plus one)
-  uint32_t pad1;
+  uint32_t bucket0;    // lane-per-shot scheduling: the circuit's first bucket (one per event, plus one)
+  uint32_t lanes_off;  // 1: its maps outgrow a lane; its shots go straight to the warp pass (no buckets)
   uint64_t item_begin, n_shots, first_shot;
   unsigned long long *tally;  // [5]: shots, discarded, overflow, kept, logical
   double *fsum;               // fidelity mode: sum of F over kept shots (may be null)
@@ -79,7 +79,8 @@ struct ShotParams {
   uint32_t *al_order, *al_start;
   unsigned int *al_count, *al_next;
   uint32_t *al_cursor;  // per item the noise cursor after its first draw (nxt, cur, kblk, w2), 16-byte aligned
-  uint32_t *al_base;    // per pre-pass block and bucket: the block's first rank in the bucket
+  uint32_t *al_base;    // per pre-pass block: the block's first rank in each bucket, then its first
+                        // slot in the warp pass's list (al_nb + 1 words per block)
   uint32_t al_grid;     // pre-pass blocks (each bins a contiguous range of items)
   uint32_t al_nb;       // buckets over all circuits of the run
   // lane-per-shot rounds: a warp left with few active lanes evicts their shots to the spill

@@ -680,11 +680,13 @@ __global__ void lane_round_setup_kernel(const __grid_constant__ ShotParams P) {
 // bucket with shared-memory atomics, then takes one global atomic per non-empty
 // bucket for its base. The first errors cluster in a few buckets, and global
 // atomics on one address serialise.
+// Items of circuits whose maps outgrow a lane go to the warp pass's list instead: the
+// block ranks them too and reserves their slots with one global atomic.
 template <bool Resume, typename R, int W>
 __global__ void __launch_bounds__(256) lane_bin_kernel(const __grid_constant__ ShotParams P) {
-  extern __shared__ uint32_t hist[];
+  extern __shared__ uint32_t hist[];  // nb buckets, then the block's count of warp-pass items
   const uint32_t nb = P.al_nb;
-  for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) hist[k] = 0u;
+  for (uint32_t k = threadIdx.x; k <= nb; k += blockDim.x) hist[k] = 0u;
   __syncthreads();
   const unsigned long long n_items =
       Resume ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
@@ -701,6 +703,10 @@ __global__ void __launch_bounds__(256) lane_bin_kernel(const __grid_constant__ S
       e = a.y < C->n_events ? a.y : C->n_events;  // a record always resumes at an event of its circuit
     } else {
       C = &P.circ[circ_of_item(P, base + i)];
+      if (C->lanes_off) {
+        reinterpret_cast<uint2 *>(P.al_ev)[i] = make_uint2(kNoRecord, atomicAdd(&hist[nb], 1u));
+        continue;
+      }
       uint32_t cur = 0, kblk = 0, nxt = 0, w2 = 0;
       if (!next_site(C, P.seed, C->first_shot + (base + i - C->item_begin), cur, kblk, nxt, w2))
         kblk = 0xFFFFFFFFu;  // a failure
@@ -713,8 +719,10 @@ __global__ void __launch_bounds__(256) lane_bin_kernel(const __grid_constant__ S
   __syncthreads();
   for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
     const uint32_t c = hist[k];
-    P.al_base[(size_t)blockIdx.x * nb + k] = c ? atomicAdd(&P.al_count[k], c) : 0u;
+    P.al_base[(size_t)blockIdx.x * (nb + 1) + k] = c ? atomicAdd(&P.al_count[k], c) : 0u;
   }
+  if (threadIdx.x == 0)
+    P.al_base[(size_t)blockIdx.x * (nb + 1) + nb] = hist[nb] ? (uint32_t)atomicAdd(P.n_rerun, (unsigned long long)hist[nb]) : 0u;
 }
 // (same grid as lane_bin_kernel: it fixes each item's block)
 template <bool Resume>
@@ -726,7 +734,12 @@ __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_cons
   const unsigned long long i0 = blockIdx.x * per, i1 = i0 + per < n_items ? i0 + per : n_items;
   for (unsigned long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const uint2 er = reinterpret_cast<const uint2 *>(P.al_ev)[i];
-    P.al_order[P.al_start[er.x] + P.al_base[(size_t)blockIdx.x * nb + er.x] + er.y] = (uint32_t)i;
+    if (er.x == kNoRecord) {  // a shot of a circuit without lanes: the warp pass's list
+      const unsigned long long slot = P.al_base[(size_t)blockIdx.x * (nb + 1) + nb] + er.y;
+      if (slot < P.rerun_cap) P.rerun[slot] = (uint32_t)i;
+      continue;
+    }
+    P.al_order[P.al_start[er.x] + P.al_base[(size_t)blockIdx.x * (nb + 1) + er.x] + er.y] = (uint32_t)i;
   }
 }
 
@@ -920,7 +933,7 @@ size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap) {
 // the histogram of all buckets in shared memory (above 48 KB by the opt-in attribute)
 template <bool Resume, typename R, int W>
 static cudaError_t launch_bin(const ShotParams &p, cudaStream_t st) {
-  const size_t sh = (size_t)p.al_nb * sizeof(uint32_t);
+  const size_t sh = ((size_t)p.al_nb + 1) * sizeof(uint32_t);
   if (sh > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(lane_bin_kernel<Resume, R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);

@@ -277,12 +277,18 @@ def test_batch_matches_single_runs_and_oracle(soft, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_batch_lane_per_shot(soft, precision):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_lane_per_shot(soft, precision, mixed):
     """A batch of windowed circuits of different sizes runs lane per shot (a
-    bucket range per circuit, warps moving between circuits): per-circuit
-    tallies against the warp-per-shot batch, and (FP64) the oracle's."""
+    bucket range per circuit, warps moving between circuits); mixed: circuits
+    with 5- and 6-qubit windows (maps beyond a lane) among them, whose shots go
+    straight to the warp pass. Per-circuit tallies against the warp-per-shot
+    batch, and (FP64) the oracle's."""
     S = soft
     batch = [C.windowed(40 + k, blocks=2 + k % 4, n_data=30 + 4 * k, p=3e-3) for k in range(5)]
+    if mixed:
+        batch.insert(1, C.windowed(50, blocks=3, n_data=28, w=5, p=2e-3))
+        batch.insert(4, C.windowed(51, blocks=2, n_data=32, w=6, p=2e-3))
     circs = [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz in batch]
     shots = [3000 + 500 * k for k in range(len(batch))]
     firsts = [777 * k for k in range(len(batch))]
