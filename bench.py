@@ -402,7 +402,9 @@ def main():
     tuned = None
     if args.autotune:
         from paper_2512_23037_gb300.autotune import autotune
-        res = autotune(compile_all(), precision="fp32", stream=stream)
+        # a sample of 2^22 shots: lane-per-shot runs pay a pre-pass per launch, so small samples
+        # would favour the warp per shot over what the full step measures
+        res = autotune(compile_all(), precision="fp32", stream=stream, sample_shots=1 << 22)
         tune.update(res["best"])
         tuned = {"best": res["best"], "table_ms": [[round(ms, 3), kw] for ms, kw in res["table"]]}
 
