@@ -70,9 +70,6 @@ Row row_of(const Pz &p) {
 
 inline int bit(const uint64_t *v, uint32_t i) { return (int)((v[i >> 6] >> (i & 63)) & 1u); }
 inline void flip(uint64_t *v, uint32_t i) { v[i >> 6] ^= 1ull << (i & 63); }
-inline void put(uint64_t *v, uint32_t i, int b) {
-  if (bit(v, i) != b) flip(v, i);
-}
 
 // Local two-qubit Pauli i^e X^x Z^z (bit 0 = first qubit, bit 1 = second).
 struct L2 {
@@ -165,12 +162,6 @@ struct Tableau {
       pend_s[i >> 6] ^= (uint64_t)(fs & 1) << (i & 63);
     }
     return !(bad & 0x80);
-  }
-
-  static bool anti(const Pz &q, const Row &r) {
-    int t = 0;
-    for (int w = 0; w < 2; ++w) t += pc((q.x[w] & r.z[w]) ^ (q.z[w] & r.x[w]));
-    return t & 1;
   }
 
   // Q = i^e0 d_beta s_gamma at zero signs. NW: the 64-bit words in use. Bits are set
