@@ -7,10 +7,13 @@
 // bucket of the event it is at, load the noiseless run's state there, and the
 // warp executes each event once for all its lanes: the event is decoded once,
 // and every lane updates its own shot's coefficient map, kept in shared memory
-// (entry i of lane l at row i, column l). A map that outgrows kLaneCap entries
-// ends the shot as a rerun; the rerun pass of the warp-per-shot kernel finishes
-// it at the full capacity. The per-shot arithmetic is that of the warp-per-shot
-// kernel (the same formulas, pruning thresholds and outcome rule), entry by entry.
+// (entry i of lane l at row i, column l). A rotation whose map would outgrow
+// kLaneCap entries hands the shot over: its state at the top of that event goes
+// to a spill record, which the warp-per-shot kernel's next pass resumes. The
+// per-shot arithmetic is that of the warp-per-shot kernel (the same formulas,
+// pruning thresholds and outcome rule), entry by entry. In a batch, each circuit
+// has its own range of buckets and a warp serves one circuit at a time; the shots
+// of circuits whose maps outgrow a lane go straight to the warp pass.
 //
 // Most shots end at the first detector after their first error, but a few run to
 // the end of the circuit, and they would hold a warp with a few active lanes. So a
