@@ -158,9 +158,15 @@ def profile_traffic(kernel_src_hash, name, shots_per_launch):
 
 
 def kernel_hash():
+    """sha256 prefix of the shot kernels' sources, code only: every line with its
+    `//` comment and surrounding whitespace removed, blank lines dropped (the
+    files hold no block comments and no string with `//`)."""
     h = hashlib.sha256()
     for f in ("kernels.cu", "kernels.cuh", "program.h", "device_common.cuh", "lanes.cu", "shot_common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2512_23037_gb300", "csrc", f), "rb").read())
+        for line in open(os.path.join(ROOT, "paper_2512_23037_gb300", "csrc", f), encoding="utf-8"):
+            code = line.split("//", 1)[0].strip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
