@@ -46,9 +46,10 @@ OPS_T_OUT, OPS_T_DIAG, OPS_MEAS, OPS_NOISE = 18, 9, 8, 3
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--shots", type=int, default=1 << 23, help="shots per step per GPU")
+    ap.add_argument("--shots", type=int, default=1 << 24,
+                    help="shots per step per GPU (default: 6 steps of 2^24 = 1.0e8 shots, the w42 job size)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

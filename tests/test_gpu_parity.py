@@ -197,12 +197,12 @@ def test_zero_and_one_shot(soft):
 
 
 def test_bench_config_sampled(soft):
-    """The bench's launch configuration (w42, FP32, 2^23 shots in one chunk,
+    """The bench's launch configuration (w42, FP32, 2^24 shots in one chunk,
     default tuning: lane per shot, eviction rounds, handover, middle pass):
     tallies are consistent and sampled shots match the oracle."""
     S = soft
     circ, noise = C.workload("w42")
-    n = 1 << 23
+    n = 1 << 24
     c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
     r = S.soft_run_shots(c, n, 0, 0, precision="fp32", record_mode=S.REC_ALL)
     rec, st = S.soft_get_records(r, n)
