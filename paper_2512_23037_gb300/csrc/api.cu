@@ -331,7 +331,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   const bool use_graph = (o.flags & SOFT_RUN_GRAPH) != 0;
   const bool fid_mode = (o.flags & SOFT_RUN_FIDELITY) != 0;
   if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY | SOFT_RUN_NO_PREFIX | SOFT_RUN_NO_LANES |
-                          SOFT_RUN_TIME_PASSES))
+                          SOFT_RUN_TIME_PASSES | SOFT_RUN_NO_WIDE_LANES))
     return fail(SOFT_E_ARG, "unknown run flags");
   if (use_graph && !o.stream) return fail(SOFT_E_ARG, "graph replay needs a non-default stream");
   const int fp32 = o.precision == SOFT_FP32;
@@ -420,7 +420,13 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   const bool spill = lanes && (rounds > 1 || two_pass) && chunk < (1ull << 31);
   const uint32_t sp_evict = rounds > 1 ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 4) : 0u;
   const uint32_t sp_hand = two_pass ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 8) : 0u;
-  const size_t n_lr = 4 + 2 * (size_t)rounds;
+  // the wide round: the handed-over shots continue in lanes of twice the map (their records
+  // are its input), and only those that outgrow it rerun in a warp. FP32 single-circuit runs
+  // only: with FP64 maps, or in batches, it measured slower than handing the shots to warps
+  // (w42: FP32 550.0 M shots/s against 533.0 M; FP64 170.7 M against 178.6 M; batch64 125.5 M
+  // against 130.3 M)
+  const bool wide = spill && two_pass && fp32 && n_circ == 1 && !(o.flags & SOFT_RUN_NO_WIDE_LANES);
+  const size_t n_lr = 4 + 2 * ((size_t)rounds + 1);
   if (spill) {
     need(&r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_evict + sp_hand));
     need(&r->d_lr, n_lr * sizeof(unsigned long long));
@@ -565,6 +571,9 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.al_grid = al_grid;
     p.lane_round = 0;
     p.lane_evict = spill && rounds > 1 ? 1u : 0u;
+    p.lane_hand = spill ? 1u : 0u;
+    p.lane_wide = wide ? 1u : 0u;
+    p.lane_wide_round = 0;
     p.sp = spill ? r->d_sp : nullptr;
     p.sp_cap = spill ? sp_evict + sp_hand : 0u;
     p.sp_evict_cap = spill ? sp_evict : 0u;
@@ -575,10 +584,11 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     h.sp_cap = p.sp_cap;
     h.sp_evict_cap = p.sp_evict_cap;
   }
-  soft::LaunchCfg c1{}, c2{}, cm{};
+  soft::LaunchCfg c1{}, c2{}, cm{}, cw{};
   p.n_items = std::min(chunk, total);
   if ((e = lanes ? soft::prepare_lanes(p, fp32, W, (int)o.blocks_per_sm, &c1)
                  : soft::prepare_shots(p, fp32, W, g1, (int)o.blocks_per_sm, &c1)) != cudaSuccess ||
+      (wide && (e = soft::prepare_lanes(p, fp32, W, 0, &cw, true)) != cudaSuccess) ||
       (two_pass && (e = soft::prepare_shots(q, fp32, W, g2, (int)o.blocks_per_sm, &c2)) != cudaSuccess) ||
       (mid_pass && (e = soft::prepare_shots(m, fp32, W, g2, (int)o.blocks_per_sm, &cm)) != cudaSuccess)) {
     soft_run_free(r);
@@ -631,6 +641,20 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
       if ((err = cudaMemsetAsync(ar.al_count, 0, 2 * (size_t)nb * sizeof(uint32_t), st)) != cudaSuccess ||
           (err = soft::launch_lane_resume_prepass(ar, fp32, W, st)) != cudaSuccess ||
           (err = soft::launch_prepared(c1, ar, st)) != cudaSuccess)
+        return err;
+      r->launches += 5;
+    }
+    if (wide) {  // the handed-over shots, bucketed by the event they resume at
+      soft::ShotParams aw = a;
+      aw.lane_round = rounds;
+      aw.lane_wide_round = 1;
+      aw.lane_evict = 0;
+      aw.lane_hand = 0;
+      aw.n_rerun_total = nullptr;  // (counted when they left the first rounds)
+      aw.n_items_dev = r->d_lr + 3 + 2 * rounds;
+      if ((err = cudaMemsetAsync(aw.al_count, 0, 2 * (size_t)nb * sizeof(uint32_t), st)) != cudaSuccess ||
+          (err = soft::launch_lane_resume_prepass(aw, fp32, W, st)) != cudaSuccess ||
+          (err = soft::launch_prepared(cw, aw, st)) != cudaSuccess)
         return err;
       r->launches += 5;
     }

@@ -87,6 +87,9 @@ struct ShotParams {
   // pool; the next round buckets them by the event they resume at and packs them into warps
   uint32_t lane_round;        // 0: shots from their start buckets; r >= 1: shots evicted before round r
   uint32_t lane_evict;        // 1: this round may evict
+  uint32_t lane_hand;         // 1: a lane whose map would outgrow it hands the shot over (a spill record)
+  uint32_t lane_wide;         // 1: a wide round takes the handed-over shots (records stay off the rerun list)
+  uint32_t lane_wide_round;   // 1: this is the wide round (its records: the handed-over ones)
   unsigned char *sp;          // spill pool, sp_cap records (layout: lane_spill_bytes): evictions in
   uint32_t sp_cap;            // [0, sp_evict_cap), shots handed from a lane to a warp after that
   uint32_t sp_evict_cap;
@@ -133,7 +136,9 @@ size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap);
 uint32_t lane_rounds();
 uint32_t lane_max_buckets();  // lane-per-shot runs hold at most this many buckets (events + 1 per circuit)
 uint32_t lane_prepass_grid();  // blocks of the bucketing pre-pass (al_base holds this many rows)
-cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg);
+// wide: the wide round's kernel (twice the lane map) instead of the first rounds'
+cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg,
+                          bool wide = false);
 uint32_t lane_map_cap();
 
 // Resolve the launch (sets the kernel's shared-memory attribute, queries

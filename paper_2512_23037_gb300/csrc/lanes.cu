@@ -48,14 +48,38 @@ constexpr uint32_t kLaneRounds = SOFT_LANE_ROUNDS;  // rounds per chunk, the las
 static_assert(kLaneRounds >= 1 && kLaneRounds <= 8, "lane rounds");
 
 
-template <typename R, int W>
+// The wide round's lanes: shots handed over by the first rounds continue in lanes
+// of twice the map.
+constexpr uint32_t kWideCap = 2 * kLaneCap;
+
+template <typename R, int W, uint32_t Cap>
 __host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
   // map keys and values; record words
-  return (size_t)kLaneCap * W * 8 * 32 + (size_t)kLaneCap * sizeof(Cx<R>) * 32 + (size_t)rw * 8 * 32;
+  return (size_t)Cap * W * 8 * 32 + (size_t)Cap * sizeof(Cx<R>) * 32 + (size_t)rw * 8 * 32;
 }
 
-template <typename R, int W>
+// Partner indices, 5 bits per entry for maps of up to 32 entries: nibbles of
+// entries 0-15 and 16-31, and a mask of the indices' fifth bit.
+template <uint32_t Cap>
+struct PartIdx {
+  uint64_t lo = 0, hi = 0;
+  uint32_t b4 = 0;
+  __device__ __forceinline__ void set(uint32_t i, uint32_t j) {
+    const uint64_t v = (uint64_t)(j & 15u) << (4 * (i & 15u));
+    if (Cap <= 16 || i < 16) lo |= v;
+    else hi |= v;
+    if (Cap > 16) b4 |= ((j >> 4) & 1u) << i;
+  }
+  __device__ __forceinline__ uint32_t get(uint32_t i) const {
+    const uint64_t w = (Cap <= 16 || i < 16) ? lo : hi;
+    const uint32_t j = (uint32_t)(w >> (4 * (i & 15u))) & 15u;
+    return Cap > 16 ? j | (((b4 >> i) & 1u) << 4) : j;
+  }
+};
+
+template <typename R, int W, uint32_t Cap>
 struct LaneShot {
+  static_assert(Cap <= 32, "lane map masks are 32-bit");
   const ShotParams &P;
   const CircDev *C;
   uint32_t lane;
@@ -73,7 +97,7 @@ struct LaneShot {
 
   __device__ LaneShot(const ShotParams &p, unsigned char *base) : P(p), C(&p.circ[0]) {
     lane = threadIdx.x & 31u;
-    const size_t kb = (size_t)kLaneCap * W * 8 * 32, vb = (size_t)kLaneCap * sizeof(Cx<R>) * 32;
+    const size_t kb = (size_t)Cap * W * 8 * 32, vb = (size_t)Cap * sizeof(Cx<R>) * 32;
     keys = reinterpret_cast<uint64_t *>(base);
     vals = reinterpret_cast<Cx<R> *>(base + kb);
     rec = reinterpret_cast<uint64_t *>(base + kb + vb);
@@ -94,16 +118,17 @@ struct LaneShot {
   // Partners (a, a ^ x) differ in bit `bit`, set in x. Each entry with the bit clear
   // looks for its partner among the entries with it set (mask `him`). Out: `paired`,
   // the entries with the bit set that have a partner; `has`, those with it clear that
-  // have one; part, the partner's index (4 bits per entry).
+  // have one; part, the partner's index.
   __device__ void partners(uint32_t n0, uint32_t bit, const uint64_t *x, uint32_t &paired, uint32_t &has,
-                           uint64_t &part) const {
+                           PartIdx<Cap> &part) const {
     uint32_t him = 0;
 #pragma unroll 1
     for (uint32_t i = 0; i < n0; ++i) him |= kbit(key(i), bit) << i;
     paired = has = 0;
-    part = 0;
+    part = PartIdx<Cap>{};
+    const uint32_t all = n0 >= 32u ? 0xFFFFFFFFu : (1u << n0) - 1u;
 #pragma unroll 1
-    for (uint32_t lo = ~him & ((1u << n0) - 1u); lo; lo &= lo - 1u) {
+    for (uint32_t lo = ~him & all; lo; lo &= lo - 1u) {
       const uint32_t i = __ffs(lo) - 1;
       const Key<W> pk = kxor(key(i), x);
 #pragma unroll 1
@@ -112,13 +137,13 @@ struct LaneShot {
         if (keq(key(j), pk)) {
           paired |= 1u << j;
           has |= 1u << i;
-          part |= (uint64_t)j << (4 * i);
+          part.set(i, j);
           break;
         }
       }
     }
   }
-  __device__ void fail_capacity() { status = (P.small_pass && C->cap > kLaneCap) ? LS_RERUN : LS_OVF; }
+  __device__ void fail_capacity() { status = (P.small_pass && C->cap > Cap) ? LS_RERUN : LS_OVF; }
   __device__ void fail_check(uint32_t code, uint64_t value) {
     status = LS_ERR;
     if (P.diag && atomicAdd(&P.diag[0], 1ull) == 0ull) {
@@ -201,7 +226,7 @@ struct LaneShot {
     }
 #pragma unroll 1
     for (uint32_t w = 0; w < C->rw; ++w) rec[(size_t)w * 32 + lane] = __ldg(&r_in[w]);
-    if (n > kLaneCap) {
+    if (n > Cap) {
       fail_capacity();
       return;
     }
@@ -359,12 +384,14 @@ struct LaneShot {
     }
     const uint32_t n0 = n;
     uint32_t paired, has;
-    uint64_t part;
+    PartIdx<Cap> part;
     partners(n0, ev_lowbit(w0), beta, paired, has, part);
     // every entry without a partner gains one: if that outgrows the lane, nothing has
-    // been written yet, and a warp can take the shot over at the top of this event
-    if (n0 + (n0 - 2u * (uint32_t)__popc(has)) > kLaneCap && P.sp && P.small_pass && C->cap > kLaneCap) {
-      status = LS_HAND;
+    // been written yet, and the shot can be taken over at the top of this event (by the
+    // wide round's lanes, or a warp); otherwise (the wide round) it reruns in a warp
+    if (n0 + (n0 - 2u * (uint32_t)__popc(has)) > Cap) {
+      if (P.lane_hand && P.sp && P.small_pass && C->cap > Cap) status = LS_HAND;
+      else fail_capacity();
       return;
     }
     uint32_t na = 0;
@@ -375,7 +402,7 @@ struct LaneShot {
       const Key<W> pk = kxor(k, beta);
       const Cx<R> v = val(i);
       if ((has >> i) & 1u) {
-        const uint32_t j = (uint32_t)(part >> (4 * i)) & 15u;
+        const uint32_t j = part.get(i);
         const Cx<R> vj = val(j);
         const Cx<R> ni = cadd(cmul(a, v), cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
         const Cx<R> nj = cadd(cmul(a, vj), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
@@ -386,7 +413,7 @@ struct LaneShot {
         const Cx<R> ni = cmul(a, v);
         const Cx<R> av = cmul(b, ipow(v, e + 2u * kpar(k, gamma)));
         set_val(i, ni);
-        if (n0 + na >= kLaneCap) {
+        if (n0 + na >= Cap) {
           fail_capacity();
           return;
         }
@@ -447,10 +474,10 @@ struct LaneShot {
   // Entry i's pair after the relabel (entry i is not a paired a1): a0, v0 = v_{a0} and
   // x1 = xi_{a1} v_{a1} (zero when absent); j, the a1 partner that i consumes (-1 if none).
   __device__ void pair_at(uint32_t i, uint32_t p, const uint64_t *ep, const uint64_t *g2, uint32_t e2, uint32_t has,
-                          uint64_t part, Key<W> &a0, Cx<R> &v0, Cx<R> &x1, int &j) const {
+                          const PartIdx<Cap> &part, Key<W> &a0, Cx<R> &v0, Cx<R> &x1, int &j) const {
     const Key<W> k = key(i);
     const bool hi = kbit(k, p);
-    j = ((has >> i) & 1u) ? (int)((part >> (4 * i)) & 15u) : -1;
+    j = ((has >> i) & 1u) ? (int)part.get(i) : -1;
     Cx<R> v1{0, 0};
     v0 = Cx<R>{0, 0};
     if (hi) v1 = val(i);
@@ -493,7 +520,7 @@ struct LaneShot {
     // pair a0 (bit p clear) with a1 = a0 ^ e_p: first the outcome probabilities, then
     // the combined values (v0 + m x1) / sqrt(2 p_m)
     uint32_t paired, has;
-    uint64_t part;
+    PartIdx<Cap> part;
     partners(n, p, ep, paired, has, part);
     double sp = 0.0, sm = 0.0;
 #pragma unroll 1
@@ -673,8 +700,14 @@ __global__ void lane_scan_kernel(const __grid_constant__ ShotParams P) {
 // ---- round r >= 1: its records are those taken since round r - 1 began (the pool's
 // count, capped at its capacity: reservations past it were not written)
 __global__ void lane_round_setup_kernel(const __grid_constant__ ShotParams P) {
-  const unsigned long long used = P.lr[0] < P.sp_evict_cap ? P.lr[0] : P.sp_evict_cap;
   const uint32_t r = P.lane_round;
+  if (P.lane_wide_round) {  // the wide round: the handed-over shots' records
+    const unsigned long long cap = P.sp_cap - P.sp_evict_cap;
+    P.lr[2 + 2 * r] = P.sp_evict_cap;
+    P.lr[3 + 2 * r] = P.lr[1] < cap ? P.lr[1] : cap;
+    return;
+  }
+  const unsigned long long used = P.lr[0] < P.sp_evict_cap ? P.lr[0] : P.sp_evict_cap;
   const unsigned long long first = r == 1 ? 0ull : P.lr[2 + 2 * (r - 1)] + P.lr[3 + 2 * (r - 1)];
   P.lr[2 + 2 * r] = first;
   P.lr[3 + 2 * r] = used > first ? used - first : 0ull;
@@ -747,8 +780,9 @@ __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_cons
 }
 
 // Multi: the run holds several circuits (a warp serves one at a time); the single-
-// circuit instantiation keeps circuit 0 and bucket offset 0 as constants.
-template <typename R, int W, bool Multi>
+// circuit instantiation keeps circuit 0 and bucket offset 0 as constants. Cap: map
+// entries per lane (kLaneCap in the first rounds, kWideCap in the wide round).
+template <typename R, int W, bool Multi, uint32_t Cap>
 __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   // per warp: tallies of its current circuit, added to the circuit's when the warp moves
@@ -757,7 +791,7 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
   const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x & 31u;
   if (lane < 5) wt[warp][lane] = 0ull;
   __syncwarp();
-  LaneShot<R, W> s(P, smem + (size_t)warp * lane_warp_bytes<R, W>(P.rw_max));
+  LaneShot<R, W, Cap> s(P, smem + (size_t)warp * lane_warp_bytes<R, W, Cap>(P.rw_max));
   const unsigned long long base = P.item_base_dev ? *P.item_base_dev : P.item_base;
   const unsigned long long n_items =
       P.lane_round ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
@@ -825,18 +859,22 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
       if (s.status == LS_RUN) s.status = LS_KEPT;
       const uint64_t off = base + item - (Multi ? C->item_begin : 0ull);  // the shot's offset within its circuit
       uint32_t entry = item;  // a rerun starts the shot again from its start
-      if (s.status == LS_HAND) {  // or a warp resumes it from its state at the top of event e
+      bool listed = true;
+      if (s.status == LS_HAND) {  // or it resumes from its state at the top of event e
         const unsigned long long h = atomicAdd(&P.lr[1], 1ull);
         if (h < (unsigned long long)(P.sp_cap - P.sp_evict_cap)) {
           const uint32_t r = P.sp_evict_cap + (uint32_t)h;
           s.evict(S, r, item, e);
-          entry = kSpillRef | r;
+          entry = kSpillRef | r;    // in a warp, from the rerun list,
+          listed = !P.lane_wide;    // or in the wide round, which takes every such record
         }
         s.status = LS_RERUN;
       }
       if (s.status == LS_RERUN) {
-        const unsigned long long i = atomicAdd(P.n_rerun, 1ull);
-        if (i < P.rerun_cap) P.rerun[i] = entry;
+        if (listed) {
+          const unsigned long long i = atomicAdd(P.n_rerun, 1ull);
+          if (i < P.rerun_cap) P.rerun[i] = entry;
+        }
         if (P.n_rerun_total) atomicAdd(P.n_rerun_total, 1ull);
       } else {
         atomicAdd(&wt[warp][0], 1ull);
@@ -912,9 +950,13 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
 
 }  // namespace
 
-size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw) {
-  const size_t per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1>(rw) : lane_warp_bytes<float, 2>(rw))
-                          : (W == 1 ? lane_warp_bytes<double, 1>(rw) : lane_warp_bytes<double, 2>(rw));
+size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw, bool wide) {
+  size_t per;
+  if (wide)
+    per = W == 1 ? lane_warp_bytes<float, 1, kWideCap>(rw) : lane_warp_bytes<float, 2, kWideCap>(rw);
+  else
+    per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1, kLaneCap>(rw) : lane_warp_bytes<float, 2, kLaneCap>(rw))
+               : (W == 1 ? lane_warp_bytes<double, 1, kLaneCap>(rw) : lane_warp_bytes<double, 2, kLaneCap>(rw));
   return per * (kLaneBlock / 32);
 }
 
@@ -956,18 +998,24 @@ cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W
 
 cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st) { return launch_bin<false, float, 1>(p, st); }
 
-cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg) {
+cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg, bool wide) {
   const bool multi = p.n_circ > 1;
-  const void *kern =
-      fp32 ? (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<float, 1, true>)
-                              : reinterpret_cast<const void *>(lane_kernel<float, 1, false>))
-                     : (multi ? reinterpret_cast<const void *>(lane_kernel<float, 2, true>)
-                              : reinterpret_cast<const void *>(lane_kernel<float, 2, false>)))
-           : (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<double, 1, true>)
-                              : reinterpret_cast<const void *>(lane_kernel<double, 1, false>))
-                     : (multi ? reinterpret_cast<const void *>(lane_kernel<double, 2, true>)
-                              : reinterpret_cast<const void *>(lane_kernel<double, 2, false>)));
-  const size_t smem = lane_smem_bytes(fp32, W, p.rw_max);
+  constexpr uint32_t C1 = kLaneCap, C2 = kWideCap;
+  const void *kern;
+  if (wide) {  // FP32 single-circuit runs only
+    if (!fp32 || multi) return cudaErrorInvalidConfiguration;
+    kern = W == 1 ? reinterpret_cast<const void *>(lane_kernel<float, 1, false, C2>)
+                  : reinterpret_cast<const void *>(lane_kernel<float, 2, false, C2>);
+  } else
+    kern = fp32 ? (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<float, 1, true, C1>)
+                                   : reinterpret_cast<const void *>(lane_kernel<float, 1, false, C1>))
+                          : (multi ? reinterpret_cast<const void *>(lane_kernel<float, 2, true, C1>)
+                                   : reinterpret_cast<const void *>(lane_kernel<float, 2, false, C1>)))
+                : (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<double, 1, true, C1>)
+                                   : reinterpret_cast<const void *>(lane_kernel<double, 1, false, C1>))
+                          : (multi ? reinterpret_cast<const void *>(lane_kernel<double, 2, true, C1>)
+                                   : reinterpret_cast<const void *>(lane_kernel<double, 2, false, C1>)));
+  const size_t smem = lane_smem_bytes(fp32, W, p.rw_max, wide);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

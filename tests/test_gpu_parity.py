@@ -529,6 +529,34 @@ def test_degenerate_circuits(soft, case):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["w42", "random40"])
+def test_wide_round_matches_oracle(soft, precision, case):
+    """Shots whose maps outgrow a lane continue in the wide round's lanes (32
+    entries) before any warp: records and statuses against the oracle, tallies
+    against runs without the wide round."""
+    S = soft
+    if case == "w42":
+        circ, noise = C.workload("w42")
+        noise = C.Noise.uniform(3e-3)  # more errors: more maps outgrow a lane
+    else:
+        circ = C.random_circuit(4040, 40, 400, t_frac=0.2, detectors=True, mpp_frac=0.05)
+        circ.cap = 256
+        noise = C.Noise(0.005, 0.005, 0.005, 0.005)
+    n_shots = 6000
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    r = S.soft_run_shots(c, n_shots, 0, 13, precision=precision, record_mode=S.REC_ALL, time_passes=True)
+    rec, st = S.soft_get_records(r, n_shots)
+    t = S.soft_tally(r)
+    assert S.soft_run_diagnostics(r)[0] == 0
+    ms, _, n_left = S.soft_run_pass_timing(r)
+    assert ms[0] > 0.0 and n_left > 0  # lanes ran, and some shots left them
+    ref = oracle.run(circ, circ.n, noise, circ.cap, 13, 0, n_shots, threads=8)
+    assert compare_records(circ, noise, 13, 0, rec, st, ref, precision) <= 2
+    t2 = S.soft_tally(S.soft_run_shots(c, n_shots, 0, 13, precision=precision, wide=False))
+    assert all(abs(t[k] - t2[k]) <= 2 for k in ("discarded", "overflow", "kept", "logical_errors"))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("n_data,n_anc", [(72, 4), (120, 8)])
 def test_lane_per_shot_two_word_keys(soft, precision, n_data, n_anc):
     """Above 64 qubits (two-word keys, signs and spill records) in the lane
