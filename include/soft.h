@@ -187,12 +187,13 @@ typedef struct {
  * warp per shot. Same results either way, another order. */
 /* SOFT_RUN_TIME_PASSES records CUDA events between the passes of every chunk
  * (ignored with SOFT_RUN_GRAPH), read back by soft_run_pass_timing. */
-/* SOFT_RUN_NO_WIDE_LANES: in FP32 single-circuit runs, shots whose map
- * outgrows a lane go to a warp at once, instead of first to the wide round's
- * lanes (twice the map; FP64 runs and batches never use it). Same results
- * either way. */
+/* The wide round (FP32 single-circuit runs; FP64 runs and batches never use
+ * it): shots whose map outgrows a lane continue in lanes of twice the map
+ * before any warp. By default it runs for chunks of at least 2^23 shots;
+ * SOFT_RUN_WIDE_LANES runs it for any chunk, SOFT_RUN_NO_WIDE_LANES never.
+ * Same results either way. */
 enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_RUN_NO_LANES = 8,
-       SOFT_RUN_TIME_PASSES = 16, SOFT_RUN_NO_WIDE_LANES = 32 };
+       SOFT_RUN_TIME_PASSES = 16, SOFT_RUN_NO_WIDE_LANES = 32, SOFT_RUN_WIDE_LANES = 64 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
  * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all

@@ -29,7 +29,8 @@ SOFT_OK = 0
 FP64, FP32 = 0, 1
 REC_NONE, REC_FIRST_K, REC_ALL = 0, 1, 2
 SHOT_KEPT, SHOT_DISCARDED, SHOT_OVERFLOW, SHOT_ERROR = 0, 1, 2, 3
-RUN_GRAPH, RUN_FIDELITY, RUN_NO_PREFIX, RUN_NO_LANES, RUN_TIME_PASSES, RUN_NO_WIDE_LANES = 1, 2, 4, 8, 16, 32
+RUN_GRAPH, RUN_FIDELITY, RUN_NO_PREFIX, RUN_NO_LANES, RUN_TIME_PASSES, RUN_NO_WIDE_LANES, RUN_WIDE_LANES = \
+    1, 2, 4, 8, 16, 32, 64
 
 
 class SoftError(RuntimeError):
@@ -180,7 +181,7 @@ def soft_compile_circuit(ops, n_qubits: int, noise, coeff_cap: int) -> Circuit:
 
 def _opts(precision="fp64", record_mode=REC_NONE, record_k=0, stream=None, group_size=0, blocks_per_sm=0,
           chunk_shots=0, first_cap=0, capture_k=0, d_records=None, d_status=None, groups_per_block=0,
-          graph=False, fidelity=False, prefix=True, lanes=True, time_passes=False, wide=True) -> _Opts:
+          graph=False, fidelity=False, prefix=True, lanes=True, time_passes=False, wide=None) -> _Opts:
     o = _Opts()
     o.precision = FP32 if precision in ("fp32", FP32) else FP64
     o.record_mode = int(record_mode)
@@ -205,7 +206,7 @@ def _opts(precision="fp64", record_mode=REC_NONE, record_k=0, stream=None, group
     o.groups_per_block = int(groups_per_block)
     o.flags = ((RUN_GRAPH if graph else 0) | (RUN_FIDELITY if fidelity else 0) | (0 if prefix else RUN_NO_PREFIX)
                | (0 if lanes else RUN_NO_LANES) | (RUN_TIME_PASSES if time_passes else 0)
-               | (0 if wide else RUN_NO_WIDE_LANES))
+               | (0 if wide is None else (RUN_WIDE_LANES if wide else RUN_NO_WIDE_LANES)))
     return o
 
 
@@ -214,7 +215,7 @@ def soft_run_shots(circ: Circuit, n_shots: int, first_shot: int = 0, seed: int =
                    blocks_per_sm: int = 0, chunk_shots: int = 0, first_cap: int = 0, capture_k: int = 0,
                    d_records=None, d_status=None, groups_per_block: int = 0, graph: bool = False,
                    fidelity: bool = False, prefix: bool = True, lanes: bool = True,
-                   time_passes: bool = False, wide: bool = True) -> Run:
+                   time_passes: bool = False, wide=None) -> Run:
     """Launch shots asynchronously on `stream` (a torch.cuda.Stream, a raw
     cudaStream_t int, or None for torch's current stream when torch is
     imported, else the legacy default stream). fidelity=True projects the
@@ -222,7 +223,9 @@ def soft_run_shots(circ: Circuit, n_shots: int, first_shot: int = 0, seed: int =
     shot (tally sum_fidelity / sum_weight). prefix=False runs every shot from
     the first event instead of from the shared noiseless prefix, lanes=False a
     warp per shot instead of a lane per shot where that applies (same results).
-    time_passes=True records events between passes for soft_run_pass_timing."""
+    time_passes=True records events between passes for soft_run_pass_timing.
+    wide: None runs the wide round (FP32 single-circuit runs) for chunks of at
+    least 2^23 shots, True for any chunk, False never."""
     o = _opts(precision, record_mode, record_k, stream, group_size, blocks_per_sm, chunk_shots, first_cap,
               capture_k, d_records, d_status, groups_per_block, graph, fidelity, prefix, lanes, time_passes, wide)
     out = ctypes.c_void_p()

@@ -331,7 +331,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   const bool use_graph = (o.flags & SOFT_RUN_GRAPH) != 0;
   const bool fid_mode = (o.flags & SOFT_RUN_FIDELITY) != 0;
   if (o.flags & ~(uint32_t)(SOFT_RUN_GRAPH | SOFT_RUN_FIDELITY | SOFT_RUN_NO_PREFIX | SOFT_RUN_NO_LANES |
-                          SOFT_RUN_TIME_PASSES | SOFT_RUN_NO_WIDE_LANES))
+                          SOFT_RUN_TIME_PASSES | SOFT_RUN_NO_WIDE_LANES | SOFT_RUN_WIDE_LANES))
     return fail(SOFT_E_ARG, "unknown run flags");
   if (use_graph && !o.stream) return fail(SOFT_E_ARG, "graph replay needs a non-default stream");
   const int fp32 = o.precision == SOFT_FP32;
@@ -424,8 +424,10 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   // are its input), and only those that outgrow it rerun in a warp. FP32 single-circuit runs
   // only: with FP64 maps, or in batches, it measured slower than handing the shots to warps
   // (w42: FP32 550.0 M shots/s against 533.0 M; FP64 170.7 M against 178.6 M; batch64 125.5 M
-  // against 130.3 M)
-  const bool wide = spill && two_pass && fp32 && n_circ == 1 && !(o.flags & SOFT_RUN_NO_WIDE_LANES);
+  // against 130.3 M). By default, only for chunks of at least 2^23 shots: its pre-pass and
+  // launch cost more than it saves in small runs (w42 at 2^21 shots: 389.0 M against 412.5 M).
+  const bool wide_ok = spill && two_pass && fp32 && n_circ == 1 && !(o.flags & SOFT_RUN_NO_WIDE_LANES);
+  const bool wide = wide_ok && ((o.flags & SOFT_RUN_WIDE_LANES) || std::min(chunk, total) >= (1ull << 23));
   const size_t n_lr = 4 + 2 * ((size_t)rounds + 1);
   if (spill) {
     need(&r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_evict + sp_hand));

@@ -544,7 +544,7 @@ def test_wide_round_matches_oracle(soft, precision, case):
         noise = C.Noise(0.005, 0.005, 0.005, 0.005)
     n_shots = 6000
     c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
-    r = S.soft_run_shots(c, n_shots, 0, 13, precision=precision, record_mode=S.REC_ALL, time_passes=True)
+    r = S.soft_run_shots(c, n_shots, 0, 13, precision=precision, record_mode=S.REC_ALL, time_passes=True, wide=True)
     rec, st = S.soft_get_records(r, n_shots)
     t = S.soft_tally(r)
     assert S.soft_run_diagnostics(r)[0] == 0
