@@ -177,8 +177,11 @@ typedef struct {
  * 32 shots per warp. Shots are bucketed by the event they start at, and each
  * warp executes one event at a time for all its lanes, each lane updating its
  * own shot's map (up to 16 entries). A shot whose map outgrows its lane is
- * rerun from its start by a warp, with a register map of up to first_cap
- * entries (default 64), and only beyond that at the circuit's cap. In a
+ * handed over at that event (its whole state in a spill record): to the wide
+ * round's lanes (see below), or to a warp with a register map of up to
+ * first_cap entries (default 64); shots beyond that rerun from their start at
+ * the circuit's cap. A warp left with few active lanes moves their shots to a
+ * second round that packs them into full warps again. In a
  * batch each circuit has its own buckets, and a warp serves one circuit at a
  * time. It applies to runs without state capture or a forced group size, when
  * every map of every circuit's noiseless run fits (at most 16 entries) and the
