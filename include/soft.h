@@ -183,8 +183,9 @@ typedef struct {
  * the circuit's cap. A warp left with few active lanes moves their shots to a
  * second round that packs them into full warps again. In a
  * batch each circuit has its own buckets, and a warp serves one circuit at a
- * time. It applies to runs without state capture or a forced group size, when
- * every map of every circuit's noiseless run fits (at most 16 entries) and the
+ * time. It applies to runs without state capture or a forced group size, to
+ * the circuits whose noiseless run's maps fit a lane (at most 16 entries; the
+ * shots of a batch's other circuits go straight to the warp pass), when those
  * circuits hold at most 50 000 events (plus one per circuit) together;
  * otherwise a warp (group) runs each shot. SOFT_RUN_NO_LANES always uses the
  * warp per shot. Same results either way, another order. */
