@@ -556,20 +556,24 @@ def test_wide_round_matches_oracle(soft, precision, case):
     assert all(abs(t[k] - t2[k]) <= 2 for k in ("discarded", "overflow", "kept", "logical_errors"))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision,wide", [("fp64", None), ("fp32", None), ("fp32", True)])
 @pytest.mark.parametrize("n_data,n_anc", [(72, 4), (120, 8)])
-def test_lane_per_shot_two_word_keys(soft, precision, n_data, n_anc):
+def test_lane_per_shot_two_word_keys(soft, precision, wide, n_data, n_anc):
     """Above 64 qubits (two-word keys, signs and spill records) in the lane
-    kernel: windowed circuits of 76 and 128 qubits, whose noiseless maps fit a
-    lane, against the oracle."""
+    kernel, and (wide) in the wide round's lanes: windowed circuits of 76 and
+    128 qubits, whose noiseless maps fit a lane, against the oracle."""
     S = soft
     circ, noise = C.windowed(11, n_data=n_data, n_anc=n_anc, blocks=4, p=4e-3)
     n_shots = 3000
     c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
-    r = S.soft_run_shots(c, n_shots, 0, 9, precision=precision, record_mode=S.REC_ALL, time_passes=True)
+    r = S.soft_run_shots(c, n_shots, 0, 9, precision=precision, record_mode=S.REC_ALL, time_passes=True,
+                         wide=wide)
     rec, st = S.soft_get_records(r, n_shots)
     assert S.soft_run_diagnostics(r)[0] == 0
-    assert S.soft_run_pass_timing(r)[0][0] > 0.0  # the lane pre-pass ran
+    ms, _, n_left = S.soft_run_pass_timing(r)
+    assert ms[0] > 0.0  # the lane pre-pass ran
+    if wide:
+        assert n_left > 0  # some shots left their lanes (to the wide round)
     ref = oracle.run(circ, circ.n, noise, circ.cap, 9, 0, n_shots, threads=8)
     assert compare_records(circ, noise, 9, 0, rec, st, ref, precision) <= 2
 
