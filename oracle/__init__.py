@@ -11,7 +11,10 @@ random Clifford+T+measurement circuits (<= 8 qubits); Clifford-only circuits
 against an independent Aaronson-Gottesman sampler; closed-form outcome
 probabilities of single-T circuits; T.T^dag = I, T^2 = S, T^8 = I;
 normalisation and the |v| bounds of Theorem 1; exact record distribution
-of the 6-qubit workload from a density-matrix run.
+of the 6-qubit workload from a density-matrix run; the noise stream's
+sequencing (per-site marginals, pairwise joints, Pauli-choice frequencies,
+thinning, and error lists recomputed from Philox blocks by the geometric
+gap's inverse CDF) and the measurement uniform's construction.
 """
 from __future__ import annotations
 
