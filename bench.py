@@ -6,7 +6,8 @@ event kinds, noise, measurement, early discard, tallies) over one batch of
 shots. Inputs (the compiled program) are resident in HBM before timing;
 L2 (129 MB) is flushed between steps with a 512 MB memset outside the timed
 events. Multi-GPU: every rank runs its own shot range (weak scaling, no data
-path collective); the time is the max over ranks.
+path collective; each step's job is split into contiguous shot ranges, and the
+tally is summed over ranks); the time is the max over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--shots S] [--impl reference]
 """
@@ -350,8 +351,12 @@ def main():
         items = [(circ0, noise0, args.shots)]
     stream = torch.cuda.current_stream() if not args.graph else torch.cuda.Stream()
     n = sum(s for _, _, s in items)  # shots per step per GPU
-    from paper_2512_23037_gb300.sharding import shot_range
-    base_shot, _ = shot_range(rank, world, n)  # disjoint shot ranges per rank
+    from paper_2512_23037_gb300.sharding import all_reduce_tally, shot_range
+
+    def firsts(k, off=0):
+        # step k's job holds world x (shots per GPU) shots of each circuit; this rank runs its
+        # contiguous part of it, so that the job's result does not depend on the rank count
+        return [shot_range(rank, world, s * world, off + k * s * world)[0] for _, _, s in items]
     dev_props = torch.cuda.get_device_properties(local)
     flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
     tune = {"group_size": args.group, "first_cap": args.first_cap, "chunk_shots": args.chunk}
@@ -366,16 +371,19 @@ def main():
 
     def launch(handles, first, precision, fidelity=False, time_passes=False):
         if len(handles) == 1:
-            return S.soft_run_shots(handles[0], items[0][2], first, 0, precision=precision, stream=stream,
+            return S.soft_run_shots(handles[0], items[0][2], first[0], 0, precision=precision, stream=stream,
                                     graph=args.graph, fidelity=fidelity, lanes=not args.warp_per_shot,
                                     time_passes=time_passes, **tune)
-        return S.soft_run_batch(handles, [s for _, _, s in items], [first] * len(handles), 0, precision=precision,
+        return S.soft_run_batch(handles, [s for _, _, s in items], first, 0, precision=precision,
                                 stream=stream, graph=args.graph, fidelity=fidelity, time_passes=time_passes, **tune)
+
+    def job_tally(t):
+        return all_reduce_tally(t, torch.distributed, device="cuda") if world > 1 else t
 
     def time_path(precision, steps, warmup, fidelity=False):
         hs = compile_all()
         for w in range(warmup):
-            r = launch(hs, base_shot + (1 << 36) + w * n, precision, fidelity)
+            r = launch(hs, firsts(w, 1 << 36), precision, fidelity)
             S.soft_tally(r)
             r.free()
         barrier()
@@ -387,7 +395,7 @@ def main():
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            r = launch(hs, base_shot + k * n, precision, fidelity, time_passes=not args.graph)
+            r = launch(hs, firsts(k), precision, fidelity, time_passes=not args.graph)
             ev1.record(stream)
             tallies.append(S.soft_tally(r))
             ms, nl = S.soft_run_timing(r)
@@ -404,7 +412,7 @@ def main():
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         if world > 1:
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item()), launches, kernel_ms, tallies, hs
+        return float(t.item()), launches, kernel_ms, [job_tally(x) for x in tallies], hs
 
     tuned = None
     if args.autotune:
@@ -454,7 +462,7 @@ def main():
         hs = compile_step()
         h2d = sum(h.info["program_bytes"] for h in hs)
         for k in range(args.steps):
-            r = launch(hs, base_shot + (1 << 38) + k * n, "fp32")
+            r = launch(hs, firsts(k, 1 << 38), "fp32")
             nxt = compile_step() if pipelined and k + 1 < args.steps else None
             S.soft_tally(r)
             r.free()
