@@ -183,7 +183,8 @@ typedef struct {
  * the circuit's cap. A warp left with few active lanes moves their shots to a
  * second round that packs them into full warps again. In a
  * batch each circuit has its own buckets, and a warp serves one circuit at a
- * time. It applies to runs without state capture or a forced group size, to
+ * time. It applies to runs without a forced group size (state capture
+ * included: a captured shot's state is written wherever it ends), to
  * the circuits whose noiseless run's maps fit a lane (at most 16 entries; the
  * shots of a batch's other circuits go straight to the warp pass), when those
  * circuits hold at most 50 000 events (plus one per circuit) together;
@@ -200,7 +201,10 @@ enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_R
        SOFT_RUN_TIME_PASSES = 16, SOFT_RUN_NO_WIDE_LANES = 32, SOFT_RUN_WIDE_LANES = 64 };
 
 /* Launch shots [first_shot, first_shot + n_shots) of a compiled circuit,
- * asynchronously on opts->stream. Philox4x32-10 keyed by `seed` drives all
+ * asynchronously on opts->stream: the paper's shot-parallel simulation
+ * (Sec. IV-B: many independent noisy shots, each evolved in the GS
+ * representation of Sec. II-C by the update rules of Theorem 1, with
+ * overflow marked when |v| exceeds the cap). Philox4x32-10 keyed by `seed` drives all
  * randomness: noise gaps on counter (shot, 0, k), measurement uniforms on
  * counter (shot, 1, ordinal).
  *   opts may be NULL (FP64, no records, auto tuning, default stream).
@@ -220,7 +224,9 @@ typedef struct {
   double sum_fidelity, sum_weight; /* SOFT_RUN_FIDELITY: sum of F over kept shots, and kept; else 0 */
 } soft_tally_t;
 
-/* One persistent launch sequence over up to 64 compiled circuits (shots and
+/* Batched form of soft_run_shots (Sec. IV-B's shot-parallel execution, over
+ * several circuits at once; Sec. V-C measures throughput against the batch
+ * size). One persistent launch sequence over up to 64 compiled circuits (shots and
  * circuits whose coefficient caps differ share the kernel; a shot's overflow
  * threshold is its own circuit's cap). Circuit i runs shots
  * [first_shots[i], first_shots[i] + n_shots[i]). All circuits must be on one
@@ -239,7 +245,9 @@ int soft_tally(soft_run *r, soft_tally_t *out);
 /* Tally of circuit `index` of a batch run (index 0 for soft_run_shots). */
 int soft_tally_batch(soft_run *r, uint32_t index, soft_tally_t *out);
 
-/* Wait, then copy records (shot-major, record_words per shot, bit j = 1 when
+/* The measurement record of each shot (the outcomes the post-selection and
+ * logical-error statistics of Sec. V-A are computed from; Sec. IV-B keeps it
+ * per shot). Wait, then copy records (shot-major, record_words per shot, bit j = 1 when
  * record j measured -1; bits after a discard are 0) and status bytes of the
  * kept shots (the first K, or all). n_words / n_status give the host buffer
  * sizes; either pointer may be NULL. */
@@ -287,7 +295,13 @@ int soft_release_workspace(void);
  * caching allocator or a fixed arena) and latency-critical loops that cannot
  * take cudaMalloc's implicit device synchronisation.
  *   Same shots, same results as soft_run_shots with default tuning, FP64 or
- *   FP32 (`precision`), launched asynchronously on `stream`.
+ *   FP32 (`precision`), launched asynchronously on `stream`. It runs a warp
+ *   per shot from the first event (no lane-per-shot scheduling, no shared
+ *   noiseless prefix), so its throughput is below soft_run_shots'. The map at
+ *   the circuit's cap must fit one block's shared memory (the device's opt-in
+ *   limit; w42's cap 2^8 does, w97's 2^12 does not): larger caps, which
+ *   soft_run_shots moves to a global-memory slab, are rejected with
+ *   SOFT_E_ARG.
  *   d_tally: caller device buffer of 5 uint64 counters (shots, discarded,
  *   overflow, kept, logical errors); the call zeroes it, then accumulates.
  *   d_status / d_records: optional caller device buffers of n_shots bytes /
@@ -300,6 +314,9 @@ int soft_release_workspace(void);
  *   so make the first call before any stream capture. All calls share the
  *   array: calls that overlap on the GPU (different streams, no ordering)
  *   race on it and give wrong results; calls ordered on one stream are safe.
+ *   The looked-up address belongs to the device's current context: after a
+ *   cudaDeviceReset of that device, do not call this entry point on it again
+ *   in the same process.
  * Errors: SOFT_E_ARG, SOFT_E_CUDA. No cudaMalloc, cudaFree or other
  * allocating routine is called. */
 int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, int32_t precision,

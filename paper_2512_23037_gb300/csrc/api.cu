@@ -286,9 +286,9 @@ void soft_run_free(soft_run *r) {
 
 }  // extern "C"
 
-namespace {
+namespace soft {
 
-soft::CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix) {
+CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix) {
   soft::CircDev d{};
   d.site_ev = reinterpret_cast<const uint32_t *>(c->d_thr + c->hp.thr.size());
   d.thr_tab = d.site_ev + c->hp.site_ev.size();
@@ -311,6 +311,12 @@ soft::CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix) {
   d.n_cb = (uint32_t)c->hp.cb.size();
   return d;
 }
+
+}  // namespace soft
+
+namespace {
+
+using soft::circ_desc;
 
 // Shared launcher of soft_run_shots and soft_run_batch.
 int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t *first_shots, uint32_t n_circ,
@@ -360,11 +366,14 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     fits[i] = circs[i]->d_traj[pk] && circs[i]->traj_max_n[pk] <= soft::lane_map_cap();
     if (fits[i]) n_buckets += circs[i]->hp.ev.size() + 1;
   }
-  const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && !(o.flags & SOFT_RUN_NO_PREFIX) && o.capture_k == 0 &&
-                     o.group_size == 0 && n_buckets > 0 && n_buckets <= soft::lane_max_buckets();
+  const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && !(o.flags & SOFT_RUN_NO_PREFIX) && o.group_size == 0 &&
+                     n_buckets > 0 && n_buckets <= soft::lane_max_buckets();
   const uint32_t nb = lanes ? (uint32_t)n_buckets : 0u;
-  // a rerun pass finishes the shots whose maps outgrow the first pass (a lane's map, or cap1)
-  const bool two_pass = (lanes ? soft::lane_map_cap() : cap1) < cap_max;
+  // a rerun pass finishes the shots whose maps outgrow the first pass (cap1). After lanes it
+  // always runs: a lane decides overflow only after pruning, and a map that outgrows the lane
+  // before pruning is staged whole by the warp pass, even when the circuit's cap is the lane's.
+  const bool lane_grow = lanes && soft::lane_map_cap() < cap_max;  // maps may outgrow a lane
+  const bool two_pass = lanes || cap1 < cap_max;
   // after lanes, a middle pass (a warp per shot, register map up to cap1) takes the shots whose
   // maps outgrew a lane, and only those that outgrow cap1 go on to the pass at the circuit's cap
   const bool mid_pass = lanes && soft::lane_map_cap() < cap1 && cap1 < cap_max;
@@ -417,16 +426,16 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   // when full, the warp reruns them from their start). Entries of the rerun list name a record
   // with their top bit, so a chunk stays below 2^31 items for it.
   const uint32_t rounds = lanes ? soft::lane_rounds() : 1u;
-  const bool spill = lanes && (rounds > 1 || two_pass) && chunk < (1ull << 31);
+  const bool spill = lanes && (rounds > 1 || lane_grow) && chunk < (1ull << 31);
   const uint32_t sp_evict = rounds > 1 ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 4) : 0u;
-  const uint32_t sp_hand = two_pass ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 8) : 0u;
+  const uint32_t sp_hand = lane_grow ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 8) : 0u;
   // the wide round: the handed-over shots continue in lanes of twice the map (their records
   // are its input), and only those that outgrow it rerun in a warp. FP32 single-circuit runs
   // only: with FP64 maps, or in batches, it measured slower than handing the shots to warps
   // (w42: FP32 550.0 M shots/s against 533.0 M; FP64 170.7 M against 178.6 M; batch64 125.5 M
   // against 130.3 M). By default, only for chunks of at least 2^23 shots: its pre-pass and
   // launch cost more than it saves in small runs (w42 at 2^21 shots: 389.0 M against 412.5 M).
-  const bool wide_ok = spill && two_pass && fp32 && n_circ == 1 && !(o.flags & SOFT_RUN_NO_WIDE_LANES);
+  const bool wide_ok = spill && lane_grow && fp32 && n_circ == 1 && !(o.flags & SOFT_RUN_NO_WIDE_LANES);
   const bool wide = wide_ok && ((o.flags & SOFT_RUN_WIDE_LANES) || std::min(chunk, total) >= (1ull << 23));
   const size_t n_lr = 4 + 2 * ((size_t)rounds + 1);
   if (spill) {

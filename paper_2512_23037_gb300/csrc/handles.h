@@ -43,3 +43,11 @@ struct soft_circuit {
   unsigned char *d_gwide = nullptr;    // wide rerun: list, counters, tapes
   size_t gwide_bytes = 0;
 };
+
+namespace soft {
+struct CircDev;
+// A launch's descriptor of compiled circuit c: its program, noise tables and
+// the gap-search index; with `prefix`, also its noiseless run's snapshots
+// for precision fp32 (shots start at their first error).
+CircDev circ_desc(const soft_circuit *c, int fp32, bool prefix);
+}  // namespace soft

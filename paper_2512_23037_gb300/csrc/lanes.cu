@@ -143,7 +143,10 @@ struct LaneShot {
       }
     }
   }
-  __device__ void fail_capacity() { status = (P.small_pass && C->cap > Cap) ? LS_RERUN : LS_OVF; }
+  // The map would outgrow the lane before pruning. Overflow is decided after pruning
+  // (|v| > the circuit's cap), so the warp pass at the circuit's cap, which stages the
+  // whole update before it prunes, reruns the shot (every lane run has that pass).
+  __device__ void fail_capacity() { status = P.small_pass ? LS_RERUN : LS_OVF; }
   __device__ void fail_check(uint32_t code, uint64_t value) {
     status = LS_ERR;
     if (P.diag && atomicAdd(&P.diag[0], 1ull) == 0ull) {
@@ -301,6 +304,25 @@ struct LaneShot {
     return a.x;
   }
 
+  // ---- the shot's final state (signs, keys, values) for state capture at offset off
+  __device__ void capture(uint64_t off) const {
+    P.st_nnz[off] = n;
+    P.st_signs[off * 4 + 0] = sd[0];
+    P.st_signs[off * 4 + 1] = (W == 2) ? sd[W - 1] : 0ull;
+    P.st_signs[off * 4 + 2] = ss[0];
+    P.st_signs[off * 4 + 3] = (W == 2) ? ss[W - 1] : 0ull;
+#pragma unroll 1
+    for (uint32_t i = 0; i < n && i < P.st_stride; ++i) {
+      const Key<W> k = key(i);
+      const Cx<R> v = val(i);
+      const size_t o = (size_t)off * P.st_stride + i;
+      P.st_keys[2 * o] = k.w[0];
+      P.st_keys[2 * o + 1] = (W == 2) ? k.w[W - 1] : 0ull;
+      P.st_vals[2 * o] = (double)v.x;
+      P.st_vals[2 * o + 1] = (double)v.y;
+    }
+  }
+
   // ---- Paulis: v'_{a^beta} = i^{e + 2 gamma.a} v_a
   __device__ void apply_pauli(const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
 #pragma unroll 1
@@ -425,6 +447,7 @@ struct LaneShot {
     }
     n = n0 + na;
     if (small) prune();
+    if (n > C->cap) status = LS_OVF;  // the overflow rule, for circuits whose cap is below the lane's
   }
 
   // ---- measurement of P, beta = 0: lambda_a = c (-1)^{gamma.a}
@@ -885,6 +908,7 @@ __global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant_
           if (s.logical) atomicAdd(&wt[warp][4], 1ull);
           if (P.fid_mode && C->fsum) atomicAdd(C->fsum, s.fid);
         }
+        if (!Multi && off < P.st_limit) s.capture(off);
         if (off < C->out_limit) {
           if (C->status) C->status[off] = (uint8_t)s.status;
           if (C->records)

@@ -1,12 +1,16 @@
 // noalloc.cu -- soft_run_shots_noalloc: the run entry point for callers that
 // must not allocate device memory.
 //
-// The regular soft_run_shots allocates its work counters and rerun list with
-// cudaMalloc on every call. This variant keeps that scratch in one
-// file-scope __device__ array instead, sized for kNoallocMaxShots shots per
-// call, so a call performs no device allocation at all: the caller passes
-// the compiled circuit and its own output buffers, and the library only
-// clears the counters (cudaMemsetAsync) and launches the same shot kernel.
+// The regular soft_run_shots carves its scratch (work counters, rerun list,
+// lane-per-shot buffers) from a per-device cached workspace, which it
+// allocates with cudaMalloc the first time, and again whenever a run needs a
+// larger one. This variant keeps its scratch in one file-scope __device__
+// array instead, sized for kNoallocMaxShots shots per call, so a call never
+// allocates: the caller passes the compiled circuit and its own output
+// buffers, and the library only clears the counters (cudaMemsetAsync) and
+// launches the warp-per-shot kernel, every shot from the first event (no
+// lane-per-shot scheduling and no shared noiseless prefix, whose buffers
+// scale with the shot count; same results, lower throughput).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -54,10 +58,15 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
     return soft::set_error(SOFT_E_ARG, "n_shots exceeds the no-alloc limit of 1048576 shots per call");
   const auto &hp = c->hp;
   const int fp32 = precision == SOFT_FP32;
-  if (soft::group_smem_bytes(fp32, hp.W, hp.cap, hp.rw) > 227 * 1024)
-    return soft::set_error(SOFT_E_ARG, "coeff_cap too large for the on-chip coefficient map");
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return soft::set_error(SOFT_E_CUDA, "cudaSetDevice failed");
+  // the whole map at the circuit's cap lives in one block's shared memory (the regular
+  // entry point moves larger caps to a global-memory slab, which this one cannot allocate)
+  int smem_optin = 0;
+  if ((e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device)) != cudaSuccess)
+    return soft::set_error(SOFT_E_CUDA, "cudaDeviceGetAttribute failed");
+  if (soft::group_smem_bytes(fp32, hp.W, hp.cap, hp.rw) > (size_t)smem_optin - 5 * 8 * soft::kMaxCirc)
+    return soft::set_error(SOFT_E_ARG, "coeff_cap too large for this entry point's shared-memory coefficient map");
   unsigned char *scratch = nullptr;
   int rc = scratch_for_device(c->device, &scratch);
   if (rc != SOFT_OK) return rc;
@@ -73,17 +82,7 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
   soft::ShotParams p{};
   p.n_circ = 1;
   soft::CircDev &d = p.circ[0];
-  d.ev = c->d_ev;
-  d.coef = c->d_coef;
-  d.cb = c->d_cb;
-  d.sites = c->d_sites;
-  d.thr = c->d_thr;
-  d.n_events = (uint32_t)hp.ev.size();
-  d.n_sites = hp.n_sites;
-  d.rw = hp.rw;
-  d.cap = hp.cap;
-  d.n_coef = (uint32_t)hp.coefs.size();
-  d.n_cb = (uint32_t)hp.cb.size();
+  d = soft::circ_desc(c, fp32, false);  // the program and the gap-search index, no prefix
   d.item_begin = 0;
   d.n_shots = n_shots;
   d.first_shot = first_shot;

@@ -5,16 +5,17 @@ memory owned by another allocator, or loops that cannot afford cudaMalloc's
 implicit synchronisation). Its outputs must equal those of soft_run_shots
 for the same shots: tallies, status bytes and records are integer results,
 compared exactly (the tolerance of the other parity tests for integer
-work). Two calls in a row check that the shared static scratch, which keeps
-the previous call's contents, is cleared correctly. This file is named to
-run last.
+work). Calls in a row check that the shared static scratch, which keeps
+the previous call's contents, is cleared correctly, and that after the first
+call the device's free memory does not change across a call. A CPU test checks
+that the entry point's source names no allocating routine. This file is named
+to run last.
 """
 import numpy as np
 import pytest
 
 from paper_2512_23037_gb300 import circuits as C
 
-pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -27,6 +28,7 @@ def env():
     return torch, S
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_noalloc_matches_regular_entry_point(env, precision):
     torch, S = env
@@ -39,18 +41,28 @@ def test_noalloc_matches_regular_entry_point(env, precision):
     tally_ref = [t["shots"], t["discarded"], t["overflow"], t["kept"], t["logical_errors"]]
     rw = c.info["record_words"]
     stream = torch.cuda.current_stream()
-    for call in range(2):
-        tally = torch.full((5,), -1, dtype=torch.int64, device="cuda")
-        status = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
-        records = torch.full((n, rw), -1, dtype=torch.int64, device="cuda")
+    # output buffers allocated once, refilled before every call
+    tally = torch.empty((5,), dtype=torch.int64, device="cuda")
+    status = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    records = torch.empty((n, rw), dtype=torch.int64, device="cuda")
+    free_after = []
+    for call in range(3):
+        tally.fill_(-1)
+        status.fill_(255)
+        records.fill_(-1)
+        torch.cuda.synchronize()
         S.soft_run_shots_noalloc(c, n, first, seed, precision, stream, tally.data_ptr(), status.data_ptr(),
                                  records.data_ptr())
         torch.cuda.synchronize()
+        free_after.append(torch.cuda.mem_get_info()[0])
         assert tally.cpu().tolist() == tally_ref, f"call {call}"
         assert np.array_equal(status.cpu().numpy(), st_ref), f"call {call}"
         assert np.array_equal(records.cpu().numpy().view(np.uint64), rec_ref), f"call {call}"
+    # after the first call (which may load kernel code), calls take no device memory
+    assert free_after[1] == free_after[2], free_after
 
 
+@pytest.mark.gpu
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     torch, S = env
     circ, noise = C.workload("tiny6")
@@ -59,3 +71,29 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     with pytest.raises(S.SoftError) as ei:
         S.soft_run_shots_noalloc(c, (1 << 20) + 1, 0, 0, "fp64", None, tally.data_ptr())
     assert ei.value.code == -1 and "limit" in str(ei.value)
+
+
+ALLOC = r"\b(cudaMalloc\w*|cudaFree\w*|cudaHostAlloc|cuMemAlloc\w*|cudaMemPool\w*)\b"
+
+
+def _function(src, signature):
+    """Text of the function that starts at `signature` (up to its closing brace
+    at the start of a line)."""
+    body = src[src.index(signature):]
+    return body[:body.index("\n}\n")]
+
+
+def test_noalloc_source_names_no_allocating_call():
+    """The entry point's file, and the launch helpers it calls, name no device
+    or pinned-host allocation routine: a regression that adds one fails here,
+    without a GPU."""
+    import os
+    import re
+    csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2512_23037_gb300",
+                        "csrc")
+    src = open(os.path.join(csrc, "noalloc.cu")).read()
+    code = "\n".join(line.split("//", 1)[0] for line in src.splitlines())
+    assert not re.findall(ALLOC, code)
+    kern = open(os.path.join(csrc, "kernels.cu")).read()
+    for sig in ("cudaError_t launch_shots(", "cudaError_t prepare_shots(", "cudaError_t launch_prepared("):
+        assert not re.findall(ALLOC, _function(kern, sig)), sig
