@@ -67,7 +67,8 @@ class _Tally(ctypes.Structure):
 EXPORTED = ["soft_compile_circuit", "soft_circuit_info", "soft_circuit_tableau", "soft_circuit_free",
             "soft_run_shots", "soft_tally", "soft_get_records", "soft_get_state", "soft_run_timing", "soft_run_pass_timing", "soft_release_workspace",
             "soft_run_free", "soft_run_shots_noalloc", "soft_run_diagnostics", "soft_run_batch",
-            "soft_tally_batch", "soft_fidelity_grad", "soft_last_error"]
+            "soft_tally_batch", "soft_fidelity_grad", "soft_last_error", "soft_peak_pipe_rate"]
+PEAK_FP64_FMA, PEAK_FP32_FMA, PEAK_INT32_LOGIC = 0, 1, 2
 
 
 def lib_path() -> str:
@@ -104,6 +105,8 @@ def load(build_if_missing: bool = True):
         L.soft_run_batch.argtypes = [vp, vp, vp, u32, u64, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
         L.soft_tally_batch.argtypes = [vp, u32, ctypes.POINTER(_Tally)]
         L.soft_fidelity_grad.argtypes = [vp, vp, u32, u64, u64, u64, ctypes.c_int32, vp, vp, vp, vp, vp, vp]
+        L.soft_peak_pipe_rate.argtypes = [ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
         L.soft_last_error.restype = ctypes.c_char_p
         _lib = L
         return L
@@ -353,3 +356,15 @@ def soft_fidelity_grad(circ: Circuit, theta, n_patterns: int, first_pattern: int
     if sums:
         return fid, pacc, grad, status, s3
     return fid, pacc, grad, status
+
+
+def soft_peak_pipe_rate(kind: int, stream=None):
+    """(ops/s, ms per launch) of one arithmetic pipe on the current device:
+    kind PEAK_FP64_FMA / PEAK_FP32_FMA (flops/s, an FMA = 2) or
+    PEAK_INT32_LOGIC (ops/s); see include/soft_peak.h."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    r, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().soft_peak_pipe_rate(int(kind), ctypes.c_void_p(int(stream) if stream else 0), ctypes.byref(r),
+                                      ctypes.byref(ms)))
+    return float(r.value), float(ms.value)

@@ -9,12 +9,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsoft.so")
-SOURCES = ["compile.cpp", "kernels.cu", "lanes.cu", "api.cu", "noalloc.cu", "adjoint.cu", "grad_api.cu"]
+SOURCES = ["compile.cpp", "kernels.cu", "lanes.cu", "api.cu", "noalloc.cu", "adjoint.cu", "grad_api.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-for _v in ("SOFT_MIN_BLOCKS_F32", "SOFT_MIN_BLOCKS_F64", "SOFT_GRAD_MIN_BLOCKS", "SOFT_LANE_CAP", "SOFT_LANE_EVICT", "SOFT_LANE_ROUNDS"):  # budget experiments
-    if os.environ.get(_v):
-        FLAGS += [f"-D{_v}={int(os.environ[_v])}"]
 
 
 def _nvcc():
@@ -26,7 +23,8 @@ def _nvcc():
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(os.path.dirname(HERE), "include", "soft.h"))
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    files += [os.path.join(inc, f) for f in os.listdir(inc)]
     return max(os.path.getmtime(f) for f in files)
 
 

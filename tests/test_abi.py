@@ -1,4 +1,4 @@
-"""C ABI library: builds, loads and exports every call include/soft.h
+"""C ABI library: builds, loads and exports every call include/*.h
 declares; host-side validation errors need no GPU."""
 import ctypes
 import os
@@ -12,9 +12,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "soft.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(soft_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(soft_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -65,3 +69,9 @@ def test_host_validation_errors(S):
     with pytest.raises(S.SoftError) as ei:
         S.soft_compile_circuit(bad, 2, C.Noise(), 16)
     assert ei.value.code == -4
+
+
+def test_peak_rejects_bad_kind(S):
+    with pytest.raises(S.SoftError) as ei:
+        S.soft_peak_pipe_rate(7)
+    assert ei.value.code == -1
