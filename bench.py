@@ -42,6 +42,11 @@ WORKLOADS = {
 # multiply-adds and the key XOR/parity), a diagonal T/Rz entry, a measurement entry visit
 # (norm and filter or pairing), a noise entry touch (key XOR and phase)
 OPS_T_OUT, OPS_T_DIAG, OPS_MEAS, OPS_NOISE = 18, 9, 8, 3
+# FP64 flops of the same units in the FP64 path (coefficients FP64): a T/Rz output entry
+# a v + b xi v' (two complex products and a complex sum), a diagonal entry (a + b xi) v (one
+# complex product), a measurement entry visit (|v|^2 and its accumulation); noise entries
+# permute and negate (no flops)
+FLOPS_T_OUT, FLOPS_T_DIAG, FLOPS_MEAS = 14, 6, 4
 
 
 def parse():
@@ -66,6 +71,10 @@ def parse():
     ap.add_argument("--grad-patterns", type=int, default=100000,
                     help="error patterns per step of the gradient leg (0 = skip it)")
     ap.add_argument("--no-fidelity", action="store_true", help="skip the exact-fidelity leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the batch64, w97 and FP32-vs-FP64 precision legs of the default w42 line")
+    ap.add_argument("--w97-chunks", type=int, default=2,
+                    help="graph-replayed 1e8-shot chunks per step of the w97 leg")
     ap.add_argument("--sweep", action="store_true",
                     help="w42 sweeps instead of the bench line: noise p in {5e-4, 1e-3, 2e-3} and shots resident "
                          "per SM (one JSON line per point)")
@@ -132,6 +141,11 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def lane_mode_of(pass_ms):
+    """A run whose bucketing pre-pass took time ran lane per shot."""
+    return pass_ms[0] > 0
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -195,20 +209,29 @@ def _ops(k, post):
             + OPS_NOISE * k["noise_entries"])
 
 
+def _flops(k, post):
+    """FP64 flops of the FP64 path from the oracle's exact counters (see _ops)."""
+    if post:
+        return FLOPS_T_OUT * k["post_t_out"] + FLOPS_T_DIAG * k["post_t_diag"] + FLOPS_MEAS * k["post_meas"]
+    return FLOPS_T_OUT * k["t_out_entries"] + FLOPS_T_DIAG * k["t_diag_entries"] + FLOPS_MEAS * k["meas_entries"]
+
+
 def ops_per_shot_items(items, sample=2000):
-    """Shot-weighted algorithmic lane ops per shot over a workload's circuits,
-    from the oracle's counters on a sample of the same workload (seed 0):
-    (executed: after the shared noiseless prefix, whole method)."""
+    """Shot-weighted algorithmic work per shot over a workload's circuits, from
+    the oracle's counters on a sample of the same workload (seed 0): lane ops
+    (executed: after the shared noiseless prefix; whole method) and FP64 flops
+    of the FP64 path (executed; whole method)."""
     import oracle
     per = sample if len(items) == 1 else max(50, sample // 10)
-    tot_post, tot_full, tot_w = 0.0, 0.0, 0
+    tot = [0.0, 0.0, 0.0, 0.0]
+    tot_w = 0
     for c, nz, shots in items:
         r = oracle.run(c, c.n, nz, c.cap, 0, 0, per, threads=os.cpu_count() or 1, records=False)
         k = r["counts"]
-        tot_post += _ops(k, True) / k["shots"] * shots
-        tot_full += _ops(k, False) / k["shots"] * shots
+        for j, v in enumerate((_ops(k, True), _ops(k, False), _flops(k, True), _flops(k, False))):
+            tot[j] += v / k["shots"] * shots
         tot_w += shots
-    return tot_post / tot_w, tot_full / tot_w
+    return [v / tot_w for v in tot]
 
 
 def grad_bench(S, C, torch, stream, n_pat, steps, warmup):
@@ -326,6 +349,147 @@ def reference_arm(args):
             "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ----------------------------------------------------------------- extra legs of the w42 line
+def _events_ms(stream, torch, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _tally_list(t):
+    return [t["shots"], t["discarded"], t["overflow"], t["kept"], t["logical_errors"]]
+
+
+def leg_batch64(S, C, torch, peak_ops, flush):
+    """The batching configuration: one launch sequence over 64 windowed circuits
+    (77.1 M shots per step), autotuned launch shape, chunks replayed from a CUDA
+    graph; FP32 and FP64, one warm-up and two timed steps each."""
+    items = C.batch_of_windowed(2, 64)
+    hs = [S.soft_compile_circuit(c.array(), c.n, nz, c.cap) for c, nz, _ in items]
+    shots = [s for _, _, s in items]
+    n = sum(shots)
+    stream = torch.cuda.Stream()
+    from paper_2512_23037_gb300.autotune import autotune
+    res = autotune(hs, precision="fp32", stream=stream, sample_shots=1 << 22)
+    tune = res["best"]
+    ops_shot, ops_full, _, _ = ops_per_shot_items(items)
+    out = {"workload": WORKLOADS["batch64"], "shots_per_step": n, "graph_replay": True, "launch_shape": tune,
+           "autotune_table_ms": [[round(ms, 3), kw] for ms, kw in res["table"]]}
+    for prec in ("fp32", "fp64"):
+        def run(k, first0):
+            return S.soft_run_batch(hs, shots, [first0 + k * n] * len(hs), 0, precision=prec, stream=stream,
+                                    graph=True, **tune)
+        S.soft_tally(run(0, 1 << 36))
+        ms_tot, tal = 0.0, None
+        for k in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ms, r = _events_ms(stream, torch, lambda: run(k, 0))
+            tal = S.soft_tally(r)
+            ms_tot += ms
+            r.free()
+        achieved = ops_shot * n * 2 / (ms_tot / 1000)
+        out[prec] = {"value": 2 * n / (ms_tot / 1000), "unit": "shots/s", "ms_per_step": ms_tot / 2,
+                     "dtype": "f32" if prec == "fp32" else "f64", "tally_last_step": tal,
+                     "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                                  "unit": "Tops/s", "frac": achieved / peak_ops,
+                                  "frac_whole_method": ops_full * n * 2 / (ms_tot / 1000) / peak_ops,
+                                  "traffic": None, "kernel": "lane_kernel + shot_kernel (whole launch sequence)",
+                                  "ops_per_shot": ops_shot, "ops_per_shot_whole_method": ops_full}}
+    for h in hs:
+        h.free()
+    return out
+
+
+def leg_w97(S, C, torch, peak_ops, n_chunks):
+    """The large throughput configuration: 97 qubits, 1e8-shot chunks replayed
+    from one captured CUDA graph, n_chunks chunks per step; FP32 and FP64, a
+    warm-up run of two 1e6-shot chunks (same kernels and graph path) and one
+    timed step each."""
+    circ, noise = C.workload("w97")
+    h = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    chunk = 100_000_000
+    n = n_chunks * chunk
+    stream = torch.cuda.Stream()
+    ops_shot, ops_full, _, _ = ops_per_shot_items([(circ, noise, 1)])
+    out = {"workload": WORKLOADS["w97"], "shots_per_step": n, "chunk_shots": chunk, "graph_replay": True,
+           "steps": 1}
+    for prec in ("fp32", "fp64"):
+        S.soft_tally(S.soft_run_shots(h, 2_000_000, 1 << 40, 0, precision=prec, stream=stream, graph=True,
+                                      chunk_shots=1_000_000))
+        torch.cuda.synchronize()
+        ms, r = _events_ms(stream, torch, lambda: S.soft_run_shots(h, n, 0, 0, precision=prec, stream=stream,
+                                                                    graph=True, chunk_shots=chunk))
+        tal = S.soft_tally(r)
+        r.free()
+        achieved = ops_shot * n / (ms / 1000)
+        out[prec] = {"value": n / (ms / 1000), "unit": "shots/s", "ms_per_step": ms,
+                     "dtype": "f32" if prec == "fp32" else "f64", "tally": tal,
+                     "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                                  "unit": "Tops/s", "frac": achieved / peak_ops,
+                                  "frac_whole_method": ops_full * n / (ms / 1000) / peak_ops, "traffic": None,
+                                  "kernel": "shot_kernel (warp per shot: the noiseless maps reach 64 entries)",
+                                  "ops_per_shot": ops_shot, "ops_per_shot_whole_method": ops_full}}
+    h.free()
+    return out
+
+
+def leg_precision(S, C, torch, n, grad_patterns):
+    """FP32 coefficients against FP64 on the same shots of w42 (seed 0, shots
+    [2^37, 2^37 + n)): shots whose status or records differ, the kept, discard and
+    logical-error rates, the exact-fidelity sums; and on the same error patterns
+    of w42rz, F and the gradient. The FP64 path is the reference here: both are
+    checked against the oracle shot for shot in the tests."""
+    circ, noise = C.workload("w42")
+    h = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    rw = h.info["record_words"]
+    first = 1 << 37
+    runs = {}
+    for prec in ("fp32", "fp64"):
+        st = torch.empty(n, dtype=torch.uint8, device="cuda")
+        rec = torch.empty((n, rw), dtype=torch.int64, device="cuda")
+        r = S.soft_run_shots(h, n, first, 0, precision=prec, record_mode=S.REC_ALL, d_records=rec.data_ptr(),
+                             d_status=st.data_ptr())
+        t = S.soft_tally(r)
+        r.free()
+        rf = S.soft_run_shots(h, n, first, 0, precision=prec, fidelity=True)
+        tf = S.soft_tally(rf)
+        rf.free()
+        runs[prec] = (st, rec, t, tf)
+    s32, r32, t32, f32 = runs["fp32"]
+    s64, r64, t64, f64 = runs["fp64"]
+    diff = (s32 != s64) | (r32 != r64).any(dim=1)
+    out = {"workload": WORKLOADS["w42"], "shots": n,
+           "shots_differing": int(diff.sum().item()),
+           "status_differing": int((s32 != s64).sum().item()),
+           "tally_fp32": _tally_list(t32), "tally_fp64": _tally_list(t64),
+           "kept_rate_diff": (t32["kept"] - t64["kept"]) / n,
+           "discard_rate_diff": (t32["discarded"] - t64["discarded"]) / n,
+           "ler_fp32": t32["logical_errors"] / max(t32["kept"], 1),
+           "ler_fp64": t64["logical_errors"] / max(t64["kept"], 1),
+           "fidelity_sum_fp32": f32["sum_fidelity"], "fidelity_sum_fp64": f64["sum_fidelity"],
+           "fidelity_sum_rel_diff": abs(f32["sum_fidelity"] - f64["sum_fidelity"]) / max(abs(f64["sum_fidelity"]),
+                                                                                        1e-300),
+           "kept_fidelity_mode": [f32["kept"], f64["kept"]]}
+    h.free()
+    if grad_patterns > 0:
+        circ, noise = C.workload("w42rz")
+        theta = C.rz_thetas(1, 72)
+        hg = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+        g = {p: S.soft_fidelity_grad(hg, theta, grad_patterns, 0, 0, p) for p in ("fp32", "fp64")}
+        ok = (g["fp32"][3] == 0) & (g["fp64"][3] == 0)
+        out["gradient"] = {"patterns": grad_patterns, "ok_both": int(ok.sum().item()),
+                           "status_differing": int((g["fp32"][3] != g["fp64"][3]).sum().item()),
+                           "max_abs_F_diff": float((g["fp32"][0] - g["fp64"][0])[ok].abs().max().item()),
+                           "max_abs_grad_diff": float((g["fp32"][2] - g["fp64"][2])[ok].abs().max().item()),
+                           "max_abs_grad_fp64": float(g["fp64"][2][ok].abs().max().item())}
+        hg.free()
+    return out
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -484,18 +648,43 @@ def main():
         return 0
     shots_all = n * world * args.steps
     value = shots_all / (ms32 / 1000)
-    ops_shot, ops_full = ops_per_shot_items(items)
+    ops_shot, ops_full, flops64_shot, flops64_full = ops_per_shot_items(items)
     peaks = measured_peaks()
     sm_clock = peaks.get("sm_max_mhz", 2070.0)
     sms = dev_props.multi_processor_count
     peak_ops = sms * 128 * sm_clock * 1e6  # FP32/INT32 lanes x clock
+    # measured issue-rate peaks of the pipes (the FP64 path's roof), clocks sampled while they run
+    pclk = Clocks(local)
+    pipe = {name: S.soft_peak_pipe_rate(kind, stream) for name, kind in
+            (("fp64_fma", S.PEAK_FP64_FMA), ("fp32_fma", S.PEAK_FP32_FMA), ("int32_logic", S.PEAK_INT32_LOGIC))}
+    pipe_clocks = pclk.stop()
+    peak_fp64 = pipe["fp64_fma"][0]
+    legs = {}
+    if args.workload == "w42" and world == 1 and not args.no_legs:
+        legs["batch64"] = leg_batch64(S, C, torch, peak_ops, flush)
+        legs["w97"] = leg_w97(S, C, torch, peak_ops, args.w97_chunks)
+        legs["precision_error"] = leg_precision(S, C, torch, n, min(args.grad_patterns, 100000))
     # dominant kernel: the first-pass shot kernel (lane per shot where it applies), timed with the
     # passes that finish its work (bucketing pre-pass, rerun of outgrown maps) by CUDA events between
     # them on the launching stream; the work is every shot's executed lane ops
     pass_ms = [sum(k[j] for k in kms32) / len(kms32) for j in range(3)]
     avg_launch_ms = sum(pass_ms)
     achieved = ops_shot * n / (avg_launch_ms / 1000)
-    lane_mode = pass_ms[0] > 0
+    fp64_roof = None
+    if ms64 is not None:
+        # the FP64 path against the measured FP64 pipe: its algorithmic FP64 flops over the same passes
+        pass64 = [sum(k[j] for k in kms64) / len(kms64) for j in range(3)]
+        a64 = flops64_shot * n / (sum(pass64) / 1000)
+        fp64_roof = {"bound": "fp64", "achieved": a64 / 1e12, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+                     "frac": a64 / peak_fp64, "frac_whole_method": flops64_full * n / (sum(pass64) / 1000) / peak_fp64,
+                     "traffic": None, "kernel": "lane_kernel<double>" if lane_mode_of(pass64) else "shot_kernel<double>",
+                     "pass_ms_per_step": {"prepass": pass64[0], "first_pass": pass64[1], "rerun": pass64[2]},
+                     "flops_per_shot": flops64_shot, "flops_per_shot_whole_method": flops64_full,
+                     "work": "FP64 flops of T/Rz output entries (14), diagonal entries (6) and measurement entry "
+                             "visits (4) a shot executes after the shared noiseless prefix (oracle counters)",
+                     "peak_basis": "measured: soft_peak_pipe_rate(FP64 FMA) in this run, 2 flops per FMA",
+                     "alu_frac": ops_shot * n / (sum(pass64) / 1000) / peak_ops}
+    lane_mode = lane_mode_of(pass_ms)
     chunks = -(-n // args.chunk) if args.chunk else -(-n // (1 << 24))
     traffic = profile_traffic(kernel_hash(), "lane_kernel_w42.md" if lane_mode else "shot_kernel_w42.md",
                               -(-n // chunks))
@@ -509,10 +698,11 @@ def main():
                    "launch_shape": {k: v for k, v in tune.items() if v} or "library default"},
         "fp64_plain": None if ms64 is None else {
             "value": shots_all / (ms64 / 1000), "unit": "shots/s", "ms_per_step": ms64 / args.steps,
-            "dtype": "f64"},
+            "dtype": "f64", "roofline": fp64_roof},
         "tally_last_step": tal32[-1],
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "frac": achieved / peak_ops, "frac_whole_method": ops_full * n / (avg_launch_ms / 1000) / peak_ops,
+                     "traffic": traffic,
                      "kernel": "lane_kernel" if lane_mode else "shot_kernel",
                      "pass_ms_per_step": {"prepass": pass_ms[0], "first_pass": pass_ms[1], "rerun": pass_ms[2]},
                      "rerun_shots_per_step": sum(k[3] for k in kms32) / len(kms32),
@@ -526,7 +716,11 @@ def main():
                 "d2h_bytes_per_step": 56, "pipelined": "the host compiles step k+1 while step k runs",
                 "serial_value": shots_all / (e2e_serial_ms / 1000)},
         "clocks": clock_info,
+        "pipe_peaks": {"fp64_fma_tflops": pipe["fp64_fma"][0] / 1e12, "fp32_fma_tflops": pipe["fp32_fma"][0] / 1e12,
+                       "int32_logic_tops": pipe["int32_logic"][0] / 1e12, "clocks": pipe_clocks,
+                       "how": "soft_peak_pipe_rate: independent FMA / logic chains on every SM, best of 5 launches"},
     }
+    line.update(legs)
     if fid_leg:
         line["fidelity_mode"] = fid_leg
     if grad_leg:

@@ -2,10 +2,13 @@
 oracle's projection runs and parameter-shift gradient, against central
 finite differences of the GPU's own F, and through torch.autograd.
 
-Bars: statuses equal; F and p_acc within 1e-10 (FP64) / 1e-4 (FP32) of the
-oracle; dF/dtheta within 1e-8 (FP64) / 1e-3 (FP32) absolute of the oracle's
-exact parameter-shift gradient (FP32 coefficients carry ~1e-6 relative error
-through ~200 updates, and the gradient differences two such sums).
+Bars: statuses equal; F and p_acc within 1e-10 (FP64) / 1e-5 (FP32) of the
+oracle; dF/dtheta within 1e-8 (FP64) / 1e-5 (FP32) absolute of the oracle's
+exact parameter-shift gradient. The FP32 bars are about 6x the largest errors
+observed on these cases on GB300 (F 1.1e-6, gradient 1.7e-6, both on the
+6-qubit case with 64-entry maps; 1e-7 to 3e-7 on the others): FP32
+coefficients carry ~1e-6 relative error through ~200 updates, and the
+gradient differences two such sums.
 """
 import numpy as np
 import pytest
@@ -15,8 +18,8 @@ from paper_2512_23037_gb300 import circuits as C
 
 pytestmark = pytest.mark.gpu
 
-FTOL = {"fp64": 1e-10, "fp32": 1e-4}
-GTOL = {"fp64": 1e-8, "fp32": 1e-3}
+FTOL = {"fp64": 1e-10, "fp32": 1e-5}
+GTOL = {"fp64": 1e-8, "fp32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -113,6 +116,40 @@ def test_gpu_gradient_matches_finite_differences(soft):
         fd = (fp - fm) / (2 * h)
         assert np.max(np.abs(fd[sel] - grad[sel, k])) < 1e-6
     assert np.abs(grad[status == 0]).max() > 1e-3
+
+
+def test_w42rz_gradient_matches_finite_differences(soft):
+    """The differentiation workload itself (w42rz: 72 angles): the adjoint
+    gradient equals central differences of the GPU's own F, h = 1e-6, for all
+    72 angles (FP64; the central difference's truncation and rounding error is
+    ~1e-10 here), on every accepted pattern of the range, of which at least 20
+    have a nonzero gradient. (Most accepted patterns have F = 1 for any angles:
+    without an effective error each Rz(theta) meets its Rz(-theta); the range
+    grows until it holds 20 that do not.)"""
+    S = soft
+    circ, noise = C.workload("w42rz")
+    theta = C.rz_thetas(1, 72)
+    c = S.soft_compile_circuit(circ.array(), circ.n, noise, circ.cap)
+    for n in (20000, 100000, 400000):
+        fid, pacc, grad, status = [t.cpu().numpy() for t in S.soft_fidelity_grad(c, theta, n, 0, 0, "fp64")]
+        sel = status == 0
+        live = sel & (np.abs(grad).max(axis=1) > 1e-6)
+        if live.sum() >= 20:
+            break
+    assert live.sum() >= 20, (n, sel.sum(), live.sum())
+    h = 1e-6
+    worst = 0.0
+    for k in range(len(theta)):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fp, _, _, sp = [t.cpu().numpy() for t in S.soft_fidelity_grad(c, tp, n, 0, 0, "fp64")]
+        fm, _, _, sm = [t.cpu().numpy() for t in S.soft_fidelity_grad(c, tm, n, 0, 0, "fp64")]
+        assert np.array_equal(sp, status) and np.array_equal(sm, status)
+        fd = (fp - fm) / (2 * h)
+        worst = max(worst, float(np.max(np.abs(fd[sel] - grad[sel, k]))))
+    assert worst < 1e-7, worst
+    assert np.abs(grad[sel]).max() > 1e-3
 
 
 def test_autograd_function(soft):
