@@ -28,11 +28,15 @@ template <typename R>
 __device__ __forceinline__ Cx<R> cscale(Cx<R> a, R s) {
   return {a.x * s, a.y * s};
 }
+// -x by flipping the sign bit (an integer op: exact, and it keeps negations off
+// GB300's narrow FP64 pipe)
+__device__ __forceinline__ double negr(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull); }
+__device__ __forceinline__ float negr(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
 // v * i^e
 template <typename R>
 __device__ __forceinline__ Cx<R> ipow(Cx<R> v, uint32_t e) {
-  Cx<R> r = (e & 1u) ? Cx<R>{-v.y, v.x} : v;
-  if (e & 2u) r = {-r.x, -r.y};
+  Cx<R> r = (e & 1u) ? Cx<R>{negr(v.y), v.x} : v;
+  if (e & 2u) r = {negr(r.x), negr(r.y)};
   return r;
 }
 template <typename R>

@@ -95,8 +95,15 @@ struct LaneShot {
   double fid;
   bool force;
 
+  // FP64 prune test (see is_small): high words of sqrt(tau/2) (1 - 2^-18) and sqrt(tau) (1 + 2^-18)
+  uint32_t hs_lo = 0, hs_hi = 0;
+
   __device__ LaneShot(const ShotParams &p, unsigned char *base) : P(p), C(&p.circ[0]) {
     lane = threadIdx.x & 31u;
+    if (sizeof(R) == 8) {
+      hs_lo = (uint32_t)((unsigned long long)__double_as_longlong(sqrt(0.5 * p.tau) * (1.0 - 0x1p-18)) >> 32);
+      hs_hi = (uint32_t)((unsigned long long)__double_as_longlong(sqrt(p.tau) * (1.0 + 0x1p-18)) >> 32);
+    }
     const size_t kb = (size_t)Cap * W * 8 * 32, vb = (size_t)Cap * sizeof(Cx<R>) * 32;
     keys = reinterpret_cast<uint64_t *>(base);
     vals = reinterpret_cast<Cx<R> *>(base + kb);
@@ -155,6 +162,19 @@ struct LaneShot {
       P.diag[3] = value;
     }
   }
+  // |v|^2 < tau, the pruning test, decided exactly as the norm computed in R decides it.
+  // FP64: when both |re| and |im| lie below sqrt(tau/2) (1 - 2^-18), or either lies above
+  // sqrt(tau) (1 + 2^-18), integer compares of their high words settle it (the computed
+  // norm's rounding cannot cross tau there); only values in that narrow band compute
+  // the norm on the FP64 pipe, GB300's narrowest.
+  __device__ __forceinline__ bool is_small(Cx<R> v, R tau) const {
+    if (sizeof(R) == 4) return norm2(v) < tau;
+    const uint32_t hx = (uint32_t)((unsigned long long)__double_as_longlong((double)v.x) >> 32) & 0x7FFFFFFFu;
+    const uint32_t hy = (uint32_t)((unsigned long long)__double_as_longlong((double)v.y) >> 32) & 0x7FFFFFFFu;
+    if (hx > hs_hi || hy > hs_hi) return false;
+    if (hx < hs_lo && hy < hs_lo) return true;
+    return norm2(v) < tau;
+  }
   // keep the entries with |v|^2 >= tau, in order
   __device__ void prune() {
     const R tau = (R)P.tau;
@@ -162,7 +182,7 @@ struct LaneShot {
 #pragma unroll 1
     for (uint32_t i = 0; i < n; ++i) {
       const Cx<R> v = val(i);
-      if (norm2(v) >= tau) {
+      if (!is_small(v, tau)) {
         if (o != i) {
           set_key(o, key(i));
           set_val(o, v);
@@ -393,13 +413,17 @@ struct LaneShot {
     }
     const R tau = (R)P.tau;
     bool small = false;
+    // the phase xi = i^e (-1)^{gamma.key} folded into b once per event: b_s = (-1)^s b i^e
+    // (exact: a multiplication by i^e swaps and negates), so that an entry only selects one
+    const Cx<R> bq = ipow(b, e), bn = Cx<R>{negr(bq.x), negr(bq.y)};
     if (diag) {
+      // v' = (a + b xi) v: one complex product per entry
+      const Cx<R> c0 = cadd(a, bq), c1 = cadd(a, bn);
 #pragma unroll 1
       for (uint32_t i = 0; i < n; ++i) {
-        const Cx<R> v = val(i);
-        const Cx<R> nv = cadd(cmul(a, v), cmul(b, ipow(v, e + 2u * kpar(key(i), gamma))));
+        const Cx<R> nv = cmul(kpar(key(i), gamma) ? c1 : c0, val(i));
         set_val(i, nv);
-        small = small || norm2(nv) < tau;
+        small = small || is_small(nv, tau);
       }
       if (small) prune();
       return;
@@ -426,14 +450,14 @@ struct LaneShot {
       if ((has >> i) & 1u) {
         const uint32_t j = part.get(i);
         const Cx<R> vj = val(j);
-        const Cx<R> ni = cadd(cmul(a, v), cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
-        const Cx<R> nj = cadd(cmul(a, vj), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
+        const Cx<R> ni = cadd(cmul(a, v), cmul(kpar(pk, gamma) ? bn : bq, vj));
+        const Cx<R> nj = cadd(cmul(a, vj), cmul(kpar(k, gamma) ? bn : bq, v));
         set_val(i, ni);
         set_val((uint32_t)j, nj);
-        small = small || norm2(ni) < tau || norm2(nj) < tau;
+        small = small || is_small(ni, tau) || is_small(nj, tau);
       } else {
         const Cx<R> ni = cmul(a, v);
-        const Cx<R> av = cmul(b, ipow(v, e + 2u * kpar(k, gamma)));
+        const Cx<R> av = cmul(kpar(k, gamma) ? bn : bq, v);
         set_val(i, ni);
         if (n0 + na >= Cap) {
           fail_capacity();
@@ -442,7 +466,7 @@ struct LaneShot {
         set_key(n0 + na, pk);
         set_val(n0 + na, av);
         ++na;
-        small = small || norm2(ni) < tau || norm2(av) < tau;
+        small = small || is_small(ni, tau) || is_small(av, tau);
       }
     }
     n = n0 + na;
@@ -485,7 +509,7 @@ struct LaneShot {
       const Key<W> k = key(i);
       if ((kpar(k, gamma) ^ sgn) != want) continue;
       const Cx<R> v = cscale(val(i), sc);
-      if (norm2(v) < tau) continue;
+      if (is_small(v, tau)) continue;
       set_key(o, k);
       set_val(o, v);
       ++o;
@@ -802,11 +826,18 @@ __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_cons
   }
 }
 
+// Blocks per SM each variant's shared memory allows (w42: FP32 16-entry lanes 6, FP64 4,
+// the wide round's 32-entry lanes 3): the register budget is set not to lower it.
+template <typename R, uint32_t Cap>
+constexpr int kLaneMinBlocks() {
+  return sizeof(R) == 4 ? (Cap <= 16 ? 6 : 3) : 4;
+}
+
 // Multi: the run holds several circuits (a warp serves one at a time); the single-
 // circuit instantiation keeps circuit 0 and bucket offset 0 as constants. Cap: map
 // entries per lane (kLaneCap in the first rounds, kWideCap in the wide round).
 template <typename R, int W, bool Multi, uint32_t Cap>
-__global__ void __launch_bounds__(kLaneBlock) lane_kernel(const __grid_constant__ ShotParams P) {
+__global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   // per warp: tallies of its current circuit, added to the circuit's when the warp moves
   // to another circuit and at the end
