@@ -89,10 +89,13 @@ WsCache g_ws[kMaxDevices];
 static cudaError_t build_prefixes(soft_circuit *c, cudaStream_t us) {
   const auto &hp = c->hp;
   const size_t n_snap = hp.ev.size() + 1;
-  uint32_t *d_stop = nullptr;
-  cudaError_t e = cudaMalloc(&d_stop, 6 * sizeof(uint32_t));
+  uint32_t *d_stop = nullptr;  // per precision: last valid event, first fidelity event, largest map, largest dimension
+  cudaError_t e = cudaMalloc(&d_stop, 8 * sizeof(uint32_t));
   if (e != cudaSuccess) return e;
   c->d_stop = d_stop;
+  if ((e = cudaMemsetAsync(d_stop, 0, 8 * sizeof(uint32_t), us)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(us)) != cudaSuccess)
+    return e;
   // the two precisions' runs are one warp each: they run side by side on two streams
   cudaStream_t ps[2] = {nullptr, nullptr};
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&ps[k], cudaStreamNonBlocking);
@@ -119,7 +122,9 @@ static cudaError_t build_prefixes(soft_circuit *c, cudaStream_t us) {
     p.cap = std::min(hp.cap, soft::kDefaultFirstCap);
     p.rw_max = hp.rw;
     p.tau = fp32 ? kTauFp32 : kTauFp64;
-    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + 3 * fp32, ps[fp32]);
+    e = soft::launch_prefix(p, fp32, hp.W, c->d_traj[fp32], d_stop + 4 * fp32, ps[fp32]);
+    if (e == cudaSuccess)
+      e = soft::launch_snap_affine(c->d_traj[fp32], (uint32_t)n_snap, hp.rw, fp32, hp.W, d_stop + 4 * fp32, ps[fp32]);
   }
   for (int k = 0; k < 2; ++k)
     if (ps[k]) {
@@ -127,14 +132,15 @@ static cudaError_t build_prefixes(soft_circuit *c, cudaStream_t us) {
       if (e == cudaSuccess) e = es;
       cudaStreamDestroy(ps[k]);
     }
-  uint32_t stop[6] = {0, 0, 0, 0, 0, 0};
+  uint32_t stop[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (e == cudaSuccess && (e = cudaMemcpyAsync(stop, d_stop, sizeof stop, cudaMemcpyDeviceToHost, us)) == cudaSuccess)
     e = cudaStreamSynchronize(us);
   if (e != cudaSuccess) return e;
   for (int k = 0; k < 2; ++k) {
-    c->traj_stop[k] = std::min<uint32_t>(stop[3 * k], (uint32_t)hp.ev.size());
-    c->traj_fid_stop[k] = std::min<uint32_t>(stop[3 * k + 1], (uint32_t)hp.ev.size());
-    c->traj_max_n[k] = stop[3 * k + 2];
+    c->traj_stop[k] = std::min<uint32_t>(stop[4 * k], (uint32_t)hp.ev.size());
+    c->traj_fid_stop[k] = std::min<uint32_t>(stop[4 * k + 1], (uint32_t)hp.ev.size());
+    c->traj_max_n[k] = stop[4 * k + 2];
+    c->traj_max_d[k] = stop[4 * k + 3];
   }
   return cudaSuccess;
 }
@@ -363,7 +369,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   uint64_t n_buckets = 0;
   std::vector<char> fits(n_circ);
   for (uint32_t i = 0; i < n_circ; ++i) {
-    fits[i] = circs[i]->d_traj[pk] && circs[i]->traj_max_n[pk] <= soft::lane_map_cap();
+    fits[i] = circs[i]->d_traj[pk] && circs[i]->traj_max_n[pk] <= soft::lane_map_cap() &&
+              circs[i]->traj_max_d[pk] <= soft::lane_map_dim();
     if (fits[i]) n_buckets += circs[i]->hp.ev.size() + 1;
   }
   const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && !(o.flags & SOFT_RUN_NO_PREFIX) && o.group_size == 0 &&

@@ -43,6 +43,31 @@ template <typename R>
 __device__ __forceinline__ R norm2(Cx<R> v) {
   return v.x * v.x + v.y * v.y;
 }
+
+// The pruning test |v|^2 < tau, decided exactly as the norm computed in R decides it.
+// FP64: when both |re| and |im| lie below sqrt(tau/2) (1 - 2^-18), or either lies above
+// sqrt(tau) (1 + 2^-18), integer compares of their high words settle it (the computed
+// norm's rounding cannot cross tau there); only values in that narrow band compute the
+// norm on the FP64 pipe, GB300's narrowest.
+template <typename R>
+struct PruneTest {
+  R tau;
+  uint32_t lo = 0, hi = 0;  // high words of the two bounds above (FP64)
+  __device__ explicit PruneTest(double t) : tau((R)t) {
+    if (sizeof(R) == 8) {
+      lo = (uint32_t)((unsigned long long)__double_as_longlong(sqrt(0.5 * t) * (1.0 - 0x1p-18)) >> 32);
+      hi = (uint32_t)((unsigned long long)__double_as_longlong(sqrt(t) * (1.0 + 0x1p-18)) >> 32);
+    }
+  }
+  __device__ __forceinline__ bool small(Cx<R> v) const {
+    if (sizeof(R) == 4) return norm2(v) < tau;
+    const uint32_t hx = (uint32_t)((unsigned long long)__double_as_longlong((double)v.x) >> 32) & 0x7FFFFFFFu;
+    const uint32_t hy = (uint32_t)((unsigned long long)__double_as_longlong((double)v.y) >> 32) & 0x7FFFFFFFu;
+    if (hx > hi || hy > hi) return false;
+    if (hx < lo && hy < lo) return true;
+    return norm2(v) < tau;
+  }
+};
 template <typename R>
 __device__ __forceinline__ double norm2d(Cx<R> v) {
   double a = (double)v.x, b = (double)v.y;

@@ -31,6 +31,7 @@ struct soft_circuit {
   uint32_t traj_stop[2] = {0, 0};
   uint32_t traj_fid_stop[2] = {0, 0};
   uint32_t traj_max_n[2] = {0, 0};  // largest map of the recorded noiseless run
+  uint32_t traj_max_d[2] = {0, 0};  // largest affine dimension of its maps (0xFF: above 5)
   uint32_t traj_stride[2] = {0, 0};
   // fidelity-gradient workspace, kept between calls (they are synchronous):
   // per-parameter coefficient table, work counter, per-warp tapes

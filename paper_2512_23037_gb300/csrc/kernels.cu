@@ -84,7 +84,9 @@ struct Shot {
   Key<W> rk;
   Cx<R> rv;
 
-  __device__ Shot(const Tile &tile, const ShotParams &p, unsigned char *base) : t(tile), P(p) {
+  PruneTest<R> pt;  // |v|^2 < tau (thresholds computed once per thread)
+
+  __device__ Shot(const Tile &tile, const ShotParams &p, unsigned char *base) : t(tile), P(p), pt(p.tau) {
     cap = P.cap;
     slots = 2 * cap;
     hsmax = P.hs_max;
@@ -314,7 +316,6 @@ struct Shot {
 
   __device__ void reg_rot(uint32_t e, uint32_t lowbit, Cx<R> a, Cx<R> b, const uint64_t *beta,
                           const uint64_t *gamma) {
-    const R tau = (R)P.tau;
     const bool valid = lane < nnz;
     const Key<W> pk = kxor(rk, beta);
     const Key<W> canon = kbit(rk, lowbit) ? pk : rk;  // the pair's member with bit lowbit clear
@@ -326,14 +327,15 @@ struct Shot {
     // one product serves both cases: b xi_{pk} v_partner (paired) or b xi_k v_k (new entry at pk)
     const Cx<R> src = has ? vj : rv;
     const uint32_t par = kpar(has ? pk : rk, gamma);
-    const Cx<R> tb = cmul(b, ipow(src, e + 2u * par));
+    const Cx<R> bq = ipow(b, e);  // b xi = (-1)^par b i^e: the phase folded into b (exact)
+    const Cx<R> tb = cmul(par ? Cx<R>{negr(bq.x), negr(bq.y)} : bq, src);
     Cx<R> nv = cmul(a, rv);
     if (has) nv = cadd(nv, tb);
     const Cx<R> av = tb;
     if (!valid) nv = Cx<R>{0, 0};
     const uint32_t ab = t.ballot(app);
     const uint32_t nA = __popc(ab);
-    const bool small = (valid && norm2(nv) < tau) || (app && norm2(av) < tau);
+    const bool small = (valid && pt.small(nv)) || (app && pt.small(av));
     const bool prune = t.any(small);
     if (nnz + nA > slots) {  // cannot happen while nnz <= cap before the gate
       fail_check(CHK_STAGE, nnz + nA);
@@ -357,7 +359,7 @@ struct Shot {
       } else if (valid) {
         rv = nv;
       }
-      if (prune) reg_compact(lane < nnz && norm2(rv) >= tau);
+      if (prune) reg_compact(lane < nnz && !pt.small(rv));
       if (nnz > ecap) fail_capacity();
       return;
     }
@@ -374,7 +376,7 @@ struct Shot {
     t.sync();
     reg = false;
     nnz += nA;
-    if (prune) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
+    if (prune) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return !pt.small(v); });
     if (nnz > ecap) {
       fail_capacity();
       return;
@@ -383,10 +385,10 @@ struct Shot {
   }
 
   __device__ void reg_rot_diag(uint32_t e, Cx<R> a, Cx<R> b, const uint64_t *gamma) {
-    const R tau = (R)P.tau;
     const bool valid = lane < nnz;
-    if (valid) rv = cadd(cmul(a, rv), cmul(b, ipow(rv, e + 2u * kpar(rk, gamma))));
-    if (t.any(valid && norm2(rv) < tau)) reg_compact(valid && norm2(rv) >= tau);
+    const Cx<R> bq = ipow(b, e);  // v' = (a + b xi) v, with a + b xi one of two constants
+    if (valid) rv = cmul(kpar(rk, gamma) ? csub(a, bq) : cadd(a, bq), rv);
+    if (t.any(valid && pt.small(rv))) reg_compact(valid && !pt.small(rv));
   }
 
   // Outcome of a non-deterministic measurement with p_+ = pp: sampled from the
@@ -492,7 +494,7 @@ struct Shot {
       reg_rot(e, lowbit, a, b, beta, gamma);
       return;
     }
-    const R tau = (R)P.tau;
+    const Cx<R> bq = ipow(b, e), bn = Cx<R>{negr(bq.x), negr(bq.y)};  // b xi: the phase folded into b
     uint32_t nA = 0;
     bool prune = false;
     const uint32_t n0 = nnz;
@@ -509,18 +511,18 @@ struct Shot {
         if (j >= 0) {
           if (!kbit(k, lowbit)) {
             Cx<R> vj = vals[j];
-            Cx<R> ni = cadd(cmul(a, v), cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
-            Cx<R> nj = cadd(cmul(a, vj), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
+            Cx<R> ni = cadd(cmul(a, v), cmul(kpar(pk, gamma) ? bn : bq, vj));
+            Cx<R> nj = cadd(cmul(a, vj), cmul(kpar(k, gamma) ? bn : bq, v));
             vals[i] = ni;
             vals[j] = nj;
-            prune = prune || norm2(ni) < tau || norm2(nj) < tau;
+            prune = prune || pt.small(ni) || pt.small(nj);
           }
         } else {
           Cx<R> ni = cmul(a, v);
           vals[i] = ni;
-          nv = cmul(b, ipow(v, e + 2u * kpar(k, gamma)));
+          nv = cmul(kpar(k, gamma) ? bn : bq, v);
           app = true;
-          prune = prune || norm2(ni) < tau || norm2(nv) < tau;
+          prune = prune || pt.small(ni) || pt.small(nv);
         }
       }
       uint32_t bal = t.ballot(app);
@@ -545,7 +547,7 @@ struct Shot {
       return;
     }
     bool pruned = t.any(prune);
-    if (pruned) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
+    if (pruned) nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return !pt.small(v); });
     if (nnz > ecap) {
       fail_capacity();
       return;
@@ -570,18 +572,17 @@ struct Shot {
       reg_rot_diag(e, a, b, gamma);
       return;
     }
-    const R tau = (R)P.tau;
+    const Cx<R> bq = ipow(b, e), c0 = cadd(a, bq), c1 = csub(a, bq);  // v' = (a + b xi) v
     bool prune = false;
     for (uint32_t i = lane; i < nnz; i += G) {
       Key<W> k = key(i);
-      Cx<R> v = vals[i];
-      Cx<R> nv = cadd(cmul(a, v), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
+      Cx<R> nv = cmul(kpar(k, gamma) ? c1 : c0, vals[i]);
       vals[i] = nv;
-      prune = prune || norm2(nv) < tau;
+      prune = prune || pt.small(nv);
     }
     t.sync();
     if (t.any(prune)) {
-      nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return norm2(v) >= tau; });
+      nnz = compact(0, nnz, [&](Key<W> &, Cx<R> &v) { return !pt.small(v); });
       rebuild();
     }
   }

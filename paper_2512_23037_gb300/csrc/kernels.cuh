@@ -140,6 +140,11 @@ uint32_t lane_prepass_grid();  // blocks of the bucketing pre-pass (al_base hold
 cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg,
                           bool wide = false);
 uint32_t lane_map_cap();
+uint32_t lane_map_dim();  // directions of a first-round lane's affine map (lane_map_cap = 2^lane_map_dim)
+// After launch_prefix: the affine form of each snapshot of the run (events [0, stop[0]]),
+// on the same stream; stop[3] (zeroed before) receives the largest dimension.
+cudaError_t launch_snap_affine(unsigned char *traj, uint32_t n_snap, uint32_t rw, int fp32, uint32_t W,
+                               uint32_t *stop, cudaStream_t st);
 
 // Resolve the launch (sets the kernel's shared-memory attribute, queries
 // occupancy). `p.hs_max` must already be hash_slots_for(p.cap). Not a stream

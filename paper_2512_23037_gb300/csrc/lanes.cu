@@ -52,107 +52,287 @@ static_assert(kLaneRounds >= 1 && kLaneRounds <= 8, "lane rounds");
 // of twice the map.
 constexpr uint32_t kWideCap = 2 * kLaneCap;
 
+// Lane map in affine form. The keys of a shot's coefficient map lie in an affine
+// space alpha0 ^ span(B[0..d)) of dimension d <= kDim (Sec. II-C: the support of v
+// grows by one direction per rotation whose beta is new, Theorem 1 (3), and shrinks
+// with measurements and cancellations). Slot s (s < 2^d) holds the entry of key
+//   key(s) = alpha0 ^ XOR over the set bits k of s of B[k],
+// with its value in row s of the lane's value column: exactly zero where no entry
+// lives, and `live` marks the slots that hold entries. Dual[k] (Dual[k] . B[j] = 1 iff
+// k = j, over GF(2)) gives the coordinates of a vector x of the span: x = XOR over
+// the k with Dual[k] . x = 1 of B[k]. So the partner key(s) ^ beta of a rotation is
+// slot s ^ c (c: beta's coordinates), a parity gamma . key(s) is g0 ^ parity(s & gl)
+// (g0 = gamma . alpha0, bit k of gl = gamma . B[k]), and a Pauli error moves alpha0
+// only: per entry only values are read and written, and no key is stored. The live
+// slots are the paper's sparse map: updates, pruning at tau and the overflow rule
+// apply to them exactly as to a sparse map.
+__host__ __device__ constexpr uint32_t lane_dim(uint32_t cap) { return cap <= 16u ? 4u : 5u; }
+
 template <typename R, int W, uint32_t Cap>
 __host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
-  // map keys and values; record words
-  return (size_t)Cap * W * 8 * 32 + (size_t)Cap * sizeof(Cx<R>) * 32 + (size_t)rw * 8 * 32;
+  // values of Cap slots; alpha0, kDim basis and kDim dual vectors (W words each); record words
+  return (size_t)Cap * sizeof(Cx<R>) * 32 + (size_t)(1 + 2 * lane_dim(Cap)) * W * 8 * 32 + (size_t)rw * 8 * 32;
 }
 
-// Partner indices, 5 bits per entry for maps of up to 32 entries: nibbles of
-// entries 0-15 and 16-31, and a mask of the indices' fifth bit.
-template <uint32_t Cap>
-struct PartIdx {
-  uint64_t lo = 0, hi = 0;
-  uint32_t b4 = 0;
-  __device__ __forceinline__ void set(uint32_t i, uint32_t j) {
-    const uint64_t v = (uint64_t)(j & 15u) << (4 * (i & 15u));
-    if (Cap <= 16 || i < 16) lo |= v;
-    else hi |= v;
-    if (Cap > 16) b4 |= ((j >> 4) & 1u) << i;
-  }
-  __device__ __forceinline__ uint32_t get(uint32_t i) const {
-    const uint64_t w = (Cap <= 16 || i < 16) ? lo : hi;
-    const uint32_t j = (uint32_t)(w >> (4 * (i & 15u))) & 15u;
-    return Cap > 16 ? j | (((b4 >> i) & 1u) << 4) : j;
-  }
-};
+// Slot masks over a cube of up to 32 slots: the slots whose index has bit k set.
+__device__ __forceinline__ uint32_t slot_bit_mask(uint32_t k) {
+  return k == 0u ? 0xAAAAAAAAu : k == 1u ? 0xCCCCCCCCu : k == 2u ? 0xF0F0F0F0u : k == 3u ? 0xFF00FF00u : 0xFFFF0000u;
+}
+// The slots s with parity(s & g) = 1.
+__device__ __forceinline__ uint32_t slot_par_mask(uint32_t g) {
+  uint32_t m = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < 5u; ++k)
+    if ((g >> k) & 1u) m ^= slot_bit_mask(k);
+  return m;
+}
+// A slot set moved by s -> s ^ c.
+__device__ __forceinline__ uint32_t slot_xor_perm(uint32_t L, uint32_t c) {
+#pragma unroll
+  for (uint32_t k = 0; k < 5u; ++k)
+    if ((c >> k) & 1u) {
+      const uint32_t M = slot_bit_mask(k), sh = 1u << k;
+      L = ((L & M) >> sh) | ((L & ~M) << sh);
+    }
+  return L;
+}
+__device__ __forceinline__ uint32_t spar(uint32_t s, uint32_t g) { return (uint32_t)__popc(s & g) & 1u; }
+template <int W>
+__device__ __forceinline__ bool wnonzero(const uint64_t *x) {
+  uint64_t o = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) o |= x[w];
+  return o != 0ull;
+}
+// The lowest set bit of a nonzero W-word vector.
+template <int W>
+__device__ __forceinline__ uint32_t wlow(const uint64_t *x) {
+  return x[0] ? (uint32_t)(__ffsll((long long)x[0]) - 1) : 64u + (uint32_t)(__ffsll((long long)x[W - 1]) - 1);
+}
 
 template <typename R, int W, uint32_t Cap>
 struct LaneShot {
-  static_assert(Cap <= 32, "lane map masks are 32-bit");
+  static constexpr uint32_t kDim = lane_dim(Cap);
+  static_assert(Cap == (1u << kDim), "a lane holds a cube of slots");
+  static constexpr uint32_t kRowB = 1, kRowD = 1 + kDim;  // rows: alpha0, B[0..kDim), Dual[0..kDim)
   const ShotParams &P;
   const CircDev *C;
   uint32_t lane;
-  uint64_t *keys;  // [i][w][lane]
-  Cx<R> *vals;     // [i][lane]
-  uint64_t *rec;           // [w][lane]
+  Cx<R> *vals;     // [slot][lane]
+  uint64_t *rows;  // [row][w][lane]
+  uint64_t *rec;   // [w][lane]
   // per-lane shot state
   uint64_t shot;
-  uint32_t n;
+  uint32_t d, live;
   uint64_t sd[W], ss[W];
   uint32_t nxt, cur, kblk, w2;
   int status, chain, logical, lastm;
   double fid;
   bool force;
 
-  // FP64 prune test (see is_small): high words of sqrt(tau/2) (1 - 2^-18) and sqrt(tau) (1 + 2^-18)
-  uint32_t hs_lo = 0, hs_hi = 0;
+  PruneTest<R> pt;  // |v|^2 < tau
 
-  __device__ LaneShot(const ShotParams &p, unsigned char *base) : P(p), C(&p.circ[0]) {
+  __device__ LaneShot(const ShotParams &p, unsigned char *base) : P(p), C(&p.circ[0]), pt(p.tau) {
     lane = threadIdx.x & 31u;
-    if (sizeof(R) == 8) {
-      hs_lo = (uint32_t)((unsigned long long)__double_as_longlong(sqrt(0.5 * p.tau) * (1.0 - 0x1p-18)) >> 32);
-      hs_hi = (uint32_t)((unsigned long long)__double_as_longlong(sqrt(p.tau) * (1.0 + 0x1p-18)) >> 32);
-    }
-    const size_t kb = (size_t)Cap * W * 8 * 32, vb = (size_t)Cap * sizeof(Cx<R>) * 32;
-    keys = reinterpret_cast<uint64_t *>(base);
-    vals = reinterpret_cast<Cx<R> *>(base + kb);
-    rec = reinterpret_cast<uint64_t *>(base + kb + vb);
+    const size_t vb = (size_t)Cap * sizeof(Cx<R>) * 32, rb = (size_t)(1 + 2 * kDim) * W * 8 * 32;
+    vals = reinterpret_cast<Cx<R> *>(base);
+    rows = reinterpret_cast<uint64_t *>(base + vb);
+    rec = reinterpret_cast<uint64_t *>(base + vb + rb);
   }
 
-  __device__ __forceinline__ Key<W> key(uint32_t i) const {
+  __device__ __forceinline__ Cx<R> val(uint32_t s) const { return vals[(size_t)s * 32 + lane]; }
+  __device__ __forceinline__ void set_val(uint32_t s, Cx<R> v) { vals[(size_t)s * 32 + lane] = v; }
+  __device__ __forceinline__ uint64_t row(uint32_t r, int w) const { return rows[((size_t)r * W + w) * 32 + lane]; }
+  __device__ __forceinline__ void set_row(uint32_t r, int w, uint64_t x) { rows[((size_t)r * W + w) * 32 + lane] = x; }
+  __device__ __forceinline__ void get_row(uint32_t r, uint64_t *x) const {
+#pragma unroll
+    for (int w = 0; w < W; ++w) x[w] = row(r, w);
+  }
+  __device__ __forceinline__ void put_row(uint32_t r, const uint64_t *x) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) set_row(r, w, x[w]);
+  }
+  __device__ __forceinline__ void xor_row(uint32_t r, const uint64_t *x) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) set_row(r, w, row(r, w) ^ x[w]);
+  }
+  __device__ __forceinline__ uint32_t row_par(uint32_t r, const uint64_t *g) const {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) t += __popcll(row(r, w) & g[w]);
+    return t & 1u;
+  }
+  __device__ __forceinline__ uint32_t row_bit(uint32_t r, uint32_t p) const {
+    return (uint32_t)((row(r, (W == 2 && p >= 64u) ? W - 1 : 0) >> (p & 63u)) & 1ull);
+  }
+  __device__ __forceinline__ uint32_t cube() const { return d >= 5u ? 0xFFFFFFFFu : (1u << (1u << d)) - 1u; }
+  __device__ __forceinline__ uint32_t nnz() const { return (uint32_t)__popc(live); }
+
+  // g . alpha0 into g0; bit k of the result: g . B[k]
+  __device__ uint32_t parities(const uint64_t *g, uint32_t &g0) const {
+    g0 = row_par(0, g);
+    uint32_t m = 0;
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k) m |= row_par(kRowB + k, g) << k;
+    return m;
+  }
+  // coordinates c of x (bit k: Dual[k] . x) and the residual r = x ^ XOR_{k in c} B[k],
+  // zero iff x lies in the span (otherwise Dual[k] . r = 0 for every k)
+  __device__ uint32_t coords(const uint64_t *x, uint64_t *r) const {
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) r[w] = x[w];
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k)
+      if (row_par(kRowD + k, x)) {
+        c |= 1u << k;
+#pragma unroll
+        for (int w = 0; w < W; ++w) r[w] ^= row(kRowB + k, w);
+      }
+    return c;
+  }
+  // B[d] = r (nonzero, Dual[k] . r = 0 for k < d); its dual e_p ^ XOR_k B[k][p] Dual[k] for
+  // the lowest set bit p of r is orthogonal to every B[k] and has Dual . r = 1, and the
+  // old duals stay dual (Dual[k] . r = 0)
+  __device__ void add_dim(const uint64_t *r) {
+    const uint32_t p = wlow<W>(r);
+    uint64_t z[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) z[w] = ((int)(p >> 6) == w) ? (1ull << (p & 63u)) : 0ull;
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k)
+      if (row_bit(kRowB + k, p)) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) z[w] ^= row(kRowD + k, w);
+      }
+    put_row(kRowB + d, r);
+    put_row(kRowD + d, z);
+    ++d;
+  }
+  // The duals of the current basis, built one vector at a time (the same construction as
+  // add_dim, on each vector's residual against the ones before it).
+  __device__ void rebuild_duals() {
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k) {
+      uint64_t r[W];
+      get_row(kRowB + k, r);
+      uint32_t cm = 0;  // Dual[j] . B[k] for j < k
+#pragma unroll 1
+      for (uint32_t j = 0; j < k; ++j)
+        if (row_par(kRowD + j, r)) cm |= 1u << j;
+#pragma unroll 1
+      for (uint32_t j = 0; j < k; ++j)
+        if ((cm >> j) & 1u) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) r[w] ^= row(kRowB + j, w);
+        }
+      const uint32_t p = wlow<W>(r);
+      uint64_t z[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) z[w] = ((int)(p >> 6) == w) ? (1ull << (p & 63u)) : 0ull;
+#pragma unroll 1
+      for (uint32_t j = 0; j < k; ++j)
+        if (row_bit(kRowB + j, p)) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) z[w] ^= row(kRowD + j, w);
+        }
+#pragma unroll 1
+      for (uint32_t j = 0; j < k; ++j)
+        if ((cm >> j) & 1u) xor_row(kRowD + j, z);
+      put_row(kRowD + k, z);
+    }
+  }
+  // Every live slot s has parity(s & g) = t, and g has bit q set (q < d): bit q of a live
+  // slot follows from the others, so the map needs one coordinate less. alpha0 ^= t B[q],
+  // B[k] ^= B[q] for the other k of g; B[q] and Dual[q] go (the other duals stay dual);
+  // each live slot drops bit q of its index.
+  __device__ void remove_dim(uint32_t q, uint32_t g, uint32_t t) {
+    uint64_t bq[W];
+    get_row(kRowB + q, bq);
+    if (t) xor_row(0, bq);
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k)
+      if (k != q && ((g >> k) & 1u)) xor_row(kRowB + k, bq);
+#pragma unroll 1
+    for (uint32_t k = q; k + 1u < d; ++k) {
+      uint64_t x[W];
+      get_row(kRowB + k + 1u, x);
+      put_row(kRowB + k, x);
+      get_row(kRowD + k + 1u, x);
+      put_row(kRowD + k, x);
+    }
+    const uint32_t lo = (1u << q) - 1u;
+    uint32_t nl = 0;
+#pragma unroll 1
+    for (uint32_t m = live; m; m &= m - 1u) {  // ascending: a slot moves down onto a vacated one
+      const uint32_t s = __ffs(m) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
+      if (s2 != s) {
+        set_val(s2, val(s));
+        set_val(s, Cx<R>{0, 0});
+      }
+      nl |= 1u << s2;
+    }
+    live = nl;
+    --d;
+  }
+  // after a measurement: all live slots share parity(s & g); drop a coordinate if g != 0
+  __device__ __forceinline__ void restrict_to(uint32_t g) {
+    g &= (d >= 32u) ? 0xFFFFFFFFu : ((1u << d) - 1u);
+    if (!g || !live) return;
+    const uint32_t t = spar(__ffs(live) - 1, g);
+    remove_dim(31u - __clz(g), g, t);
+  }
+  // drop the coordinates no live slot uses
+  __device__ void compact_dead() {
+#pragma unroll 1
+    for (uint32_t k = d; k-- > 0;)
+      if (!(live & slot_bit_mask(k))) remove_dim(k, 1u << k, 0);
+  }
+  // key of slot s
+  __device__ Key<W> key_of(uint32_t s) const {
     Key<W> k;
 #pragma unroll
-    for (int w = 0; w < W; ++w) k.w[w] = keys[((size_t)i * W + w) * 32 + lane];
+    for (int w = 0; w < W; ++w) k.w[w] = row(0, w);
+#pragma unroll 1
+    for (uint32_t j = 0; j < d; ++j)
+      if ((s >> j) & 1u) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) k.w[w] ^= row(kRowB + j, w);
+      }
     return k;
   }
-  __device__ __forceinline__ void set_key(uint32_t i, const Key<W> &k) {
+  // The map from explicit entries (a spill record): alpha0 = the first key, each further
+  // key's residual a new direction. False if it needs more than kDim directions.
+  template <typename KeyAt, typename ValAt>
+  __device__ bool load_entries(uint32_t n, KeyAt key_at, ValAt val_at) {
+#pragma unroll 1
+    for (uint32_t s = 0; s < Cap; ++s) set_val(s, Cx<R>{0, 0});
+    d = 0;
+    live = 0;
+    if (n == 0) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) keys[((size_t)i * W + w) * 32 + lane] = k.w[w];
-  }
-  __device__ __forceinline__ Cx<R> val(uint32_t i) const { return vals[(size_t)i * 32 + lane]; }
-  __device__ __forceinline__ void set_val(uint32_t i, Cx<R> v) { vals[(size_t)i * 32 + lane] = v; }
-  // Partners (a, a ^ x) differ in bit `bit`, set in x. Each entry with the bit clear
-  // looks for its partner among the entries with it set (mask `him`). Out: `paired`,
-  // the entries with the bit set that have a partner; `has`, those with it clear that
-  // have one; part, the partner's index.
-  __device__ void partners(uint32_t n0, uint32_t bit, const uint64_t *x, uint32_t &paired, uint32_t &has,
-                           PartIdx<Cap> &part) const {
-    uint32_t him = 0;
-#pragma unroll 1
-    for (uint32_t i = 0; i < n0; ++i) him |= kbit(key(i), bit) << i;
-    paired = has = 0;
-    part = PartIdx<Cap>{};
-    const uint32_t all = n0 >= 32u ? 0xFFFFFFFFu : (1u << n0) - 1u;
-#pragma unroll 1
-    for (uint32_t lo = ~him & all; lo; lo &= lo - 1u) {
-      const uint32_t i = __ffs(lo) - 1;
-      const Key<W> pk = kxor(key(i), x);
-#pragma unroll 1
-      for (uint32_t m = him & ~paired; m; m &= m - 1u) {
-        const uint32_t j = __ffs(m) - 1;
-        if (keq(key(j), pk)) {
-          paired |= 1u << j;
-          has |= 1u << i;
-          part.set(i, j);
-          break;
-        }
-      }
+      for (int w = 0; w < W; ++w) set_row(0, w, 0ull);
+      return true;
     }
+    const Key<W> k0 = key_at(0);
+    put_row(0, k0.w);
+#pragma unroll 1
+    for (uint32_t i = 0; i < n; ++i) {
+      const Key<W> k = key_at(i);
+      const Key<W> x = kxor(k, k0.w);
+      uint64_t r[W];
+      uint32_t c = coords(x.w, r);
+      if (wnonzero<W>(r)) {
+        if (d == kDim) return false;
+        add_dim(r);
+        c |= 1u << (d - 1u);
+      }
+      set_val(c, val_at(i));
+      live |= 1u << c;
+    }
+    return true;
   }
-  // The map would outgrow the lane before pruning. Overflow is decided after pruning
-  // (|v| > the circuit's cap), so the warp pass at the circuit's cap, which stages the
-  // whole update before it prunes, reruns the shot (every lane run has that pass).
+
   __device__ void fail_capacity() { status = P.small_pass ? LS_RERUN : LS_OVF; }
   __device__ void fail_check(uint32_t code, uint64_t value) {
     status = LS_ERR;
@@ -161,36 +341,6 @@ struct LaneShot {
       P.diag[2] = shot;
       P.diag[3] = value;
     }
-  }
-  // |v|^2 < tau, the pruning test, decided exactly as the norm computed in R decides it.
-  // FP64: when both |re| and |im| lie below sqrt(tau/2) (1 - 2^-18), or either lies above
-  // sqrt(tau) (1 + 2^-18), integer compares of their high words settle it (the computed
-  // norm's rounding cannot cross tau there); only values in that narrow band compute
-  // the norm on the FP64 pipe, GB300's narrowest.
-  __device__ __forceinline__ bool is_small(Cx<R> v, R tau) const {
-    if (sizeof(R) == 4) return norm2(v) < tau;
-    const uint32_t hx = (uint32_t)((unsigned long long)__double_as_longlong((double)v.x) >> 32) & 0x7FFFFFFFu;
-    const uint32_t hy = (uint32_t)((unsigned long long)__double_as_longlong((double)v.y) >> 32) & 0x7FFFFFFFu;
-    if (hx > hs_hi || hy > hs_hi) return false;
-    if (hx < hs_lo && hy < hs_lo) return true;
-    return norm2(v) < tau;
-  }
-  // keep the entries with |v|^2 >= tau, in order
-  __device__ void prune() {
-    const R tau = (R)P.tau;
-    uint32_t o = 0;
-#pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      const Cx<R> v = val(i);
-      if (!is_small(v, tau)) {
-        if (o != i) {
-          set_key(o, key(i));
-          set_val(o, v);
-        }
-        ++o;
-      }
-    }
-    n = o;
   }
 
   __device__ double uniform(uint32_t ord) const {
@@ -218,8 +368,9 @@ struct LaneShot {
     return (R)rsqrt(x);
   }
 
-  // ---- start: shot s at event e of the noiseless run
-  // (the pre-pass drew the shot's first error: its noise cursor comes with the item)
+  // ---- start: shot s at event e of the noiseless run (its map in affine form, computed
+  // once per snapshot when the circuit was compiled); the pre-pass drew the shot's first
+  // error: its noise cursor comes with the item
   __device__ void begin(uint64_t s, uint32_t e, uint4 cursor) {
     shot = s;
     status = LS_RUN;
@@ -235,9 +386,7 @@ struct LaneShot {
     const unsigned char *in = C->traj + (size_t)e * C->traj_stride;
     const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);
     const uint64_t *r_in = reinterpret_cast<const uint64_t *>(in + sizeof(SnapHdr));
-    const uint64_t *k_in = r_in + C->rw;
-    const Cx<R> *v_in = reinterpret_cast<const Cx<R> *>(k_in + kSnapMax * W);
-    n = __ldg(&h->nnz);
+    const SnapAffine<R, W> *a = reinterpret_cast<const SnapAffine<R, W> *>(in + snap_affine_off<R, W>(C->rw));
     chain = (int)__ldg(&h->chain);
     logical = (int)__ldg(&h->logical);
     lastm = (int)__ldg(&h->lastm);
@@ -249,25 +398,34 @@ struct LaneShot {
     }
 #pragma unroll 1
     for (uint32_t w = 0; w < C->rw; ++w) rec[(size_t)w * 32 + lane] = __ldg(&r_in[w]);
-    if (n > Cap) {
+    const uint2 dl = __ldg(reinterpret_cast<const uint2 *>(&a->d));
+    d = 0;
+    live = 0;
+    if (dl.x > kDim) {
       fail_capacity();
       return;
     }
-#pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      Key<W> k;
+    d = dl.x;
+    live = dl.y;
 #pragma unroll
-      for (int w = 0; w < W; ++w) k.w[w] = __ldg(&k_in[i * W + w]);
-      set_key(i, k);
-      set_val(i, v_in[i]);
-    }
+    for (int w = 0; w < W; ++w) set_row(0, w, __ldg(&a->rows[0][w]));
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k)
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        set_row(kRowB + k, w, __ldg(&a->rows[1 + k][w]));
+        set_row(kRowD + k, w, __ldg(&a->rows[1 + kSnapDim + k][w]));
+      }
+#pragma unroll 1
+    for (uint32_t j = 0; j < Cap; ++j) set_val(j, ((live >> j) & 1u) ? a->v[j] : Cx<R>{0, 0});
   }
 
-  // ---- eviction: the shot's whole state into record r, to resume at event ev
+  // ---- eviction: the shot's whole state into record r, to resume at event ev (entries
+  // in slot order, at most kLaneCap of them: a first-round lane holds no more)
   __device__ void evict(const Spill<R, W> &S, uint32_t r, uint32_t item, uint32_t ev) const {
     const size_t c = S.cap;
-    S.ha[r] = make_uint4(item, ev, n, (uint32_t)(chain & 1) | ((uint32_t)(logical & 1) << 1) |
-                                          (((uint32_t)lastm & 255u) << 8));
+    S.ha[r] = make_uint4(item, ev, nnz(), (uint32_t)(chain & 1) | ((uint32_t)(logical & 1) << 1) |
+                                              (((uint32_t)lastm & 255u) << 8));
     S.hb[r] = make_uint4(nxt, cur, kblk, w2);
     S.fid[r] = fid;
 #pragma unroll
@@ -277,12 +435,14 @@ struct LaneShot {
     }
 #pragma unroll 1
     for (uint32_t w = 0; w < C->rw; ++w) S.rec[w * c + r] = rec[(size_t)w * 32 + lane];
+    uint32_t i = 0;
 #pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      const Key<W> k = key(i);
+    for (uint32_t m = live; m && i < kLaneCap; m &= m - 1u, ++i) {
+      const uint32_t s = __ffs(m) - 1;
+      const Key<W> k = key_of(s);
 #pragma unroll
       for (int w = 0; w < W; ++w) S.keys[((size_t)i * W + w) * c + r] = k.w[w];
-      S.vals[(size_t)i * c + r] = val(i);
+      S.vals[(size_t)i * c + r] = val(s);
     }
   }
   // ---- resumption from record r; returns the shot's item (chunk-local index)
@@ -292,7 +452,7 @@ struct LaneShot {
     shot = first + a.x;
     status = LS_RUN;
     force = false;
-    n = a.z;
+    const uint32_t n = a.z;
     chain = (int)(a.w & 1u);
     logical = (int)((a.w >> 1) & 1u);
     lastm = (int)(int8_t)((a.w >> 8) & 255u);
@@ -308,33 +468,37 @@ struct LaneShot {
     }
 #pragma unroll 1
     for (uint32_t w = 0; w < C->rw; ++w) rec[(size_t)w * 32 + lane] = S.rec[w * c + r];
+    d = 0;
+    live = 0;
     if (n > kLaneCap) {  // a record never holds more; checked so that a bad record cannot index past the map
       fail_check(CHK_NNZ, n);
-      n = 0;
       return a.x;
     }
-#pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      Key<W> k;
+    const bool ok = load_entries(
+        n,
+        [&](uint32_t i) {
+          Key<W> k;
 #pragma unroll
-      for (int w = 0; w < W; ++w) k.w[w] = S.keys[((size_t)i * W + w) * c + r];
-      set_key(i, k);
-      set_val(i, S.vals[(size_t)i * c + r]);
-    }
+          for (int w = 0; w < W; ++w) k.w[w] = S.keys[((size_t)i * W + w) * c + r];
+          return k;
+        },
+        [&](uint32_t i) { return S.vals[(size_t)i * c + r]; });
+    if (!ok) fail_capacity();  // (records come from lanes of at most kDim directions)
     return a.x;
   }
-
   // ---- the shot's final state (signs, keys, values) for state capture at offset off
   __device__ void capture(uint64_t off) const {
-    P.st_nnz[off] = n;
+    P.st_nnz[off] = nnz();
     P.st_signs[off * 4 + 0] = sd[0];
     P.st_signs[off * 4 + 1] = (W == 2) ? sd[W - 1] : 0ull;
     P.st_signs[off * 4 + 2] = ss[0];
     P.st_signs[off * 4 + 3] = (W == 2) ? ss[W - 1] : 0ull;
+    uint32_t i = 0;
 #pragma unroll 1
-    for (uint32_t i = 0; i < n && i < P.st_stride; ++i) {
-      const Key<W> k = key(i);
-      const Cx<R> v = val(i);
+    for (uint32_t m = live; m && i < P.st_stride; m &= m - 1u, ++i) {
+      const uint32_t s = __ffs(m) - 1;
+      const Key<W> k = key_of(s);
+      const Cx<R> v = val(s);
       const size_t o = (size_t)off * P.st_stride + i;
       P.st_keys[2 * o] = k.w[0];
       P.st_keys[2 * o + 1] = (W == 2) ? k.w[W - 1] : 0ull;
@@ -343,14 +507,16 @@ struct LaneShot {
     }
   }
 
-  // ---- Paulis: v'_{a^beta} = i^{e + 2 gamma.a} v_a
+  // ---- Paulis: v'_{a^beta} = i^{e + 2 gamma.a} v_a: phases per entry, then alpha0 moves
   __device__ void apply_pauli(const uint64_t *beta, const uint64_t *gamma, uint32_t e) {
+    uint32_t g0;
+    const uint32_t gl = parities(gamma, g0);
 #pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      const Key<W> k = key(i);
-      set_val(i, ipow(val(i), e + 2u * kpar(k, gamma)));
-      set_key(i, kxor(k, beta));
+    for (uint32_t m = live; m; m &= m - 1u) {
+      const uint32_t s = __ffs(m) - 1;
+      set_val(s, ipow(val(s), e + 2u * (g0 ^ spar(s, gl))));
     }
+    xor_row(0, beta);
   }
   __device__ void apply_error(uint32_t s) {
     if (s >= C->n_sites) {
@@ -389,7 +555,9 @@ struct LaneShot {
     apply_pauli(beta, gamma, ((__ldg(&S->c0) >> (2u * code)) + 2u * pe) & 3u);
   }
 
-  // ---- a I + b Z_q: paired entries (a, a^beta) mix, an unpaired entry gains its partner
+  // ---- a I + b Z_q: v'_a = a v_a + b xi_{a^beta} v_{a^beta}; xi = i^e (-1)^{gamma.key}
+  // folded into b (b or -b per entry, exact), and a diagonal rotation (beta = 0) is one
+  // product (a + b xi) v per entry
   __device__ void rot(uint32_t w0, uint32_t ci, const uint64_t *beta, const uint64_t *gamma, bool diag) {
     uint32_t pe = 0;
 #pragma unroll
@@ -411,67 +579,70 @@ struct LaneShot {
       a = Cx<R>{(R)d0.x, (R)d0.y};
       b = Cx<R>{(R)d1.x, (R)d1.y};
     }
-    const R tau = (R)P.tau;
-    bool small = false;
-    // the phase xi = i^e (-1)^{gamma.key} folded into b once per event: b_s = (-1)^s b i^e
-    // (exact: a multiplication by i^e swaps and negates), so that an entry only selects one
     const Cx<R> bq = ipow(b, e), bn = Cx<R>{negr(bq.x), negr(bq.y)};
+    uint32_t drop = 0;
     if (diag) {
-      // v' = (a + b xi) v: one complex product per entry
+      uint32_t g0;
+      const uint32_t gl = parities(gamma, g0);
       const Cx<R> c0 = cadd(a, bq), c1 = cadd(a, bn);
 #pragma unroll 1
-      for (uint32_t i = 0; i < n; ++i) {
-        const Cx<R> nv = cmul(kpar(key(i), gamma) ? c1 : c0, val(i));
-        set_val(i, nv);
-        small = small || is_small(nv, tau);
+      for (uint32_t m = live; m; m &= m - 1u) {
+        const uint32_t s = __ffs(m) - 1;
+        const Cx<R> nv = cmul((g0 ^ spar(s, gl)) ? c1 : c0, val(s));
+        const bool sm = pt.small(nv);
+        set_val(s, sm ? Cx<R>{0, 0} : nv);
+        drop |= (uint32_t)sm << s;
       }
-      if (small) prune();
+      live &= ~drop;
       return;
     }
-    const uint32_t n0 = n;
-    uint32_t paired, has;
-    PartIdx<Cap> part;
-    partners(n0, ev_lowbit(w0), beta, paired, has, part);
-    // every entry without a partner gains one: if that outgrows the lane, nothing has
-    // been written yet, and the shot can be taken over at the top of this event (by the
-    // wide round's lanes, or a warp); otherwise (the wide round) it reruns in a warp
-    if (n0 + (n0 - 2u * (uint32_t)__popc(has)) > Cap) {
-      if (P.lane_hand && P.sp && P.small_pass && C->cap > Cap) status = LS_HAND;
-      else fail_capacity();
-      return;
+    uint64_t r[W];
+    uint32_t c = coords(beta, r);
+    const bool fresh = wnonzero<W>(r);  // beta outside the span: every entry gains a partner
+    if (fresh && d == kDim) {
+      compact_dead();
+      if (d == kDim) {
+        // the map would outgrow the lane: nothing has been written yet, so the shot can be
+        // taken over at the top of this event (by the wide round's lanes, or a warp);
+        // otherwise (the wide round) it reruns in a warp
+        if (P.lane_hand && P.sp && P.small_pass && C->cap > Cap) status = LS_HAND;
+        else fail_capacity();
+        return;
+      }
+      c = coords(beta, r);
     }
-    uint32_t na = 0;
+    if (fresh) {
+      add_dim(r);
+      c |= 1u << (d - 1u);
+    }
+    uint32_t g0;
+    const uint32_t gl = parities(gamma, g0);
+    const uint32_t spread = live | slot_xor_perm(live, c);
+    const uint32_t lead = spread & ~slot_bit_mask(__ffs(c) - 1) & cube();  // one member of each pair
 #pragma unroll 1
-    for (uint32_t i = 0; i < n0; ++i) {
-      if ((paired >> i) & 1u) continue;  // the pair's member with bit lowbit clear updates both
-      const Key<W> k = key(i);
-      const Key<W> pk = kxor(k, beta);
-      const Cx<R> v = val(i);
-      if ((has >> i) & 1u) {
-        const uint32_t j = part.get(i);
-        const Cx<R> vj = val(j);
-        const Cx<R> ni = cadd(cmul(a, v), cmul(kpar(pk, gamma) ? bn : bq, vj));
-        const Cx<R> nj = cadd(cmul(a, vj), cmul(kpar(k, gamma) ? bn : bq, v));
-        set_val(i, ni);
-        set_val((uint32_t)j, nj);
-        small = small || is_small(ni, tau) || is_small(nj, tau);
+    for (uint32_t m = lead; m; m &= m - 1u) {
+      const uint32_t s = __ffs(m) - 1, t = s ^ c;
+      const uint32_t ls = (live >> s) & 1u, lt = (live >> t) & 1u;
+      const Cx<R> vs = val(s), vt = val(t);
+      const Cx<R> bs = (g0 ^ spar(s, gl)) ? bn : bq, bt = (g0 ^ spar(t, gl)) ? bn : bq;
+      Cx<R> ns, nt;
+      if (ls && lt) {
+        ns = cadd(cmul(a, vs), cmul(bt, vt));
+        nt = cadd(cmul(a, vt), cmul(bs, vs));
+      } else if (ls) {  // an entry without a partner gains one
+        ns = cmul(a, vs);
+        nt = cmul(bs, vs);
       } else {
-        const Cx<R> ni = cmul(a, v);
-        const Cx<R> av = cmul(kpar(k, gamma) ? bn : bq, v);
-        set_val(i, ni);
-        if (n0 + na >= Cap) {
-          fail_capacity();
-          return;
-        }
-        set_key(n0 + na, pk);
-        set_val(n0 + na, av);
-        ++na;
-        small = small || is_small(ni, tau) || is_small(av, tau);
+        ns = cmul(bt, vt);
+        nt = cmul(a, vt);
       }
+      const bool ss_ = pt.small(ns), st_ = pt.small(nt);
+      set_val(s, ss_ ? Cx<R>{0, 0} : ns);
+      set_val(t, st_ ? Cx<R>{0, 0} : nt);
+      drop |= ((uint32_t)ss_ << s) | ((uint32_t)st_ << t);
     }
-    n = n0 + na;
-    if (small) prune();
-    if (n > C->cap) status = LS_OVF;  // the overflow rule, for circuits whose cap is below the lane's
+    live = spread & ~drop;
+    if (nnz() > C->cap) status = LS_OVF;  // the overflow rule, for circuits whose cap is below the lane's
   }
 
   // ---- measurement of P, beta = 0: lambda_a = c (-1)^{gamma.a}
@@ -485,55 +656,41 @@ struct LaneShot {
       return 1;
     }
     const uint32_t sgn = e >> 1;
-    bool h0 = false, h1 = false;
-#pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      if (kpar(key(i), gamma) ^ sgn) h1 = true;
-      else h0 = true;
+    uint32_t g0;
+    const uint32_t gl = parities(gamma, g0);
+    const uint32_t pm = slot_par_mask(gl) & cube();
+    const uint32_t neg = live & (((sgn ^ g0) & 1u) ? ~pm : pm);  // slots with eigenvalue -1
+    const uint32_t pos = live & ~neg;
+    if (!neg || !pos) {  // decided (all eigenvalues equal): integer test only
+      restrict_to(gl);
+      return neg ? -1 : 1;
     }
-    if (!(h0 && h1)) return h1 ? -1 : 1;
     double sp = 0.0, sm = 0.0;
 #pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      const double a2 = norm2d(val(i));
-      if (kpar(key(i), gamma) ^ sgn) sm += a2;
+    for (uint32_t m = live; m; m &= m - 1u) {
+      const uint32_t s = __ffs(m) - 1;
+      const double a2 = norm2d(val(s));
+      if ((neg >> s) & 1u) sm += a2;
       else sp += a2;
     }
     const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt(m == 1 ? sp : sm);
-    const uint32_t want = (m == 1) ? 0u : 1u;
-    const R tau = (R)P.tau;
-    uint32_t o = 0;
+    const uint32_t keep = (m == 1) ? pos : neg;
+    uint32_t nl = 0;
 #pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      const Key<W> k = key(i);
-      if ((kpar(k, gamma) ^ sgn) != want) continue;
-      const Cx<R> v = cscale(val(i), sc);
-      if (is_small(v, tau)) continue;
-      set_key(o, k);
-      set_val(o, v);
-      ++o;
+    for (uint32_t mm = live; mm; mm &= mm - 1u) {
+      const uint32_t s = __ffs(mm) - 1;
+      Cx<R> v{0, 0};
+      if ((keep >> s) & 1u) {
+        v = cscale(val(s), sc);
+        if (pt.small(v)) v = Cx<R>{0, 0};
+        else nl |= 1u << s;
+      }
+      set_val(s, v);
     }
-    n = o;
+    live = nl;
+    restrict_to(gl);
     return m;
-  }
-
-  // Entry i's pair after the relabel (entry i is not a paired a1): a0, v0 = v_{a0} and
-  // x1 = xi_{a1} v_{a1} (zero when absent); j, the a1 partner that i consumes (-1 if none).
-  __device__ void pair_at(uint32_t i, uint32_t p, const uint64_t *ep, const uint64_t *g2, uint32_t e2, uint32_t has,
-                          const PartIdx<Cap> &part, Key<W> &a0, Cx<R> &v0, Cx<R> &x1, int &j) const {
-    const Key<W> k = key(i);
-    const bool hi = kbit(k, p);
-    j = ((has >> i) & 1u) ? (int)part.get(i) : -1;
-    Cx<R> v1{0, 0};
-    v0 = Cx<R>{0, 0};
-    if (hi) v1 = val(i);
-    else {
-      v0 = val(i);
-      if (j >= 0) v1 = val((uint32_t)j);
-    }
-    a0 = hi ? kxor(k, ep) : k;
-    x1 = ipow(v1, e2 + 2u * kpar(kxor(a0, ep), g2));
   }
 
   // ---- measurement of P, beta != 0 (case B): row operations on the signs, relabel,
@@ -558,46 +715,80 @@ struct LaneShot {
     for (int w = 0; w < W; ++w) ss[w] ^= (ssp ? J[w] : 0ull) ^ __ldg(&B->Hs[w]);
     if (sdJ ^ __ldg(&B->hdp)) wflip<W>(sd, p);
     const uint32_t e2 = (__ldg(&B->e0b) + 2u * (wbit<W>(sd, p) + wpar<W>(ss, g2))) & 3u;
-    // relabel a_j ^= a_p (j in J)
+    // relabel a_j ^= a_p (j in J), a linear map L of the keys: alpha0 and every B[k] go
+    // through it, and the duals through its transpose (D ^= (D . J) e_p; L is its own inverse)
 #pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      const Key<W> k = key(i);
-      if (kbit(k, p)) set_key(i, kxor(k, J));
+    for (uint32_t k = 0; k <= d; ++k) {
+      const uint32_t rr = k == 0 ? 0u : kRowB + k - 1u;
+      if (row_bit(rr, p)) xor_row(rr, J);
     }
-    // pair a0 (bit p clear) with a1 = a0 ^ e_p: first the outcome probabilities, then
-    // the combined values (v0 + m x1) / sqrt(2 p_m)
-    uint32_t paired, has;
-    PartIdx<Cap> part;
-    partners(n, p, ep, paired, has, part);
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k)
+      if (row_par(kRowD + k, J)) xor_row(kRowD + k, ep);
+    // pair a0 (key bit p clear) with a1 = a0 ^ e_p: first the outcome probabilities, then
+    // the combined values (v0 + m x1) / sqrt(2 p_m), x1 = xi_{a1} v_{a1}
+    uint32_t g20;
+    const uint32_t gl2 = parities(g2, g20);
+    uint32_t bp = 0;  // bit k: B[k][p]
+#pragma unroll 1
+    for (uint32_t k = 0; k < d; ++k) bp |= row_bit(kRowB + k, p) << k;
+    const uint32_t cb = cube();
+    const uint32_t kb = (row_bit(0, p) ? ~slot_par_mask(bp) : slot_par_mask(bp)) & cb;  // slots whose key has bit p
+    uint64_t rr[W];
+    const uint32_t c = coords(ep, rr);
+    const bool lone = wnonzero<W>(rr);  // e_p outside the span: no entry has a partner
+    const uint32_t spread = lone ? live : (live | slot_xor_perm(live, c));
+    const uint32_t lead = lone ? live : (spread & ~kb);  // a0 members (lone: every entry)
     double sp = 0.0, sm = 0.0;
 #pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      if ((paired >> i) & 1u) continue;  // a paired a1 only feeds its a0's pair
-      Key<W> a0;
-      Cx<R> v0, x1;
-      int j;
-      pair_at(i, p, ep, g2, e2, has, part, a0, v0, x1, j);
+    for (uint32_t m = lead; m; m &= m - 1u) {
+      const uint32_t s = __ffs(m) - 1;
+      Cx<R> v0{0, 0}, x1{0, 0};
+      if (lone) {
+        if ((kb >> s) & 1u) x1 = ipow(val(s), e2 + 2u * (g20 ^ spar(s, gl2)));
+        else v0 = val(s);
+      } else {
+        const uint32_t t = s ^ c;
+        v0 = val(s);
+        x1 = ipow(val(t), e2 + 2u * (g20 ^ spar(t, gl2)));
+      }
       sp += 0.5 * norm2d(cadd(v0, x1));
       sm += 0.5 * norm2d(csub(v0, x1));
     }
     const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt(2.0 * (m == 1 ? sp : sm));
-    // In place: a pair's result goes to the slot of the entry that forms it (the a0
-    // member, or a lone a1), and the consumed a1 partner's value is zeroed (the partners
-    // were found before any write); the prune then drops the zeroed and the negligible
-    // entries, keeping slot order.
+    uint32_t nl = 0;
 #pragma unroll 1
-    for (uint32_t i = 0; i < n; ++i) {
-      if ((paired >> i) & 1u) continue;
-      Key<W> a0;
-      Cx<R> v0, x1;
-      int j;
-      pair_at(i, p, ep, g2, e2, has, part, a0, v0, x1, j);
-      set_key(i, a0);
-      set_val(i, cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc));
-      if (j >= 0) set_val((uint32_t)j, Cx<R>{0, 0});  // only an a0 entry has a partner here
+    for (uint32_t mm = lead; mm; mm &= mm - 1u) {
+      const uint32_t s = __ffs(mm) - 1;
+      Cx<R> v0{0, 0}, x1{0, 0};
+      if (lone) {
+        if ((kb >> s) & 1u) x1 = ipow(val(s), e2 + 2u * (g20 ^ spar(s, gl2)));
+        else v0 = val(s);
+      } else {
+        const uint32_t t = s ^ c;
+        v0 = val(s);
+        x1 = ipow(val(t), e2 + 2u * (g20 ^ spar(t, gl2)));
+        set_val(t, Cx<R>{0, 0});
+      }
+      Cx<R> nv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
+      if (pt.small(nv)) nv = Cx<R>{0, 0};
+      else nl |= 1u << s;
+      set_val(s, nv);
     }
-    prune();
+    live = nl;
+    if (lone) {
+      // every key loses bit p (a1 keys become a1 ^ e_p); injective on the space since e_p is
+      // not in the span, so the slots stay, and the basis is rebuilt with new duals
+#pragma unroll 1
+      for (uint32_t k = 0; k <= d; ++k) {
+        const uint32_t r2 = k == 0 ? 0u : kRowB + k - 1u;
+        if (row_bit(r2, p)) xor_row(r2, ep);
+      }
+      rebuild_duals();
+    } else {
+      restrict_to(bp);  // the kept keys have bit p clear: parity(s & bp) = alpha0[p]
+    }
     // replacement: d_j <- d_j s_p (j in G), d_p <- old s_p, s_p <- m P
 #pragma unroll
     for (int w = 0; w < W; ++w) sd[w] ^= (ssp ? __ldg(&B->G[w]) : 0ull) ^ __ldg(&B->Hd[w]);
@@ -697,6 +888,67 @@ struct LaneShot {
     (void)ev;
   }
 };
+
+// ---- the affine form (SnapAffine) of every valid snapshot of a noiseless run (events
+// [0, stop[0]]), one thread per snapshot, once per compiled circuit and precision; the
+// largest dimension goes to stop[3] (0xFF where a map needs more than kSnapDim)
+template <typename R, int W>
+__global__ void snap_affine_kernel(unsigned char *traj, uint32_t n_snap, uint32_t stride, uint32_t rw,
+                                   uint32_t *stop) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_snap || e > stop[0]) return;
+  unsigned char *in = traj + (size_t)e * stride;
+  const SnapHdr *h = reinterpret_cast<const SnapHdr *>(in);
+  const uint64_t *k_in = reinterpret_cast<const uint64_t *>(in + sizeof(SnapHdr)) + rw;
+  const Cx<R> *v_in = reinterpret_cast<const Cx<R> *>(k_in + kSnapMax * W);
+  SnapAffine<R, W> *out = reinterpret_cast<SnapAffine<R, W> *>(in + snap_affine_off<R, W>(rw));
+  const uint32_t n = h->nnz < kSnapMax ? h->nnz : kSnapMax;
+  constexpr uint32_t kB = 1, kD = 1 + kSnapDim;
+  uint64_t rw_[1 + 2 * kSnapDim][W];
+  for (uint32_t r = 0; r < 1 + 2 * kSnapDim; ++r)
+    for (int w = 0; w < W; ++w) rw_[r][w] = 0ull;
+  for (uint32_t j = 0; j < (1u << kSnapDim); ++j) out->v[j] = Cx<R>{0, 0};
+  uint32_t d = 0, live = 0;
+  bool ok = true;
+  if (n) {
+    for (int w = 0; w < W; ++w) rw_[0][w] = k_in[w];
+  }
+  for (uint32_t i = 0; i < n && ok; ++i) {
+    uint64_t x[W], r[W];
+    for (int w = 0; w < W; ++w) r[w] = x[w] = k_in[i * W + w] ^ rw_[0][w];
+    uint32_t c = 0;
+    for (uint32_t k = 0; k < d; ++k)
+      if (wpar<W>(rw_[kD + k], x)) {
+        c |= 1u << k;
+        for (int w = 0; w < W; ++w) r[w] ^= rw_[kB + k][w];
+      }
+    if (wnonzero<W>(r)) {
+      if (d == kSnapDim) {
+        ok = false;
+        break;
+      }
+      const uint32_t p = wlow<W>(r);  // the new direction's dual (as in LaneShot::add_dim)
+      uint64_t z[W];
+      for (int w = 0; w < W; ++w) z[w] = ((int)(p >> 6) == w) ? (1ull << (p & 63u)) : 0ull;
+      for (uint32_t k = 0; k < d; ++k)
+        if (wbit<W>(rw_[kB + k], p))
+          for (int w = 0; w < W; ++w) z[w] ^= rw_[kD + k][w];
+      for (int w = 0; w < W; ++w) {
+        rw_[kB + d][w] = r[w];
+        rw_[kD + d][w] = z[w];
+      }
+      c |= 1u << d;
+      ++d;
+    }
+    out->v[c] = v_in[i];
+    live |= 1u << c;
+  }
+  for (uint32_t r = 0; r < 1 + 2 * kSnapDim; ++r)
+    for (int w = 0; w < W; ++w) out->rows[r][w] = rw_[r][w];
+  out->d = ok ? d : 0xFFFFFFFFu;
+  out->live = live;
+  atomicMax(&stop[3], ok ? d : 0xFFu);
+}
 
 // ---- bucketing pre-pass. Buckets: per circuit of the run, one per event plus one
 // (shots that start past the end), circuit after circuit from circuit.bucket0.
@@ -1016,6 +1268,20 @@ size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw, bool wide) {
 }
 
 uint32_t lane_map_cap() { return kLaneCap; }
+uint32_t lane_map_dim() { return lane_dim(kLaneCap); }
+
+cudaError_t launch_snap_affine(unsigned char *traj, uint32_t n_snap, uint32_t rw, int fp32, uint32_t W,
+                               uint32_t *stop, cudaStream_t st) {
+  const unsigned grid = (n_snap + 127) / 128;
+  if (fp32) {
+    if (W == 1) snap_affine_kernel<float, 1><<<grid, 128, 0, st>>>(traj, n_snap, (uint32_t)snap_stride<float, 1>(rw), rw, stop);
+    else snap_affine_kernel<float, 2><<<grid, 128, 0, st>>>(traj, n_snap, (uint32_t)snap_stride<float, 2>(rw), rw, stop);
+  } else {
+    if (W == 1) snap_affine_kernel<double, 1><<<grid, 128, 0, st>>>(traj, n_snap, (uint32_t)snap_stride<double, 1>(rw), rw, stop);
+    else snap_affine_kernel<double, 2><<<grid, 128, 0, st>>>(traj, n_snap, (uint32_t)snap_stride<double, 2>(rw), rw, stop);
+  }
+  return cudaGetLastError();
+}
 uint32_t lane_rounds() { return kLaneRounds; }
 uint32_t lane_max_buckets() { return kLaneMaxBuckets; }
 uint32_t lane_prepass_grid() {

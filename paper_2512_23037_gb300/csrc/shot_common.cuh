@@ -79,10 +79,26 @@ struct SnapHdr {
   uint64_t pad[2];
 };
 constexpr uint32_t kSnapMax = 64;
+
+// The snapshot's map in the affine form of the lane kernels (lanes.cu): d directions
+// (0xFFFFFFFF: more than kSnapDim), the live slots, rows alpha0, B[0..kSnapDim),
+// Dual[0..kSnapDim), and the values of 2^kSnapDim slots (zero where not live). Computed
+// once per circuit and precision, after the noiseless run.
+constexpr uint32_t kSnapDim = 5;
 template <typename R, int W>
-__host__ __device__ constexpr size_t snap_stride(uint32_t rw) {
+struct SnapAffine {
+  uint32_t d, live;
+  uint64_t rows[1 + 2 * kSnapDim][W];
+  Cx<R> v[1u << kSnapDim];
+};
+template <typename R, int W>
+__host__ __device__ constexpr size_t snap_affine_off(uint32_t rw) {
   return (sizeof(SnapHdr) + (size_t)rw * 8 + kSnapMax * (size_t)W * 8 + kSnapMax * sizeof(Cx<R>) + 15) &
          ~(size_t)15;
+}
+template <typename R, int W>
+__host__ __device__ constexpr size_t snap_stride(uint32_t rw) {
+  return (snap_affine_off<R, W>(rw) + sizeof(SnapAffine<R, W>) + 15) & ~(size_t)15;
 }
 
 #ifndef SOFT_LANE_CAP
