@@ -57,8 +57,8 @@ constexpr uint32_t kWideCap = 2 * kLaneCap;
 // grows by one direction per rotation whose beta is new, Theorem 1 (3), and shrinks
 // with measurements and cancellations). Slot s (s < 2^d) holds the entry of key
 //   key(s) = alpha0 ^ XOR over the set bits k of s of B[k],
-// with its value in row s of the lane's value column: exactly zero where no entry
-// lives, and `live` marks the slots that hold entries. Dual[k] (Dual[k] . B[j] = 1 iff
+// with its value in row s of the lane's value column, and `live` marks the slots that
+// hold entries (values elsewhere are never read). Dual[k] (Dual[k] . B[j] = 1 iff
 // k = j, over GF(2)) gives the coordinates of a vector x of the span: x = XOR over
 // the k with Dual[k] . x = 1 of B[k]. So the partner key(s) ^ beta of a rotation is
 // slot s ^ c (c: beta's coordinates), a parity gamma . key(s) is g0 ^ parity(s & gl)
@@ -266,10 +266,7 @@ struct LaneShot {
 #pragma unroll 1
     for (uint32_t m = live; m; m &= m - 1u) {  // ascending: a slot moves down onto a vacated one
       const uint32_t s = __ffs(m) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
-      if (s2 != s) {
-        set_val(s2, val(s));
-        set_val(s, Cx<R>{0, 0});
-      }
+      if (s2 != s) set_val(s2, val(s));
       nl |= 1u << s2;
     }
     live = nl;
@@ -305,8 +302,6 @@ struct LaneShot {
   // key's residual a new direction. False if it needs more than kDim directions.
   template <typename KeyAt, typename ValAt>
   __device__ bool load_entries(uint32_t n, KeyAt key_at, ValAt val_at) {
-#pragma unroll 1
-    for (uint32_t s = 0; s < Cap; ++s) set_val(s, Cx<R>{0, 0});
     d = 0;
     live = 0;
     if (n == 0) {
@@ -417,7 +412,10 @@ struct LaneShot {
         set_row(kRowD + k, w, __ldg(&a->rows[1 + kSnapDim + k][w]));
       }
 #pragma unroll 1
-    for (uint32_t j = 0; j < Cap; ++j) set_val(j, ((live >> j) & 1u) ? a->v[j] : Cx<R>{0, 0});
+    for (uint32_t m = live; m; m &= m - 1u) {
+      const uint32_t j = __ffs(m) - 1;
+      set_val(j, a->v[j]);
+    }
   }
 
   // ---- eviction: the shot's whole state into record r, to resume at event ev (entries
@@ -590,7 +588,7 @@ struct LaneShot {
         const uint32_t s = __ffs(m) - 1;
         const Cx<R> nv = cmul((g0 ^ spar(s, gl)) ? c1 : c0, val(s));
         const bool sm = pt.small(nv);
-        set_val(s, sm ? Cx<R>{0, 0} : nv);
+        if (!sm) set_val(s, nv);
         drop |= (uint32_t)sm << s;
       }
       live &= ~drop;
@@ -623,7 +621,7 @@ struct LaneShot {
     for (uint32_t m = lead; m; m &= m - 1u) {
       const uint32_t s = __ffs(m) - 1, t = s ^ c;
       const uint32_t ls = (live >> s) & 1u, lt = (live >> t) & 1u;
-      const Cx<R> vs = val(s), vt = val(t);
+      const Cx<R> vs = ls ? val(s) : Cx<R>{0, 0}, vt = lt ? val(t) : Cx<R>{0, 0};
       const Cx<R> bs = (g0 ^ spar(s, gl)) ? bn : bq, bt = (g0 ^ spar(t, gl)) ? bn : bq;
       Cx<R> ns, nt;
       if (ls && lt) {
@@ -637,8 +635,8 @@ struct LaneShot {
         nt = cmul(a, vt);
       }
       const bool ss_ = pt.small(ns), st_ = pt.small(nt);
-      set_val(s, ss_ ? Cx<R>{0, 0} : ns);
-      set_val(t, st_ ? Cx<R>{0, 0} : nt);
+      if (!ss_) set_val(s, ns);
+      if (!st_) set_val(t, nt);
       drop |= ((uint32_t)ss_ << s) | ((uint32_t)st_ << t);
     }
     live = spread & ~drop;
@@ -680,13 +678,13 @@ struct LaneShot {
 #pragma unroll 1
     for (uint32_t mm = live; mm; mm &= mm - 1u) {
       const uint32_t s = __ffs(mm) - 1;
-      Cx<R> v{0, 0};
       if ((keep >> s) & 1u) {
-        v = cscale(val(s), sc);
-        if (pt.small(v)) v = Cx<R>{0, 0};
-        else nl |= 1u << s;
+        const Cx<R> v = cscale(val(s), sc);
+        if (!pt.small(v)) {
+          set_val(s, v);
+          nl |= 1u << s;
+        }
       }
-      set_val(s, v);
     }
     live = nl;
     restrict_to(gl);
@@ -749,8 +747,8 @@ struct LaneShot {
         else v0 = val(s);
       } else {
         const uint32_t t = s ^ c;
-        v0 = val(s);
-        x1 = ipow(val(t), e2 + 2u * (g20 ^ spar(t, gl2)));
+        if ((live >> s) & 1u) v0 = val(s);
+        if ((live >> t) & 1u) x1 = ipow(val(t), e2 + 2u * (g20 ^ spar(t, gl2)));
       }
       sp += 0.5 * norm2d(cadd(v0, x1));
       sm += 0.5 * norm2d(csub(v0, x1));
@@ -767,14 +765,14 @@ struct LaneShot {
         else v0 = val(s);
       } else {
         const uint32_t t = s ^ c;
-        v0 = val(s);
-        x1 = ipow(val(t), e2 + 2u * (g20 ^ spar(t, gl2)));
-        set_val(t, Cx<R>{0, 0});
+        if ((live >> s) & 1u) v0 = val(s);
+        if ((live >> t) & 1u) x1 = ipow(val(t), e2 + 2u * (g20 ^ spar(t, gl2)));
       }
-      Cx<R> nv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
-      if (pt.small(nv)) nv = Cx<R>{0, 0};
-      else nl |= 1u << s;
-      set_val(s, nv);
+      const Cx<R> nv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
+      if (!pt.small(nv)) {
+        set_val(s, nv);
+        nl |= 1u << s;
+      }
     }
     live = nl;
     if (lone) {
@@ -1078,11 +1076,13 @@ __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_cons
   }
 }
 
-// Blocks per SM each variant's shared memory allows (w42: FP32 16-entry lanes 6, FP64 4,
-// the wide round's 32-entry lanes 3): the register budget is set not to lower it.
+// Register budget: resident blocks per SM the compiler must allow. FP32 16-slot lanes: 8
+// (64 registers; the shared memory allows 8 on w42; measured 617 M shots/s against 604 M
+// at 6 blocks and 76 registers), the wide round's 32-slot lanes 3 (shared memory allows
+// 3-4), FP64: 5 (its shared memory allows 5; 272.8 M against 266.7 M at 4).
 template <typename R, uint32_t Cap>
 constexpr int kLaneMinBlocks() {
-  return sizeof(R) == 4 ? (Cap <= 16 ? 6 : 3) : 4;
+  return sizeof(R) == 4 ? (Cap <= 16 ? 8 : 3) : 5;
 }
 
 // Multi: the run holds several circuits (a warp serves one at a time); the single-
@@ -1260,7 +1260,8 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
 size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw, bool wide) {
   size_t per;
   if (wide)
-    per = W == 1 ? lane_warp_bytes<float, 1, kWideCap>(rw) : lane_warp_bytes<float, 2, kWideCap>(rw);
+    per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1, kWideCap>(rw) : lane_warp_bytes<float, 2, kWideCap>(rw))
+               : (W == 1 ? lane_warp_bytes<double, 1, kWideCap>(rw) : lane_warp_bytes<double, 2, kWideCap>(rw));
   else
     per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1, kLaneCap>(rw) : lane_warp_bytes<float, 2, kLaneCap>(rw))
                : (W == 1 ? lane_warp_bytes<double, 1, kLaneCap>(rw) : lane_warp_bytes<double, 2, kLaneCap>(rw));
@@ -1323,10 +1324,12 @@ cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_
   const bool multi = p.n_circ > 1;
   constexpr uint32_t C1 = kLaneCap, C2 = kWideCap;
   const void *kern;
-  if (wide) {  // FP32 single-circuit runs only
-    if (!fp32 || multi) return cudaErrorInvalidConfiguration;
-    kern = W == 1 ? reinterpret_cast<const void *>(lane_kernel<float, 1, false, C2>)
-                  : reinterpret_cast<const void *>(lane_kernel<float, 2, false, C2>);
+  if (wide) {  // single-circuit runs only
+    if (multi) return cudaErrorInvalidConfiguration;
+    kern = fp32 ? (W == 1 ? reinterpret_cast<const void *>(lane_kernel<float, 1, false, C2>)
+                          : reinterpret_cast<const void *>(lane_kernel<float, 2, false, C2>))
+                : (W == 1 ? reinterpret_cast<const void *>(lane_kernel<double, 1, false, C2>)
+                          : reinterpret_cast<const void *>(lane_kernel<double, 2, false, C2>));
   } else
     kern = fp32 ? (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<float, 1, true, C1>)
                                    : reinterpret_cast<const void *>(lane_kernel<float, 1, false, C1>))
