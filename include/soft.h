@@ -176,7 +176,8 @@ typedef struct {
 /* Lane-per-shot scheduling (the default where it applies): one shot per lane,
  * 32 shots per warp. Shots are bucketed by the event they start at, and each
  * warp executes one event at a time for all its lanes, each lane updating its
- * own shot's map (up to 16 entries). A shot whose map outgrows its lane is
+ * own shot's map (up to 16 entries, whose keys a lane keeps as an affine space
+ * of at most 4 directions). A shot whose map outgrows its lane is
  * handed over at that event (its whole state in a spill record): to the wide
  * round's lanes (see below), or to a warp with a register map of up to
  * first_cap entries (default 64); shots beyond that rerun from their start at
@@ -185,17 +186,18 @@ typedef struct {
  * batch each circuit has its own buckets, and a warp serves one circuit at a
  * time. It applies to runs without a forced group size (state capture
  * included: a captured shot's state is written wherever it ends), to
- * the circuits whose noiseless run's maps fit a lane (at most 16 entries; the
+ * the circuits whose noiseless run's maps fit a lane (at most 16 entries in at
+ * most 4 directions; the
  * shots of a batch's other circuits go straight to the warp pass), when those
  * circuits hold at most 50 000 events (plus one per circuit) together;
  * otherwise a warp (group) runs each shot. SOFT_RUN_NO_LANES always uses the
  * warp per shot. Same results either way, another order. */
 /* SOFT_RUN_TIME_PASSES records CUDA events between the passes of every chunk
  * (ignored with SOFT_RUN_GRAPH), read back by soft_run_pass_timing. */
-/* The wide round (FP32 single-circuit runs; FP64 runs and batches never use
- * it): shots whose map outgrows a lane continue in lanes of twice the map
- * before any warp. By default it runs for chunks of at least 2^23 shots;
- * SOFT_RUN_WIDE_LANES runs it for any chunk, SOFT_RUN_NO_WIDE_LANES never.
+/* The wide round (single-circuit runs; batches never use it): shots whose map
+ * outgrows a lane continue in lanes of twice the map before any warp. By
+ * default it runs for FP32 chunks of at least 2^23 shots; SOFT_RUN_WIDE_LANES
+ * runs it for any chunk and either precision, SOFT_RUN_NO_WIDE_LANES never.
  * Same results either way. */
 enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_RUN_NO_LANES = 8,
        SOFT_RUN_TIME_PASSES = 16, SOFT_RUN_NO_WIDE_LANES = 32, SOFT_RUN_WIDE_LANES = 64 };
