@@ -196,8 +196,8 @@ typedef struct {
  * (ignored with SOFT_RUN_GRAPH), read back by soft_run_pass_timing. */
 /* The wide round (single-circuit runs; batches never use it): shots whose map
  * outgrows a lane continue in lanes of twice the map before any warp. By
- * default it runs for FP32 chunks of at least 2^23 shots; SOFT_RUN_WIDE_LANES
- * runs it for any chunk and either precision, SOFT_RUN_NO_WIDE_LANES never.
+ * default it runs for chunks of at least 2^23 shots; SOFT_RUN_WIDE_LANES runs
+ * it for any chunk, SOFT_RUN_NO_WIDE_LANES never.
  * Same results either way. */
 enum { SOFT_RUN_GRAPH = 1, SOFT_RUN_FIDELITY = 2, SOFT_RUN_NO_PREFIX = 4, SOFT_RUN_NO_LANES = 8,
        SOFT_RUN_TIME_PASSES = 16, SOFT_RUN_NO_WIDE_LANES = 32, SOFT_RUN_WIDE_LANES = 64 };

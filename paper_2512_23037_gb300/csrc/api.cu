@@ -437,13 +437,13 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   const uint32_t sp_evict = rounds > 1 ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 4) : 0u;
   const uint32_t sp_hand = lane_grow ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 8) : 0u;
   // the wide round: the handed-over shots continue in lanes of twice the map (their records
-  // are its input), and only those that outgrow it rerun in a warp. FP32 single-circuit runs
-  // only: with FP64 maps, or in batches, it measured slower than handing the shots to warps
-  // (w42: FP32 550.0 M shots/s against 533.0 M; FP64 170.7 M against 178.6 M; batch64 125.5 M
-  // against 130.3 M). By default, only for chunks of at least 2^23 shots: its pre-pass and
-  // launch cost more than it saves in small runs (w42 at 2^21 shots: 389.0 M against 412.5 M).
+  // are its input), and only those that outgrow it rerun in a warp. Single-circuit runs only
+  // (batches measured slower: 125.5 M against 130.3 M shots/s on batch64, before the affine
+  // lanes). By default only for chunks of at least 2^23 shots: its pre-pass and launch cost
+  // more than it saves in small runs (w42 at 2^21 shots: 389.0 M against 412.5 M). w42 at 2^24:
+  // FP32 550.0 M against 533.0 M (sparse lanes); FP64 348.2 M against 344.5 M (affine lanes).
   const bool wide_ok = spill && lane_grow && n_circ == 1 && !(o.flags & SOFT_RUN_NO_WIDE_LANES);
-  const bool wide = wide_ok && ((o.flags & SOFT_RUN_WIDE_LANES) || (fp32 && std::min(chunk, total) >= (1ull << 23)));
+  const bool wide = wide_ok && ((o.flags & SOFT_RUN_WIDE_LANES) || std::min(chunk, total) >= (1ull << 23));
   const size_t n_lr = 4 + 2 * ((size_t)rounds + 1);
   if (spill) {
     need(&r->d_sp, soft::lane_spill_bytes(fp32, W, rw_max, sp_evict + sp_hand));

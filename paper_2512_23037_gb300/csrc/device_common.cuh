@@ -12,26 +12,54 @@ template <typename R>
 struct Cx {
   R x, y;
 };
+// Real arithmetic with fixed rounding: explicit round-to-nearest intrinsics, so that no
+// product is contracted into a fused multiply-add differently in different kernels (the
+// noiseless-run snapshots come from one kernel and must equal, bit for bit, what the shot
+// kernels compute on the same events). A negated operand of a product or a fused
+// multiply-add is an instruction modifier, not an operation.
+__device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mulr(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mulr(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double addr(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float addr(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double subr(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float subr(float a, float b) { return __fsub_rn(a, b); }
+// a b: each component one product and one fused multiply-add
 template <typename R>
 __device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
-  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+  return {fmar(a.x, b.x, mulr(-a.y, b.y)), fmar(a.x, b.y, mulr(a.y, b.x))};
 }
 template <typename R>
 __device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) {
-  return {a.x + b.x, a.y + b.y};
+  return {addr(a.x, b.x), addr(a.y, b.y)};
 }
 template <typename R>
 __device__ __forceinline__ Cx<R> csub(Cx<R> a, Cx<R> b) {
-  return {a.x - b.x, a.y - b.y};
+  return {subr(a.x, b.x), subr(a.y, b.y)};
 }
 template <typename R>
 __device__ __forceinline__ Cx<R> cscale(Cx<R> a, R s) {
-  return {a.x * s, a.y * s};
+  return {mulr(a.x, s), mulr(a.y, s)};
 }
-// -x by flipping the sign bit (an integer op: exact, and it keeps negations off
-// GB300's narrow FP64 pipe)
-__device__ __forceinline__ double negr(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull); }
-__device__ __forceinline__ float negr(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
+// a v + b w as one chain of fused multiply-adds per component
+template <typename R>
+__device__ __forceinline__ Cx<R> cmad2(Cx<R> a, Cx<R> v, Cx<R> b, Cx<R> w) {
+  return {fmar(a.x, v.x, fmar(-a.y, v.y, fmar(b.x, w.x, mulr(-b.y, w.y)))),
+          fmar(a.x, v.y, fmar(a.y, v.x, fmar(b.x, w.y, mulr(b.y, w.x))))};
+}
+// -x by flipping the sign bit, for a negated value that is stored or selected rather than
+// fed to an arithmetic instruction. For FP64 the flip is an explicit 32-bit xor of the
+// high word in inline PTX: written as a plain negation (or a bit flip the compiler
+// recognizes as one) it becomes a DADD on GB300's narrow FP64 pipe, which measured
+// 0.91 G DADDs per 2^22 shots of the FP64 lane kernel, 22 % of its time.
+__device__ __forceinline__ double negr(double x) {
+  int hi = __double2hiint(x);
+  const int lo = __double2loint(x);
+  asm("xor.b32 %0, %0, 0x80000000;" : "+r"(hi));
+  return __hiloint2double(hi, lo);
+}
+__device__ __forceinline__ float negr(float x) { return -x; }
 // v * i^e
 template <typename R>
 __device__ __forceinline__ Cx<R> ipow(Cx<R> v, uint32_t e) {
@@ -41,7 +69,7 @@ __device__ __forceinline__ Cx<R> ipow(Cx<R> v, uint32_t e) {
 }
 template <typename R>
 __device__ __forceinline__ R norm2(Cx<R> v) {
-  return v.x * v.x + v.y * v.y;
+  return fmar(v.x, v.x, mulr(v.y, v.y));
 }
 
 // The pruning test |v|^2 < tau, decided exactly as the norm computed in R decides it.
@@ -70,8 +98,8 @@ struct PruneTest {
 };
 template <typename R>
 __device__ __forceinline__ double norm2d(Cx<R> v) {
-  double a = (double)v.x, b = (double)v.y;
-  return a * a + b * b;
+  const double a = (double)v.x, b = (double)v.y;
+  return __fma_rn(a, a, __dmul_rn(b, b));
 }
 
 template <int W>
@@ -133,11 +161,14 @@ __device__ __forceinline__ void wflip(uint64_t *a, uint32_t i) {
     if ((int)(i >> 6) == w) a[w] ^= 1ull << (i & 63);
 }
 
-// Philox4x32-10, counter (shot_lo, shot_hi, stream, index), key = seed.
+// Philox4x32-10, counter (shot_lo, shot_hi, stream, index), key = seed. Rolled: the
+// round loop is not unrolled, for kernels whose instruction fetch limits them (the lane
+// kernel: 3.6 % faster on w42 FP32); same values.
+template <bool Rolled = false>
 __device__ __forceinline__ uint4 philox(uint64_t seed, uint64_t shot, uint32_t stream, uint32_t idx) {
   uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32), c2 = stream, c3 = idx;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-#pragma unroll
+#pragma unroll (Rolled ? 1 : 10)
   for (int r = 0; r < 10; ++r) {
     if (r) {
       k0 += 0x9E3779B9u;

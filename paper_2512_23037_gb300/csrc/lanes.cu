@@ -339,7 +339,7 @@ struct LaneShot {
   }
 
   __device__ double uniform(uint32_t ord) const {
-    uint4 w = philox(P.seed, shot, 1u, ord);
+    uint4 w = philox<true>(P.seed, shot, 1u, ord);
     uint64_t m = ((uint64_t)w.x << 21) ^ (uint64_t)(w.y >> 11);
     return (double)m * 0x1p-53;
   }
@@ -624,9 +624,9 @@ struct LaneShot {
       const Cx<R> vs = ls ? val(s) : Cx<R>{0, 0}, vt = lt ? val(t) : Cx<R>{0, 0};
       const Cx<R> bs = (g0 ^ spar(s, gl)) ? bn : bq, bt = (g0 ^ spar(t, gl)) ? bn : bq;
       Cx<R> ns, nt;
-      if (ls && lt) {
-        ns = cadd(cmul(a, vs), cmul(bt, vt));
-        nt = cadd(cmul(a, vt), cmul(bs, vs));
+      if (ls && lt) {  // one fused chain per component
+        ns = cmad2(a, vs, bt, vt);
+        nt = cmad2(a, vt, bs, vs);
       } else if (ls) {  // an entry without a partner gains one
         ns = cmul(a, vs);
         nt = cmul(bs, vs);
@@ -804,7 +804,7 @@ struct LaneShot {
   __device__ void step(uint32_t ev, const uint4 &hdr, const uint64_t *body, const Ev<W> *E) {
     while (nxt < hdr.y && status == LS_RUN) {
       apply_error(nxt);
-      if (!next_site(C, P.seed, shot, cur, kblk, nxt, w2)) status = LS_ERR;
+      if (!next_site<true>(C, P.seed, shot, cur, kblk, nxt, w2)) status = LS_ERR;
     }
     if (status != LS_RUN) return;
     const uint64_t *dsd = body, *dss = body + W, *beta = body + 2 * W, *gamma = body + 3 * W;

@@ -17,6 +17,7 @@ namespace dev {
 // of the noise stream against the thresholds thr (the smallest gap g with
 // U < thr[g]), then thinning. nxt = the site (0xFFFFFFFF if none), w2 = its
 // Pauli choice word. False if the guard ran out (impossible for valid tables).
+template <bool Rolled = false>
 __device__ __forceinline__ bool next_site(const CircDev *C, uint64_t seed, uint64_t shot, uint32_t &cur,
                                           uint32_t &kblk, uint32_t &nxt, uint32_t &w2) {
   const uint32_t n_sites = C->n_sites;
@@ -26,7 +27,7 @@ __device__ __forceinline__ bool next_site(const CircDev *C, uint64_t seed, uint6
       nxt = 0xFFFFFFFFu;
       return true;
     }
-    uint4 w = philox(seed, shot, 0u, kblk++);
+    uint4 w = philox<Rolled>(seed, shot, 0u, kblk++);
     uint64_t U = (uint64_t)w.x | ((uint64_t)w.y << 32);
     const uint32_t rem = n_sites - cur;
     uint32_t lo = 0, hi = rem;
