@@ -674,15 +674,16 @@ def _lane_case(case):
     return circ, noise, {}
 
 
-@pytest.mark.parametrize("precision,wide", [("fp64", None), ("fp32", False), ("fp32", True)])
+@pytest.mark.parametrize("precision,wide", [("fp64", False), ("fp64", True), ("fp32", False), ("fp32", True)])
 @pytest.mark.parametrize("case", ["w42", "w42_p3e-3", "w42_mid32", "random40_mpp", "win76", "win128"])
 def test_lane_kernel_states_match_oracle(soft, precision, wide, case):
     """State capture keeps lane-per-shot scheduling: each captured shot's final
     signs, keys and values are written from wherever it ends (a first-round
     lane, an eviction round, the wide round's lanes, the middle warp pass after
     a hand-over, the pass at the circuit's cap), and equal the oracle's within
-    1e-12 (FP64) / 1e-5 (FP32) for kept and discarded shots. Theorem 1 (update
-    rules) in the GS representation of Sec. II-C."""
+    1e-12 (FP64) / 1e-5 (FP32) for kept and discarded shots, with and without
+    the wide round in either precision. Theorem 1 (update rules) in the GS
+    representation of Sec. II-C."""
     S = soft
     circ, noise, kw = _lane_case(case)
     k = 512
