@@ -311,14 +311,11 @@ int soft_release_workspace(void);
  *   Scratch (work counters and the rerun list) lives in one static device
  *   array of about 4 MiB, sized for at most 1048576 shots per call; every GPU
  *   that loads the library keeps it until the process exits. Larger n_shots
- *   is rejected with SOFT_E_ARG. The first call on a device looks up that
- *   array's device address (cudaGetSymbolAddress) with the device current,
- *   so make the first call before any stream capture. All calls share the
- *   array: calls that overlap on the GPU (different streams, no ordering)
- *   race on it and give wrong results; calls ordered on one stream are safe.
- *   The looked-up address belongs to the device's current context: after a
- *   cudaDeviceReset of that device, do not call this entry point on it again
- *   in the same process.
+ *   is rejected with SOFT_E_ARG. Each call looks up that array's device
+ *   address (cudaGetSymbolAddress, which allocates nothing) with the
+ *   circuit's device current. All calls share the array: calls that overlap
+ *   on the GPU (different streams, no ordering) race on it and give wrong
+ *   results; calls ordered on one stream are safe.
  * Errors: SOFT_E_ARG, SOFT_E_CUDA. No cudaMalloc, cudaFree or other
  * allocating routine is called. */
 int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_t first_shot, uint64_t seed, int32_t precision,

@@ -13,8 +13,6 @@
 // scale with the shot count; same results, lower throughput).
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/soft.h"
 #include "handles.h"
 #include "kernels.cuh"
@@ -27,23 +25,15 @@ constexpr size_t kScratchBytes = kCounterBytes + kNoallocMaxShots * sizeof(uint3
 
 // The scratch itself. In host code `g_noalloc_scratch` is only a host-side
 // stand-in for the symbol, never a device address: the address comes from
-// cudaGetSymbolAddress, taken once per device with that device current.
+// cudaGetSymbolAddress in the current context, taken on every call (it
+// allocates nothing, and no cached address can outlive a context reset).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-
-int scratch_for_device(int dev, unsigned char **out) {
-  if (dev < 0 || dev >= kMaxDevices) return soft::set_error(SOFT_E_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return soft::set_error(SOFT_E_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
-    g_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char *>(g_addr[dev]);
+int scratch_address(unsigned char **out) {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) return soft::set_error(SOFT_E_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
+  *out = static_cast<unsigned char *>(p);
   return SOFT_OK;
 }
 
@@ -68,7 +58,7 @@ extern "C" int soft_run_shots_noalloc(soft_circuit *c, uint64_t n_shots, uint64_
   if (soft::group_smem_bytes(fp32, hp.W, hp.cap, hp.rw) > (size_t)smem_optin - 5 * 8 * soft::kMaxCirc)
     return soft::set_error(SOFT_E_ARG, "coeff_cap too large for this entry point's shared-memory coefficient map");
   unsigned char *scratch = nullptr;
-  int rc = scratch_for_device(c->device, &scratch);
+  int rc = scratch_address(&scratch);  // with the circuit's device current
   if (rc != SOFT_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
