@@ -84,6 +84,13 @@ struct Shot {
   Key<W> rk;
   Cx<R> rv;
 
+  // The phase xi = i^e (-1)^{gamma.key} of a rotation: i^e folded into b once per event
+  // (b xi is then b i^e or its negation, exact) takes instructions off the narrow FP64 pipe.
+  // FP32 with two key words applies it per entry instead: there the folded constants stay
+  // live across the entry loops of a kernel already at its register limit (80), and the
+  // 97-qubit workload ran 27.1 M shots/s that way against 24.3 M folded. With one key word
+  // (w42's warp passes) folding measured faster (1.26 against 1.50 ms per 2^24-shot step).
+  static constexpr bool kFoldPhase = sizeof(R) == 8 || W == 1;
   PruneTest<R> pt;  // |v|^2 < tau (thresholds computed once per thread)
 
   __device__ Shot(const Tile &tile, const ShotParams &p, unsigned char *base) : t(tile), P(p), pt(p.tau) {
@@ -327,8 +334,13 @@ struct Shot {
     // one product serves both cases: b xi_{pk} v_partner (paired) or b xi_k v_k (new entry at pk)
     const Cx<R> src = has ? vj : rv;
     const uint32_t par = kpar(has ? pk : rk, gamma);
-    const Cx<R> bq = ipow(b, e);  // b xi = (-1)^par b i^e: the phase folded into b (exact)
-    const Cx<R> tb = cmul(par ? Cx<R>{negr(bq.x), negr(bq.y)} : bq, src);
+    Cx<R> tb;  // b xi v (the phase folded into b in FP64, exact; see kFoldPhase)
+    if (kFoldPhase) {
+      const Cx<R> bq = ipow(b, e);
+      tb = cmul(par ? Cx<R>{negr(bq.x), negr(bq.y)} : bq, src);
+    } else {
+      tb = cmul(b, ipow(src, e + 2u * par));
+    }
     Cx<R> nv = cmul(a, rv);
     if (has) nv = cadd(nv, tb);
     const Cx<R> av = tb;
@@ -386,8 +398,12 @@ struct Shot {
 
   __device__ void reg_rot_diag(uint32_t e, Cx<R> a, Cx<R> b, const uint64_t *gamma) {
     const bool valid = lane < nnz;
-    const Cx<R> bq = ipow(b, e);  // v' = (a + b xi) v, with a + b xi one of two constants
-    if (valid) rv = cmul(kpar(rk, gamma) ? csub(a, bq) : cadd(a, bq), rv);
+    if (kFoldPhase) {
+      const Cx<R> bq = ipow(b, e);  // v' = (a + b xi) v, with a + b xi one of two constants
+      if (valid) rv = cmul(kpar(rk, gamma) ? csub(a, bq) : cadd(a, bq), rv);
+    } else if (valid) {
+      rv = cadd(cmul(a, rv), cmul(b, ipow(rv, e + 2u * kpar(rk, gamma))));
+    }
     if (t.any(valid && pt.small(rv))) reg_compact(valid && !pt.small(rv));
   }
 
@@ -415,7 +431,7 @@ struct Shot {
     const bool neg = valid && (kpar(rk, gamma) ^ sgn);
     const bool h1 = t.any(neg), h0 = t.any(valid && !neg);
     if (!(h0 && h1)) return h1 ? -1 : 1;
-    const double a2 = valid ? norm2d(rv) : 0.0;
+    const double a2 = valid ? pnorm(rv) : 0.0;
     const double sp = tile_sum(neg ? 0.0 : a2), sm = tile_sum(neg ? a2 : 0.0);
     const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt_as<R>(m == 1 ? sp : sm);
@@ -442,8 +458,8 @@ struct Shot {
       if (partner) v1 = vj;
     }
     const Cx<R> x1 = ipow(v1, e2 + 2u * kpar(kxor(a0, ep), g2));
-    const double sp = tile_sum(owner ? 0.5 * norm2d(cadd(v0, x1)) : 0.0);
-    const double sm = tile_sum(owner ? 0.5 * norm2d(csub(v0, x1)) : 0.0);
+    const double sp = tile_sum(owner ? 0.5 * pnorm(cadd(v0, x1)) : 0.0);
+    const double sm = tile_sum(owner ? 0.5 * pnorm(csub(v0, x1)) : 0.0);
     const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt_as<R>(2.0 * (m == 1 ? sp : sm));
     if (owner) {
@@ -511,8 +527,14 @@ struct Shot {
         if (j >= 0) {
           if (!kbit(k, lowbit)) {
             Cx<R> vj = vals[j];
-            Cx<R> ni = cadd(cmul(a, v), cmul(kpar(pk, gamma) ? bn : bq, vj));
-            Cx<R> nj = cadd(cmul(a, vj), cmul(kpar(k, gamma) ? bn : bq, v));
+            Cx<R> ni, nj;
+            if (kFoldPhase) {
+              ni = cadd(cmul(a, v), cmul(kpar(pk, gamma) ? bn : bq, vj));
+              nj = cadd(cmul(a, vj), cmul(kpar(k, gamma) ? bn : bq, v));
+            } else {
+              ni = cadd(cmul(a, v), cmul(b, ipow(vj, e + 2u * kpar(pk, gamma))));
+              nj = cadd(cmul(a, vj), cmul(b, ipow(v, e + 2u * kpar(k, gamma))));
+            }
             vals[i] = ni;
             vals[j] = nj;
             prune = prune || pt.small(ni) || pt.small(nj);
@@ -520,7 +542,7 @@ struct Shot {
         } else {
           Cx<R> ni = cmul(a, v);
           vals[i] = ni;
-          nv = cmul(kpar(k, gamma) ? bn : bq, v);
+          nv = kFoldPhase ? cmul(kpar(k, gamma) ? bn : bq, v) : cmul(b, ipow(v, e + 2u * kpar(k, gamma)));
           app = true;
           prune = prune || pt.small(ni) || pt.small(nv);
         }
@@ -576,7 +598,8 @@ struct Shot {
     bool prune = false;
     for (uint32_t i = lane; i < nnz; i += G) {
       Key<W> k = key(i);
-      Cx<R> nv = cmul(kpar(k, gamma) ? c1 : c0, vals[i]);
+      Cx<R> nv = kFoldPhase ? cmul(kpar(k, gamma) ? c1 : c0, vals[i])
+                            : cadd(cmul(a, vals[i]), cmul(b, ipow(vals[i], e + 2u * kpar(k, gamma))));
       vals[i] = nv;
       prune = prune || pt.small(nv);
     }
@@ -610,7 +633,7 @@ struct Shot {
     if (!(h0 && h1)) return h1 ? -1 : 1;
     double sp = 0.0, sm = 0.0;
     for (uint32_t i = lane; i < nnz; i += G) {
-      double a2 = norm2d(vals[i]);
+      double a2 = pnorm(vals[i]);
       if (kpar(key(i), gamma) ^ sgn) sm += a2;
       else sp += a2;
     }
@@ -695,8 +718,8 @@ struct Shot {
       }
       Key<W> a1 = hi ? k : kxor(k, ep);
       Cx<R> x1 = ipow(v1, e2 + 2u * kpar(a1, g2));
-      sp += 0.5 * norm2d(cadd(v0, x1));
-      sm += 0.5 * norm2d(csub(v0, x1));
+      sp += 0.5 * pnorm(cadd(v0, x1));
+      sm += 0.5 * pnorm(csub(v0, x1));
     }
     sp = tile_sum(sp);
     sm = tile_sum(sm);

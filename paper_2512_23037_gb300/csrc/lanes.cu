@@ -247,6 +247,19 @@ struct LaneShot {
   // B[k] ^= B[q] for the other k of g; B[q] and Dual[q] go (the other duals stay dual);
   // each live slot drops bit q of its index.
   __device__ void remove_dim(uint32_t q, uint32_t g, uint32_t t) {
+    remove_rows(q, g, t);
+    const uint32_t lo = (1u << q) - 1u;
+    uint32_t nl = 0;
+#pragma unroll 1
+    for (uint32_t m = live; m; m &= m - 1u) {  // ascending: a slot moves down onto a vacated one
+      const uint32_t s = __ffs(m) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
+      if (s2 != s) set_val(s2, val(s));
+      nl |= 1u << s2;
+    }
+    live = nl;
+  }
+  // the rows' part of remove_dim (d decreases); the caller moves the slots
+  __device__ void remove_rows(uint32_t q, uint32_t g, uint32_t t) {
     uint64_t bq[W];
     get_row(kRowB + q, bq);
     if (t) xor_row(0, bq);
@@ -261,15 +274,6 @@ struct LaneShot {
       get_row(kRowD + k + 1u, x);
       put_row(kRowD + k, x);
     }
-    const uint32_t lo = (1u << q) - 1u;
-    uint32_t nl = 0;
-#pragma unroll 1
-    for (uint32_t m = live; m; m &= m - 1u) {  // ascending: a slot moves down onto a vacated one
-      const uint32_t s = __ffs(m) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
-      if (s2 != s) set_val(s2, val(s));
-      nl |= 1u << s2;
-    }
-    live = nl;
     --d;
   }
   // after a measurement: all live slots share parity(s & g); drop a coordinate if g != 0
@@ -280,10 +284,13 @@ struct LaneShot {
     remove_dim(31u - __clz(g), g, t);
   }
   // drop the coordinates no live slot uses
-  __device__ void compact_dead() {
+  __device__ void compact_dead(uint32_t &gl) {
 #pragma unroll 1
     for (uint32_t k = d; k-- > 0;)
-      if (!(live & slot_bit_mask(k))) remove_dim(k, 1u << k, 0);
+      if (!(live & slot_bit_mask(k))) {
+        remove_dim(k, 1u << k, 0);
+        gl = (gl & ((1u << k) - 1u)) | ((gl >> (k + 1u)) << k);  // the parities follow the coordinates
+      }
   }
   // key of slot s
   __device__ Key<W> key_of(uint32_t s) const {
@@ -555,8 +562,10 @@ struct LaneShot {
 
   // ---- a I + b Z_q: v'_a = a v_a + b xi_{a^beta} v_{a^beta}; xi = i^e (-1)^{gamma.key}
   // folded into b (b or -b per entry, exact), and a diagonal rotation (beta = 0) is one
-  // product (a + b xi) v per entry
-  __device__ void rot(uint32_t w0, uint32_t ci, const uint64_t *beta, const uint64_t *gamma, bool diag) {
+  // product (a + b xi) v per entry. gl, g0: gamma's parities with the basis and alpha0 on
+  // entry (they follow the basis through the changes made here).
+  __device__ void rot(uint32_t w0, uint32_t ci, const uint64_t *beta, const uint64_t *gamma, bool diag, uint32_t gl,
+                      const uint32_t g0) {
     uint32_t pe = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) pe += diag ? __popcll(ss[w] & gamma[w]) : __popcll(sd[w] & beta[w]) + __popcll(ss[w] & gamma[w]);
@@ -580,8 +589,6 @@ struct LaneShot {
     const Cx<R> bq = ipow(b, e), bn = Cx<R>{negr(bq.x), negr(bq.y)};
     uint32_t drop = 0;
     if (diag) {
-      uint32_t g0;
-      const uint32_t gl = parities(gamma, g0);
       const Cx<R> c0 = cadd(a, bq), c1 = cadd(a, bn);
 #pragma unroll 1
       for (uint32_t m = live; m; m &= m - 1u) {
@@ -598,7 +605,7 @@ struct LaneShot {
     uint32_t c = coords(beta, r);
     const bool fresh = wnonzero<W>(r);  // beta outside the span: every entry gains a partner
     if (fresh && d == kDim) {
-      compact_dead();
+      compact_dead(gl);
       if (d == kDim) {
         // the map would outgrow the lane: nothing has been written yet, so the shot can be
         // taken over at the top of this event (by the wide round's lanes, or a warp);
@@ -612,9 +619,8 @@ struct LaneShot {
     if (fresh) {
       add_dim(r);
       c |= 1u << (d - 1u);
+      gl |= row_par(kRowB + d - 1u, gamma) << (d - 1u);
     }
-    uint32_t g0;
-    const uint32_t gl = parities(gamma, g0);
     const uint32_t spread = live | slot_xor_perm(live, c);
     const uint32_t lead = spread & ~slot_bit_mask(__ffs(c) - 1) & cube();  // one member of each pair
 #pragma unroll 1
@@ -643,8 +649,9 @@ struct LaneShot {
     if (nnz() > C->cap) status = LS_OVF;  // the overflow rule, for circuits whose cap is below the lane's
   }
 
-  // ---- measurement of P, beta = 0: lambda_a = c (-1)^{gamma.a}
-  __device__ int meas_a(uint32_t w0, uint32_t ord, const uint64_t *gamma) {
+  // ---- measurement of P, beta = 0: lambda_a = c (-1)^{gamma.a}; gl, g0: gamma's parities
+  // with the basis and alpha0
+  __device__ int meas_a(uint32_t w0, uint32_t ord, const uint64_t *gamma, const uint32_t gl, const uint32_t g0) {
     uint32_t pe = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) pe += __popcll(ss[w] & gamma[w]);
@@ -654,8 +661,6 @@ struct LaneShot {
       return 1;
     }
     const uint32_t sgn = e >> 1;
-    uint32_t g0;
-    const uint32_t gl = parities(gamma, g0);
     const uint32_t pm = slot_par_mask(gl) & cube();
     const uint32_t neg = live & (((sgn ^ g0) & 1u) ? ~pm : pm);  // slots with eigenvalue -1
     const uint32_t pos = live & ~neg;
@@ -667,27 +672,29 @@ struct LaneShot {
 #pragma unroll 1
     for (uint32_t m = live; m; m &= m - 1u) {
       const uint32_t s = __ffs(m) - 1;
-      const double a2 = norm2d(val(s));
+      const double a2 = pnorm(val(s));
       if ((neg >> s) & 1u) sm += a2;
       else sp += a2;
     }
     const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt(m == 1 ? sp : sm);
     const uint32_t keep = (m == 1) ? pos : neg;
+    // the kept slots share parity(s & gl) = t (gl != 0: both eigenvalues occur), so bit q of
+    // their index is redundant; each is scaled straight into its slot of the restricted map
+    // (restrict_to's result, in one pass)
+    const uint32_t q = 31u - __clz(gl), lo = (1u << q) - 1u, t = spar(__ffs(keep) - 1, gl);
     uint32_t nl = 0;
 #pragma unroll 1
-    for (uint32_t mm = live; mm; mm &= mm - 1u) {
-      const uint32_t s = __ffs(mm) - 1;
-      if ((keep >> s) & 1u) {
-        const Cx<R> v = cscale(val(s), sc);
-        if (!pt.small(v)) {
-          set_val(s, v);
-          nl |= 1u << s;
-        }
+    for (uint32_t mm = keep; mm; mm &= mm - 1u) {  // ascending: a write lands on a slot already read
+      const uint32_t s = __ffs(mm) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
+      const Cx<R> v = cscale(val(s), sc);
+      if (!pt.small(v)) {
+        set_val(s2, v);
+        nl |= 1u << s2;
       }
     }
+    if (nl) remove_rows(q, gl, t);
     live = nl;
-    restrict_to(gl);
     return m;
   }
 
@@ -750,8 +757,8 @@ struct LaneShot {
         if ((live >> s) & 1u) v0 = val(s);
         if ((live >> t) & 1u) x1 = ipow(val(t), e2 + 2u * (g20 ^ spar(t, gl2)));
       }
-      sp += 0.5 * norm2d(cadd(v0, x1));
-      sm += 0.5 * norm2d(csub(v0, x1));
+      sp += 0.5 * pnorm(cadd(v0, x1));
+      sm += 0.5 * pnorm(csub(v0, x1));
     }
     const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt(2.0 * (m == 1 ? sp : sm));
@@ -814,13 +821,18 @@ struct LaneShot {
       ss[w] ^= dss[w];
     }
     const uint32_t w0 = hdr.x, type = ev_type(w0), flags = ev_flags(w0);
-    switch (type) {
-      case EV_ROT: rot(w0, hdr.z, beta, gamma, false); break;
-      case EV_ROT_DIAG: rot(w0, hdr.z, beta, gamma, true); break;
-      case EV_MEAS_A:
-      case EV_MEAS_B: {
+    // gamma's parities with alpha0 and the basis, once for the event types that use them.
+    // This kernel is bound by instruction fetch, so each helper is inlined at as few sites as
+    // possible: one parity computation here instead of one per handler, one rotation handler
+    // for both kinds, and the handlers in a chain of tests in order of frequency (a `break`
+    // leaves the chain) rather than a jump table (w42: FP32 660 -> 675 M shots/s, FP64
+    // 352 -> 382 M).
+    uint32_t g0 = 0, gl = 0;
+    if (type == EV_ROT || type == EV_ROT_DIAG || type == EV_MEAS_A) gl = parities(gamma, g0);
+    do {
+      if (type == EV_MEAS_A || type == EV_MEAS_B) {
         force = P.fid_mode && (flags & F_FIDELITY);
-        const int m = (type == EV_MEAS_A) ? meas_a(w0, hdr.z, gamma) : meas_b(hdr.z, (uint32_t)beta[0]);
+        const int m = (type == EV_MEAS_A) ? meas_a(w0, hdr.z, gamma, gl, g0) : meas_b(hdr.z, (uint32_t)beta[0]);
         if (status != LS_RUN) break;
         if (force && m == -1) {
           fid = 0.0;
@@ -850,7 +862,11 @@ struct LaneShot {
         if ((flags & F_DETECTOR) && ((m == -1 ? 1u : 0u) ^ ((flags & F_INVERT) ? 1u : 0u))) status = LS_DISC;
         break;
       }
-      case EV_PAULI: {
+      if (type == EV_ROT || type == EV_ROT_DIAG) {
+        rot(w0, hdr.z, beta, gamma, type == EV_ROT_DIAG, gl, g0);
+        break;
+      }
+      if (type == EV_PAULI) {
         uint32_t cond;
         if (flags & F_COND_LAST) cond = (lastm == -1);
         else cond = rec_bit((int32_t)hdr.z) ^ rec_bit((int32_t)hdr.w);
@@ -862,7 +878,7 @@ struct LaneShot {
         }
         break;
       }
-      case EV_PARITY: {
+      if (type == EV_PARITY) {
         const int par = chain ^ (int)rec_bit((int32_t)hdr.z) ^ (int)rec_bit((int32_t)hdr.w) ^
                         ((flags & F_INVERT) ? 1 : 0);
         if (flags & F_CHAIN) {
@@ -874,8 +890,7 @@ struct LaneShot {
         }
         break;
       }
-      default: break;
-    }
+    } while (false);
     if (status == LS_HAND) {  // back to the top of the event: the signs as before its XOR
 #pragma unroll
       for (int w = 0; w < W; ++w) {
