@@ -602,11 +602,14 @@ struct LaneShot {
       return;
     }
     uint64_t r[W];
-    uint32_t c = coords(beta, r);
-    const bool fresh = wnonzero<W>(r);  // beta outside the span: every entry gains a partner
-    if (fresh && d == kDim) {
-      compact_dead(gl);
-      if (d == kDim) {
+    uint32_t c;
+    bool fresh;
+#pragma unroll 1
+    for (uint32_t pass = 0;; ++pass) {
+      c = coords(beta, r);
+      fresh = wnonzero<W>(r);  // beta outside the span: every entry gains a partner
+      if (!fresh || d < kDim) break;
+      if (pass) {
         // the map would outgrow the lane: nothing has been written yet, so the shot can be
         // taken over at the top of this event (by the wide round's lanes, or a warp);
         // otherwise (the wide round) it reruns in a warp
@@ -614,7 +617,7 @@ struct LaneShot {
         else fail_capacity();
         return;
       }
-      c = coords(beta, r);
+      compact_dead(gl);
     }
     if (fresh) {
       add_dim(r);
@@ -664,24 +667,30 @@ struct LaneShot {
     const uint32_t pm = slot_par_mask(gl) & cube();
     const uint32_t neg = live & (((sgn ^ g0) & 1u) ? ~pm : pm);  // slots with eigenvalue -1
     const uint32_t pos = live & ~neg;
-    if (!neg || !pos) {  // decided (all eigenvalues equal): integer test only
-      restrict_to(gl);
-      return neg ? -1 : 1;
-    }
-    double sp = 0.0, sm = 0.0;
+    int m;
+    R sc = (R)1;
+    uint32_t keep;
+    if (!neg || !pos) {  // decided (all eigenvalues equal): integer test only, no scaling
+      m = neg ? -1 : 1;
+      keep = live;
+      if (!gl || !live) return m;
+    } else {
+      double sp = 0.0, sm = 0.0;
 #pragma unroll 1
-    for (uint32_t m = live; m; m &= m - 1u) {
-      const uint32_t s = __ffs(m) - 1;
-      const double a2 = pnorm(val(s));
-      if ((neg >> s) & 1u) sm += a2;
-      else sp += a2;
+      for (uint32_t mm = live; mm; mm &= mm - 1u) {
+        const uint32_t s = __ffs(mm) - 1;
+        const double a2 = pnorm(val(s));
+        if ((neg >> s) & 1u) sm += a2;
+        else sp += a2;
+      }
+      m = pick(ord, sp, sm);
+      sc = inv_sqrt(m == 1 ? sp : sm);
+      keep = (m == 1) ? pos : neg;
     }
-    const int m = pick(ord, sp, sm);
-    const R sc = inv_sqrt(m == 1 ? sp : sm);
-    const uint32_t keep = (m == 1) ? pos : neg;
-    // the kept slots share parity(s & gl) = t (gl != 0: both eigenvalues occur), so bit q of
-    // their index is redundant; each is scaled straight into its slot of the restricted map
-    // (restrict_to's result, in one pass)
+    // the kept slots share parity(s & gl) = t, so bit q of their index is redundant; each is
+    // scaled straight into its slot of the restricted map. A decided outcome goes through
+    // the same loop with the scale 1 (exact; no kept value is below tau), so that the
+    // restriction is inlined once (w42 FP32: 676 -> 708 M shots/s)
     const uint32_t q = 31u - __clz(gl), lo = (1u << q) - 1u, t = spar(__ffs(keep) - 1, gl);
     uint32_t nl = 0;
 #pragma unroll 1
