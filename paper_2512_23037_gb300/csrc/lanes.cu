@@ -38,7 +38,7 @@ enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_R
 constexpr int kLaneBlock = 128;
 constexpr uint32_t kLaneMaxBuckets = 50000;  // the pre-pass histogram of all buckets: 200 KB of shared memory
 #ifndef SOFT_LANE_EVICT
-#define SOFT_LANE_EVICT 8
+#define SOFT_LANE_EVICT 10
 #endif
 constexpr uint32_t kEvictBelow = SOFT_LANE_EVICT;  // a warp with this many active lanes or fewer evicts them
 #ifndef SOFT_LANE_ROUNDS
@@ -1184,6 +1184,8 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
       }
       if (active && s.status == LS_RUN) s.step(e, hdr, body, E);
     }
+    // a spill record to write (a hand-over or an eviction), written once below
+    uint32_t ev_r = 0xFFFFFFFFu, ev_e = 0;
     // finish: ended, or past the last event
     if (active && (s.status != LS_RUN || e + 1u >= n_ev)) {
       if (s.status == LS_RUN) s.status = LS_KEPT;
@@ -1194,7 +1196,8 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
         const unsigned long long h = atomicAdd(&P.lr[1], 1ull);
         if (h < (unsigned long long)(P.sp_cap - P.sp_evict_cap)) {
           const uint32_t r = P.sp_evict_cap + (uint32_t)h;
-          s.evict(S, r, item, e);
+          ev_r = r;
+          ev_e = e;
           entry = kSpillRef | r;    // in a warp, from the rerun list,
           listed = !P.lane_wide;    // or in the wide round, which takes every such record
         }
@@ -1237,12 +1240,14 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
         if (active) {
           const unsigned long long r = r0 + __popc(am & ((1u << lane) - 1u));
           if (r < P.sp_evict_cap) {
-            s.evict(S, (uint32_t)r, item, e + 1u);
+            ev_r = (uint32_t)r;
+            ev_e = e + 1u;
             active = false;
           }
         }
       }
     }
+    if (ev_r != 0xFFFFFFFFu) s.evict(S, ev_r, item, ev_e);
     uint32_t en = e + 1u > n_ev ? 0u : e + 1u;  // (within the circuit, cyclically)
     if (!__any_sync(0xFFFFFFFFu, active)) {
       // all lanes idle: the next bucket of any circuit (cyclically) that still has shots, or stop
