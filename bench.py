@@ -440,7 +440,9 @@ def leg_w97(S, C, torch, peak_ops, n_chunks):
                      "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                                   "unit": "Tops/s", "frac": achieved / peak_ops,
                                   "equivalent_frac_whole_method": ops_full * n / (ms / 1000) / peak_ops, "traffic": None,
-                                  "kernel": "shot_kernel (warp per shot: the noiseless maps reach 64 entries)",
+                                  "kernel": ("lane_kernel (64-entry lanes: the noiseless maps reach 64 entries) + "
+                                             "shot_kernel (shots that outgrow them)") if prec == "fp32" else
+                                            "shot_kernel (warp per shot: 64-entry lanes are FP32 only)",
                                   "ops_per_shot": ops_shot, "ops_per_shot_whole_method": ops_full}}
     h.free()
     return out

@@ -186,12 +186,15 @@ typedef struct {
  * batch each circuit has its own buckets, and a warp serves one circuit at a
  * time. It applies to runs without a forced group size (state capture
  * included: a captured shot's state is written wherever it ends), to
- * the circuits whose noiseless run's maps fit a lane (at most 16 entries in at
- * most 4 directions; the
- * shots of a batch's other circuits go straight to the warp pass), when those
- * circuits hold at most 50 000 events (plus one per circuit) together;
- * otherwise a warp (group) runs each shot. SOFT_RUN_NO_LANES always uses the
- * warp per shot. Same results either way, another order. */
+ * the circuits whose noiseless run's maps fit a lane, when those circuits hold
+ * at most 50 000 events (plus one per circuit) together; otherwise a warp
+ * (group) runs each shot. A circuit whose noiseless maps need more than 16
+ * entries or 4 directions gets lanes of 32 entries (5 directions) or, with
+ * SOFT_FP32 coefficients, of 64 (6 directions): these neither hand over nor
+ * evict, and a shot that outgrows one reruns from its start in a warp. The
+ * shots of a batch's other circuits go straight to the warp pass.
+ * SOFT_RUN_NO_LANES always uses the warp per shot. Same results either way,
+ * another order. */
 /* SOFT_RUN_TIME_PASSES records CUDA events between the passes of every chunk
  * (ignored with SOFT_RUN_GRAPH), read back by soft_run_pass_timing. */
 /* The wide round (single-circuit runs; batches never use it): shots whose map

@@ -361,29 +361,32 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     total += n_shots[i];
   }
   const uint32_t cap1 = o.first_cap ? std::min(o.first_cap, cap_max) : std::min(kDefaultFirstCap, cap_max);
-  // lane-per-shot scheduling: the noiseless prefix, no state capture, group size not forced,
-  // a circuit whose noiseless run's maps fit a lane's map, and at most lane_max_buckets
-  // buckets (one per event, plus one, per such circuit). The shots of the other circuits of a
-  // batch go straight to the warp pass that follows the lanes.
+  // lane-per-shot scheduling: the noiseless prefix, group size not forced, a circuit whose
+  // noiseless run's maps fit a lane's map (16 entries; else 32; else, FP32, 64), and at most
+  // lane_max_buckets buckets (one per event, plus one, per such circuit). The shots of the
+  // other circuits of a batch go straight to the warp pass that follows the lanes.
   const int pk = o.precision == SOFT_FP32 ? 1 : 0;
-  uint64_t n_buckets = 0;
-  std::vector<char> fits(n_circ);
+  const uint32_t lc16 = soft::lane_map_cap();
+  std::vector<uint32_t> lcap(n_circ);  // each circuit's lane map (0: none)
+  uint64_t nbc[3] = {0, 0, 0};         // buckets of the circuits of 16-, 32- and 64-entry lanes
+  auto lane_class = [&](uint32_t c) { return c == lc16 ? 0 : c == 2 * lc16 ? 1 : c == 4 * lc16 ? 2 : 3; };
   for (uint32_t i = 0; i < n_circ; ++i) {
-    fits[i] = circs[i]->d_traj[pk] && circs[i]->traj_max_n[pk] <= soft::lane_map_cap() &&
-              circs[i]->traj_max_d[pk] <= soft::lane_map_dim();
-    if (fits[i]) n_buckets += circs[i]->hp.ev.size() + 1;
+    lcap[i] = circs[i]->d_traj[pk] ? soft::lane_first_cap(circs[i]->traj_max_n[pk], circs[i]->traj_max_d[pk], fp32) : 0u;
+    if (lcap[i]) nbc[lane_class(lcap[i])] += circs[i]->hp.ev.size() + 1;
   }
+  const uint64_t n_buckets = nbc[0] + nbc[1] + nbc[2];
   const bool lanes = !(o.flags & SOFT_RUN_NO_LANES) && !(o.flags & SOFT_RUN_NO_PREFIX) && o.group_size == 0 &&
                      n_buckets > 0 && n_buckets <= soft::lane_max_buckets();
   const uint32_t nb = lanes ? (uint32_t)n_buckets : 0u;
+  const bool lanes16 = lanes && nbc[0] > 0;  // the lanes that evict, hand over and feed the wide round
   // a rerun pass finishes the shots whose maps outgrow the first pass (cap1). After lanes it
   // always runs: a lane decides overflow only after pruning, and a map that outgrows the lane
   // before pruning is staged whole by the warp pass, even when the circuit's cap is the lane's.
-  const bool lane_grow = lanes && soft::lane_map_cap() < cap_max;  // maps may outgrow a lane
+  const bool lane_grow = lanes16 && lc16 < cap_max;  // maps may outgrow a 16-entry lane
   const bool two_pass = lanes || cap1 < cap_max;
   // after lanes, a middle pass (a warp per shot, register map up to cap1) takes the shots whose
   // maps outgrew a lane, and only those that outgrow cap1 go on to the pass at the circuit's cap
-  const bool mid_pass = lanes && soft::lane_map_cap() < cap1 && cap1 < cap_max;
+  const bool mid_pass = lanes && lc16 < cap1 && cap1 < cap_max;
   const uint32_t g1 = o.group_size ? o.group_size : 32u;
   const uint32_t g2 = 32;
   const size_t smem_limit = 227 * 1024 - 5 * sizeof(unsigned long long) * soft::kMaxCirc;
@@ -433,7 +436,7 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   // when full, the warp reruns them from their start). Entries of the rerun list name a record
   // with their top bit, so a chunk stays below 2^31 items for it.
   const uint32_t rounds = lanes ? soft::lane_rounds() : 1u;
-  const bool spill = lanes && (rounds > 1 || lane_grow) && chunk < (1ull << 31);
+  const bool spill = lanes16 && (rounds > 1 || lane_grow) && chunk < (1ull << 31);
   const uint32_t sp_evict = rounds > 1 ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 4) : 0u;
   const uint32_t sp_hand = lane_grow ? (uint32_t)std::max<uint64_t>(std::min<uint64_t>(chunk, 1024), chunk / 8) : 0u;
   // the wide round: the handed-over shots continue in lanes of twice the map (their records
@@ -511,23 +514,34 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     soft_run_free(r);
     return cuda_fail(e, "cudaMemsetAsync");
   }
-  // launch parameters: one descriptor per circuit, items laid out circuit after circuit
+  // launch parameters: one descriptor per circuit, items laid out circuit after circuit. With
+  // lanes the descriptors go in order of lane map (16, 32, 64 entries, none), so that each
+  // map size's circuits hold a contiguous range of buckets for its own lane launch; each
+  // descriptor keeps its circuit's tally (a batch has no records or captured states).
+  std::vector<uint32_t> ord(n_circ);
+  for (uint32_t i = 0; i < n_circ; ++i) ord[i] = i;
+  if (lanes)
+    std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
+      return (lcap[x] ? lane_class(lcap[x]) : 3) < (lcap[y] ? lane_class(lcap[y]) : 3);
+    });
   soft::ShotParams p{};
   p.n_circ = n_circ;
   uint64_t begin = 0;
-  for (uint32_t i = 0; i < n_circ; ++i) {
-    p.circ[i] = circ_desc(circs[i], fp32, !(o.flags & SOFT_RUN_NO_PREFIX));
-    p.circ[i].item_begin = begin;
-    p.circ[i].n_shots = n_shots[i];
-    p.circ[i].first_shot = first_shots[i];
-    p.circ[i].tally = r->d_tally + 5 * i;
-    p.circ[i].fsum = fid_mode ? r->d_fsum + i : nullptr;
+  for (uint32_t k = 0; k < n_circ; ++k) {
+    const uint32_t i = ord[k];
+    p.circ[k] = circ_desc(circs[i], fp32, !(o.flags & SOFT_RUN_NO_PREFIX));
+    p.circ[k].item_begin = begin;
+    p.circ[k].n_shots = n_shots[i];
+    p.circ[k].first_shot = first_shots[i];
+    p.circ[k].tally = r->d_tally + 5 * i;
+    p.circ[k].fsum = fid_mode ? r->d_fsum + i : nullptr;
     begin += n_shots[i];
   }
-  for (uint32_t i = 0, b = 0; lanes && i < n_circ; ++i) {  // each circuit's buckets, circuit after circuit
-    p.circ[i].bucket0 = b;
-    p.circ[i].lanes_off = fits[i] ? 0u : 1u;
-    if (fits[i]) b += p.circ[i].n_events + 1;
+  for (uint32_t k = 0, b = 0; lanes && k < n_circ; ++k) {  // each circuit's buckets, circuit after circuit
+    const uint32_t i = ord[k];
+    p.circ[k].bucket0 = b;
+    p.circ[k].lanes_off = lcap[i] ? 0u : 1u;
+    if (lcap[i]) b += p.circ[k].n_events + 1;
   }
   p.circ[0].status = r->d_status;
   p.circ[0].records = r->d_records;
@@ -586,6 +600,8 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     p.al_next = p.al_count + nb;
     p.al_base = p.al_next + nb;
     p.al_nb = nb;
+    p.al_lo = 0;  // the 16-entry lanes' buckets; the larger lanes' launches set their own
+    p.al_hi = (uint32_t)nbc[0];
     p.al_grid = al_grid;
     p.lane_round = 0;
     p.lane_evict = spill && rounds > 1 ? 1u : 0u;
@@ -602,11 +618,25 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     h.sp_cap = p.sp_cap;
     h.sp_evict_cap = p.sp_evict_cap;
   }
-  soft::LaunchCfg c1{}, c2{}, cm{}, cw{};
+  soft::LaunchCfg c1{}, c2{}, cm{}, cw{}, cb[2]{};
   p.n_items = std::min(chunk, total);
-  if ((e = lanes ? soft::prepare_lanes(p, fp32, W, (int)o.blocks_per_sm, &c1)
-                 : soft::prepare_shots(p, fp32, W, g1, (int)o.blocks_per_sm, &c1)) != cudaSuccess ||
-      (wide && (e = soft::prepare_lanes(p, fp32, W, 0, &cw, true)) != cudaSuccess) ||
+  // the larger lanes (32 and 64 entries): one launch each over their circuits' buckets, after
+  // the 16-entry lanes' first round; they never evict or hand over
+  soft::ShotParams pb[2] = {p, p};
+  for (int k = 0; k < 2; ++k) {
+    pb[k].al_lo = (uint32_t)(nbc[0] + (k ? nbc[1] : 0));
+    pb[k].al_hi = pb[k].al_lo + (uint32_t)nbc[1 + k];
+    pb[k].lane_evict = pb[k].lane_hand = pb[k].lane_wide = 0;
+    pb[k].sp = nullptr;
+    pb[k].sp_cap = pb[k].sp_evict_cap = 0;
+    pb[k].lr = nullptr;
+  }
+  if ((e = !lanes ? soft::prepare_shots(p, fp32, W, g1, (int)o.blocks_per_sm, &c1)
+                  : lanes16 ? soft::prepare_lanes(p, fp32, W, (int)o.blocks_per_sm, &c1, lc16) : cudaSuccess) !=
+          cudaSuccess ||
+      (lanes && nbc[1] && (e = soft::prepare_lanes(pb[0], fp32, W, 0, &cb[0], 2 * lc16)) != cudaSuccess) ||
+      (lanes && nbc[2] && (e = soft::prepare_lanes(pb[1], fp32, W, 0, &cb[1], 4 * lc16)) != cudaSuccess) ||
+      (wide && (e = soft::prepare_lanes(p, fp32, W, 0, &cw, 2 * lc16)) != cudaSuccess) ||
       (two_pass && (e = soft::prepare_shots(q, fp32, W, g2, (int)o.blocks_per_sm, &c2)) != cudaSuccess) ||
       (mid_pass && (e = soft::prepare_shots(m, fp32, W, g2, (int)o.blocks_per_sm, &cm)) != cudaSuccess)) {
     soft_run_free(r);
@@ -648,8 +678,20 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
     if ((err = mark(lanes)) != cudaSuccess) return err;
     if (spill && (err = cudaMemsetAsync(r->d_lr, 0, n_lr * sizeof(unsigned long long), st)) != cudaSuccess)
       return err;
-    if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
-    r->launches++;
+    if (!lanes || lanes16) {
+      if ((err = soft::launch_prepared(c1, a, st)) != cudaSuccess) return err;
+      r->launches++;
+    }
+    // the larger lanes, before any later round re-buckets (it clears every bucket's counters)
+    for (int k = 0; lanes && k < 2; ++k)
+      if (nbc[1 + k]) {
+        soft::ShotParams ab = pb[k];
+        ab.n_items = cnt;
+        ab.item_base = base;
+        if (dev_base) ab.item_base_dev = r->d_work + 3;
+        if ((err = soft::launch_prepared(cb[k], ab, st)) != cudaSuccess) return err;
+        r->launches++;
+      }
     // later rounds: the evicted shots, bucketed by the event they resume at
     for (uint32_t rd = 1; spill && rd < rounds; ++rd) {
       soft::ShotParams ar = a;

@@ -83,6 +83,7 @@ struct ShotParams {
                         // slot in the warp pass's list (al_nb + 1 words per block)
   uint32_t al_grid;     // pre-pass blocks (each bins a contiguous range of items)
   uint32_t al_nb;       // buckets over all circuits of the run
+  uint32_t al_lo, al_hi;  // a lane launch's buckets [al_lo, al_hi) (circuits of one lane map size)
   // lane-per-shot rounds: a warp left with few active lanes evicts their shots to the spill
   // pool; the next round buckets them by the event they resume at and packs them into warps
   uint32_t lane_round;        // 0: shots from their start buckets; r >= 1: shots evicted before round r
@@ -136,10 +137,14 @@ size_t lane_spill_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap);
 uint32_t lane_rounds();
 uint32_t lane_max_buckets();  // lane-per-shot runs hold at most this many buckets (events + 1 per circuit)
 uint32_t lane_prepass_grid();  // blocks of the bucketing pre-pass (al_base holds this many rows)
-// wide: the wide round's kernel (twice the lane map) instead of the first rounds'
+// cap: the lane map's entries: lane_map_cap() for the first rounds, twice that for the wide
+// round, or lane_first_cap()'s answer for circuits of larger maps
 cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg,
-                          bool wide = false);
+                          uint32_t cap);
 uint32_t lane_map_cap();
+// The smallest lane map (16, 32 or, with FP32 coefficients, 64 entries) that holds a circuit
+// whose noiseless run's maps reach max_n entries in max_d directions; 0 if none does.
+uint32_t lane_first_cap(uint32_t max_n, uint32_t max_d, int fp32);
 uint32_t lane_map_dim();  // directions of a first-round lane's affine map (lane_map_cap = 2^lane_map_dim)
 // After launch_prefix: the affine form of each snapshot of the run (events [0, stop[0]]),
 // on the same stream; stop[3] (zeroed before) receives the largest dimension.

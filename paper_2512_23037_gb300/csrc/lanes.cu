@@ -51,6 +51,10 @@ static_assert(kLaneRounds >= 1 && kLaneRounds <= 8, "lane rounds");
 // The wide round's lanes: shots handed over by the first rounds continue in lanes
 // of twice the map.
 constexpr uint32_t kWideCap = 2 * kLaneCap;
+// First-pass lanes for circuits whose noiseless maps outgrow kLaneCap: 32 entries (kWideCap)
+// or, with FP32 coefficients, 64 entries. These never evict or hand over: a shot whose map
+// outgrows them runs again from its start in a warp.
+constexpr uint32_t kLaneBigCap = 4 * kLaneCap;
 
 // Lane map in affine form. The keys of a shot's coefficient map lie in an affine
 // space alpha0 ^ span(B[0..d)) of dimension d <= kDim (Sec. II-C: the support of v
@@ -66,7 +70,20 @@ constexpr uint32_t kWideCap = 2 * kLaneCap;
 // only: per entry only values are read and written, and no key is stored. The live
 // slots are the paper's sparse map: updates, pruning at tau and the overflow rule
 // apply to them exactly as to a sparse map.
-__host__ __device__ constexpr uint32_t lane_dim(uint32_t cap) { return cap <= 16u ? 4u : 5u; }
+__host__ __device__ constexpr uint32_t lane_dim(uint32_t cap) { return cap <= 16u ? 4u : cap <= 32u ? 5u : 6u; }
+// A set of slots: one bit per slot of the lane's cube (32 bits up to 32 slots, 64 for 64).
+template <uint32_t Cap>
+struct SlotSet {
+  using T = uint32_t;
+};
+template <>
+struct SlotSet<64> {
+  using T = unsigned long long;
+};
+__device__ __forceinline__ uint32_t mffs(uint32_t m) { return (uint32_t)__ffs(m); }
+__device__ __forceinline__ uint32_t mffs(unsigned long long m) { return (uint32_t)__ffsll((long long)m); }
+__device__ __forceinline__ uint32_t mpopc(uint32_t m) { return (uint32_t)__popc(m); }
+__device__ __forceinline__ uint32_t mpopc(unsigned long long m) { return (uint32_t)__popcll(m); }
 
 template <typename R, int W, uint32_t Cap>
 __host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
@@ -74,25 +91,37 @@ __host__ __device__ inline size_t lane_warp_bytes(uint32_t rw) {
   return (size_t)Cap * sizeof(Cx<R>) * 32 + (size_t)(1 + 2 * lane_dim(Cap)) * W * 8 * 32 + (size_t)rw * 8 * 32;
 }
 
-// Slot masks over a cube of up to 32 slots: the slots whose index has bit k set.
-__device__ __forceinline__ uint32_t slot_bit_mask(uint32_t k) {
-  return k == 0u ? 0xAAAAAAAAu : k == 1u ? 0xCCCCCCCCu : k == 2u ? 0xF0F0F0F0u : k == 3u ? 0xFF00FF00u : 0xFFFF0000u;
+// Slot masks over a cube of up to 32 (M = uint32_t) or 64 slots: the slots whose index has
+// bit k set.
+template <typename M>
+__device__ __forceinline__ M slot_bit_mask(uint32_t k) {
+  if (sizeof(M) == 4)
+    return (M)(k == 0u ? 0xAAAAAAAAu : k == 1u ? 0xCCCCCCCCu : k == 2u ? 0xF0F0F0F0u : k == 3u ? 0xFF00FF00u : 0xFFFF0000u);
+  return (M)(k == 0u   ? 0xAAAAAAAAAAAAAAAAull
+             : k == 1u ? 0xCCCCCCCCCCCCCCCCull
+             : k == 2u ? 0xF0F0F0F0F0F0F0F0ull
+             : k == 3u ? 0xFF00FF00FF00FF00ull
+             : k == 4u ? 0xFFFF0000FFFF0000ull
+                       : 0xFFFFFFFF00000000ull);
 }
 // The slots s with parity(s & g) = 1.
-__device__ __forceinline__ uint32_t slot_par_mask(uint32_t g) {
-  uint32_t m = 0;
+template <typename M>
+__device__ __forceinline__ M slot_par_mask(uint32_t g) {
+  M m = 0;
 #pragma unroll
-  for (uint32_t k = 0; k < 5u; ++k)
-    if ((g >> k) & 1u) m ^= slot_bit_mask(k);
+  for (uint32_t k = 0; k < (sizeof(M) == 4 ? 5u : 6u); ++k)
+    if ((g >> k) & 1u) m ^= slot_bit_mask<M>(k);
   return m;
 }
 // A slot set moved by s -> s ^ c.
-__device__ __forceinline__ uint32_t slot_xor_perm(uint32_t L, uint32_t c) {
+template <typename M>
+__device__ __forceinline__ M slot_xor_perm(M L, uint32_t c) {
 #pragma unroll
-  for (uint32_t k = 0; k < 5u; ++k)
+  for (uint32_t k = 0; k < (sizeof(M) == 4 ? 5u : 6u); ++k)
     if ((c >> k) & 1u) {
-      const uint32_t M = slot_bit_mask(k), sh = 1u << k;
-      L = ((L & M) >> sh) | ((L & ~M) << sh);
+      const M B = slot_bit_mask<M>(k);
+      const uint32_t sh = 1u << k;
+      L = ((L & B) >> sh) | ((L & ~B) << sh);
     }
   return L;
 }
@@ -115,6 +144,7 @@ struct LaneShot {
   static constexpr uint32_t kDim = lane_dim(Cap);
   static_assert(Cap == (1u << kDim), "a lane holds a cube of slots");
   static constexpr uint32_t kRowB = 1, kRowD = 1 + kDim;  // rows: alpha0, B[0..kDim), Dual[0..kDim)
+  using Mask = typename SlotSet<Cap>::T;  // a set of the cube's slots
   const ShotParams &P;
   const CircDev *C;
   uint32_t lane;
@@ -123,7 +153,8 @@ struct LaneShot {
   uint64_t *rec;   // [w][lane]
   // per-lane shot state
   uint64_t shot;
-  uint32_t d, live;
+  uint32_t d;
+  Mask live;
   uint64_t sd[W], ss[W];
   uint32_t nxt, cur, kblk, w2;
   int status, chain, logical, lastm;
@@ -165,8 +196,11 @@ struct LaneShot {
   __device__ __forceinline__ uint32_t row_bit(uint32_t r, uint32_t p) const {
     return (uint32_t)((row(r, (W == 2 && p >= 64u) ? W - 1 : 0) >> (p & 63u)) & 1ull);
   }
-  __device__ __forceinline__ uint32_t cube() const { return d >= 5u ? 0xFFFFFFFFu : (1u << (1u << d)) - 1u; }
-  __device__ __forceinline__ uint32_t nnz() const { return (uint32_t)__popc(live); }
+  __device__ __forceinline__ Mask cube() const {
+    if (sizeof(Mask) == 4) return (Mask)(d >= 5u ? 0xFFFFFFFFu : (1u << (1u << d)) - 1u);
+    return (Mask)(d >= 6u ? ~0ull : (1ull << (1u << d)) - 1ull);
+  }
+  __device__ __forceinline__ uint32_t nnz() const { return mpopc(live); }
 
   // g . alpha0 into g0; bit k of the result: g . B[k]
   __device__ uint32_t parities(const uint64_t *g, uint32_t &g0) const {
@@ -249,12 +283,12 @@ struct LaneShot {
   __device__ void remove_dim(uint32_t q, uint32_t g, uint32_t t) {
     remove_rows(q, g, t);
     const uint32_t lo = (1u << q) - 1u;
-    uint32_t nl = 0;
+    Mask nl = 0;
 #pragma unroll 1
-    for (uint32_t m = live; m; m &= m - 1u) {  // ascending: a slot moves down onto a vacated one
-      const uint32_t s = __ffs(m) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
+    for (Mask m = live; m; m &= m - (Mask)1) {  // ascending: a slot moves down onto a vacated one
+      const uint32_t s = mffs(m) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
       if (s2 != s) set_val(s2, val(s));
-      nl |= 1u << s2;
+      nl |= (Mask)1 << s2;
     }
     live = nl;
   }
@@ -280,14 +314,14 @@ struct LaneShot {
   __device__ __forceinline__ void restrict_to(uint32_t g) {
     g &= (d >= 32u) ? 0xFFFFFFFFu : ((1u << d) - 1u);
     if (!g || !live) return;
-    const uint32_t t = spar(__ffs(live) - 1, g);
+    const uint32_t t = spar(mffs(live) - 1, g);
     remove_dim(31u - __clz(g), g, t);
   }
   // drop the coordinates no live slot uses
   __device__ void compact_dead(uint32_t &gl) {
 #pragma unroll 1
     for (uint32_t k = d; k-- > 0;)
-      if (!(live & slot_bit_mask(k))) {
+      if (!(live & slot_bit_mask<Mask>(k))) {
         remove_dim(k, 1u << k, 0);
         gl = (gl & ((1u << k) - 1u)) | ((gl >> (k + 1u)) << k);  // the parities follow the coordinates
       }
@@ -330,7 +364,7 @@ struct LaneShot {
         c |= 1u << (d - 1u);
       }
       set_val(c, val_at(i));
-      live |= 1u << c;
+      live |= (Mask)1 << c;
     }
     return true;
   }
@@ -400,7 +434,7 @@ struct LaneShot {
     }
 #pragma unroll 1
     for (uint32_t w = 0; w < C->rw; ++w) rec[(size_t)w * 32 + lane] = __ldg(&r_in[w]);
-    const uint2 dl = __ldg(reinterpret_cast<const uint2 *>(&a->d));
+    const uint2 dl = __ldg(reinterpret_cast<const uint2 *>(&a->d));  // d and the low word of live
     d = 0;
     live = 0;
     if (dl.x > kDim) {
@@ -408,7 +442,8 @@ struct LaneShot {
       return;
     }
     d = dl.x;
-    live = dl.y;
+    live = (Mask)dl.y;  // (no slot at or above 2^kDim is live)
+    if (sizeof(Mask) == 8) live |= (Mask)__ldg(&a->live_hi) << 16 << 16;
 #pragma unroll
     for (int w = 0; w < W; ++w) set_row(0, w, __ldg(&a->rows[0][w]));
 #pragma unroll 1
@@ -419,8 +454,8 @@ struct LaneShot {
         set_row(kRowD + k, w, __ldg(&a->rows[1 + kSnapDim + k][w]));
       }
 #pragma unroll 1
-    for (uint32_t m = live; m; m &= m - 1u) {
-      const uint32_t j = __ffs(m) - 1;
+    for (Mask m = live; m; m &= m - (Mask)1) {
+      const uint32_t j = mffs(m) - 1;
       set_val(j, a->v[j]);
     }
   }
@@ -442,8 +477,8 @@ struct LaneShot {
     for (uint32_t w = 0; w < C->rw; ++w) S.rec[w * c + r] = rec[(size_t)w * 32 + lane];
     uint32_t i = 0;
 #pragma unroll 1
-    for (uint32_t m = live; m && i < kLaneCap; m &= m - 1u, ++i) {
-      const uint32_t s = __ffs(m) - 1;
+    for (Mask m = live; m && i < kLaneCap; m &= m - (Mask)1, ++i) {
+      const uint32_t s = mffs(m) - 1;
       const Key<W> k = key_of(s);
 #pragma unroll
       for (int w = 0; w < W; ++w) S.keys[((size_t)i * W + w) * c + r] = k.w[w];
@@ -500,8 +535,8 @@ struct LaneShot {
     P.st_signs[off * 4 + 3] = (W == 2) ? ss[W - 1] : 0ull;
     uint32_t i = 0;
 #pragma unroll 1
-    for (uint32_t m = live; m && i < P.st_stride; m &= m - 1u, ++i) {
-      const uint32_t s = __ffs(m) - 1;
+    for (Mask m = live; m && i < P.st_stride; m &= m - (Mask)1, ++i) {
+      const uint32_t s = mffs(m) - 1;
       const Key<W> k = key_of(s);
       const Cx<R> v = val(s);
       const size_t o = (size_t)off * P.st_stride + i;
@@ -517,8 +552,8 @@ struct LaneShot {
     uint32_t g0;
     const uint32_t gl = parities(gamma, g0);
 #pragma unroll 1
-    for (uint32_t m = live; m; m &= m - 1u) {
-      const uint32_t s = __ffs(m) - 1;
+    for (Mask m = live; m; m &= m - (Mask)1) {
+      const uint32_t s = mffs(m) - 1;
       set_val(s, ipow(val(s), e + 2u * (g0 ^ spar(s, gl))));
     }
     xor_row(0, beta);
@@ -587,16 +622,16 @@ struct LaneShot {
       b = Cx<R>{(R)d1.x, (R)d1.y};
     }
     const Cx<R> bq = ipow(b, e), bn = Cx<R>{negr(bq.x), negr(bq.y)};
-    uint32_t drop = 0;
+    Mask drop = 0;
     if (diag) {
       const Cx<R> c0 = cadd(a, bq), c1 = cadd(a, bn);
 #pragma unroll 1
-      for (uint32_t m = live; m; m &= m - 1u) {
-        const uint32_t s = __ffs(m) - 1;
+      for (Mask m = live; m; m &= m - (Mask)1) {
+        const uint32_t s = mffs(m) - 1;
         const Cx<R> nv = cmul((g0 ^ spar(s, gl)) ? c1 : c0, val(s));
         const bool sm = pt.small(nv);
         if (!sm) set_val(s, nv);
-        drop |= (uint32_t)sm << s;
+        drop |= (Mask)sm << s;
       }
       live &= ~drop;
       return;
@@ -624,12 +659,12 @@ struct LaneShot {
       c |= 1u << (d - 1u);
       gl |= row_par(kRowB + d - 1u, gamma) << (d - 1u);
     }
-    const uint32_t spread = live | slot_xor_perm(live, c);
-    const uint32_t lead = spread & ~slot_bit_mask(__ffs(c) - 1) & cube();  // one member of each pair
+    const Mask spread = live | slot_xor_perm<Mask>(live, c);
+    const Mask lead = spread & ~slot_bit_mask<Mask>(__ffs(c) - 1) & cube();  // one member of each pair
 #pragma unroll 1
-    for (uint32_t m = lead; m; m &= m - 1u) {
-      const uint32_t s = __ffs(m) - 1, t = s ^ c;
-      const uint32_t ls = (live >> s) & 1u, lt = (live >> t) & 1u;
+    for (Mask m = lead; m; m &= m - (Mask)1) {
+      const uint32_t s = mffs(m) - 1, t = s ^ c;
+      const uint32_t ls = (uint32_t)(live >> s) & 1u, lt = (uint32_t)(live >> t) & 1u;
       const Cx<R> vs = ls ? val(s) : Cx<R>{0, 0}, vt = lt ? val(t) : Cx<R>{0, 0};
       const Cx<R> bs = (g0 ^ spar(s, gl)) ? bn : bq, bt = (g0 ^ spar(t, gl)) ? bn : bq;
       Cx<R> ns, nt;
@@ -646,7 +681,7 @@ struct LaneShot {
       const bool ss_ = pt.small(ns), st_ = pt.small(nt);
       if (!ss_) set_val(s, ns);
       if (!st_) set_val(t, nt);
-      drop |= ((uint32_t)ss_ << s) | ((uint32_t)st_ << t);
+      drop |= ((Mask)ss_ << s) | ((Mask)st_ << t);
     }
     live = spread & ~drop;
     if (nnz() > C->cap) status = LS_OVF;  // the overflow rule, for circuits whose cap is below the lane's
@@ -664,12 +699,12 @@ struct LaneShot {
       return 1;
     }
     const uint32_t sgn = e >> 1;
-    const uint32_t pm = slot_par_mask(gl) & cube();
-    const uint32_t neg = live & (((sgn ^ g0) & 1u) ? ~pm : pm);  // slots with eigenvalue -1
-    const uint32_t pos = live & ~neg;
+    const Mask pm = slot_par_mask<Mask>(gl) & cube();
+    const Mask neg = live & (((sgn ^ g0) & 1u) ? ~pm : pm);  // slots with eigenvalue -1
+    const Mask pos = live & ~neg;
     int m;
     R sc = (R)1;
-    uint32_t keep;
+    Mask keep;
     if (!neg || !pos) {  // decided (all eigenvalues equal): integer test only, no scaling
       m = neg ? -1 : 1;
       keep = live;
@@ -677,8 +712,8 @@ struct LaneShot {
     } else {
       double sp = 0.0, sm = 0.0;
 #pragma unroll 1
-      for (uint32_t mm = live; mm; mm &= mm - 1u) {
-        const uint32_t s = __ffs(mm) - 1;
+      for (Mask mm = live; mm; mm &= mm - (Mask)1) {
+        const uint32_t s = mffs(mm) - 1;
         const double a2 = pnorm(val(s));
         if ((neg >> s) & 1u) sm += a2;
         else sp += a2;
@@ -691,15 +726,15 @@ struct LaneShot {
     // scaled straight into its slot of the restricted map. A decided outcome goes through
     // the same loop with the scale 1 (exact; no kept value is below tau), so that the
     // restriction is inlined once (w42 FP32: 676 -> 708 M shots/s)
-    const uint32_t q = 31u - __clz(gl), lo = (1u << q) - 1u, t = spar(__ffs(keep) - 1, gl);
-    uint32_t nl = 0;
+    const uint32_t q = 31u - __clz(gl), lo = (1u << q) - 1u, t = spar(mffs(keep) - 1, gl);
+    Mask nl = 0;
 #pragma unroll 1
-    for (uint32_t mm = keep; mm; mm &= mm - 1u) {  // ascending: a write lands on a slot already read
-      const uint32_t s = __ffs(mm) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
+    for (Mask mm = keep; mm; mm &= mm - (Mask)1) {  // ascending: a write lands on a slot already read
+      const uint32_t s = mffs(mm) - 1, s2 = (s & lo) | ((s >> (q + 1u)) << q);
       const Cx<R> v = cscale(val(s), sc);
       if (!pt.small(v)) {
         set_val(s2, v);
-        nl |= 1u << s2;
+        nl |= (Mask)1 << s2;
       }
     }
     if (nl) remove_rows(q, gl, t);
@@ -746,17 +781,17 @@ struct LaneShot {
     uint32_t bp = 0;  // bit k: B[k][p]
 #pragma unroll 1
     for (uint32_t k = 0; k < d; ++k) bp |= row_bit(kRowB + k, p) << k;
-    const uint32_t cb = cube();
-    const uint32_t kb = (row_bit(0, p) ? ~slot_par_mask(bp) : slot_par_mask(bp)) & cb;  // slots whose key has bit p
+    const Mask cb = cube();
+    const Mask kb = (row_bit(0, p) ? ~slot_par_mask<Mask>(bp) : slot_par_mask<Mask>(bp)) & cb;  // slots whose key has bit p
     uint64_t rr[W];
     const uint32_t c = coords(ep, rr);
     const bool lone = wnonzero<W>(rr);  // e_p outside the span: no entry has a partner
-    const uint32_t spread = lone ? live : (live | slot_xor_perm(live, c));
-    const uint32_t lead = lone ? live : (spread & ~kb);  // a0 members (lone: every entry)
+    const Mask spread = lone ? live : (live | slot_xor_perm<Mask>(live, c));
+    const Mask lead = lone ? live : (spread & ~kb);  // a0 members (lone: every entry)
     double sp = 0.0, sm = 0.0;
 #pragma unroll 1
-    for (uint32_t m = lead; m; m &= m - 1u) {
-      const uint32_t s = __ffs(m) - 1;
+    for (Mask m = lead; m; m &= m - (Mask)1) {
+      const uint32_t s = mffs(m) - 1;
       Cx<R> v0{0, 0}, x1{0, 0};
       if (lone) {
         if ((kb >> s) & 1u) x1 = ipow(val(s), e2 + 2u * (g20 ^ spar(s, gl2)));
@@ -771,10 +806,10 @@ struct LaneShot {
     }
     const int m = pick(ord, sp, sm);
     const R sc = inv_sqrt(2.0 * (m == 1 ? sp : sm));
-    uint32_t nl = 0;
+    Mask nl = 0;
 #pragma unroll 1
-    for (uint32_t mm = lead; mm; mm &= mm - 1u) {
-      const uint32_t s = __ffs(mm) - 1;
+    for (Mask mm = lead; mm; mm &= mm - (Mask)1) {
+      const uint32_t s = mffs(mm) - 1;
       Cx<R> v0{0, 0}, x1{0, 0};
       if (lone) {
         if ((kb >> s) & 1u) x1 = ipow(val(s), e2 + 2u * (g20 ^ spar(s, gl2)));
@@ -787,7 +822,7 @@ struct LaneShot {
       const Cx<R> nv = cscale(m == 1 ? cadd(v0, x1) : csub(v0, x1), sc);
       if (!pt.small(nv)) {
         set_val(s, nv);
-        nl |= 1u << s;
+        nl |= (Mask)1 << s;
       }
     }
     live = nl;
@@ -930,7 +965,8 @@ __global__ void snap_affine_kernel(unsigned char *traj, uint32_t n_snap, uint32_
   for (uint32_t r = 0; r < 1 + 2 * kSnapDim; ++r)
     for (int w = 0; w < W; ++w) rw_[r][w] = 0ull;
   for (uint32_t j = 0; j < (1u << kSnapDim); ++j) out->v[j] = Cx<R>{0, 0};
-  uint32_t d = 0, live = 0;
+  uint32_t d = 0;
+  unsigned long long live = 0;
   bool ok = true;
   if (n) {
     for (int w = 0; w < W; ++w) rw_[0][w] = k_in[w];
@@ -963,12 +999,13 @@ __global__ void snap_affine_kernel(unsigned char *traj, uint32_t n_snap, uint32_
       ++d;
     }
     out->v[c] = v_in[i];
-    live |= 1u << c;
+    live |= 1ull << c;
   }
   for (uint32_t r = 0; r < 1 + 2 * kSnapDim; ++r)
     for (int w = 0; w < W; ++w) out->rows[r][w] = rw_[r][w];
   out->d = ok ? d : 0xFFFFFFFFu;
-  out->live = live;
+  out->live_lo = (uint32_t)live;
+  out->live_hi = (uint32_t)(live >> 32);
   atomicMax(&stop[3], ok ? d : 0xFFu);
 }
 
@@ -1106,7 +1143,7 @@ __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_cons
 // 3-4), FP64: 5 (its shared memory allows 5; 272.8 M against 266.7 M at 4).
 template <typename R, uint32_t Cap>
 constexpr int kLaneMinBlocks() {
-  return sizeof(R) == 4 ? (Cap <= 16 ? 8 : 3) : 5;
+  return sizeof(R) == 4 ? (Cap <= 16 ? 8 : Cap <= 32 ? 3 : 2) : 5;
 }
 
 // Multi: the run holds several circuits (a warp serves one at a time); the single-
@@ -1127,11 +1164,14 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
       P.lane_round ? P.lr[3 + 2 * P.lane_round] : (P.n_items_dev ? *P.n_items_dev : P.n_items);
   const unsigned long long rec0 = P.lane_round ? P.lr[2 + 2 * P.lane_round] : 0ull;
   const Spill<R, W> S(P.sp, P.sp_cap, P.rw_max);
-  const uint32_t nb = P.al_nb;
-  // warps start spread evenly over all buckets, so that they meet buckets that still hold shots
+  // a batch's launch serves the buckets [P.al_lo, P.al_hi) of its lane map size's circuits
+  // (read from the launch parameters where used, so that no register holds them through the
+  // loop); a single circuit's, all of them
+  if (Multi && P.al_hi <= P.al_lo) return;
+  // warps start spread evenly over the buckets, so that they meet buckets that still hold shots
   const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x / 32) + warp;
   const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x / 32);
-  uint32_t g = (uint32_t)((gw * (unsigned long long)nb) / nw);
+  uint32_t g = (Multi ? P.al_lo : 0u) + (uint32_t)((gw * (unsigned long long)(Multi ? P.al_hi - P.al_lo : P.al_nb)) / nw);
   uint32_t ci = Multi ? circ_of_bucket(P, g) : 0u;
   const CircDev *C = &P.circ[ci];
   uint32_t n_ev = C->n_events, e = Multi ? g - C->bucket0 : g;
@@ -1147,7 +1187,7 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
   };
   bool active = false;
   uint32_t item = 0;
-  const unsigned long long limit = (n_items + 2ull) * (nb + 2ull) + 64ull;
+  const unsigned long long limit = (n_items + 2ull) * ((Multi ? P.al_hi - P.al_lo : P.al_nb) + 2ull) + 64ull;
   for (unsigned long long guard = 0; guard < limit; ++guard) {
     g = Multi ? C->bucket0 + e : e;
     // idle lanes claim shots that start at event e of circuit ci (one atomic per warp)
@@ -1253,9 +1293,10 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
       // all lanes idle: the next bucket of any circuit (cyclically) that still has shots, or stop
       uint32_t found = 0xFFFFFFFFu;
       if (lane == 0) {
-        const uint32_t g1 = (Multi ? C->bucket0 : 0u) + en;
+        const uint32_t b_lo = Multi ? P.al_lo : 0u, nb = Multi ? P.al_hi - P.al_lo : P.al_nb;
+        const uint32_t g1 = (Multi ? C->bucket0 : 0u) + en - b_lo;
         for (uint32_t k = 0; k < nb; ++k) {
-          const uint32_t c = (g1 + k) % nb;
+          const uint32_t c = b_lo + (g1 + k) % nb;
           if (*(volatile unsigned int *)&P.al_next[c] < __ldg(&P.al_start[c + 1]) - __ldg(&P.al_start[c])) {
             found = c;
             break;
@@ -1286,19 +1327,26 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
 
 }  // namespace
 
-size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw, bool wide) {
-  size_t per;
-  if (wide)
-    per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1, kWideCap>(rw) : lane_warp_bytes<float, 2, kWideCap>(rw))
-               : (W == 1 ? lane_warp_bytes<double, 1, kWideCap>(rw) : lane_warp_bytes<double, 2, kWideCap>(rw));
-  else
-    per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1, kLaneCap>(rw) : lane_warp_bytes<float, 2, kLaneCap>(rw))
-               : (W == 1 ? lane_warp_bytes<double, 1, kLaneCap>(rw) : lane_warp_bytes<double, 2, kLaneCap>(rw));
+template <uint32_t Cap>
+static size_t lane_smem_bytes_t(int fp32, uint32_t W, uint32_t rw) {
+  const size_t per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1, Cap>(rw) : lane_warp_bytes<float, 2, Cap>(rw))
+                          : (W == 1 ? lane_warp_bytes<double, 1, Cap>(rw) : lane_warp_bytes<double, 2, Cap>(rw));
   return per * (kLaneBlock / 32);
+}
+size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap) {
+  return cap == kLaneBigCap ? lane_smem_bytes_t<kLaneBigCap>(fp32, W, rw)
+         : cap == kWideCap  ? lane_smem_bytes_t<kWideCap>(fp32, W, rw)
+                            : lane_smem_bytes_t<kLaneCap>(fp32, W, rw);
 }
 
 uint32_t lane_map_cap() { return kLaneCap; }
 uint32_t lane_map_dim() { return lane_dim(kLaneCap); }
+uint32_t lane_first_cap(uint32_t max_n, uint32_t max_d, int fp32) {
+  if (max_n <= kLaneCap && max_d <= lane_dim(kLaneCap)) return kLaneCap;
+  if (max_n <= kWideCap && max_d <= lane_dim(kWideCap)) return kWideCap;
+  if (fp32 && max_n <= kLaneBigCap && max_d <= lane_dim(kLaneBigCap)) return kLaneBigCap;
+  return 0;
+}
 
 cudaError_t launch_snap_affine(unsigned char *traj, uint32_t n_snap, uint32_t rw, int fp32, uint32_t W,
                                uint32_t *stop, cudaStream_t st) {
@@ -1349,26 +1397,30 @@ cudaError_t launch_lane_resume_prepass(const ShotParams &p, int fp32, uint32_t W
 
 cudaError_t launch_lane_prepass(const ShotParams &p, cudaStream_t st) { return launch_bin<false, float, 1>(p, st); }
 
-cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg, bool wide) {
+template <uint32_t Cap>
+static const void *lane_kernel_for(int fp32, uint32_t W, bool multi) {
+  if (fp32)
+    return W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<float, 1, true, Cap>)
+                           : reinterpret_cast<const void *>(lane_kernel<float, 1, false, Cap>))
+                  : (multi ? reinterpret_cast<const void *>(lane_kernel<float, 2, true, Cap>)
+                           : reinterpret_cast<const void *>(lane_kernel<float, 2, false, Cap>));
+  if constexpr (Cap == kLaneBigCap) {
+    return nullptr;  // 64-entry lanes: FP32 only (an FP64 warp's map would not leave room for two blocks)
+  } else {
+    return W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<double, 1, true, Cap>)
+                           : reinterpret_cast<const void *>(lane_kernel<double, 1, false, Cap>))
+                  : (multi ? reinterpret_cast<const void *>(lane_kernel<double, 2, true, Cap>)
+                           : reinterpret_cast<const void *>(lane_kernel<double, 2, false, Cap>));
+  }
+}
+
+cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_per_sm, LaunchCfg *cfg, uint32_t cap) {
   const bool multi = p.n_circ > 1;
-  constexpr uint32_t C1 = kLaneCap, C2 = kWideCap;
-  const void *kern;
-  if (wide) {  // single-circuit runs only
-    if (multi) return cudaErrorInvalidConfiguration;
-    kern = fp32 ? (W == 1 ? reinterpret_cast<const void *>(lane_kernel<float, 1, false, C2>)
-                          : reinterpret_cast<const void *>(lane_kernel<float, 2, false, C2>))
-                : (W == 1 ? reinterpret_cast<const void *>(lane_kernel<double, 1, false, C2>)
-                          : reinterpret_cast<const void *>(lane_kernel<double, 2, false, C2>));
-  } else
-    kern = fp32 ? (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<float, 1, true, C1>)
-                                   : reinterpret_cast<const void *>(lane_kernel<float, 1, false, C1>))
-                          : (multi ? reinterpret_cast<const void *>(lane_kernel<float, 2, true, C1>)
-                                   : reinterpret_cast<const void *>(lane_kernel<float, 2, false, C1>)))
-                : (W == 1 ? (multi ? reinterpret_cast<const void *>(lane_kernel<double, 1, true, C1>)
-                                   : reinterpret_cast<const void *>(lane_kernel<double, 1, false, C1>))
-                          : (multi ? reinterpret_cast<const void *>(lane_kernel<double, 2, true, C1>)
-                                   : reinterpret_cast<const void *>(lane_kernel<double, 2, false, C1>)));
-  const size_t smem = lane_smem_bytes(fp32, W, p.rw_max, wide);
+  const void *kern = cap == kLaneBigCap ? lane_kernel_for<kLaneBigCap>(fp32, W, multi)
+                     : cap == kWideCap  ? lane_kernel_for<kWideCap>(fp32, W, multi)
+                                        : lane_kernel_for<kLaneCap>(fp32, W, multi);
+  if (!kern) return cudaErrorInvalidConfiguration;
+  const size_t smem = lane_smem_bytes(fp32, W, p.rw_max, cap);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -82,13 +82,13 @@ struct SnapHdr {
 constexpr uint32_t kSnapMax = 64;
 
 // The snapshot's map in the affine form of the lane kernels (lanes.cu): d directions
-// (0xFFFFFFFF: more than kSnapDim), the live slots, rows alpha0, B[0..kSnapDim),
-// Dual[0..kSnapDim), and the values of 2^kSnapDim slots (zero where not live). Computed
-// once per circuit and precision, after the noiseless run.
-constexpr uint32_t kSnapDim = 5;
+// (0xFFFFFFFF: more than kSnapDim), the live slots (bit s: slot s), rows alpha0,
+// B[0..kSnapDim), Dual[0..kSnapDim), and the values of 2^kSnapDim slots (zero where not
+// live). Computed once per circuit and precision, after the noiseless run.
+constexpr uint32_t kSnapDim = 6;
 template <typename R, int W>
 struct SnapAffine {
-  uint32_t d, live;
+  uint32_t d, live_lo, live_hi, pad;  // live: the slot set, in two words
   uint64_t rows[1 + 2 * kSnapDim][W];
   Cx<R> v[1u << kSnapDim];
 };
