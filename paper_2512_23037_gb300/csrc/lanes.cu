@@ -12,8 +12,10 @@
 // to a spill record, which the warp-per-shot kernel's next pass resumes. The
 // per-shot arithmetic is that of the warp-per-shot kernel (the same formulas,
 // pruning thresholds and outcome rule), entry by entry. In a batch, each circuit
-// has its own range of buckets and a warp serves one circuit at a time; the shots
-// of circuits whose maps outgrow a lane go straight to the warp pass.
+// has its own range of buckets and a warp serves one circuit at a time. Circuits
+// whose noiseless maps outgrow kLaneCap get lanes of 32 or (FP32) 64 entries, one
+// launch per size over that size's buckets; the shots of circuits beyond those go
+// straight to the warp pass.
 //
 // Most shots end at the first detector after their first error, but a few run to
 // the end of the circuit, and they would hold a warp with a few active lanes. So a
@@ -1148,7 +1150,8 @@ constexpr int kLaneMinBlocks() {
 
 // Multi: the run holds several circuits (a warp serves one at a time); the single-
 // circuit instantiation keeps circuit 0 and bucket offset 0 as constants. Cap: map
-// entries per lane (kLaneCap in the first rounds, kWideCap in the wide round).
+// entries per lane (kLaneCap in the first rounds, kWideCap in the wide round, or
+// kWideCap / kLaneBigCap as the first pass of circuits with larger noiseless maps).
 template <typename R, int W, bool Multi, uint32_t Cap>
 __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
