@@ -1194,6 +1194,23 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
   for (unsigned long long guard = 0; guard < limit; ++guard) {
     g = Multi ? C->bucket0 + e : e;
     // idle lanes claim shots that start at event e of circuit ci (one atomic per warp)
+    // the event's header and body, loaded before the claims so that their latency overlaps
+    // the claims' (w42 FP32: 710.8 -> 715.0 M shots/s)
+    const Ev<W> *E = evs + e;
+    uint4 hdr = make_uint4(0u, 0u, 0u, 0u);
+    uint64_t body[4 * W];
+#pragma unroll
+    for (int k = 0; k < 4 * W; ++k) body[k] = 0ull;
+    if (e < n_ev) {  // (no event past the last)
+      hdr = __ldg(reinterpret_cast<const uint4 *>(E));
+      const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(&E->dsd[0]);
+#pragma unroll
+      for (int k = 0; k < 2 * W; ++k) {
+        const ulonglong2 v = __ldg(bp + k);
+        body[2 * k] = v.x;
+        body[2 * k + 1] = v.y;
+      }
+    }
     const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !active);
     if (idle) {
       const uint32_t b0 = __ldg(&P.al_start[g]), sz = __ldg(&P.al_start[g + 1]) - b0;
@@ -1215,16 +1232,6 @@ __global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_ker
       }
     }
     if (e < n_ev && __any_sync(0xFFFFFFFFu, active && s.status == LS_RUN)) {
-      const Ev<W> *E = evs + e;
-      const uint4 hdr = __ldg(reinterpret_cast<const uint4 *>(E));
-      uint64_t body[4 * W];
-      const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(&E->dsd[0]);
-#pragma unroll
-      for (int k = 0; k < 2 * W; ++k) {
-        const ulonglong2 v = __ldg(bp + k);
-        body[2 * k] = v.x;
-        body[2 * k + 1] = v.y;
-      }
       if (active && s.status == LS_RUN) s.step(e, hdr, body, E);
     }
     // a spill record to write (a hand-over or an eviction), written once below
