@@ -695,7 +695,8 @@ def main():
                      "alu_frac": ops_shot * n / (sum(pass64) / 1000) / peak_ops, "equivalent_note": EQUIV_NOTE}
     lane_mode = lane_mode_of(pass_ms)
     chunks = -(-n // args.chunk) if args.chunk else -(-n // (1 << 24))
-    traffic = profile_traffic(kernel_hash(), "lane_kernel_w42.md" if lane_mode else "shot_kernel_w42.md",
+    # the ncu summary of this workload's first-pass kernel (w42, w97), if one matches the source
+    traffic = profile_traffic(kernel_hash(), ("lane_kernel_%s.md" if lane_mode else "shot_kernel_%s.md") % args.workload,
                               -(-n // chunks))
     line = {
         "metric": "shots/s", "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
