@@ -439,7 +439,9 @@ def leg_w97(S, C, torch, peak_ops, n_chunks):
                      "dtype": "f32" if prec == "fp32" else "f64", "tally": tal,
                      "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                                   "unit": "Tops/s", "frac": achieved / peak_ops,
-                                  "equivalent_frac_whole_method": ops_full * n / (ms / 1000) / peak_ops, "traffic": None,
+                                  "equivalent_frac_whole_method": ops_full * n / (ms / 1000) / peak_ops,
+                                  # the 64-entry lanes' DRAM bytes per 1e8-shot launch (its ncu summary)
+                                  "traffic": profile_traffic(kernel_hash(), "lane_kernel_w97.md", chunk) if prec == "fp32" else None,
                                   "kernel": ("lane_kernel (64-entry lanes: the noiseless maps reach 64 entries) + "
                                              "shot_kernel (shots that outgrow them)") if prec == "fp32" else
                                             "shot_kernel (warp per shot: 64-entry lanes are FP32 only)",
