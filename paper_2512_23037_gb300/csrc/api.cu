@@ -386,9 +386,11 @@ int run_many(soft_circuit *const *circs, const uint64_t *n_shots, const uint64_t
   const bool two_pass = lanes || cap1 < cap_max;
   // after lanes, a middle pass (a warp per shot, map up to cap1 entries) takes the shots whose
   // maps outgrew a lane, and only those that outgrow cap1 go on to the pass at the circuit's
-  // cap. Not when every lane of the run holds 64 entries already: a shot that outgrew one goes
-  // straight to the circuit's cap (w97 FP32: 44.7 M shots/s against 44.5 M through a middle
-  // pass at 64, and 27.0 M through one at 256, whose larger maps cut its residency)
+  // cap. Not when every lane of the run holds 64 entries already: then a shot that outgrew one
+  // goes straight to the circuit's cap (w97 FP32: 44.7 M shots/s against 44.5 M through a
+  // middle pass at 64, and 27.0 M through one at 256, whose larger maps cut its residency).
+  // With smaller lanes in the run it stays for all (many maps that outgrow a 64-entry lane's
+  // six directions still fit 64 entries: batch64 FP32 113 M shots/s when they skipped it)
   const bool mid_pass = lanes && lc16 < cap1 && cap1 < cap_max && (nbc[0] > 0 || nbc[1] > 0);
   const uint32_t g1 = o.group_size ? o.group_size : 32u;
   const uint32_t g2 = 32;
