@@ -38,6 +38,11 @@ namespace cg = cooperative_groups;
 
 enum : int { LS_RUN = -1, LS_KEPT = 0, LS_DISC = 1, LS_OVF = 2, LS_ERR = 3, LS_RERUN = 4, LS_HAND = 5 };
 constexpr int kLaneBlock = 128;
+// threads per block of a lane launch: 2 warps for 32-entry lanes (their shared memory per
+// warp fits more warps per SM in small blocks: FP64 10 against 8, FP32 18 against 16; w42
+// FP64 406.5 -> 421.0 M shots/s, FP32 713 -> 720 M through the wide round), 4 otherwise
+template <uint32_t Cap>
+__host__ __device__ constexpr int lane_block() { return Cap == 32u ? 64 : kLaneBlock; }
 constexpr uint32_t kLaneMaxBuckets = 50000;  // the pre-pass histogram of all buckets: 200 KB of shared memory
 #ifndef SOFT_LANE_EVICT
 #define SOFT_LANE_EVICT 10
@@ -1141,11 +1146,12 @@ __global__ void __launch_bounds__(256) lane_bin_scatter_kernel(const __grid_cons
 
 // Register budget: resident blocks per SM the compiler must allow. FP32 16-slot lanes: 8
 // (64 registers; the shared memory allows 8 on w42; measured 617 M shots/s against 604 M
-// at 6 blocks and 76 registers), the wide round's 32-slot lanes 3 (shared memory allows
-// 3-4), FP64: 5 (its shared memory allows 5; 272.8 M against 266.7 M at 4).
+// at 6 blocks and 76 registers); 32-slot lanes (blocks of 2 warps): 8 in FP32, 4 in FP64,
+// which leave the registers they use (shared memory allows 9 and 5); 64-slot lanes: 2;
+// FP64 16-slot lanes: 5 (its shared memory allows 5; 272.8 M against 266.7 M at 4).
 template <typename R, uint32_t Cap>
 constexpr int kLaneMinBlocks() {
-  return sizeof(R) == 4 ? (Cap <= 16 ? 8 : Cap <= 32 ? 3 : 2) : 5;
+  return sizeof(R) == 4 ? (Cap <= 16 ? 8 : Cap <= 32 ? 8 : 2) : (Cap == 32 ? 4 : 5);
 }
 
 // Multi: the run holds several circuits (a warp serves one at a time); the single-
@@ -1153,11 +1159,11 @@ constexpr int kLaneMinBlocks() {
 // entries per lane (kLaneCap in the first rounds, kWideCap in the wide round, or
 // kWideCap / kLaneBigCap as the first pass of circuits with larger noiseless maps).
 template <typename R, int W, bool Multi, uint32_t Cap>
-__global__ void __launch_bounds__(kLaneBlock, kLaneMinBlocks<R, Cap>()) lane_kernel(const __grid_constant__ ShotParams P) {
+__global__ void __launch_bounds__(lane_block<Cap>(), kLaneMinBlocks<R, Cap>()) lane_kernel(const __grid_constant__ ShotParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   // per warp: tallies of its current circuit, added to the circuit's when the warp moves
   // to another circuit and at the end
-  __shared__ unsigned long long wt[kLaneBlock / 32][5];
+  __shared__ unsigned long long wt[lane_block<Cap>() / 32][5];
   const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x & 31u;
   if (lane < 5) wt[warp][lane] = 0ull;
   __syncwarp();
@@ -1341,7 +1347,7 @@ template <uint32_t Cap>
 static size_t lane_smem_bytes_t(int fp32, uint32_t W, uint32_t rw) {
   const size_t per = fp32 ? (W == 1 ? lane_warp_bytes<float, 1, Cap>(rw) : lane_warp_bytes<float, 2, Cap>(rw))
                           : (W == 1 ? lane_warp_bytes<double, 1, Cap>(rw) : lane_warp_bytes<double, 2, Cap>(rw));
-  return per * (kLaneBlock / 32);
+  return per * (lane_block<Cap>() / 32);
 }
 size_t lane_smem_bytes(int fp32, uint32_t W, uint32_t rw, uint32_t cap) {
   return cap == kLaneBigCap ? lane_smem_bytes_t<kLaneBigCap>(fp32, W, rw)
@@ -1437,12 +1443,13 @@ cudaError_t prepare_lanes(const ShotParams &p, int fp32, uint32_t W, int blocks_
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLaneBlock, smem)) != cudaSuccess) return e;
+  const int block = cap == kWideCap ? lane_block<kWideCap>() : kLaneBlock;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem)) != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
   cfg->kern = kern;
   cfg->grid = (unsigned)(occ * sms);
-  cfg->block = kLaneBlock;
+  cfg->block = (unsigned)block;
   cfg->smem = smem;
   return cudaSuccess;
 }
